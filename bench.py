@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the BCM fractional step on GB300: cell-updates/s and HBM roofline.
+
+Workload: flow past a fixed sphere (R = 0.25 at (1,1,1)) in [0,4]x[0,2]x[0,2],
+16x8x8 cubes of 16^3 cells (4,194,304 cells), Re 300, inflow U = 1, convective
+outflow, slip side walls; synthetic initial state (uniform inflow velocity).
+One "step" = one fractional time step: momentum + IB forcing, Poisson RHS,
+pressure solve to relative residual 1e-8, projection + FP64 divergence check.
+
+value      FP32 sweeps inside FP64 defect correction (mixed), device-timed
+fp64       the plain FP64 path at the same residual, device-timed
+e2e        the mixed step through the C ABI with the state copied host->device
+           from pinned memory before and device->host after every step
+roofline   the dominant kernel's algorithmic bytes / its CUDA-event time vs
+           the measured HBM copy bandwidth
+cpu_baseline  the FP64 CPU oracle on the host cores (bounded sample)
+
+--impl reference runs that oracle alone as the reference arm.
+With N > 1 (torchrun) every rank runs an independent replica (the workload has
+one simulation and no data-path exchange): weak scaling, value = sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1808_04099_gb300 import workloads as W  # noqa: E402
+
+RTOL = 1e-8
+METRIC = "cell-updates/s per step & % HBM roofline, FP32+refine vs FP64 at residual 1e-8"
+
+# Algorithmic bytes per cell of each kernel class (halo reads of neighbour cubes are
+# counted 0: they are served by L2).  S = state/vector size (4 mixed, 8 FP64).
+def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
+    S = 8 if f64 else 4
+    return {
+        "momentum": 12 * S + phi_frac * S,      # u,v,w,N^{n-1} in; u*,N^n out; phi near body
+        "rhs": 3 * S + 8,                       # u* in, b (FP64) out
+        "residual": (8 + 8 + 8) if f64 else (8 + 8 + 4 + 4),  # x,b in; r out (+ e = 0)
+        "cg_a": 4 * S,                          # r, p_old in; p_new, q out
+        "cg_b": 6 * S,                          # x, p, r, q in; x, r out
+        "add_correction": 8 + 4 + 8,            # x64, e in; x64 out
+        "correct": 8 + 8 + 6 * S,               # p, b, u* in; u out
+        "solid_fraction": S + 1,
+        "misc": 0.0,
+    }[kernel]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.uuid = uuid
+        self.out = os.path.join("/tmp", f"bcm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.out, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.out) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def run_oracle_sample(spec, steps: int = 1):
+    """Time the FP64 CPU oracle (as it stands) for `steps` steps of `spec`."""
+    import oracle as O
+    o = O.Oracle(spec)
+    st = o.new_state(W.initial_state(spec))
+    t0 = time.perf_counter()
+    stats, rc = o.step(st, steps, rtol=RTOL)
+    dt = time.perf_counter() - t0
+    return spec.n_cells * steps / dt, dt, O.Oracle.threads(), stats
+
+
+def reference_sample_spec():
+    """Bounded sample of the workload for the CPU reference arm: the same sphere flow
+    and cube layout at half resolution (8^3-cell cubes, 524,288 cells)."""
+    return W.sphere_channel(16, 8, 8, 8, steps=1, rtol=RTOL, name="sphere_16x8x8_B8")
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- reference arm
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    spec = reference_sample_spec()
+    import oracle as O
+    for _ in range(args.warmup):
+        run_oracle_sample(spec, 1)
+    times = []
+    for _ in range(args.steps):
+        v, dt, cores, _ = run_oracle_sample(spec, 1)
+        times.append(dt)
+    total = sum(times)
+    value = spec.n_cells * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "sphere_Re300_16x8x8_cubes_of_8^3 (bounded CPU sample of "
+                                   "the 16^3-cube workload)", "cells": spec.n_cells,
+                       "rtol": RTOL, "flush": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": O.Oracle.threads(),
+                             "kind": "oracle",
+                             "sample": "one fractional step of the sphere flow at half resolution "
+                                       "(16x8x8 cubes of 8^3 = 524,288 cells) per timed step"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+
+def timed_steps(g, n, stream):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(n):
+        g.step(1, rtol=RTOL, max_iter=20000, stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def gpu_arm(args, ws, rank, local):
+    import torch
+    from paper_1808_04099_gb300 import bcm
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = W.config_sphere(args.steps)
+    state = W.initial_state(spec)
+    n = spec.n_cells
+    peak, peak_kind = measured_peaks()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+
+    # ---- mixed precision: the headline value
+    g = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+    g.load_state(state)
+    stream = g.stream
+    for _ in range(args.warmup):
+        g.step(1, rtol=RTOL, stats=False)
+    g.profile_read(reset=True)
+    barrier(ws)
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    ms = timed_steps(g, args.steps, stream)
+    clk = clocks.stop()
+    barrier(ws)
+    _, launches = g.profile_read(reset=True)
+    st = g.step(0, rtol=RTOL)[0] if True else None
+    ms_max = max_over_ranks(ms, ws)
+    value = sum_over_ranks(n * args.steps / (ms / 1e3), ws) if ws > 1 else n * args.steps / (ms_max / 1e3)
+
+    # ---- per-kernel CUDA-event timing (same workload, profiling on)
+    kprof_steps = max(2, min(args.steps, 5))
+    g.profile(True)
+    for _ in range(kprof_steps):
+        g.step(1, rtol=RTOL, stats=False)
+    prof, _ = g.profile_read(reset=True)
+    g.profile(False)
+    phi_frac = float(torch.count_nonzero(g.field(bcm.PHI)).item()) / n
+    kern = {}
+    for k, (tot, cnt) in prof.items():
+        if cnt:
+            bpc = bytes_per_cell(k, False, phi_frac)
+            avg = tot / cnt
+            kern[k] = {"launches": cnt, "total_ms": tot, "avg_us": 1e3 * avg,
+                       "GBps": (bpc * n / (avg / 1e3)) / 1e9 if bpc else None,
+                       "bytes_per_cell": bpc}
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    d = kern[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"], "peak": peak,
+                "unit": "GB/s", "frac": d["GBps"] / peak if d["GBps"] else None,
+                "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": d["bytes_per_cell"] * n}
+    share = {k: kern[k]["total_ms"] / sum(v["total_ms"] for v in kern.values()) for k in kern}
+
+    # ---- e2e through the C ABI with host buffers (pinned), mixed precision
+    fids = [bcm.U, bcm.V, bcm.W, bcm.P, bcm.NX, bcm.NY, bcm.NZ, bcm.UB]
+    views = [g.field(f) for f in fids]
+    host = [torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in views]
+    for h, v in zip(host, views):
+        h.copy_(v)
+    out_idx = [0, 1, 2, 3]
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    d2h = sum(host[i].numel() * host[i].element_size() for i in out_idx) + \
+        spec.n_sims * 64
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = args.steps
+    ev0.record(stream)
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            for h, v in zip(host, views):
+                v.copy_(h, non_blocking=True)
+        g.step(1, rtol=RTOL, stats=False)
+        with torch.cuda.stream(stream):
+            for i in out_idx:
+                host[i].copy_(views[i], non_blocking=True)
+        g.step(0, rtol=RTOL)   # reads the step's stats to the host (synchronises)
+        for i in (4, 5, 6, 7):  # lagged convection and outflow state stay current
+            host[i].copy_(views[i], non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    e2e_value = n * e2e_steps / (e2e_ms / 1e3) * (ws if ws > 1 else 1)
+    h2d_step = h2d
+    d2h_step = d2h + sum(host[i].numel() * host[i].element_size() for i in (4, 5, 6, 7))
+    del g
+
+    # ---- the plain FP64 path at the same residual
+    g64 = bcm.Grid(spec, bcm.PREC_F64, device=dev)
+    g64.load_state(state)
+    for _ in range(args.warmup):
+        g64.step(1, rtol=RTOL, stats=False)
+    ms64 = timed_steps(g64, args.steps, g64.stream)
+    st64 = g64.step(0, rtol=RTOL)[0]
+    g64.profile(True)
+    for _ in range(kprof_steps):
+        g64.step(1, rtol=RTOL, stats=False)
+    prof64, _ = g64.profile_read(reset=True)
+    g64.profile(False)
+    del g64
+    ms64 = max_over_ranks(ms64, ws)
+    fp64_value = n * args.steps / (ms64 / 1e3) * (ws if ws > 1 else 1)
+    k64 = {k: {"launches": c, "avg_us": 1e3 * t / c,
+               "GBps": bytes_per_cell(k, True, phi_frac) * n / (t / c / 1e3) / 1e9}
+           for k, (t, c) in prof64.items() if c}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        full = W.config_sphere(1)
+        v, dt, cores, _ = run_oracle_sample(full, 1)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"one fractional step of the full 4,194,304-cell sphere flow at "
+                         f"rtol 1e-8 from the same initial state ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "sphere_Re300_16x8x8_cubes_of_16^3", "cells": n,
+                       "rtol": RTOL, "precision": "FP32 sweeps + FP64 defect correction",
+                       "flush": "inputs larger than L2 (state 318 MB/step)",
+                       "cg_iters_last_step": st["cg_iters"],
+                       "refine_cycles_last_step": st["refine_cycles"],
+                       "rel_resid_last_step": st["rel_resid"],
+                       "div_rel_last_step": st["div_rel"]},
+            "fp64": {"value": fp64_value, "unit": "cell-updates/s",
+                     "ms_per_step": ms64 / args.steps, "cg_iters_last_step": st64["cg_iters"],
+                     "rel_resid_last_step": st64["rel_resid"], "kernels": k64},
+            "speedup_mixed_vs_fp64": value / fp64_value,
+            "roofline": roofline,
+            "kernels": kern, "kernel_share": share,
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s",
+                    "h2d_bytes_per_step": h2d_step, "d2h_bytes_per_step": d2h_step},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+    else:
+        gpu_arm(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * bcm.h -- C ABI of the GB300 (sm_103a) Building Cube Method time-step library.
+ *
+ * The library advances incompressible-flow simulations on block-structured
+ * Cartesian grids of equal cubes (arXiv:1808.04099, section "Building Cube
+ * Method") by the fractional-step method of section "Numerical algorithm":
+ * momentum sub-step (Eq. substep1, explicit here), immersed-boundary forcing,
+ * pressure Poisson equation (Eq. poisson) and projection.  Every step of that
+ * path runs in this library's CUDA kernels; nothing falls back to the CPU.
+ *
+ * Conventions for every entry point
+ *   - Plain C types only.  "dev" pointers are CUDA device pointers on the device
+ *     that was current at bcm_create_grid; "host" pointers are host memory.
+ *   - All device work is issued on the stream given to bcm_create_grid and is
+ *     asynchronous unless the call returns host results (bcm_step / bcm_solve_pressure
+ *     with a non-NULL stats pointer synchronise that stream).
+ *   - Errors are returned as bcm_status; nothing throws or aborts across the ABI.
+ *     bcm_last_error() gives a message for the calling thread's last failure.
+ *   - Memory: the caller owns the device workspace (bcm_workspace_bytes) and every
+ *     pointer it passes; the library keeps only small host tables and never calls
+ *     cudaMalloc.  Field views returned by bcm_field point into the workspace.
+ *   - rho = 1 throughout (kinematic pressure).
+ *
+ * Field layout (every cell field): cube-major, x fastest inside a cube:
+ *   index = cube * B^3 + (k * B + j) * B + i,  B = cells_per_edge.
+ * Outflow face values (BCM_UB): [n_slots][3][B][B]; one slot per (cube, face)
+ * pair on an OUTFLOW domain face, in cube order then face order (-x,+x,-y,+y,-z,+z);
+ * inside a face patch the lower-numbered tangential axis is fastest.
+ */
+#ifndef BCM_H
+#define BCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcm_grid bcm_grid; /* opaque; created by bcm_create_grid */
+
+typedef enum {
+    BCM_OK = 0,
+    BCM_E_INVALID = -1,       /* bad argument or inconsistent grid description */
+    BCM_E_CUDA = -2,          /* a CUDA runtime call failed (message has the code) */
+    BCM_E_NOT_CONVERGED = -3, /* a pressure solve hit max_iter; fields stay valid */
+    BCM_E_NONFINITE = -4,     /* NaN or Inf found in a residual */
+    BCM_E_TIMEOUT = -5,       /* reserved: a bounded device wait ran out */
+    BCM_E_BOUNDS = -6         /* a size exceeds a documented maximum */
+} bcm_status;
+
+enum { BCM_PREC_F64 = 0, BCM_PREC_F32_REFINE = 1 };
+
+/* Domain-face boundary conditions (face order -x,+x,-y,+y,-z,+z). */
+enum {
+    BCM_BC_WALL = 0,     /* no-slip wall moving with sim_bc_vel (a lid) */
+    BCM_BC_INFLOW = 1,   /* prescribed velocity sim_bc_vel x inflow profile */
+    BCM_BC_SLIP = 2,     /* free slip */
+    BCM_BC_OUTFLOW = 3,  /* convective outflow (speed sim_uconv), pressure 0 */
+    BCM_BC_PERIODIC = 4  /* periodic; the opposite face must also be periodic */
+};
+
+enum { BCM_BODY_NONE = 0, BCM_BODY_SPHERE = 1, BCM_BODY_ELLIPSOID = 2 };
+
+/* Field ids for bcm_field. */
+enum {
+    BCM_U = 0, BCM_V = 1, BCM_W = 2, /* cell velocity (state, storage type of the mode) */
+    BCM_P = 3,                       /* pressure (always FP64) */
+    BCM_PHI = 4,                     /* solid fraction */
+    BCM_NX = 5, BCM_NY = 6, BCM_NZ = 7, /* lagged convection N^{n-1} (state) */
+    BCM_USTAR = 8, BCM_VSTAR = 9, BCM_WSTAR = 10, /* u* after IB forcing */
+    BCM_RHS = 11,                    /* Poisson right-hand side b (FP64) */
+    BCM_UB = 12,                     /* outflow face values (state) */
+    BCM_NFIELDS = 13
+};
+
+/* Grid description.  All arrays are host memory, read during bcm_create_grid only.
+ * Several independent simulations ("sims") may share one grid; their cubes are
+ * contiguous ranges of the cube list.  Cube corners are in units of the finest cell
+ * size h0 / 2^max_level; a level-l cube spans B * 2^(max_level-l) such units.
+ * Face neighbours may differ by at most one level (ratio 2). */
+typedef struct {
+    int32_t n_sims;
+    int32_t n_cubes;
+    int32_t cells_per_edge;       /* B: 4, 8 or 16 */
+    int32_t max_level;            /* 0 or 1 */
+    int32_t precision;            /* BCM_PREC_* */
+    int32_t reserved;
+    const int32_t *sim_cube_offset; /* [n_sims+1] */
+    const int32_t *cube_ijk;        /* [n_cubes*3] base corners */
+    const int8_t *cube_level;       /* [n_cubes] */
+    const int32_t *sim_extent;      /* [n_sims*3] domain size, finest-cell units */
+    const double *sim_origin;       /* [n_sims*3] */
+    const double *sim_h0;           /* [n_sims] level-0 cell size */
+    const int32_t *sim_bc;          /* [n_sims*6] BCM_BC_* */
+    const double *sim_bc_vel;       /* [n_sims*6*3] wall / inflow velocity per face */
+    const double *sim_nu;           /* [n_sims] kinematic viscosity */
+    const double *sim_dt;           /* [n_sims] time step (constant) */
+    const double *sim_uconv;        /* [n_sims] convective outflow speed */
+} bcm_grid_desc;
+
+/* A rigid body moving with centre(t) = center + vel t and orientation
+ * exp(t [omega]x) R(quat); quat = (w, x, y, z).  Sphere radius = axes[0]. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double center[3], axes[3], quat[4], omega[3], vel[3];
+} bcm_body;
+
+typedef struct {
+    int32_t cg_iters;      /* PCG iterations of the last solve (mixed: inner, summed) */
+    int32_t refine_cycles; /* FP64 defect-correction cycles (mixed mode; else 0) */
+    int32_t steps;         /* steps taken so far */
+    int32_t converged;     /* 1 if the last solve met rtol */
+    double rel_resid;      /* ||rhs - K p|| / ||rhs|| at exit (FP64 residual in mixed mode) */
+    double div_rel;        /* ||D U^{n+1}|| / ||D U*|| of the corrected face velocities */
+    double drag[3];        /* force of the fluid on the bodies, last step */
+    double umax;           /* max |u| after the last step */
+} bcm_stats;
+
+/* Bytes of device workspace the grid needs (fields, solver vectors, tables).
+ * Returns 0 for an invalid description (see bcm_last_error). */
+size_t bcm_workspace_bytes(const bcm_grid_desc *desc);
+
+/* Build the grid: face adjacency (same level, 2:1, domain faces, periodic wrap),
+ * boundary tables and per-sim parameters, written into dev_workspace (>= bytes of
+ * bcm_workspace_bytes, 256-byte aligned).  Fields start at zero.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  Paper: "Building Cube Method"
+ * (cubes in linear arrays with corners, size and adjacency). */
+bcm_status bcm_create_grid(const bcm_grid_desc *desc, void *dev_workspace, size_t bytes,
+                           void *cuda_stream, bcm_grid **out);
+bcm_status bcm_destroy_grid(bcm_grid *grid);
+
+/* Device view of one field: *dev_ptr, element count and element size in bytes. */
+bcm_status bcm_field(bcm_grid *grid, int field, void **dev_ptr, size_t *count,
+                     int32_t *elem_bytes);
+
+/* Set the bodies (up to 4) and the eight inflow-profile amplitudes (may be NULL) of
+ * one sim, and recompute its solid fraction at the sim's current time.  The inflow
+ * profile on INFLOW faces is 1 + sum_m a_m sin(k_m pi s/L_s) sin(l_m pi t/L_t) with
+ * (k,l) = (1,1),(1,2),(2,1),(2,2),(1,3),(3,1),(2,3),(3,2) over the face's two
+ * tangential coordinates.  The paper represents bodies by Lagrangian particles
+ * ("Lagrangian-Eulerian approach"); here a per-cell solid fraction
+ * phi = (1 - tanh(d / 1.5h)) / 2 of the signed distance d stands in for them. */
+bcm_status bcm_set_geometry(bcm_grid *grid, int sim, const bcm_body *bodies, int n_bodies,
+                            const double *inflow_modes);
+
+/* Reset step counters (time = 0) of all sims; the next step starts AB2 with Euler. */
+bcm_status bcm_reset_time(bcm_grid *grid);
+
+/* Advance every sim by n_steps fractional steps ("Numerical algorithm"):
+ * solid fraction (moving bodies), momentum sub-step with halo staging, IB forcing,
+ * Poisson right-hand side, Jacobi-PCG pressure solve to relative residual rtol
+ * (FP64, or FP32 inner PCG inside FP64 defect correction), projection.
+ * stats: host array [n_sims] or NULL (then nothing is synchronised). */
+bcm_status bcm_step(bcm_grid *grid, int n_steps, double rtol, int max_iter, bcm_stats *stats);
+
+/* Solve the pressure Poisson equation (Eq. poisson) for the current BCM_RHS into
+ * BCM_P (warm start from BCM_P).  stats as in bcm_step. */
+bcm_status bcm_solve_pressure(bcm_grid *grid, double rtol, int max_iter, bcm_stats *stats);
+
+/* Copy one cell field with its two-layer face halos, filled by the paper's halo
+ * rules ("Building Cube Method", Fig. halo-hanging-node): same-level copy,
+ * fine->coarse mean of the 2x2x2 fine cells, coarse->fine copy of the coarse cell,
+ * and the domain boundary rules.  kind 0,1,2 = velocity component (field BCM_U,
+ * BCM_V, BCM_W or the starred ones), 3 = pressure rules.  dev_out: FP64
+ * [n_cubes][(B+4)^3], z slowest; cells that are not face halos are set to 0.
+ * The field is converted to FP64. */
+bcm_status bcm_fill_halo(bcm_grid *grid, int field, int kind, double *dev_out);
+
+/* y = K x with K = -V A the flux-form pressure operator of Eq. poisson (FP64). */
+bcm_status bcm_apply_poisson(bcm_grid *grid, const double *dev_x, double *dev_y);
+
+/* Kernel classes for bcm_profile_read. */
+enum {
+    BCM_K_SOLID_FRACTION = 0, /* solid fraction and body index per cell */
+    BCM_K_MOMENTUM = 1,       /* halo staging + momentum sub-step + IB forcing */
+    BCM_K_RHS = 2,            /* Poisson right-hand side */
+    BCM_K_RESIDUAL = 3,       /* FP64 residual (PCG start / defect-correction cycle) */
+    BCM_K_CG_A = 4,           /* PCG pass A: new direction, K p, <p, Kp> */
+    BCM_K_CG_B = 5,           /* PCG pass B: iterate and residual update, <r,z>, <r,r> */
+    BCM_K_ADD_CORRECTION = 6, /* mixed: x += e */
+    BCM_K_CORRECT = 7,        /* projection + FP64 divergence check */
+    BCM_K_MISC = 8,           /* bookkeeping and test-path kernels */
+    BCM_NKERNELS = 9
+};
+
+/* Timing of the library's own kernels: while enabled, every kernel the grid launches
+ * is bracketed by two CUDA events on the grid's stream.  No device memory is used. */
+bcm_status bcm_profile(bcm_grid *grid, int enable);
+
+/* Per-class totals since the last reset: total_ms[BCM_NKERNELS] and
+ * launches[BCM_NKERNELS] of timed launches (either may be NULL), and launch_count,
+ * every kernel launch issued (timed or not).  Synchronises the grid's stream when
+ * timed launches are pending.  reset != 0 clears all counters after reading. */
+bcm_status bcm_profile_read(bcm_grid *grid, double *total_ms, int64_t *launches,
+                            int64_t *launch_count, int reset);
+
+const char *bcm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,242 @@
+"""Python binding of libbcm.so (include/bcm.h): argument marshalling only.
+
+PyTorch provides the device workspace (one uint8 tensor) and the CUDA stream;
+every step of the time step runs in the library's kernels.  There is no CPU or
+PyTorch fallback: if the library cannot be built or loaded, this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional
+
+import numpy as np
+
+from . import _build
+
+# status codes
+BCM_OK, BCM_E_INVALID, BCM_E_CUDA, BCM_E_NOT_CONVERGED = 0, -1, -2, -3
+BCM_E_NONFINITE, BCM_E_TIMEOUT, BCM_E_BOUNDS = -4, -5, -6
+PREC_F64, PREC_F32_REFINE = 0, 1
+(U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)
+
+EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
+            "bcm_set_geometry", "bcm_reset_time", "bcm_step", "bcm_solve_pressure",
+            "bcm_fill_halo", "bcm_apply_poisson", "bcm_profile", "bcm_profile_read",
+            "bcm_last_error"]
+KERNEL_NAMES = ["solid_fraction", "momentum", "rhs", "residual", "cg_a", "cg_b",
+                "add_correction", "correct", "misc"]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n_sims", C.c_int32), ("n_cubes", C.c_int32), ("cells_per_edge", C.c_int32),
+                ("max_level", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("sim_cube_offset", C.c_void_p), ("cube_ijk", C.c_void_p),
+                ("cube_level", C.c_void_p), ("sim_extent", C.c_void_p),
+                ("sim_origin", C.c_void_p), ("sim_h0", C.c_void_p), ("sim_bc", C.c_void_p),
+                ("sim_bc_vel", C.c_void_p), ("sim_nu", C.c_void_p), ("sim_dt", C.c_void_p),
+                ("sim_uconv", C.c_void_p)]
+
+
+class Body(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("center", C.c_double * 3),
+                ("axes", C.c_double * 3), ("quat", C.c_double * 4), ("omega", C.c_double * 3),
+                ("vel", C.c_double * 3)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cg_iters", C.c_int32), ("refine_cycles", C.c_int32), ("steps", C.c_int32),
+                ("converged", C.c_int32), ("rel_resid", C.c_double), ("div_rel", C.c_double),
+                ("drag", C.c_double * 3), ("umax", C.c_double)]
+
+    def as_dict(self):
+        return {"cg_iters": self.cg_iters, "refine_cycles": self.refine_cycles,
+                "steps": self.steps, "converged": self.converged, "rel_resid": self.rel_resid,
+                "div_rel": self.div_rel, "drag": list(self.drag), "umax": self.umax}
+
+
+class BCMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"bcm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Load libbcm.so (building it in-tree first when sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libbcm.so is missing; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.bcm_workspace_bytes.restype = C.c_size_t
+        L.bcm_workspace_bytes.argtypes = [P]
+        L.bcm_create_grid.argtypes = [P, P, C.c_size_t, P, C.POINTER(C.c_void_p)]
+        L.bcm_destroy_grid.argtypes = [P]
+        L.bcm_field.argtypes = [P, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
+                                C.POINTER(C.c_int32)]
+        L.bcm_set_geometry.argtypes = [P, C.c_int, P, C.c_int, P]
+        L.bcm_reset_time.argtypes = [P]
+        L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
+        L.bcm_solve_pressure.argtypes = [P, C.c_double, C.c_int, P]
+        L.bcm_fill_halo.argtypes = [P, C.c_int, C.c_int, P]
+        L.bcm_apply_poisson.argtypes = [P, P, P]
+        L.bcm_profile.argtypes = [P, C.c_int]
+        L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
+        L.bcm_last_error.restype = C.c_char_p
+        for name in EXPORTED:
+            getattr(L, name).restype = getattr(L, name).restype or C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, allow=()):
+    if rc != BCM_OK and rc not in allow:
+        raise BCMError(rc, lib().bcm_last_error().decode())
+    return rc
+
+
+def _body_struct(b) -> Body:
+    s = Body()
+    s.kind = int(b.kind)
+    s.center[:] = list(map(float, b.center))
+    s.axes[:] = list(map(float, b.axes))
+    s.quat[:] = list(map(float, b.quat))
+    s.omega[:] = list(map(float, b.omega))
+    s.vel[:] = list(map(float, b.vel))
+    return s
+
+
+class Grid:
+    """One BCM grid (one or more independent sims) living in a torch-owned workspace."""
+
+    def __init__(self, spec, precision: int = PREC_F64, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the BCM library needs a CUDA device")
+        L = lib()
+        self.spec = spec
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self._arrays = [np.ascontiguousarray(spec.sim_cube_offset, np.int32),
+                        np.ascontiguousarray(spec.cube_ijk, np.int32),
+                        np.ascontiguousarray(spec.cube_level, np.int8),
+                        np.ascontiguousarray(spec.sim_extent, np.int32),
+                        np.ascontiguousarray(spec.sim_origin, np.float64),
+                        np.ascontiguousarray(spec.sim_h0, np.float64),
+                        np.ascontiguousarray(spec.sim_bc, np.int32),
+                        np.ascontiguousarray(spec.sim_bc_vel, np.float64),
+                        np.ascontiguousarray(spec.sim_nu, np.float64),
+                        np.ascontiguousarray(spec.sim_dt, np.float64),
+                        np.ascontiguousarray(spec.sim_uconv, np.float64)]
+        d = GridDesc()
+        d.n_sims, d.n_cubes, d.cells_per_edge = spec.n_sims, spec.n_cubes, spec.B
+        d.max_level, d.precision = spec.max_level, precision
+        (d.sim_cube_offset, d.cube_ijk, d.cube_level, d.sim_extent, d.sim_origin, d.sim_h0,
+         d.sim_bc, d.sim_bc_vel, d.sim_nu, d.sim_dt, d.sim_uconv) = \
+            [a.ctypes.data for a in self._arrays]
+        self._desc = d
+        nbytes = L.bcm_workspace_bytes(C.byref(d))
+        if nbytes == 0:
+            raise BCMError(BCM_E_INVALID, L.bcm_last_error().decode())
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            self._off0 = (-base) % 256
+            self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+            h = C.c_void_p()
+            _check(L.bcm_create_grid(C.byref(d), C.c_void_p(base + self._off0), nbytes,
+                                     C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self.nbytes = nbytes
+        for s, bodies in enumerate(spec.bodies):
+            if bodies or np.any(spec.inflow_modes[s]):
+                self.set_geometry(s, bodies, spec.inflow_modes[s])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.bcm_destroy_grid(h)
+            self._h = None
+
+    # ------------------------------------------------------------------ fields
+    def field(self, fid: int):
+        """Zero-copy torch view of one field (shares the workspace)."""
+        import torch
+        ptr, cnt, eb = C.c_void_p(), C.c_size_t(), C.c_int32()
+        _check(lib().bcm_field(self._h, fid, C.byref(ptr), C.byref(cnt), C.byref(eb)))
+        off = ptr.value - self.workspace.data_ptr()
+        n = cnt.value * eb.value
+        dt = torch.float64 if eb.value == 8 else torch.float32
+        return self.workspace[off:off + n].view(dt)
+
+    def load_state(self, state):
+        """Copy a workloads.State (host arrays) into the grid's fields."""
+        import torch
+        for fid, arr in ((U, state.u), (V, state.v), (W, state.w), (P, state.p)):
+            t = self.field(fid)
+            t.copy_(torch.as_tensor(np.asarray(arr).reshape(-1)).to(t.dtype))
+        ub = self.field(UB)
+        if ub.numel():
+            ub.copy_(torch.as_tensor(np.asarray(state.ub).reshape(-1)).to(ub.dtype))
+        for fid in (NX, NY, NZ):
+            self.field(fid).zero_()
+        self.reset_time()
+
+    def numpy(self, fid: int) -> np.ndarray:
+        import torch
+        torch.cuda.current_stream(self.device).synchronize()
+        self.stream.synchronize()
+        return self.field(fid).double().cpu().numpy()
+
+    # -------------------------------------------------------------- operations
+    def set_geometry(self, sim: int, bodies, modes=None):
+        arr = (Body * max(1, len(bodies)))(*[_body_struct(b) for b in bodies])
+        m = None if modes is None else np.ascontiguousarray(modes, np.float64)
+        _check(lib().bcm_set_geometry(self._h, sim, arr if bodies else None, len(bodies),
+                                      m.ctypes.data if m is not None else None))
+
+    def reset_time(self):
+        _check(lib().bcm_reset_time(self._h))
+
+    def step(self, n: int = 1, rtol: float = 1e-10, max_iter: int = 20000, stats: bool = True,
+             allow_not_converged: bool = False) -> Optional[List[dict]]:
+        st = (Stats * self.spec.n_sims)() if stats else None
+        rc = lib().bcm_step(self._h, n, rtol, max_iter, st)
+        _check(rc, (BCM_E_NOT_CONVERGED,) if allow_not_converged else ())
+        return [s.as_dict() for s in st] if stats else None
+
+    def solve_pressure(self, rtol: float = 1e-12, max_iter: int = 20000):
+        st = (Stats * self.spec.n_sims)()
+        _check(lib().bcm_solve_pressure(self._h, rtol, max_iter, st))
+        return [s.as_dict() for s in st]
+
+    def profile(self, enable: bool):
+        _check(lib().bcm_profile(self._h, int(enable)))
+
+    def profile_read(self, reset: bool = True):
+        """{kernel: (total_ms, timed_launches)} and the count of all launches."""
+        ms = (C.c_double * len(KERNEL_NAMES))()
+        n = (C.c_int64 * len(KERNEL_NAMES))()
+        total = C.c_int64()
+        _check(lib().bcm_profile_read(self._h, ms, n, C.byref(total), int(reset)))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_NAMES)}, total.value
+
+    def fill_halo(self, fid: int, kind: int):
+        import torch
+        G = self.spec.B + 4
+        out = torch.zeros(self.spec.n_cubes * G ** 3, dtype=torch.float64, device=self.device)
+        _check(lib().bcm_fill_halo(self._h, fid, kind, C.c_void_p(out.data_ptr())))
+        return out
+
+    def apply_poisson(self, x):
+        import torch
+        x = x.to(self.device, torch.float64).contiguous()
+        y = torch.empty_like(x)
+        _check(lib().bcm_apply_poisson(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y

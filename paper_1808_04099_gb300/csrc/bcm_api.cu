@@ -1,0 +1,709 @@
+// bcm_api.cu -- host runtime and C ABI of the BCM library (see include/bcm.h).
+//
+// Grid build ("Building Cube Method": cubes kept in linear arrays with corner,
+// size and adjacency), workspace layout, and the drivers of the fractional step
+// ("Numerical algorithm"): FracTimeStep -> PoissonSolve -> velocity correction.
+// The host never touches field data; every arithmetic step runs in the kernels of
+// bcm_kernels.cu on the grid's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bcm.h"
+#include "bcm_internal.cuh"
+#include "bcm_kernels.h"
+
+using namespace bcm;
+
+static thread_local std::string g_last_error;
+
+static bcm_status fail(bcm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(BCM_E_CUDA, "%s failed: %s (%d)", #expr, cudaGetErrorString(e_), (int)e_); \
+  } while (0)
+
+// --------------------------------------------------------------- workspace
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t u, v, w, us, vs, ws, nx, ny, nz, phi, ub, p, b, bid, near_, r, p0, p1, q, e;
+  size_t nb, aux, sim, lvl, ijk, w3, slot, sp, ss, counter, flags, guard;
+  size_t total;
+  size_t n_slots;
+};
+
+struct HostTables {
+  std::vector<int> nb, aux, sim, lvl, ijk, w3, slot;
+  std::vector<SimParams> sp;
+  int n_slots = 0;
+  int two_level = 0;
+};
+
+int face_axis(int f) { return f >> 1; }
+
+bcm_status validate(const bcm_grid_desc* d) {
+  if (!d) return fail(BCM_E_INVALID, "desc is NULL");
+  if (d->n_sims < 1 || d->n_cubes < 1) return fail(BCM_E_INVALID, "empty grid");
+  if (d->cells_per_edge != 4 && d->cells_per_edge != 8 && d->cells_per_edge != 16)
+    return fail(BCM_E_INVALID, "cells_per_edge must be 4, 8 or 16");
+  if (d->max_level < 0 || d->max_level > 1) return fail(BCM_E_INVALID, "max_level must be 0 or 1");
+  if (d->precision != BCM_PREC_F64 && d->precision != BCM_PREC_F32_REFINE)
+    return fail(BCM_E_INVALID, "unknown precision %d", d->precision);
+  if (!d->sim_cube_offset || !d->cube_ijk || !d->cube_level || !d->sim_extent ||
+      !d->sim_origin || !d->sim_h0 || !d->sim_bc || !d->sim_bc_vel || !d->sim_nu ||
+      !d->sim_dt || !d->sim_uconv)
+    return fail(BCM_E_INVALID, "a descriptor array is NULL");
+  if (d->sim_cube_offset[0] != 0 || d->sim_cube_offset[d->n_sims] != d->n_cubes)
+    return fail(BCM_E_INVALID, "sim_cube_offset must run from 0 to n_cubes");
+  for (int s = 0; s < d->n_sims; ++s) {
+    if (d->sim_cube_offset[s + 1] <= d->sim_cube_offset[s])
+      return fail(BCM_E_INVALID, "sim %d has no cubes", s);
+    if (!(d->sim_h0[s] > 0) || !(d->sim_dt[s] > 0) || !(d->sim_nu[s] >= 0))
+      return fail(BCM_E_INVALID, "sim %d: h0, dt must be > 0 and nu >= 0", s);
+    for (int f = 0; f < 6; ++f) {
+      int bc = d->sim_bc[6 * s + f];
+      if (bc < BC_WALL || bc > BC_PERIODIC) return fail(BCM_E_INVALID, "sim %d: bad bc", s);
+      int opp = d->sim_bc[6 * s + (f ^ 1)];
+      if ((bc == BC_PERIODIC) != (opp == BC_PERIODIC))
+        return fail(BCM_E_INVALID, "sim %d: periodic faces must come in pairs", s);
+    }
+  }
+  for (int c = 0; c < d->n_cubes; ++c)
+    if (d->cube_level[c] < 0 || d->cube_level[c] > d->max_level)
+      return fail(BCM_E_INVALID, "cube %d: level out of range", c);
+  return BCM_OK;
+}
+
+struct Key {
+  int s, l, x, y, z;
+  bool operator==(const Key& o) const {
+    return s == o.s && l == o.l && x == o.x && y == o.y && z == o.z;
+  }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int v : {k.s, k.l, k.x, k.y, k.z}) h = (h ^ (uint32_t)v) * 1099511628211ull;
+    return (size_t)h;
+  }
+};
+
+int wrapi(int x, int n) { return ((x % n) + n) % n; }
+
+// Face adjacency, Jacobi face weights and outflow slots for every cube.
+bcm_status build_tables(const bcm_grid_desc* d, HostTables& T) {
+  const int n = d->n_cubes, B = d->cells_per_edge, ML = d->max_level;
+  std::unordered_map<Key, int, KeyHash> index;
+  index.reserve((size_t)n * 2);
+  T.sim.resize(n);
+  T.lvl.resize(n);
+  T.ijk.assign(d->cube_ijk, d->cube_ijk + 3 * (size_t)n);
+  for (int s = 0; s < d->n_sims; ++s)
+    for (int c = d->sim_cube_offset[s]; c < d->sim_cube_offset[s + 1]; ++c) {
+      T.sim[c] = s;
+      T.lvl[c] = d->cube_level[c];
+      Key k{s, T.lvl[c], T.ijk[3 * c], T.ijk[3 * c + 1], T.ijk[3 * c + 2]};
+      if (!index.emplace(k, c).second) return fail(BCM_E_INVALID, "duplicate cube %d", c);
+      const int sp = B << (ML - T.lvl[c]);
+      for (int e = 0; e < 3; ++e) {
+        int x = T.ijk[3 * c + e];
+        if (x < 0 || x + sp > d->sim_extent[3 * s + e] || x % sp != 0)
+          return fail(BCM_E_INVALID, "cube %d lies outside its domain or off its lattice", c);
+      }
+    }
+  auto find = [&](int s, int l, int x, int y, int z) {
+    auto it = index.find(Key{s, l, x, y, z});
+    return it == index.end() ? -1 : it->second;
+  };
+  T.nb.assign(6 * (size_t)n, NB_BOUNDARY);
+  T.aux.assign(24 * (size_t)n, -1);
+  T.w3.assign(6 * (size_t)n, 3);
+  T.slot.assign(6 * (size_t)n, -1);
+  int slots = 0;
+  for (int c = 0; c < n; ++c) {
+    const int s = T.sim[c], l = T.lvl[c];
+    const int sp = B << (ML - l);
+    const int* ext = d->sim_extent + 3 * s;
+    for (int f = 0; f < 6; ++f) {
+      const int dd = face_axis(f), side = f & 1, bc = d->sim_bc[6 * s + f];
+      int X[3] = {T.ijk[3 * c], T.ijk[3 * c + 1], T.ijk[3 * c + 2]};
+      const bool edge = side ? (X[dd] + sp == ext[dd]) : (X[dd] == 0);
+      if (edge && bc != BC_PERIODIC) {
+        T.nb[6 * c + f] = NB_BOUNDARY;
+        T.w3[6 * c + f] = (bc == BC_OUTFLOW) ? 6 : 0;
+        if (bc == BC_OUTFLOW) T.slot[6 * c + f] = slots++;
+        continue;
+      }
+      int Y[3] = {X[0], X[1], X[2]};
+      Y[dd] = wrapi(X[dd] + (side ? sp : -sp), ext[dd]);
+      int m = find(s, l, Y[0], Y[1], Y[2]);
+      if (m >= 0) {
+        T.nb[6 * c + f] = m;
+        continue;
+      }
+      if (l > 0) {  // coarser neighbour
+        int P[3] = {X[0], X[1], X[2]}, Q[3];
+        P[dd] = wrapi(X[dd] + (side ? sp : -1), ext[dd]);
+        for (int e = 0; e < 3; ++e) Q[e] = P[e] / (2 * sp) * (2 * sp);
+        m = find(s, l - 1, Q[0], Q[1], Q[2]);
+        if (m >= 0) {
+          T.nb[6 * c + f] = NB_COARSE;
+          T.aux[(6 * c + f) * 4] = m;
+          T.w3[6 * c + f] = 2;
+          T.two_level = 1;
+          continue;
+        }
+      }
+      if (l < ML) {  // four finer neighbours
+        const int fsp = sp / 2;
+        bool ok = true;
+        for (int qb = 0; qb < 2; ++qb)
+          for (int qa = 0; qa < 2; ++qa) {
+            int Z[3] = {X[0], X[1], X[2]};
+            Z[dd] = wrapi(X[dd] + (side ? sp : -fsp), ext[dd]);
+            Z[tan1(dd)] += qa * fsp;
+            Z[tan2(dd)] += qb * fsp;
+            int mm = find(s, l + 1, Z[0], Z[1], Z[2]);
+            T.aux[(6 * c + f) * 4 + qb * 2 + qa] = mm;
+            if (mm < 0) ok = false;
+          }
+        if (ok) {
+          T.nb[6 * c + f] = NB_FINE;
+          T.w3[6 * c + f] = 4;
+          T.two_level = 1;
+          continue;
+        }
+      }
+      return fail(BCM_E_INVALID, "cube %d face %d has no neighbour (hole or level jump > 1)", c, f);
+    }
+  }
+  T.n_slots = slots;
+  // per-sim constants
+  T.sp.assign(d->n_sims, SimParams{});
+  for (int s = 0; s < d->n_sims; ++s) {
+    SimParams& p = T.sp[s];
+    memset(&p, 0, sizeof p);
+    p.h0 = d->sim_h0[s];
+    p.hf = d->sim_h0[s] / double(1 << ML);
+    p.nu = d->sim_nu[s];
+    p.dt = d->sim_dt[s];
+    p.uconv = d->sim_uconv[s];
+    p.all_neumann = 1;
+    for (int e = 0; e < 3; ++e) {
+      p.origin[e] = d->sim_origin[3 * s + e];
+      p.extent[e] = d->sim_extent[3 * s + e];
+      p.L[e] = p.extent[e] * p.hf;
+    }
+    for (int f = 0; f < 6; ++f) {
+      p.bc[f] = d->sim_bc[6 * s + f];
+      if (p.bc[f] == BC_OUTFLOW) p.all_neumann = 0;
+      for (int e = 0; e < 3; ++e) p.bcvel[f][e] = d->sim_bc_vel[18 * s + 3 * f + e];
+    }
+    p.cube_begin = d->sim_cube_offset[s];
+    p.cube_end = d->sim_cube_offset[s + 1];
+    p.n_cells = (p.cube_end - p.cube_begin) * B * B * B;
+    for (int l = 0; l < 2; ++l) {
+      const double h = p.h0 / double(1 << l);
+      for (int w = 0; w < kW3; ++w) p.invdiag[l][w] = w > 0 ? 3.0 / (h * w) : 0.0;
+    }
+  }
+  return BCM_OK;
+}
+
+Layout plan(const bcm_grid_desc* d, int n_slots) {
+  Layout L{};
+  const size_t n = (size_t)d->n_cubes * d->cells_per_edge * d->cells_per_edge * d->cells_per_edge;
+  const size_t S = d->precision == BCM_PREC_F64 ? 8 : 4;   // state storage
+  const size_t V = S;                                      // PCG vector storage
+  const size_t nub = (size_t)n_slots * 3 * d->cells_per_edge * d->cells_per_edge;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  };
+  L.u = take(n * S); L.v = take(n * S); L.w = take(n * S);
+  L.us = take(n * S); L.vs = take(n * S); L.ws = take(n * S);
+  L.nx = take(n * S); L.ny = take(n * S); L.nz = take(n * S);
+  L.phi = take(n * S); L.ub = take(nub * S);
+  L.p = take(n * 8); L.b = take(n * 8);
+  L.bid = take(n); L.near_ = take(d->n_cubes);
+  L.r = take(n * V); L.p0 = take(n * V); L.p1 = take(n * V); L.q = take(n * V);
+  L.e = take(d->precision == BCM_PREC_F64 ? 0 : n * 4);
+  L.nb = take(6 * sizeof(int) * d->n_cubes);
+  L.aux = take(24 * sizeof(int) * d->n_cubes);
+  L.sim = take(sizeof(int) * d->n_cubes);
+  L.lvl = take(sizeof(int) * d->n_cubes);
+  L.ijk = take(3 * sizeof(int) * d->n_cubes);
+  L.w3 = take(6 * sizeof(int) * d->n_cubes);
+  L.slot = take(6 * sizeof(int) * d->n_cubes);
+  L.sp = take(sizeof(SimParams) * d->n_sims);
+  L.ss = take(sizeof(SimState) * d->n_sims);
+  L.counter = take(64);
+  L.flags = take(64);
+  L.guard = take(64);
+  L.total = off;
+  L.n_slots = n_slots;
+  return L;
+}
+
+}  // namespace
+
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // pairs (start, end)
+  std::vector<int> cls;            // class of each recorded pair
+  size_t used = 0;
+  double total_ms[BCM_NKERNELS] = {};
+  long long launches[BCM_NKERNELS] = {};
+};
+
+struct bcm_grid {
+  bcm_grid_desc desc;
+  KernelTimer timer;
+  long long launch_count = 0;
+  HostTables T;
+  Layout L;
+  unsigned char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  Ctx ctx;
+  int B = 0, f64 = 1;
+  size_t n_cells = 0;
+  int device = 0;
+};
+
+namespace {
+
+// Issue one kernel launch of class k; with timing on, bracket it by two events.
+template <class F>
+bcm_status run(bcm_grid* g, int k, F&& launch) {
+  KernelTimer& t = g->timer;
+  if (t.on) {
+    if (t.used + 2 > t.pool.size()) {
+      for (int q = 0; q < 256; ++q) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        t.pool.push_back(e);
+      }
+    }
+    CUDA_TRY(cudaEventRecord(t.pool[t.used], g->stream));
+  }
+  CUDA_TRY(launch());
+  g->launch_count += 1;
+  if (t.on) {
+    CUDA_TRY(cudaEventRecord(t.pool[t.used + 1], g->stream));
+    t.cls.push_back(k);
+    t.used += 2;
+  }
+  return BCM_OK;
+}
+
+#define RUN(k, expr)                                             \
+  do {                                                           \
+    bcm_status s_ = run(g, (k), [&]() { return (expr); });       \
+    if (s_ != BCM_OK) return s_;                                 \
+  } while (0)
+
+// Fold recorded event pairs into per-class totals (synchronises the stream).
+bcm_status drain_timer(bcm_grid* g) {
+  KernelTimer& t = g->timer;
+  if (t.used == 0) return BCM_OK;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  for (size_t q = 0; q < t.cls.size(); ++q) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, t.pool[2 * q], t.pool[2 * q + 1]));
+    t.total_ms[t.cls[q]] += ms;
+    t.launches[t.cls[q]] += 1;
+  }
+  t.cls.clear();
+  t.used = 0;
+  return BCM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" const char* bcm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" size_t bcm_workspace_bytes(const bcm_grid_desc* desc) {
+  if (validate(desc) != BCM_OK) return 0;
+  HostTables T;
+  if (build_tables(desc, T) != BCM_OK) return 0;
+  return plan(desc, T.n_slots).total;
+}
+
+extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_workspace, size_t bytes,
+                                      void* cuda_stream, bcm_grid** out) {
+  if (!out) return fail(BCM_E_INVALID, "out is NULL");
+  *out = nullptr;
+  bcm_status st = validate(desc);
+  if (st != BCM_OK) return st;
+  bcm_grid* g = new bcm_grid();
+  g->desc = *desc;
+  st = build_tables(desc, g->T);
+  if (st != BCM_OK) {
+    delete g;
+    return st;
+  }
+  g->L = plan(desc, g->T.n_slots);
+  if (!dev_workspace || bytes < g->L.total) {
+    size_t need = g->L.total;
+    delete g;
+    return fail(BCM_E_INVALID, "workspace too small: need %zu bytes", need);
+  }
+  if (((uintptr_t)dev_workspace) % kAlign) {
+    delete g;
+    return fail(BCM_E_INVALID, "workspace must be %zu-byte aligned", kAlign);
+  }
+  cudaGetDevice(&g->device);
+  g->ws = (unsigned char*)dev_workspace;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->B = desc->cells_per_edge;
+  g->f64 = desc->precision == BCM_PREC_F64;
+  g->n_cells = (size_t)desc->n_cubes * g->B * g->B * g->B;
+  const Layout& L = g->L;
+  unsigned char* W = g->ws;
+  cudaStream_t s = g->stream;
+  const int n = desc->n_cubes;
+  auto fail_free = [&](bcm_status code) {
+    delete g;
+    return code;
+  };
+#define UP(off, vec, bytes)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = cudaMemcpyAsync(W + (off), (vec), (bytes), cudaMemcpyHostToDevice, s); \
+    if (e_ != cudaSuccess)                                                               \
+      return fail_free(fail(BCM_E_CUDA, "table upload: %s", cudaGetErrorString(e_)));     \
+  } while (0)
+  {
+    cudaError_t e = cudaMemsetAsync(W, 0, L.total, s);
+    if (e != cudaSuccess) return fail_free(fail(BCM_E_CUDA, "memset: %s", cudaGetErrorString(e)));
+  }
+  UP(L.nb, g->T.nb.data(), sizeof(int) * 6 * n);
+  UP(L.aux, g->T.aux.data(), sizeof(int) * 24 * n);
+  UP(L.sim, g->T.sim.data(), sizeof(int) * n);
+  UP(L.lvl, g->T.lvl.data(), sizeof(int) * n);
+  UP(L.ijk, g->T.ijk.data(), sizeof(int) * 3 * n);
+  UP(L.w3, g->T.w3.data(), sizeof(int) * 6 * n);
+  UP(L.slot, g->T.slot.data(), sizeof(int) * 6 * n);
+  UP(L.sp, g->T.sp.data(), sizeof(SimParams) * desc->n_sims);
+#undef UP
+  {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_free(fail(BCM_E_CUDA, "create sync: %s", cudaGetErrorString(e)));
+  }
+  Ctx& x = g->ctx;
+  x.B = g->B;
+  x.f64 = g->f64;
+  x.stream = s;
+  DevGrid& G = x.g;
+  G.n_cubes = n;
+  G.n_sims = desc->n_sims;
+  G.max_level = desc->max_level;
+  G.two_level = g->T.two_level;
+  G.nb = (const int*)(W + L.nb);
+  G.aux = (const int*)(W + L.aux);
+  G.sim = (const int*)(W + L.sim);
+  G.lvl = (const int*)(W + L.lvl);
+  G.ijk = (const int*)(W + L.ijk);
+  G.w3 = (const int*)(W + L.w3);
+  G.slot = (const int*)(W + L.slot);
+  G.near = (const unsigned char*)(W + L.near_);
+  G.sp = (const SimParams*)(W + L.sp);
+  G.ss = (SimState*)(W + L.ss);
+  G.counter = (unsigned int*)(W + L.counter);
+  G.flags = (int*)(W + L.flags);
+  Fields& F = x.f;
+  F.u = W + L.u; F.v = W + L.v; F.w = W + L.w;
+  F.us = W + L.us; F.vs = W + L.vs; F.ws = W + L.ws;
+  F.nx = W + L.nx; F.ny = W + L.ny; F.nz = W + L.nz;
+  F.phi = W + L.phi; F.ub = W + L.ub;
+  F.p = (double*)(W + L.p); F.b = (double*)(W + L.b);
+  F.bid = W + L.bid; F.near = W + L.near_;
+  F.r = W + L.r; F.p0 = W + L.p0; F.p1 = W + L.p1; F.q = W + L.q;
+  F.e = g->f64 ? nullptr : (float*)(W + L.e);
+  F.guard = (unsigned int*)(W + L.guard);
+  *out = g;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_destroy_grid(bcm_grid* g) {
+  if (g) {
+    for (cudaEvent_t e : g->timer.pool) cudaEventDestroy(e);
+  }
+  delete g;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_field(bcm_grid* g, int field, void** dev_ptr, size_t* count,
+                                int32_t* elem_bytes) {
+  if (!g || !dev_ptr) return fail(BCM_E_INVALID, "NULL argument");
+  const Layout& L = g->L;
+  const int S = g->f64 ? 8 : 4;
+  size_t off = 0, cnt = g->n_cells;
+  int eb = S;
+  switch (field) {
+    case BCM_U: off = L.u; break;
+    case BCM_V: off = L.v; break;
+    case BCM_W: off = L.w; break;
+    case BCM_P: off = L.p; eb = 8; break;
+    case BCM_PHI: off = L.phi; break;
+    case BCM_NX: off = L.nx; break;
+    case BCM_NY: off = L.ny; break;
+    case BCM_NZ: off = L.nz; break;
+    case BCM_USTAR: off = L.us; break;
+    case BCM_VSTAR: off = L.vs; break;
+    case BCM_WSTAR: off = L.ws; break;
+    case BCM_RHS: off = L.b; eb = 8; break;
+    case BCM_UB: off = L.ub; cnt = (size_t)L.n_slots * 3 * g->B * g->B; break;
+    default: return fail(BCM_E_INVALID, "unknown field %d", field);
+  }
+  *dev_ptr = g->ws + off;
+  if (count) *count = cnt;
+  if (elem_bytes) *elem_bytes = eb;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_set_geometry(bcm_grid* g, int sim, const bcm_body* bodies, int n_bodies,
+                                       const double* inflow_modes) {
+  if (!g || sim < 0 || sim >= g->desc.n_sims) return fail(BCM_E_INVALID, "bad grid or sim");
+  if (n_bodies < 0 || n_bodies > kMaxBodies)
+    return fail(BCM_E_BOUNDS, "n_bodies must be in [0, %d]", kMaxBodies);
+  if (n_bodies > 0 && !bodies) return fail(BCM_E_INVALID, "bodies is NULL");
+  SimParams& p = g->T.sp[sim];
+  p.n_bodies = n_bodies;
+  p.moving = 0;
+  for (int b = 0; b < kMaxBodies; ++b) memset(&p.bodies[b], 0, sizeof(bcm_body));
+  for (int b = 0; b < n_bodies; ++b) {
+    const bcm_body& bd = bodies[b];
+    if (bd.kind != BCM_BODY_SPHERE && bd.kind != BCM_BODY_ELLIPSOID)
+      return fail(BCM_E_INVALID, "body %d: unknown kind", b);
+    for (int e = 0; e < 3; ++e)
+      if (!(bd.axes[e] > 0) && !(bd.kind == BCM_BODY_SPHERE && e > 0))
+        return fail(BCM_E_INVALID, "body %d: axes must be > 0", b);
+    p.bodies[b] = bd;
+    for (int e = 0; e < 3; ++e)
+      if (bd.vel[e] != 0.0 || bd.omega[e] != 0.0) p.moving = 1;
+  }
+  p.has_modes = 0;
+  for (int m = 0; m < kModes; ++m) {
+    p.modes[m] = inflow_modes ? inflow_modes[m] : 0.0;
+    if (p.modes[m] != 0.0) p.has_modes = 1;
+  }
+  CUDA_TRY(cudaMemcpyAsync(g->ws + g->L.sp + sizeof(SimParams) * sim, &p, sizeof(SimParams),
+                           cudaMemcpyHostToDevice, g->stream));
+  // the host copy must stay valid until the copy has run
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(g->ctx, sim));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_reset_time(bcm_grid* g) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  std::vector<SimState> zero(g->desc.n_sims);
+  memset(zero.data(), 0, sizeof(SimState) * zero.size());
+  CUDA_TRY(cudaMemcpyAsync(g->ws + g->L.ss, zero.data(), sizeof(SimState) * zero.size(),
+                           cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return BCM_OK;
+}
+
+// ----------------------------------------------------------- solve drivers
+
+namespace {
+
+
+constexpr int kCheckEvery = 8;       // host-driven loops: iterations between flag reads
+constexpr int kMaxCycles = 30;       // mixed: defect-correction cycles
+constexpr double kInnerRtol = 1e-3;  // mixed: inner FP32 PCG reduction per cycle
+
+bcm_status read_flags(bcm_grid* g, int flags[2]) {
+  CUDA_TRY(cudaMemcpyAsync(flags, g->ws + g->L.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                           g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return BCM_OK;
+}
+
+// Jacobi-PCG on K p = -V (b - mean), warm start p (Saad Alg. 9.1); FP64 vectors, or
+// FP32 inner PCG inside FP64 defect correction (mixed).  Loop control is read from
+// device flags every kCheckEvery iterations; finished sims skip their cubes.
+bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
+  if (g->T.two_level)
+    return fail(BCM_E_INVALID, "the flux-form 2:1 Poisson kernels are not available");
+  Ctx& x = g->ctx;
+  SolveParams prm{};
+  prm.rtol = rtol;
+  prm.inner_rtol = kInnerRtol;
+  prm.max_iter = max_iter;
+  prm.inner_max_iter = max_iter;
+  prm.max_cycles = kMaxCycles;
+  prm.mixed = g->f64 ? 0 : 1;
+  prm.guard = x.f.guard;
+  prm.guard_limit = 0;
+  RUN(BCM_K_MISC, launch_solve_begin(x));
+  RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
+  int flags[2] = {0, 0};
+  bcm_status st = read_flags(g, flags);
+  if (st != BCM_OK) return st;
+  if (g->f64) {
+    int it = 0;
+    while (!flags[0] && it < max_iter) {
+      for (int m = 0; m < kCheckEvery && it < max_iter; ++m, ++it)
+      {
+        RUN(BCM_K_CG_A, launch_cg_a(x, prm));
+        RUN(BCM_K_CG_B, launch_cg_b(x, prm));
+      }
+      if ((st = read_flags(g, flags)) != BCM_OK) return st;
+    }
+    return BCM_OK;
+  }
+  int cycles = 0;
+  while (!flags[1] && cycles <= kMaxCycles) {
+    int it = 0;
+    while (!flags[0] && it < max_iter) {
+      for (int m = 0; m < kCheckEvery && it < max_iter; ++m, ++it)
+      {
+        RUN(BCM_K_CG_A, launch_cg_a(x, prm));
+        RUN(BCM_K_CG_B, launch_cg_b(x, prm));
+      }
+      if ((st = read_flags(g, flags)) != BCM_OK) return st;
+    }
+    RUN(BCM_K_ADD_CORRECTION, launch_add_correction(x));
+    RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
+    if ((st = read_flags(g, flags)) != BCM_OK) return st;
+    ++cycles;
+  }
+  return BCM_OK;
+}
+
+bcm_status collect(bcm_grid* g, bcm_stats* out) {
+  std::vector<SimState> ss(g->desc.n_sims);
+  CUDA_TRY(cudaMemcpyAsync(ss.data(), g->ws + g->L.ss, sizeof(SimState) * ss.size(),
+                           cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  bcm_status st = BCM_OK;
+  for (size_t s = 0; s < ss.size(); ++s) {
+    const SimState& t = ss[s];
+    bcm_stats& o = out[s];
+    o.cg_iters = t.total_iters;
+    o.refine_cycles = g->f64 ? 0 : t.cycles;
+    o.steps = t.step;
+    o.converged = t.converged;
+    o.rel_resid = t.bb > 0 ? sqrt(t.rr64 / t.bb) : 0.0;
+    o.div_rel = t.div_den > 0 ? sqrt(t.div_num / t.div_den) : 0.0;
+    for (int e = 0; e < 3; ++e) o.drag[e] = t.drag[e];
+    double um;
+    memcpy(&um, &t.umax_bits, sizeof um);
+    o.umax = um;
+    if (t.nonfinite) st = BCM_E_NONFINITE;
+    else if (!t.converged && st == BCM_OK) st = BCM_E_NOT_CONVERGED;
+  }
+  if (st == BCM_E_NONFINITE) return fail(st, "non-finite residual");
+  if (st == BCM_E_NOT_CONVERGED) return fail(st, "pressure solve did not reach rtol");
+  return st;
+}
+
+}  // namespace
+
+extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_iter,
+                               bcm_stats* stats) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (n_steps < 0 || !(rtol > 0) || max_iter < 1)
+    return fail(BCM_E_INVALID, "need n_steps >= 0, rtol > 0, max_iter >= 1");
+  Ctx& x = g->ctx;
+  bool moving = false;
+  for (const auto& p : g->T.sp) moving |= (p.n_bodies > 0 && p.moving);
+  bcm_status last = BCM_OK;
+  for (int n = 0; n < n_steps; ++n) {
+    if (moving) RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -2));
+    RUN(BCM_K_MOMENTUM, launch_momentum(x));
+    RUN(BCM_K_RHS, launch_rhs(x));
+    bcm_status st = solve(g, rtol, max_iter);
+    if (st != BCM_OK) return st;
+    RUN(BCM_K_CORRECT, launch_correct(x));
+    RUN(BCM_K_MISC, launch_step_end(x));
+  }
+  if (stats) last = collect(g, stats);
+  return last;
+}
+
+extern "C" bcm_status bcm_profile(bcm_grid* g, int enable) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  bcm_status st = drain_timer(g);
+  if (st != BCM_OK) return st;
+  g->timer.on = enable != 0;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_profile_read(bcm_grid* g, double* total_ms, int64_t* launches,
+                                       int64_t* launch_count, int reset) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  bcm_status st = drain_timer(g);
+  if (st != BCM_OK) return st;
+  for (int k = 0; k < BCM_NKERNELS; ++k) {
+    if (total_ms) total_ms[k] = g->timer.total_ms[k];
+    if (launches) launches[k] = g->timer.launches[k];
+  }
+  if (launch_count) *launch_count = g->launch_count;
+  if (reset) {
+    for (int k = 0; k < BCM_NKERNELS; ++k) {
+      g->timer.total_ms[k] = 0.0;
+      g->timer.launches[k] = 0;
+    }
+    g->launch_count = 0;
+  }
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_solve_pressure(bcm_grid* g, double rtol, int max_iter, bcm_stats* stats) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (!(rtol > 0) || max_iter < 1) return fail(BCM_E_INVALID, "need rtol > 0, max_iter >= 1");
+  RUN(BCM_K_MISC, launch_bmean(g->ctx));
+  bcm_status st = solve(g, rtol, max_iter);
+  if (st != BCM_OK) return st;
+  if (stats) return collect(g, stats);
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_fill_halo(bcm_grid* g, int field, int kind, double* dev_out) {
+  if (!g || !dev_out) return fail(BCM_E_INVALID, "NULL argument");
+  if (kind < 0 || kind > 3) return fail(BCM_E_INVALID, "kind must be 0..3");
+  void* ptr;
+  size_t cnt;
+  int32_t eb;
+  bcm_status st = bcm_field(g, field, &ptr, &cnt, &eb);
+  if (st != BCM_OK) return st;
+  if (field == BCM_UB) return fail(BCM_E_INVALID, "BCM_UB is not a cell field");
+  RUN(BCM_K_MISC, launch_fill_halo(g->ctx, ptr, eb == 8, kind, dev_out));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_apply_poisson(bcm_grid* g, const double* x, double* y) {
+  if (!g || !x || !y) return fail(BCM_E_INVALID, "NULL argument");
+  if (g->T.two_level) return fail(BCM_E_INVALID, "the flux-form 2:1 operator is not available");
+  RUN(BCM_K_MISC, launch_apply_poisson(g->ctx, x, y));
+  return BCM_OK;
+}

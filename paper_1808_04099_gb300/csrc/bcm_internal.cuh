@@ -1,0 +1,267 @@
+// bcm_internal.cuh -- device-side data structures and helpers of the BCM library.
+//
+// Data layout in HBM (all inside the caller's workspace):
+//   cell fields   cube-major SoA, B^3 values per cube, x fastest (coalesced rows)
+//   cube tables   int32 face adjacency [n_cubes*6], 2:1 partners [n_cubes*24],
+//                 sim id, level, corner, face Jacobi weights, outflow slots
+//   sim tables    SimParams (read-only) and SimState (solver scalars, accumulators)
+// Halos are never stored: every stencil kernel stages its cube (or a z-slab of it)
+// plus a one-cell face halo in shared memory, reading the halo straight from the
+// neighbouring cubes' interiors (Z-ordered cubes keep those reads L2-resident).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bcm.h"
+
+namespace bcm {
+
+constexpr int kMaxBodies = 4;
+constexpr int kModes = 8;
+constexpr int kW3 = 37;  // sums of face Jacobi weights in thirds (0..36)
+
+enum { BC_WALL = 0, BC_INFLOW = 1, BC_SLIP = 2, BC_OUTFLOW = 3, BC_PERIODIC = 4 };
+enum { NB_BOUNDARY = -1, NB_COARSE = -2, NB_FINE = -3 };
+
+// Per-sim constants (written once at grid creation / set_geometry).
+struct SimParams {
+  double origin[3];
+  double h0;          // level-0 cell size
+  double hf;          // finest cell size (corner unit)
+  double nu, dt, uconv;
+  double bcvel[6][3];
+  double modes[kModes];
+  double L[3];        // domain lengths
+  double invdiag[2][kW3];  // 1 / diag(K) per level and face-weight sum (thirds)
+  bcm_body bodies[kMaxBodies];
+  int n_bodies, has_modes, moving, all_neumann;
+  int extent[3];
+  int bc[6];
+  int cube_begin, cube_end;
+  int n_cells;
+  int pad;
+};
+
+// Per-sim mutable state (solver scalars and atomic accumulators).
+struct SimState {
+  double acc[8];       // atomics: see ACC_* below
+  double drag_acc[3];
+  double drag[3];
+  double bb;           // ||rhs||^2
+  double tol2;         // rtol^2 ||rhs||^2 (outer)
+  double rz, rr, alpha, beta;
+  double inner_tol2;
+  double rr64;         // FP64 residual^2 (mixed) / final rr (FP64 mode)
+  double bmean;        // volume mean of b (all-Neumann sims)
+  double div_num, div_den;
+  unsigned long long umax_bits;
+  int iter;            // iterations of the running (inner) CG
+  int done;            // running CG finished
+  int outer_done;      // mixed: defect correction finished
+  int cycles;          // mixed: residual evaluations
+  int total_iters;     // CG iterations of this solve (summed over cycles)
+  int step;            // steps taken (time = step * dt)
+  int zero_rhs;        // b == 0: p = 0
+  int converged;
+  int nonfinite;
+  int pad;
+};
+
+enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 5,
+       ACC_DIVN = 6, ACC_DIVD = 7 };
+
+// Device view of the grid tables, passed by value to every kernel.
+struct DevGrid {
+  int n_cubes, n_sims, max_level, two_level;
+  const int* __restrict__ nb;     // [6n] same-level id or NB_* code
+  const int* __restrict__ aux;    // [24n] coarse id (slot 0) or 4 fine ids
+  const int* __restrict__ sim;    // [n]
+  const int* __restrict__ lvl;    // [n]
+  const int* __restrict__ ijk;    // [3n]
+  const int* __restrict__ w3;     // [6n] Jacobi face weight in thirds (0,2,3,4,6)
+  const int* __restrict__ slot;   // [6n] outflow slot or -1
+  const unsigned char* __restrict__ near;  // [n] cube may hold phi != 0
+  const SimParams* __restrict__ sp;
+  SimState* ss;
+  unsigned int* counter;          // last-block tickets
+  int* flags;                     // [0] every running CG finished, [1] every defect correction finished
+};
+
+__host__ __device__ __forceinline__ int tan1(int d) { return d == 0 ? 1 : 0; }
+__host__ __device__ __forceinline__ int tan2(int d) { return d == 2 ? 1 : 2; }
+
+// ---------------------------------------------------------------- geometry
+
+template <int B>
+__device__ __forceinline__ double cell_h(const DevGrid& g, int c) {
+  return g.sp[g.sim[c]].h0 / double(1 << g.lvl[c]);
+}
+
+template <int B>
+__device__ __forceinline__ int cell_span(const DevGrid& g, int c) {
+  return 1 << (g.max_level - g.lvl[c]);
+}
+
+// Physical coordinate of cell index n (halo indices allowed) of cube c along axis e.
+template <int B>
+__device__ __forceinline__ double centre(const DevGrid& g, int c, int e, int n) {
+  const SimParams& p = g.sp[g.sim[c]];
+  return p.origin[e] + g.ijk[3 * c + e] * p.hf + (n + 0.5) * cell_h<B>(g, c);
+}
+
+// Inflow profile factor 1 + sum a_m sin(k pi s/Ls) sin(l pi t/Lt) on face f of cube c.
+template <int B>
+__device__ double inflow_profile(const DevGrid& g, int c, int f, int a, int b) {
+  const int mk[kModes] = {1, 1, 2, 2, 1, 3, 2, 3};
+  const int ml[kModes] = {1, 2, 1, 2, 3, 1, 3, 2};
+  const SimParams& p = g.sp[g.sim[c]];
+  int d = f >> 1, e1 = tan1(d), e2 = tan2(d);
+  double y = centre<B>(g, c, e1, a) - p.origin[e1];
+  double z = centre<B>(g, c, e2, b) - p.origin[e2];
+  double prof = 1.0;
+  for (int m = 0; m < kModes; ++m)
+    prof += p.modes[m] * sin(mk[m] * M_PI * y / p.L[e1]) * sin(ml[m] * M_PI * z / p.L[e2]);
+  return prof;
+}
+
+// Wall / inflow velocity component comp on face f of cube c at tangential (a, b).
+template <int B>
+__device__ __forceinline__ double face_velocity(const DevGrid& g, int c, int f, int comp, int a,
+                                                int b) {
+  const SimParams& p = g.sp[g.sim[c]];
+  double w = p.bcvel[f][comp];
+  if (p.bc[f] == BC_INFLOW && p.has_modes) w *= inflow_profile<B>(g, c, f, a, b);
+  return w;
+}
+
+// Cell index of (normal index n along d, tangential a, b).
+template <int B>
+__device__ __forceinline__ int cell_of(int d, int n, int a, int b) {
+  int q[3];
+  q[d] = n;
+  q[tan1(d)] = a;
+  q[tan2(d)] = b;
+  return (q[2] * B + q[1]) * B + q[0];
+}
+
+// ----------------------------------------------------------------- halo value
+//
+// Value of the ghost cell at distance layer+1 outside face f of cube c, tangential
+// (a, b), by the halo rules of the paper ("Building Cube Method"):
+//   same level: copy of the neighbour's boundary interior cell;
+//   coarse neighbour (this cube fine): the coarse cell covering the ghost (injection);
+//   fine neighbours (this cube coarse): mean of the 2x2x2 fine cells it covers;
+//   domain face: bc(f, a, b, mirror interior value).
+// val(cube, cell) returns the interior value of any cube.
+template <int B, class T, class Val, class Bc>
+__device__ __forceinline__ T halo_value(const DevGrid& g, int c, int f, int a, int b, int layer,
+                                        const Val& val, const Bc& bc) {
+  const int d = f >> 1, side = f & 1;
+  const int n = g.nb[6 * c + f];
+  if (n >= 0) return val(n, cell_of<B>(d, side ? layer : B - 1 - layer, a, b));
+  if (n == NB_BOUNDARY)
+    return bc(f, a, b, val(c, cell_of<B>(d, side ? B - 1 - layer : layer, a, b)));
+  if (n == NB_COARSE) {
+    const int C = g.aux[(6 * c + f) * 4];
+    const int sf = 1 << (g.max_level - g.lvl[c]), sc = 2 * sf;
+    const int A = (g.ijk[3 * c + tan1(d)] + a * sf - g.ijk[3 * C + tan1(d)]) / sc;
+    const int Bb = (g.ijk[3 * c + tan2(d)] + b * sf - g.ijk[3 * C + tan2(d)]) / sc;
+    return val(C, cell_of<B>(d, side ? 0 : B - 1, A, Bb));
+  }
+  // NB_FINE
+  const int qa = (2 * a) / B, qb = (2 * b) / B;
+  const int F = g.aux[(6 * c + f) * 4 + qb * 2 + qa];
+  const int fa = 2 * a - qa * B, fb = 2 * b - qb * B;
+  T sum = T(0);
+  for (int l2 = 0; l2 < 2; ++l2) {
+    const int fn = side ? 2 * layer + l2 : B - 1 - 2 * layer - l2;
+    for (int bb = 0; bb < 2; ++bb)
+      for (int aa = 0; aa < 2; ++aa) sum += val(F, cell_of<B>(d, fn, fa + aa, fb + bb));
+  }
+  return T(0.125) * sum;
+}
+
+// ---------------------------------------------------------------- slab staging
+//
+// A CTA owns planes [z0, z0+KS) of one cube.  Shared memory holds those planes
+// plus one plane below and above, each (B+2)^2 with a one-cell x/y ring.  Edge and
+// corner ring cells are never read by the 7-point stencils and stay unset.
+template <int B, int KS>
+struct Slab {
+  static constexpr int P = B + 2;
+  static constexpr int N = (KS + 2) * P * P;
+  __device__ __forceinline__ static int at(int i, int j, int kk) {
+    return (kk * P + (j + 1)) * P + (i + 1);
+  }
+};
+
+template <int B, int KS, int NT, class T, class Val, class Bc>
+__device__ __forceinline__ void stage_slab(T* __restrict__ S, const DevGrid& g, int c, int z0,
+                                           const Val& val, const Bc& bc) {
+  using SL = Slab<B, KS>;
+  constexpr int BB = B * B;
+  for (int idx = threadIdx.x; idx < (KS + 2) * BB; idx += NT) {
+    const int kk = idx / BB, rem = idx - kk * BB, j = rem / B, i = rem - j * B;
+    const int k = z0 - 1 + kk;
+    T v;
+    if (k < 0) v = halo_value<B, T>(g, c, 4, i, j, 0, val, bc);
+    else if (k >= B) v = halo_value<B, T>(g, c, 5, i, j, 0, val, bc);
+    else v = val(c, (k * B + j) * B + i);
+    S[SL::at(i, j, kk)] = v;
+  }
+  for (int idx = threadIdx.x; idx < 4 * KS * B; idx += NT) {
+    const int f = idx / (KS * B), rem = idx - f * (KS * B), kk = rem / B, t = rem - kk * B;
+    const int k = z0 + kk;
+    const T v = halo_value<B, T>(g, c, f, t, k, 0, val, bc);
+    if (f < 2) S[SL::at(f == 0 ? -1 : B, t, kk + 1)] = v;
+    else S[SL::at(t, f == 2 ? -1 : B, kk + 1)] = v;
+  }
+}
+
+// --------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block of NV doubles per thread; result valid in thread 0.
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q * 32 + warp] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = lane < NT / 32 ? red[q * 32 + lane] : 0.0;
+      v[q] = warp_sum(x);
+    }
+  }
+}
+
+// Last-block election: every block must call this exactly once per launch.
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int total = gridDim.x * gridDim.y;
+    const unsigned int t = atomicAdd(counter, 1u);
+    is_last = (t == total - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
+__device__ __forceinline__ double ld_acc(const double* p) { return __ldcg(p); }
+
+}  // namespace bcm

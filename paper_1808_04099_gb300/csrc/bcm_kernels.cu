@@ -1,0 +1,1105 @@
+// bcm_kernels.cu -- sm_103a kernels of the BCM fractional step (arXiv:1808.04099,
+// section "Numerical algorithm"): solid fraction, momentum + IB forcing, Poisson
+// right-hand side, Jacobi-PCG passes, FP64 residual for defect correction, and the
+// projection.  All of them are HBM-bandwidth bound stencils or streams (no dense
+// contraction, so no tensor cores): cube-major SoA rows are read coalesced, each
+// CTA stages its cube (or a z-slab) plus a one-cell face halo in shared memory, and
+// Krylov dot products are reduced with warp shuffles into FP64 per-sim atomics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bcm_internal.cuh"
+#include "bcm_kernels.h"
+
+namespace bcm {
+
+// ------------------------------------------------------------ small helpers
+
+template <int B>
+__device__ __forceinline__ int face_w3_sum(const DevGrid& g, int c, int cell) {
+  const int i = cell % B, j = (cell / B) % B, k = cell / (B * B);
+  int s3 = 18;
+  if (i == 0) s3 += g.w3[6 * c + 0] - 3;
+  if (i == B - 1) s3 += g.w3[6 * c + 1] - 3;
+  if (j == 0) s3 += g.w3[6 * c + 2] - 3;
+  if (j == B - 1) s3 += g.w3[6 * c + 3] - 3;
+  if (k == 0) s3 += g.w3[6 * c + 4] - 3;
+  if (k == B - 1) s3 += g.w3[6 * c + 5] - 3;
+  return s3;
+}
+
+// 1 / diag(K) of a cell: Jacobi preconditioner of the PCG (R11).
+template <int B>
+__device__ __forceinline__ double inv_diag(const DevGrid& g, int c, int cell) {
+  return g.sp[g.sim[c]].invdiag[g.lvl[c]][face_w3_sum<B>(g, c, cell)];
+}
+
+// Ghost rule that is never used (faces whose values come from the boundary data).
+struct KeepBC {
+  template <class U>
+  __device__ __forceinline__ U operator()(int, int, int, U x) const { return x; }
+};
+
+// Pressure-like ghost: Neumann (mirror) except Dirichlet p = 0 at outflow faces.
+struct PressureBC {
+  const SimParams* sp;
+  template <class T>
+  __device__ __forceinline__ T operator()(int f, int, int, T p0) const {
+    return sp->bc[f] == BC_OUTFLOW ? -p0 : p0;
+  }
+};
+
+// Velocity ghost rules (R8) for component comp.
+template <int B, class T>
+struct VelocityBC {
+  const DevGrid* g;
+  const SimParams* sp;
+  const T* ub;
+  int c, comp;
+  __device__ __forceinline__ T operator()(int f, int a, int b, T u0) const {
+    const int bc = sp->bc[f];
+    if (bc == BC_SLIP) return (comp == (f >> 1)) ? -u0 : u0;
+    if (bc == BC_OUTFLOW) {
+      const int sl = g->slot[6 * c + f];
+      return T(2) * ub[((size_t)(sl * 3 + comp) * B + b) * B + a] - u0;
+    }
+    return T(2.0 * face_velocity<B>(*g, c, f, comp, a, b)) - u0;
+  }
+};
+
+template <class T>
+struct FieldVal {
+  const T* f;
+  int B3;
+  __device__ __forceinline__ T operator()(int c, int cell) const {
+    return f[(size_t)c * B3 + cell];
+  }
+};
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v) {
+  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// Device-side loop control for CUDA-graph while nodes (0 handle = host-driven loop).
+__device__ __forceinline__ void set_cond(unsigned long long handle, unsigned int v) {
+  if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, v);
+}
+
+// ------------------------------------------------------------- body geometry
+
+// Signed distance of point x to a body at time t (body pose precomputed), and the
+// rigid-body velocity there.  Sphere: exact; ellipsoid: k0 (k0 - 1) / k1 (R9).
+struct Pose {
+  double c[3];
+  double R[3][3];
+  int kind;
+  double ax[3], om[3], v[3];
+};
+
+__device__ void make_pose(const bcm_body& b, double t, Pose& P) {
+  P.kind = b.kind;
+  for (int e = 0; e < 3; ++e) {
+    P.c[e] = b.center[e] + b.vel[e] * t;
+    P.ax[e] = b.axes[e];
+    P.om[e] = b.omega[e];
+    P.v[e] = b.vel[e];
+  }
+  const double w = b.quat[0], x = b.quat[1], y = b.quat[2], z = b.quat[3];
+  double R0[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                     {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                     {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+  double th[3] = {b.omega[0] * t, b.omega[1] * t, b.omega[2] * t};
+  double a = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+  double Rt[3][3];
+  if (a == 0.0) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Rt[i][j] = (i == j) ? 1.0 : 0.0;
+  } else {
+    double k[3] = {th[0] / a, th[1] / a, th[2] / a};
+    double cs = cos(a), sn = sin(a);
+    double K[3][3] = {{0, -k[2], k[1]}, {k[2], 0, -k[0]}, {-k[1], k[0], 0}};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double kk = 0;
+        for (int m = 0; m < 3; ++m) kk += K[i][m] * K[m][j];
+        Rt[i][j] = (i == j ? 1.0 : 0.0) + sn * K[i][j] + (1 - cs) * kk;
+      }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0;
+      for (int m = 0; m < 3; ++m) acc += Rt[i][m] * R0[m][j];
+      P.R[i][j] = acc;
+    }
+}
+
+__device__ double pose_sd(const Pose& P, const double* x) {
+  double r[3] = {x[0] - P.c[0], x[1] - P.c[1], x[2] - P.c[2]};
+  if (P.kind == BCM_BODY_SPHERE) return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) - P.ax[0];
+  double y[3];
+  for (int j = 0; j < 3; ++j) y[j] = P.R[0][j] * r[0] + P.R[1][j] * r[1] + P.R[2][j] * r[2];
+  double k0 = 0, k1 = 0;
+  for (int e = 0; e < 3; ++e) {
+    k0 += (y[e] / P.ax[e]) * (y[e] / P.ax[e]);
+    k1 += (y[e] / (P.ax[e] * P.ax[e])) * (y[e] / (P.ax[e] * P.ax[e]));
+  }
+  k0 = sqrt(k0);
+  k1 = sqrt(k1);
+  if (k1 == 0.0) return -fmin(P.ax[0], fmin(P.ax[1], P.ax[2]));
+  return k0 * (k0 - 1.0) / k1;
+}
+
+// ===========================================================================
+// (a2) solid fraction phi = (1 - tanh(d/eps))/2, eps = 1.5 h, 0 beyond 20 eps (R5)
+// ===========================================================================
+template <int B, int NT, class T>
+__global__ __launch_bounds__(NT) void k_solid_fraction(DevGrid g, T* __restrict__ phi,
+                                                       unsigned char* __restrict__ bid,
+                                                       unsigned char* __restrict__ near,
+                                                       int sim_filter) {
+  constexpr int B3 = B * B * B;
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  // sim_filter: -1 every sim, -2 sims with moving bodies, >= 0 that sim only
+  if (sp.n_bodies == 0 || (sim_filter == -2 && !sp.moving) || (sim_filter >= 0 && s != sim_filter))
+    return;
+  __shared__ Pose P[kMaxBodies];
+  __shared__ int any_near;
+  const double t = g.ss[s].step * sp.dt;
+  if (threadIdx.x < sp.n_bodies) make_pose(sp.bodies[threadIdx.x], t, P[threadIdx.x]);
+  if (threadIdx.x == 0) any_near = 0;
+  __syncthreads();
+  const double h = cell_h<B>(g, c), eps = 1.5 * h;
+  // conservative cube cull: the signed-distance estimate is >= (|y|/amax - 1) amin
+  if (threadIdx.x == 0) {
+    int nearc = 0;
+    for (int bi = 0; bi < sp.n_bodies; ++bi) {
+      double d2 = 0.0;
+      for (int e = 0; e < 3; ++e) {
+        double lo = sp.origin[e] + g.ijk[3 * c + e] * sp.hf + 0.5 * h;
+        double hi = lo + (B - 1) * h;
+        double q = fmin(fmax(P[bi].c[e], lo), hi) - P[bi].c[e];
+        d2 += q * q;
+      }
+      double amax = fmax(P[bi].ax[0], fmax(P[bi].ax[1], P[bi].ax[2]));
+      double amin = fmin(P[bi].ax[0], fmin(P[bi].ax[1], P[bi].ax[2]));
+      if (P[bi].kind == BCM_BODY_SPHERE) amax = amin = P[bi].ax[0];
+      double dlow = (sqrt(d2) / amax - 1.0) * amin;
+      if (dlow < 20.0 * eps * 1.0000001) nearc = 1;
+    }
+    any_near = nearc;
+  }
+  __syncthreads();
+  if (!any_near) {
+    if (near[c]) {
+      for (int q = threadIdx.x; q < B3; q += NT) phi[(size_t)c * B3 + q] = T(0);
+      __syncthreads();
+      if (threadIdx.x == 0) near[c] = 0;
+    }
+    return;
+  }
+  for (int q = threadIdx.x; q < B3; q += NT) {
+    const int i = q % B, j = (q / B) % B, k = q / (B * B);
+    double x[3] = {centre<B>(g, c, 0, i), centre<B>(g, c, 1, j), centre<B>(g, c, 2, k)};
+    double best = INFINITY;
+    int bb = 0;
+    for (int bi = 0; bi < sp.n_bodies; ++bi) {
+      double d = pose_sd(P[bi], x);
+      if (d < best) {
+        best = d;
+        bb = bi;
+      }
+    }
+    double f = (best < 20.0 * eps) ? 0.5 * (1.0 - tanh(best / eps)) : 0.0;
+    phi[(size_t)c * B3 + q] = T(f);
+    bid[(size_t)c * B3 + q] = (unsigned char)bb;
+  }
+  if (threadIdx.x == 0) near[c] = 1;
+}
+
+// ===========================================================================
+// (a3,a5,a6,a7) momentum sub-step + IB forcing, fused with the halo staging.
+//   N_c = (1/h) sum_d [F+ - F-],  F+ = (u_d,i + u_d,i+1)/2 (u_c,i + u_c,i+1)/2
+//   L u_c = (1/h^2) sum_d (u_c,i+1 - 2 u_c,i + u_c,i-1)
+//   u~ = u + dt [-(3/2 N^n - 1/2 N^{n-1}) + nu L u]      (R3; N^{-1} := N^0)
+//   u* = u~ + phi (u_s - u~),  drag -= phi (u_s - u~) V / dt   (R5)
+// and the convective outflow face update u_b^{n+1} (R8).
+// ===========================================================================
+template <int B, int KS, int NT, class T>
+__global__ __launch_bounds__(NT) void k_momentum(
+    DevGrid g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+    T* __restrict__ us, T* __restrict__ vs, T* __restrict__ ws, T* __restrict__ nx,
+    T* __restrict__ ny, T* __restrict__ nz, const T* __restrict__ phi,
+    const unsigned char* __restrict__ bid, T* __restrict__ ub) {
+  using SL = Slab<B, KS>;
+  constexpr int B3 = B * B * B, NSL = B / KS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + SL::N;
+  T* S2 = S1 + SL::N;
+  __shared__ double red[3 * 32];
+  const int c = blockIdx.x / NSL, z0 = (blockIdx.x % NSL) * KS;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  {
+    VelocityBC<B, T> b0{&g, &sp, ub, c, 0}, b1{&g, &sp, ub, c, 1}, b2{&g, &sp, ub, c, 2};
+    stage_slab<B, KS, NT>(S0, g, c, z0, FieldVal<T>{u, B3}, b0);
+    stage_slab<B, KS, NT>(S1, g, c, z0, FieldVal<T>{v, B3}, b1);
+    stage_slab<B, KS, NT>(S2, g, c, z0, FieldVal<T>{w, B3}, b2);
+  }
+  __syncthreads();
+  const double hd = cell_h<B>(g, c);
+  const T h = T(hd), ih = T(1.0 / hd), ih2 = T(1.0 / (hd * hd));
+  const T dt = T(sp.dt), nu = T(sp.nu);
+  const bool first = g.ss[s].step == 0;
+  const bool has_phi = g.near[c] != 0;
+  const double t = g.ss[s].step * sp.dt;
+  const T* Sf[3] = {S0, S1, S2};
+  T* outs[3] = {us, vs, ws};
+  T* Ns[3] = {nx, ny, nz};
+  T fsum[3] = {T(0), T(0), T(0)};
+  for (int q = threadIdx.x; q < KS * B * B; q += NT) {
+    const int kk = q / (B * B), rem = q - kk * B * B, j = rem / B, i = rem - j * B;
+    const int k = z0 + kk;
+    const size_t gi = (size_t)c * B3 + (k * B + j) * B + i;
+    const int o = SL::at(i, j, kk + 1);
+    const int off[3] = {1, SL::P, SL::P * SL::P};
+    T ph = T(0);
+    T usb[3] = {T(0), T(0), T(0)};
+    if (has_phi) {
+      ph = phi[gi];
+      if (ph != T(0)) {
+        const bcm_body& bd = sp.bodies[bid[gi]];
+        double x[3] = {centre<B>(g, c, 0, i), centre<B>(g, c, 1, j), centre<B>(g, c, 2, k)};
+        double r[3];
+        for (int e = 0; e < 3; ++e) r[e] = x[e] - (bd.center[e] + bd.vel[e] * t);
+        usb[0] = T(bd.vel[0] + bd.omega[1] * r[2] - bd.omega[2] * r[1]);
+        usb[1] = T(bd.vel[1] + bd.omega[2] * r[0] - bd.omega[0] * r[2]);
+        usb[2] = T(bd.vel[2] + bd.omega[0] * r[1] - bd.omega[1] * r[0]);
+      }
+    }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const T* Sc = Sf[comp];
+      const T u0 = Sc[o];
+      T N = T(0), L = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T* Sd = Sf[d];
+        const int e = off[d];
+        const T Fp = T(0.5) * (Sd[o] + Sd[o + e]) * (T(0.5) * (u0 + Sc[o + e]));
+        const T Fm = T(0.5) * (Sd[o - e] + Sd[o]) * (T(0.5) * (Sc[o - e] + u0));
+        N += Fp - Fm;
+        L += Sc[o + e] - T(2) * u0 + Sc[o - e];
+      }
+      N *= ih;
+      L *= ih2;
+      const T Np = first ? N : Ns[comp][gi];
+      const T ut = u0 + dt * (-(T(1.5) * N - T(0.5) * Np) + nu * L);
+      const T du = ph * (usb[comp] - ut);
+      outs[comp][gi] = ut + du;
+      Ns[comp][gi] = N;
+      fsum[comp] += du;
+    }
+  }
+  // convective outflow: u_b^{n+1} = u_b - U_c dt (u_b - u_0) / (h/2), this slab's cells
+  for (int f = 0; f < 6; ++f) {
+    const int sl = g.slot[6 * c + f];
+    if (sl < 0) continue;
+    const int d = f >> 1, side = f & 1;
+    const T coef = T(sp.uconv * sp.dt / (0.5 * hd));
+    if (d == 2) {
+      if ((side == 0 && z0 != 0) || (side == 1 && z0 + KS != B)) continue;
+      for (int q = threadIdx.x; q < 3 * B * B; q += NT) {
+        const int comp = q / (B * B), rem = q - comp * B * B, b = rem / B, a = rem - b * B;
+        const T u0 = Sf[comp][SL::at(a, b, side ? KS : 1)];
+        T* pb = &ub[((size_t)(sl * 3 + comp) * B + b) * B + a];
+        *pb = *pb - coef * (*pb - u0);
+      }
+    } else {
+      for (int q = threadIdx.x; q < 3 * KS * B; q += NT) {
+        const int comp = q / (KS * B), rem = q - comp * KS * B, kk = rem / B, t2 = rem - kk * B;
+        const int k = z0 + kk, a = t2, b = k;
+        const int nrm = side ? B - 1 : 0;
+        const int o = d == 0 ? SL::at(nrm, t2, kk + 1) : SL::at(t2, nrm, kk + 1);
+        const T u0 = Sf[comp][o];
+        T* pb = &ub[((size_t)(sl * 3 + comp) * B + b) * B + a];
+        *pb = *pb - coef * (*pb - u0);
+      }
+    }
+  }
+  if (has_phi) {  // drag: force of the fluid on the body = -sum f V, f = du/dt
+    double vals[3] = {double(fsum[0]), double(fsum[1]), double(fsum[2])};
+    block_sum<NT, 3>(vals, red);
+    if (threadIdx.x == 0) {
+      const double scale = -hd * hd * hd / sp.dt;
+      for (int e = 0; e < 3; ++e) atomicAdd(&g.ss[s].drag_acc[e], vals[e] * scale);
+    }
+  }
+}
+
+// ===========================================================================
+// (a8) Poisson right-hand side b = (1/dt)(1/h) sum_f A U_f.n  (R2): interior faces
+// average the two cells, domain faces take the boundary normal velocity.
+// ===========================================================================
+template <int B, int KS, int NT, class T>
+__global__ __launch_bounds__(NT) void k_rhs(DevGrid g, const T* __restrict__ us,
+                                            const T* __restrict__ vs, const T* __restrict__ ws,
+                                            const T* __restrict__ ub, double* __restrict__ b) {
+  using SL = Slab<B, KS>;
+  constexpr int B3 = B * B * B, NSL = B / KS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + SL::N;
+  T* S2 = S1 + SL::N;
+  __shared__ double red[32];
+  const int c = blockIdx.x / NSL, z0 = (blockIdx.x % NSL) * KS;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  KeepBC keep;
+  stage_slab<B, KS, NT>(S0, g, c, z0, FieldVal<T>{us, B3}, keep);
+  stage_slab<B, KS, NT>(S1, g, c, z0, FieldVal<T>{vs, B3}, keep);
+  stage_slab<B, KS, NT>(S2, g, c, z0, FieldVal<T>{ws, B3}, keep);
+  __syncthreads();
+  const T* Sf[3] = {S0, S1, S2};
+  const double hd = cell_h<B>(g, c);
+  const double scale = 1.0 / (hd * sp.dt);
+  bool bnd[6];
+  for (int f = 0; f < 6; ++f) bnd[f] = g.nb[6 * c + f] == NB_BOUNDARY;
+  double bsum = 0.0;
+  for (int q = threadIdx.x; q < KS * B * B; q += NT) {
+    const int kk = q / (B * B), rem = q - kk * B * B, j = rem / B, i = rem - j * B;
+    const int k = z0 + kk;
+    const int ii[3] = {i, j, k};
+    const int o = SL::at(i, j, kk + 1);
+    const int off[3] = {1, SL::P, SL::P * SL::P};
+    T div = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* Sd = Sf[d];
+      const int e = off[d];
+      const int a = ii[tan1(d)], bb = ii[tan2(d)];
+      T Um, Up;
+      if (ii[d] == 0 && bnd[2 * d]) {
+        const int f = 2 * d, bc = sp.bc[f];
+        Um = bc == BC_SLIP ? T(0)
+             : bc == BC_OUTFLOW ? ub[((size_t)(g.slot[6 * c + f] * 3 + d) * B + bb) * B + a]
+                                : T(face_velocity<B>(g, c, f, d, a, bb));
+      } else {
+        Um = T(0.5) * (Sd[o - e] + Sd[o]);
+      }
+      if (ii[d] == B - 1 && bnd[2 * d + 1]) {
+        const int f = 2 * d + 1, bc = sp.bc[f];
+        Up = bc == BC_SLIP ? T(0)
+             : bc == BC_OUTFLOW ? ub[((size_t)(g.slot[6 * c + f] * 3 + d) * B + bb) * B + a]
+                                : T(face_velocity<B>(g, c, f, d, a, bb));
+      } else {
+        Up = T(0.5) * (Sd[o] + Sd[o + e]);
+      }
+      div = div - Um;
+      div = div + Up;
+    }
+    const double bv = double(div) * scale;
+    b[(size_t)c * B3 + (k * B + j) * B + i] = bv;
+    bsum += bv;
+  }
+  double vals[1] = {bsum};
+  block_sum<NT, 1>(vals, red);
+  if (threadIdx.x == 0 && sp.all_neumann) atomicAdd(&g.ss[s].acc[ACC_BSUM], vals[0]);
+  if (last_block(g.counter)) {
+    for (int q = threadIdx.x; q < g.n_sims; q += NT) {
+      SimState& st = g.ss[q];
+      st.bmean = g.sp[q].all_neumann ? ld_acc(&st.acc[ACC_BSUM]) / g.sp[q].n_cells : 0.0;
+      st.acc[ACC_BSUM] = 0.0;
+    }
+    if (threadIdx.x == 0) *g.counter = 0;
+  }
+}
+
+// ===========================================================================
+// (a9, a10) residual r = rhs - K x of the FP64 iterate x = p, rhs = -V (b - mean).
+// FP64 mode: r starts the PCG.  Mixed mode: one defect-correction cycle; r is
+// stored in FP32 as the inner right-hand side and the inner iterate e is zeroed.
+// ===========================================================================
+template <int B, int NT, class TV, bool MIXED>
+__global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __restrict__ b,
+                                                 const double* __restrict__ x,
+                                                 TV* __restrict__ r, float* __restrict__ e,
+                                                 SolveParams prm) {
+  using SL = Slab<B, B>;
+  constexpr int B3 = B * B * B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);
+  __shared__ double red[4 * 32];
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  SimState& st = g.ss[s];
+  const bool skip = MIXED ? (st.outer_done != 0) : false;
+  double acc4[4] = {0, 0, 0, 0};  // bb, rr64, rz, rr (inner, mixed)
+  if (!skip) {
+    stage_slab<B, B, NT>(S, g, c, 0, FieldVal<double>{x, B3}, PressureBC{&sp});
+    __syncthreads();
+    const double hd = cell_h<B>(g, c), V = hd * hd * hd, mean = st.bmean;
+    float rz32 = 0.f, rr32 = 0.f;
+    for (int q = threadIdx.x; q < B3; q += NT) {
+      const int k = q / (B * B), rem = q - k * B * B, j = rem / B, i = rem - j * B;
+      const int o = SL::at(i, j, k + 1);
+      const double pc = S[o];
+      const double acc = (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) +
+                         (pc - S[o + SL::P]) + (pc - S[o - SL::P * SL::P]) +
+                         (pc - S[o + SL::P * SL::P]);
+      const size_t gi = (size_t)c * B3 + q;
+      const double rhs = -V * (b[gi] - mean);
+      const double rv = rhs - hd * acc;
+      acc4[0] += rhs * rhs;
+      if (MIXED) {
+        const float r32 = float(rv);
+        r[gi] = TV(r32);
+        e[gi] = 0.f;
+        const float z32 = r32 * float(inv_diag<B>(g, c, q));
+        rz32 += r32 * z32;
+        rr32 += r32 * r32;
+        acc4[1] += rv * rv;
+      } else {
+        r[gi] = TV(rv);
+        const double z = rv * inv_diag<B>(g, c, q);
+        acc4[2] += rv * z;
+        acc4[3] += rv * rv;
+      }
+    }
+    if (MIXED) {
+      acc4[2] = rz32;
+      acc4[3] = rr32;
+    }
+  }
+  block_sum<NT, 4>(acc4, red);
+  if (threadIdx.x == 0 && !skip) {
+    atomicAdd(&st.acc[ACC_BB], acc4[0]);
+    if (MIXED) atomicAdd(&st.acc[ACC_RR64], acc4[1]);
+    atomicAdd(&st.acc[ACC_RZ], acc4[2]);
+    atomicAdd(&st.acc[ACC_RR], acc4[3]);
+  }
+  if (last_block(g.counter)) {
+    int alive = 0;
+    for (int q = threadIdx.x; q < g.n_sims; q += NT) {
+      SimState& t = g.ss[q];
+      const double bb = ld_acc(&t.acc[ACC_BB]), rr64 = ld_acc(&t.acc[ACC_RR64]);
+      const double rz = ld_acc(&t.acc[ACC_RZ]), rr = ld_acc(&t.acc[ACC_RR]);
+      t.acc[ACC_BB] = t.acc[ACC_RR64] = t.acc[ACC_RZ] = t.acc[ACC_RR] = 0.0;
+      if (MIXED && t.outer_done) continue;
+      if (MIXED) {
+        t.cycles += 1;
+        if (t.cycles == 1) {
+          t.bb = bb;
+          t.tol2 = prm.rtol * prm.rtol * bb;
+          t.zero_rhs = (bb == 0.0);
+        }
+        t.rr64 = rr64;
+        const bool ok = t.zero_rhs || rr64 <= t.tol2;
+        if (!isfinite(rr64)) t.nonfinite = 1;
+        if (ok || t.cycles > prm.max_cycles || t.nonfinite) {
+          t.outer_done = 1;
+          t.done = 1;
+          t.converged = ok;
+        } else {
+          t.rz = rz;
+          t.rr = rr;
+          t.inner_tol2 = prm.inner_rtol * prm.inner_rtol * rr;
+          t.iter = 0;
+          t.beta = 0.0;
+          t.done = (rr == 0.0);
+          alive |= !t.done;
+        }
+      } else {
+        t.bb = bb;
+        t.tol2 = prm.rtol * prm.rtol * bb;
+        t.zero_rhs = (bb == 0.0);
+        t.rz = rz;
+        t.rr = rr;
+        t.rr64 = rr;
+        t.iter = 0;
+        t.total_iters = 0;
+        t.beta = 0.0;
+        if (!isfinite(rr)) t.nonfinite = 1;
+        t.done = t.zero_rhs || rr <= t.tol2 || t.nonfinite;
+        t.converged = t.zero_rhs || rr <= t.tol2;
+        alive |= !t.done;
+      }
+    }
+    int outer_alive = 0;
+    if (MIXED)
+      for (int q = threadIdx.x; q < g.n_sims; q += NT) outer_alive |= !g.ss[q].outer_done;
+    alive = __syncthreads_or(alive);
+    outer_alive = __syncthreads_or(outer_alive);
+    if (threadIdx.x == 0) {
+      *g.counter = 0;
+      g.flags[0] = !alive;
+      g.flags[1] = MIXED ? !outer_alive : 1;
+      set_cond(prm.cond_inner, alive ? 1u : 0u);
+      if (MIXED) set_cond(prm.cond_outer, outer_alive ? 1u : 0u);
+    }
+  }
+}
+
+// ===========================================================================
+// (a9) PCG pass A:  p_new = z + beta p_old (z = r / diag, staged with halo),
+//                   q = K p_new,  <p_new, q>;  then alpha = rz / <p, q> per sim.
+// ===========================================================================
+template <int B, int NT, class TV>
+__global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r,
+                                             TV* __restrict__ p0, TV* __restrict__ p1,
+                                             TV* __restrict__ q, SolveParams prm) {
+  using SL = Slab<B, B>;
+  constexpr int B3 = B * B * B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* S = reinterpret_cast<TV*>(smem_raw);
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  SimState& st = g.ss[s];
+  double pq = 0.0;
+  if (!st.done) {
+    const int it = st.iter;
+    const TV* pold = (it & 1) ? p1 : p0;
+    TV* pnew = (it & 1) ? p0 : p1;
+    const TV beta = TV(st.beta);
+    const bool first = (it == 0);
+    struct PVal {
+      const DevGrid* g;
+      const TV* r;
+      const TV* po;
+      TV beta;
+      bool first;
+      __device__ __forceinline__ TV operator()(int cc, int cell) const {
+        const size_t gi = (size_t)cc * B3 + cell;
+        const TV z = r[gi] * TV(inv_diag<B>(*g, cc, cell));
+        return first ? z : z + beta * po[gi];
+      }
+    } val{&g, r, pold, beta, first};
+    stage_slab<B, B, NT>(S, g, c, 0, val, PressureBC{&sp});
+    __syncthreads();
+    const TV h = TV(cell_h<B>(g, c));
+    TV part = TV(0);
+    for (int qq = threadIdx.x; qq < B3; qq += NT) {
+      const int k = qq / (B * B), rem = qq - k * B * B, j = rem / B, i = rem - j * B;
+      const int o = SL::at(i, j, k + 1);
+      const TV pc = S[o];
+      const TV acc = (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) +
+                     (pc - S[o + SL::P]) + (pc - S[o - SL::P * SL::P]) +
+                     (pc - S[o + SL::P * SL::P]);
+      const TV qv = h * acc;
+      const size_t gi = (size_t)c * B3 + qq;
+      pnew[gi] = pc;
+      q[gi] = qv;
+      part += pc * qv;
+    }
+    pq = double(part);
+  }
+  double vals[1] = {pq};
+  block_sum<NT, 1>(vals, red);
+  if (threadIdx.x == 0 && !st.done) atomicAdd(&st.acc[ACC_PQ], vals[0]);
+  if (last_block(g.counter)) {
+    for (int qq = threadIdx.x; qq < g.n_sims; qq += NT) {
+      SimState& t = g.ss[qq];
+      const double pqs = ld_acc(&t.acc[ACC_PQ]);
+      t.acc[ACC_PQ] = 0.0;
+      if (t.done) continue;
+      t.alpha = (pqs != 0.0) ? t.rz / pqs : 0.0;
+      if (!isfinite(pqs)) {
+        t.nonfinite = 1;
+        t.alpha = 0.0;
+      }
+    }
+    if (threadIdx.x == 0) *g.counter = 0;
+  }
+}
+
+// ===========================================================================
+// (a9) PCG pass B:  x += alpha p,  r -= alpha q,  z = r / diag,  <r,z>, <r,r>;
+// then beta, convergence test and loop control per sim.
+// ===========================================================================
+template <int B, int NT, class TV, class TX>
+__global__ __launch_bounds__(NT) void k_cg_b(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
+                                             const TV* __restrict__ p0,
+                                             const TV* __restrict__ p1,
+                                             const TV* __restrict__ q, SolveParams prm) {
+  constexpr int B3 = B * B * B;
+  __shared__ double red[2 * 32];
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  SimState& st = g.ss[s];
+  double vals[2] = {0.0, 0.0};
+  const bool active = !st.done && !st.nonfinite;
+  if (active) {
+    const TV* pn = (st.iter & 1) ? p0 : p1;
+    const TV alpha = TV(st.alpha);
+    TV rz = TV(0), rr = TV(0);
+    for (int qq = threadIdx.x; qq < B3; qq += NT) {
+      const size_t gi = (size_t)c * B3 + qq;
+      const TV pv = pn[gi];
+      x[gi] = TX(x[gi] + alpha * pv);
+      const TV rv = r[gi] - alpha * q[gi];
+      r[gi] = rv;
+      const TV z = rv * TV(inv_diag<B>(g, c, qq));
+      rz += rv * z;
+      rr += rv * rv;
+    }
+    vals[0] = double(rz);
+    vals[1] = double(rr);
+  }
+  block_sum<NT, 2>(vals, red);
+  if (threadIdx.x == 0 && active) {
+    atomicAdd(&st.acc[ACC_RZ], vals[0]);
+    atomicAdd(&st.acc[ACC_RR], vals[1]);
+  }
+  if (last_block(g.counter)) {
+    int alive = 0;
+    for (int qq = threadIdx.x; qq < g.n_sims; qq += NT) {
+      SimState& t = g.ss[qq];
+      const double rz = ld_acc(&t.acc[ACC_RZ]), rr = ld_acc(&t.acc[ACC_RR]);
+      t.acc[ACC_RZ] = t.acc[ACC_RR] = 0.0;
+      if (t.done) continue;
+      if (t.nonfinite || !isfinite(rr)) {
+        t.nonfinite = 1;
+        t.done = 1;
+        continue;
+      }
+      t.beta = (t.rz != 0.0) ? rz / t.rz : 0.0;
+      t.rz = rz;
+      t.rr = rr;
+      t.iter += 1;
+      t.total_iters += 1;
+      const bool inner = prm.mixed != 0;
+      const double tol2 = inner ? t.inner_tol2 : t.tol2;
+      const bool ok = rr <= tol2;
+      if (!inner) {
+        t.rr64 = rr;
+        t.converged = ok;
+      }
+      if (ok || t.iter >= (inner ? prm.inner_max_iter : prm.max_iter)) t.done = 1;
+      alive |= !t.done;
+    }
+    alive = __syncthreads_or(alive);
+    if (threadIdx.x == 0) {
+      *g.counter = 0;
+      g.flags[0] = !alive;
+      set_cond(prm.cond_inner, alive ? 1u : 0u);
+    }
+  }
+  // independent guard on the graph loop: a bounded number of body executions
+  if (prm.cond_inner && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned int n = atomicAdd(prm.guard, 1u) + 1u;
+    if (n >= (unsigned int)prm.guard_limit) cudaGraphSetConditional(
+        (cudaGraphConditionalHandle)prm.cond_inner, 0u);
+  }
+}
+
+// Mixed mode: x64 += e32 after an inner solve (sims still correcting).
+template <int B, int NT>
+__global__ __launch_bounds__(NT) void k_add_correction(DevGrid g, double* __restrict__ x,
+                                                       const float* __restrict__ e) {
+  constexpr int B3 = B * B * B;
+  const int c = blockIdx.x;
+  if (g.ss[g.sim[c]].outer_done) return;
+  for (int q = threadIdx.x; q < B3; q += NT) {
+    const size_t gi = (size_t)c * B3 + q;
+    x[gi] += double(e[gi]);
+  }
+}
+
+// ===========================================================================
+// (a11) projection: u = u* - dt * (mean of the two face gradients of p) (R1, R2),
+// plus the FP64 divergence check ||b - A p|| / ||b|| = ||D U^{n+1}|| / ||D U*||
+// and max |u|.
+// ===========================================================================
+template <int B, int NT, class T>
+__global__ __launch_bounds__(NT) void k_correct(DevGrid g, double* __restrict__ p,
+                                                const double* __restrict__ b,
+                                                const T* __restrict__ us,
+                                                const T* __restrict__ vs,
+                                                const T* __restrict__ ws, T* __restrict__ u,
+                                                T* __restrict__ v, T* __restrict__ w) {
+  using SL = Slab<B, B>;
+  constexpr int B3 = B * B * B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);
+  __shared__ double red[2 * 32];
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  SimState& st = g.ss[s];
+  const bool zero = st.zero_rhs != 0;
+  struct PV {
+    const double* p;
+    bool zero;
+    __device__ __forceinline__ double operator()(int cc, int cell) const {
+      return zero ? 0.0 : p[(size_t)cc * B3 + cell];
+    }
+  } val{p, zero};
+  stage_slab<B, B, NT>(S, g, c, 0, val, PressureBC{&sp});
+  __syncthreads();
+  const double hd = cell_h<B>(g, c);
+  const double ih = 1.0 / hd, ih2 = ih * ih;
+  const T cdt = T(0.5 * sp.dt);
+  const T* stars[3] = {us, vs, ws};
+  T* outs[3] = {u, v, w};
+  double dn = 0.0, dd = 0.0;
+  float umax = 0.f;
+  for (int q = threadIdx.x; q < B3; q += NT) {
+    const int k = q / (B * B), rem = q - k * B * B, j = rem / B, i = rem - j * B;
+    const int o = SL::at(i, j, k + 1);
+    const int off[3] = {1, SL::P, SL::P * SL::P};
+    const size_t gi = (size_t)c * B3 + q;
+    const double pc = S[o];
+    double lap = 0.0;
+    double m2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double dm = pc - S[o - off[d]], dp = S[o + off[d]] - pc;
+      lap += dp - dm;
+      const T grad = T((dm + dp) * ih);  // (gm + gp) with gm, gp the face gradients
+      const T nv = stars[d][gi] - cdt * grad;
+      outs[d][gi] = nv;
+      m2 += double(nv) * double(nv);
+    }
+    if (zero) p[gi] = 0.0;
+    const double bv = b[gi];
+    const double res = bv - lap * ih2;  // b - A p
+    dn += res * res;
+    dd += bv * bv;
+    umax = fmaxf(umax, float(sqrt(m2)));
+  }
+  double vals[2] = {dn, dd};
+  block_sum<NT, 2>(vals, red);
+  // max |u|
+  float um = umax;
+  for (int o2 = 16; o2 > 0; o2 >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o2));
+  if ((threadIdx.x & 31) == 0) atomic_max_pos(&st.umax_bits, double(um));
+  if (threadIdx.x == 0) {
+    atomicAdd(&st.acc[ACC_DIVN], vals[0]);
+    atomicAdd(&st.acc[ACC_DIVD], vals[1]);
+  }
+}
+
+// Step bookkeeping: drag, divergence ratio, time step counter.
+__global__ void k_step_end(DevGrid g) {
+  for (int s = threadIdx.x; s < g.n_sims; s += blockDim.x) {
+    SimState& t = g.ss[s];
+    for (int e = 0; e < 3; ++e) {
+      t.drag[e] = t.drag_acc[e];
+      t.drag_acc[e] = 0.0;
+    }
+    const double dn = t.acc[ACC_DIVN], dd = t.acc[ACC_DIVD];
+    t.div_num = dn;
+    t.div_den = dd;
+    t.acc[ACC_DIVN] = t.acc[ACC_DIVD] = 0.0;
+    t.step += 1;
+  }
+}
+
+// Volume mean of b per all-Neumann sim (standalone pressure solves).
+template <int B, int NT>
+__global__ __launch_bounds__(NT) void k_bmean(DevGrid g, const double* __restrict__ b) {
+  constexpr int B3 = B * B * B;
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < B3; q += NT) acc += b[(size_t)c * B3 + q];
+  double vals[1] = {acc};
+  block_sum<NT, 1>(vals, red);
+  if (threadIdx.x == 0 && g.sp[s].all_neumann) atomicAdd(&g.ss[s].acc[ACC_BSUM], vals[0]);
+  if (last_block(g.counter)) {
+    for (int q = threadIdx.x; q < g.n_sims; q += NT) {
+      SimState& st = g.ss[q];
+      st.bmean = g.sp[q].all_neumann ? ld_acc(&st.acc[ACC_BSUM]) / g.sp[q].n_cells : 0.0;
+      st.acc[ACC_BSUM] = 0.0;
+    }
+    if (threadIdx.x == 0) *g.counter = 0;
+  }
+}
+
+// Reset per-solve state before a pressure solve; zero the graph-loop guard.
+__global__ void k_solve_begin(DevGrid g, unsigned int* guard) {
+  for (int s = threadIdx.x; s < g.n_sims; s += blockDim.x) {
+    SimState& t = g.ss[s];
+    t.iter = 0;
+    t.done = 0;
+    t.outer_done = 0;
+    t.cycles = 0;
+    t.total_iters = 0;
+    t.converged = 0;
+    t.nonfinite = 0;
+    t.zero_rhs = 0;
+    t.umax_bits = 0ull;
+  }
+  if (threadIdx.x == 0) guard[0] = 0u;
+}
+
+// ===========================================================================
+// Test-path kernels: the paper's two-layer halo fill and y = K x.
+// ===========================================================================
+template <int B, int NT, class T>
+__global__ __launch_bounds__(NT) void k_fill_halo(DevGrid g, const T* __restrict__ f, int kind,
+                                                  const T* __restrict__ ub,
+                                                  double* __restrict__ out) {
+  constexpr int B3 = B * B * B, G = B + 4;
+  const int c = blockIdx.x;
+  const SimParams& sp = g.sp[g.sim[c]];
+  double* o = out + (size_t)c * G * G * G;
+  struct DV {
+    const T* f;
+    __device__ __forceinline__ double operator()(int cc, int cell) const {
+      return double(f[(size_t)cc * B3 + cell]);
+    }
+  } val{f};
+  for (int q = threadIdx.x; q < G * G * G; q += NT) {
+    const int i = q % G - 2, j = (q / G) % G - 2, k = q / (G * G) - 2;
+    const int out_i = (i < 0 || i >= B), out_j = (j < 0 || j >= B), out_k = (k < 0 || k >= B);
+    double vv = 0.0;
+    if (!out_i && !out_j && !out_k) {
+      vv = val(c, (k * B + j) * B + i);
+    } else if (out_i + out_j + out_k == 1) {
+      int f2, a, bb, layer;
+      if (out_i) { f2 = i < 0 ? 0 : 1; layer = i < 0 ? -1 - i : i - B; a = j; bb = k; }
+      else if (out_j) { f2 = j < 0 ? 2 : 3; layer = j < 0 ? -1 - j : j - B; a = i; bb = k; }
+      else { f2 = k < 0 ? 4 : 5; layer = k < 0 ? -1 - k : k - B; a = i; bb = j; }
+      if (kind == 3) {
+        vv = halo_value<B, double>(g, c, f2, a, bb, layer, val, PressureBC{&sp});
+      } else {
+        struct VB {
+          const DevGrid* g;
+          const SimParams* sp;
+          const T* ub;
+          int c, comp;
+          __device__ double operator()(int fc, int a2, int b2, double u0) const {
+            const int bc = sp->bc[fc];
+            if (bc == BC_SLIP) return (comp == (fc >> 1)) ? -u0 : u0;
+            if (bc == BC_OUTFLOW)
+              return 2.0 * double(ub[((size_t)(g->slot[6 * c + fc] * 3 + comp) * B + b2) * B + a2]) - u0;
+            return 2.0 * face_velocity<B>(*g, c, fc, comp, a2, b2) - u0;
+          }
+        } vb{&g, &sp, ub, c, kind};
+        vv = halo_value<B, double>(g, c, f2, a, bb, layer, val, vb);
+      }
+    }
+    o[q] = vv;
+  }
+}
+
+template <int B, int NT>
+__global__ __launch_bounds__(NT) void k_apply_poisson(DevGrid g, const double* __restrict__ x,
+                                                      double* __restrict__ y) {
+  using SL = Slab<B, B>;
+  constexpr int B3 = B * B * B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);
+  const int c = blockIdx.x;
+  const SimParams& sp = g.sp[g.sim[c]];
+  stage_slab<B, B, NT>(S, g, c, 0, FieldVal<double>{x, B3}, PressureBC{&sp});
+  __syncthreads();
+  const double h = cell_h<B>(g, c);
+  for (int q = threadIdx.x; q < B3; q += NT) {
+    const int k = q / (B * B), rem = q - k * B * B, j = rem / B, i = rem - j * B;
+    const int o = SL::at(i, j, k + 1);
+    const double pc = S[o];
+    const double acc = (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) +
+                       (pc - S[o + SL::P]) + (pc - S[o - SL::P * SL::P]) +
+                       (pc - S[o + SL::P * SL::P]);
+    y[(size_t)c * B3 + q] = h * acc;
+  }
+}
+
+// ===========================================================================
+// Launchers
+// ===========================================================================
+
+template <int B>
+constexpr int threads_for() { return B == 16 ? 256 : (B == 8 ? 128 : 64); }
+// z-slab depth of the three-field kernels (shared memory 3 (KS+2)(B+2)^2 values)
+template <int B, class T>
+constexpr int slab3() { return B == 16 ? (sizeof(T) == 8 ? 4 : 8) : B; }
+
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define BCM_DISPATCH_B(Bv, ...)                      \
+  switch (Bv) {                                      \
+    case 4: { constexpr int B = 4; __VA_ARGS__; break; }   \
+    case 8: { constexpr int B = 8; __VA_ARGS__; break; }   \
+    case 16: { constexpr int B = 16; __VA_ARGS__; break; } \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+template <class T>
+static cudaError_t solid_fraction_t(const Ctx& x, int sim_filter) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    k_solid_fraction<B, NT, T><<<x.g.n_cubes, NT, 0, x.stream>>>(
+        x.g, (T*)x.f.phi, x.f.bid, x.f.near, sim_filter);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_solid_fraction(const Ctx& x, int sim_filter) {
+  return x.f64 ? solid_fraction_t<double>(x, sim_filter) : solid_fraction_t<float>(x, sim_filter);
+}
+
+template <class T>
+static cudaError_t momentum_t(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>(), KS = slab3<B, T>();
+    const size_t sm = 3 * sizeof(T) * Slab<B, KS>::N;
+    auto kern = k_momentum<B, KS, NT, T>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(
+        x.g, (const T*)x.f.u, (const T*)x.f.v, (const T*)x.f.w, (T*)x.f.us, (T*)x.f.vs,
+        (T*)x.f.ws, (T*)x.f.nx, (T*)x.f.ny, (T*)x.f.nz, (const T*)x.f.phi, x.f.bid,
+        (T*)x.f.ub);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_momentum(const Ctx& x) {
+  return x.f64 ? momentum_t<double>(x) : momentum_t<float>(x);
+}
+
+template <class T>
+static cudaError_t rhs_t(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>(), KS = slab3<B, T>();
+    const size_t sm = 3 * sizeof(T) * Slab<B, KS>::N;
+    auto kern = k_rhs<B, KS, NT, T>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(x.g, (const T*)x.f.us, (const T*)x.f.vs,
+                                                      (const T*)x.f.ws, (const T*)x.f.ub, x.f.b);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_rhs(const Ctx& x) { return x.f64 ? rhs_t<double>(x) : rhs_t<float>(x); }
+
+cudaError_t launch_bmean(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    k_bmean<B, NT><<<x.g.n_cubes, NT, 0, x.stream>>>(x.g, x.f.b);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_begin(const Ctx& x) {
+  k_solve_begin<<<1, 128, 0, x.stream>>>(x.g, x.f.guard);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Ctx& x, const SolveParams& prm) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    const size_t sm = sizeof(double) * Slab<B, B>::N;
+    if (x.f64) {
+      auto kern = k_residual<B, NT, double, false>;
+      cudaError_t e = allow_smem(kern, sm);
+      if (e != cudaSuccess) return e;
+      kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, x.f.b, x.f.p, (double*)x.f.r, nullptr, prm);
+    } else {
+      auto kern = k_residual<B, NT, float, true>;
+      cudaError_t e = allow_smem(kern, sm);
+      if (e != cudaSuccess) return e;
+      kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, x.f.b, x.f.p, (float*)x.f.r, x.f.e, prm);
+    }
+  });
+  return cudaGetLastError();
+}
+
+template <class TV>
+static cudaError_t cg_a_t(const Ctx& x, const SolveParams& prm) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    const size_t sm = sizeof(TV) * Slab<B, B>::N;
+    auto ka = k_cg_a<B, NT, TV>;
+    cudaError_t e = allow_smem(ka, sm);
+    if (e != cudaSuccess) return e;
+    ka<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, (const TV*)x.f.r, (TV*)x.f.p0, (TV*)x.f.p1,
+                                          (TV*)x.f.q, prm);
+  });
+  return cudaGetLastError();
+}
+template <class TV, class TX>
+static cudaError_t cg_b_t(const Ctx& x, const SolveParams& prm, TX* xv) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    k_cg_b<B, NT, TV, TX><<<x.g.n_cubes, NT, 0, x.stream>>>(
+        x.g, xv, (TV*)x.f.r, (const TV*)x.f.p0, (const TV*)x.f.p1, (const TV*)x.f.q, prm);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm) {
+  return x.f64 ? cg_a_t<double>(x, prm) : cg_a_t<float>(x, prm);
+}
+cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm) {
+  return x.f64 ? cg_b_t<double, double>(x, prm, x.f.p) : cg_b_t<float, float>(x, prm, x.f.e);
+}
+
+cudaError_t launch_add_correction(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    k_add_correction<B, NT><<<x.g.n_cubes, NT, 0, x.stream>>>(x.g, x.f.p, x.f.e);
+  });
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t correct_t(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    const size_t sm = sizeof(double) * Slab<B, B>::N;
+    auto kern = k_correct<B, NT, T>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, x.f.p, x.f.b, (const T*)x.f.us,
+                                            (const T*)x.f.vs, (const T*)x.f.ws, (T*)x.f.u,
+                                            (T*)x.f.v, (T*)x.f.w);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_correct(const Ctx& x) {
+  return x.f64 ? correct_t<double>(x) : correct_t<float>(x);
+}
+
+cudaError_t launch_step_end(const Ctx& x) {
+  k_step_end<<<1, 128, 0, x.stream>>>(x.g);
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t fill_halo_t(const Ctx& x, const void* f, int kind, double* out) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    k_fill_halo<B, NT, T><<<x.g.n_cubes, NT, 0, x.stream>>>(x.g, (const T*)f, kind,
+                                                            (const T*)x.f.ub, out);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_fill_halo(const Ctx& x, const void* f, int f64_field, int kind, double* out) {
+  return f64_field ? fill_halo_t<double>(x, f, kind, out) : fill_halo_t<float>(x, f, kind, out);
+}
+
+cudaError_t launch_apply_poisson(const Ctx& x, const double* in, double* out) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    const size_t sm = sizeof(double) * Slab<B, B>::N;
+    auto kern = k_apply_poisson<B, NT>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, in, out);
+  });
+  return cudaGetLastError();
+}
+
+}  // namespace bcm

@@ -1,0 +1,56 @@
+// bcm_kernels.h -- host-side launch interface of the BCM kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bcm_internal.cuh"
+
+namespace bcm {
+
+// Device pointers of every field and solver vector (all inside the workspace).
+struct Fields {
+  void *u, *v, *w, *us, *vs, *ws, *nx, *ny, *nz, *phi, *ub;  // state storage type
+  double *p, *b;                                              // FP64 always
+  unsigned char *bid, *near;
+  void *r, *p0, *p1, *q;  // PCG vectors: FP64 (plain) or FP32 (mixed inner)
+  float *e;               // mixed: inner iterate (correction of p)
+  unsigned int* guard;    // graph-loop body counter
+};
+
+struct SolveParams {
+  double rtol;            // outer (FP64) relative residual target
+  double inner_rtol;      // mixed: inner FP32 PCG relative reduction per cycle
+  int max_iter;           // FP64 mode: PCG iterations
+  int inner_max_iter;     // mixed: inner iterations per cycle
+  int max_cycles;         // mixed: defect-correction cycles
+  int mixed;
+  unsigned long long cond_inner, cond_outer;  // graph conditional handles (0 = none)
+  unsigned int* guard;
+  int guard_limit;
+  int pad;
+};
+
+struct Ctx {
+  DevGrid g;
+  Fields f;
+  int B;
+  int f64;  // state in FP64 (plain mode) or FP32 (mixed mode)
+  cudaStream_t stream;
+};
+
+cudaError_t launch_solid_fraction(const Ctx& x, int sim_filter);
+cudaError_t launch_momentum(const Ctx& x);
+cudaError_t launch_rhs(const Ctx& x);
+cudaError_t launch_bmean(const Ctx& x);
+cudaError_t launch_solve_begin(const Ctx& x);
+cudaError_t launch_residual(const Ctx& x, const SolveParams& prm);
+cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm);
+cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm);
+cudaError_t launch_add_correction(const Ctx& x);
+cudaError_t launch_correct(const Ctx& x);
+cudaError_t launch_step_end(const Ctx& x);
+cudaError_t launch_fill_halo(const Ctx& x, const void* f, int f64_field, int kind, double* out);
+cudaError_t launch_apply_poisson(const Ctx& x, const double* in, double* out);
+
+}  // namespace bcm

@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances (relative L2 per field): FP64 path 1e-10 (velocity vector, each velocity
+component and pressure), FP32 sweeps inside FP64 defect correction 1e-6 (velocity
+vector and pressure: FP32 storage rounds every component to ~6e-8 of |u|, which is
+far more than 1e-6 of a component that is itself small, e.g. the cross-flow
+components of a cavity).  Both sides solve the pressure Poisson
+equation to a tighter residual than the tolerance so that the solver stopping point
+does not dominate the comparison (two CG runs stopped at residual t differ by up
+to about cond(K) * t).  Halo fills are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1808_04099_gb300 import workloads as W
+from _util import demean_per_sim, oracle_run, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, skipped there
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1808_04099_gb300 import bcm  # noqa: E402
+
+TOL64 = 1e-10
+TOL32 = 1e-6
+
+
+def gpu_grid(spec, prec=bcm.PREC_F64, state=None):
+    g = bcm.Grid(spec, prec)
+    if state is not None:
+        g.load_state(state)
+    return g
+
+
+def compare_fields(g, st, spec, tol, per_component=True):
+    """Relative L2 error of the velocity field (as a vector) and of the pressure
+    (mean removed in all-Neumann sims); with per_component also of u, v, w alone."""
+    vel = np.concatenate([g.numpy(f) for f in (bcm.U, bcm.V, bcm.W)])
+    ref = np.concatenate([st[k] for k in ("u", "v", "w")])
+    out = {"velocity": rel_l2(vel, ref),
+           "p": rel_l2(demean_per_sim(g.numpy(bcm.P), spec), demean_per_sim(st["p"], spec))}
+    if per_component:
+        for name, fid in (("u", bcm.U), ("v", bcm.V), ("w", bcm.W)):
+            out[name] = rel_l2(g.numpy(fid), st[name])
+    for k, v in out.items():
+        assert v <= tol, (k, v, out)
+    return out
+
+
+HALO_SPECS = {
+    "periodic": lambda: W.periodic_box(3, 4),
+    "cavity": lambda: W.cavity(2, 8),
+    "channel": lambda: W.sphere_channel(4, 2, 2, 8),
+    "two_level": lambda: W.two_level_channel(4, 2, 2, 8, (1, 0, 0), (3, 2, 2), 1 / 16., 0),
+    "B16": lambda: W.sphere_channel(2, 1, 1, 16, length=(2.0, 1.0, 1.0)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(HALO_SPECS))
+def test_halo_fill_bitwise(name):
+    spec = HALO_SPECS[name]()
+    rng = np.random.default_rng(7)
+    g = gpu_grid(spec)
+    o = O.Oracle(spec)
+    ub = rng.standard_normal(g.field(bcm.UB).numel())
+    g.field(bcm.UB).copy_(torch.from_numpy(ub))
+    G = spec.B + 4
+    for kind, fid in ((0, bcm.U), (1, bcm.V), (2, bcm.W), (3, bcm.P)):
+        f = rng.standard_normal(spec.n_cells)
+        g.field(fid).copy_(torch.from_numpy(f))
+        got = g.fill_halo(fid, kind).cpu().numpy().reshape(spec.n_cubes, G, G, G)
+        want = o.fill_ghosts(f, kind, ub.reshape(-1, 3, spec.B, spec.B) if ub.size else None)
+        assert np.array_equal(got, want), (name, kind, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize("name", ["periodic", "cavity", "channel", "B16"])
+def test_poisson_operator(name):
+    spec = HALO_SPECS[name]()
+    x = np.random.default_rng(8).standard_normal(spec.n_cells)
+    g = gpu_grid(spec)
+    y = g.apply_poisson(torch.from_numpy(x)).cpu().numpy()
+    assert rel_l2(y, O.Oracle(spec).apply_poisson(x)) < 1e-14
+
+
+@pytest.mark.parametrize("name", ["cavity", "channel", "B16"])
+def test_pressure_solve(name):
+    spec = HALO_SPECS[name]()
+    b = np.random.default_rng(9).standard_normal(spec.n_cells)
+    g = gpu_grid(spec)
+    g.field(bcm.RHS).copy_(torch.from_numpy(b))
+    st = g.solve_pressure(1e-13)
+    assert st[0]["converged"] == 1 and st[0]["rel_resid"] <= 1e-13
+    p_ref, ost, rc = O.Oracle(spec).solve_pressure(b, rtol=1e-13)
+    p = g.numpy(bcm.P)
+    assert rel_l2(demean_per_sim(p, spec), demean_per_sim(p_ref, spec)) < 1e-11
+    assert abs(st[0]["cg_iters"] - ost[0]["cg_iters"]) <= 2
+
+
+STEP_CASES = {
+    "cavity_B8": (lambda: W.cavity(2, 8), 1e-3, 4),
+    "cavity_B16": (lambda: W.cavity(2, 16), 1e-3, 3),
+    "sphere_B8": (lambda: W.sphere_channel(4, 2, 2, 8, radius=0.3), 0.0, 4),
+    "periodic_B4": (lambda: W.periodic_box(3, 4), 0.3, 3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STEP_CASES))
+def test_step_fp64(name):
+    mk, noise, steps = STEP_CASES[name]
+    spec = mk()
+    state = W.initial_state(spec, seed=11, noise=noise)
+    ost, ostats = oracle_run(spec, state, steps, 1e-13)
+    g = gpu_grid(spec, bcm.PREC_F64, state)
+    gst = g.step(steps, rtol=1e-13)
+    compare_fields(g, ost, spec, TOL64)
+    s, r = gst[0], ostats[0]
+    assert s["steps"] == steps and s["converged"] == 1
+    assert abs(s["div_rel"] - r["div_rel"]) <= 1e-12 + 1e-3 * r["div_rel"]
+    for e in range(3):
+        assert abs(s["drag"][e] - r["drag"][e]) <= 1e-9 * (abs(r["drag"][0]) + 1e-30)
+    assert abs(s["umax"] - r["umax"]) <= 1e-7 * r["umax"]
+
+
+@pytest.mark.parametrize("name", ["cavity_B8", "sphere_B8", "cavity_B16"])
+def test_step_mixed(name):
+    mk, noise, steps = STEP_CASES[name]
+    spec = mk()
+    state = W.initial_state(spec, seed=12, noise=noise)
+    ost, ostats = oracle_run(spec, state, steps, 1e-13)
+    g = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
+    gst = g.step(steps, rtol=1e-12)
+    assert gst[0]["converged"] == 1 and gst[0]["refine_cycles"] >= 1
+    compare_fields(g, ost, spec, TOL32, per_component=False)
+
+
+def test_batched_ragged_sims():
+    """Several sims of different sizes and kinds in one flattened cube list."""
+    specs = [W.cavity(2, 8, re=400.0), W.sphere_channel(4, 2, 2, 8, radius=0.3),
+             W.cavity(3, 4, re=150.0), W.sphere_channel(2, 1, 1, 8, length=(2.0, 1.0, 1.0),
+                                                        radius=0.2, center=(0.6, 0.5, 0.5))]
+    spec = W.concat(specs)
+    state = W.initial_state(spec, seed=13, noise=1e-3)
+    ost, ostats = oracle_run(spec, state, 3, 1e-13)
+    g = gpu_grid(spec, bcm.PREC_F64, state)
+    gst = g.step(3, rtol=1e-13)
+    compare_fields(g, ost, spec, TOL64)
+    for s in range(spec.n_sims):
+        assert gst[s]["converged"] == 1
+        assert abs(gst[s]["cg_iters"] - ostats[s]["cg_iters"]) <= 3
+
+
+def test_rotating_ellipsoids():
+    spec = W.sphere_channel(4, 2, 2, 8)
+    rng = np.random.default_rng(3)
+    bodies = []
+    for k in range(3):
+        q = rng.normal(size=4)
+        bodies.append(W.Body(W.BODY_ELLIPSOID, np.array([0.7 + 0.6 * k, 1.0, 1.0]),
+                             rng.uniform(0.1, 0.25, 3), q / np.linalg.norm(q),
+                             rng.normal(size=3), np.array([0.05, 0, 0])))
+    spec.bodies = [bodies]
+    state = W.initial_state(spec, seed=14)
+    ost, ostats = oracle_run(spec, state, 3, 1e-13)
+    g = gpu_grid(spec, bcm.PREC_F64, state)
+    gst = g.step(3, rtol=1e-13)
+    compare_fields(g, ost, spec, TOL64)
+    for e in range(3):
+        assert abs(gst[0]["drag"][e] - ostats[0]["drag"][e]) <= 1e-8 * abs(ostats[0]["drag"][0])
+    phi_o = O.Oracle(spec).solid_fraction([3 * spec.sim_dt[0]])[0]
+    assert rel_l2(g.numpy(bcm.PHI), phi_o) < 1e-12
+
+
+def test_inflow_modes():
+    modes = np.array([0.1, -0.05, 0.02, 0.0, 0.03, -0.01, 0.0, 0.04])
+    spec = W.sphere_channel(4, 2, 2, 8, modes=modes)
+    state = W.initial_state(spec, seed=15)
+    ost, _ = oracle_run(spec, state, 2, 1e-13)
+    g = gpu_grid(spec, bcm.PREC_F64, state)
+    g.step(2, rtol=1e-13)
+    compare_fields(g, ost, spec, TOL64)
+
+
+def test_not_converged_status():
+    spec = W.cavity(2, 8)
+    g = gpu_grid(spec, bcm.PREC_F64, W.initial_state(spec, 1, 1e-2))
+    with pytest.raises(bcm.BCMError) as ei:
+        g.step(1, rtol=1e-14, max_iter=3)
+    assert ei.value.status == bcm.BCM_E_NOT_CONVERGED
+    st = g.step(1, rtol=1e-14, max_iter=3, allow_not_converged=True)
+    assert st[0]["cg_iters"] == 3 and st[0]["converged"] == 0
+
+
+def test_nonfinite_detected():
+    spec = W.cavity(2, 8)
+    state = W.initial_state(spec, 1, 1e-2)
+    state.u[100] = np.nan
+    g = gpu_grid(spec, bcm.PREC_F64, state)
+    with pytest.raises(bcm.BCMError) as ei:
+        g.step(1, rtol=1e-10)
+    assert ei.value.status == bcm.BCM_E_NONFINITE
+
+
+def test_full_size_sphere_one_step_fp64():
+    """The sphere flow at its full size (16x8x8 cubes of 16^3, 4.19M cells) in the
+    launch configuration the benchmark times: one FP64 step against the oracle."""
+    spec = W.config_sphere(1)
+    state = W.initial_state(spec)
+    ost, ostats = oracle_run(spec, state, 1, 1e-11)
+    g = gpu_grid(spec, bcm.PREC_F64, state)
+    gst = g.step(1, rtol=1e-11)
+    res = compare_fields(g, ost, spec, 1e-8)
+    assert gst[0]["drag"][0] > 0
+    assert abs(gst[0]["drag"][0] - ostats[0]["drag"][0]) <= 1e-8 * ostats[0]["drag"][0]
+
+
+def test_full_size_sphere_mixed_properties():
+    """Mixed precision at full size, two steps at residual 1e-8: the FP64 residual
+    meets rtol, the corrected face velocities are as divergence free as the
+    residual says, and velocity stays within 1e-6 of the FP64 GPU path."""
+    spec = W.config_sphere(2)
+    state = W.initial_state(spec)
+    g32 = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
+    s32 = g32.step(2, rtol=1e-10)
+    g64 = gpu_grid(spec, bcm.PREC_F64, state)
+    s64 = g64.step(2, rtol=1e-10)
+    assert s32[0]["converged"] == 1 and s32[0]["rel_resid"] <= 1e-10
+    assert s32[0]["div_rel"] <= 1e-9
+    vel32 = np.concatenate([g32.numpy(f) for f in (bcm.U, bcm.V, bcm.W)])
+    vel64 = np.concatenate([g64.numpy(f) for f in (bcm.U, bcm.V, bcm.W)])
+    assert rel_l2(vel32, vel64) <= TOL32
+    assert rel_l2(g32.numpy(bcm.P), g64.numpy(bcm.P)) <= TOL32
