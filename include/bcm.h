@@ -45,7 +45,7 @@ typedef enum {
     BCM_E_CUDA = -2,          /* a CUDA runtime call failed (message has the code) */
     BCM_E_NOT_CONVERGED = -3, /* a pressure solve hit max_iter; fields stay valid */
     BCM_E_NONFINITE = -4,     /* NaN or Inf found in a residual */
-    BCM_E_TIMEOUT = -5,       /* reserved: a bounded device wait ran out */
+    BCM_E_TIMEOUT = -5,       /* a bounded device wait (grid barrier) ran out */
     BCM_E_BOUNDS = -6         /* a size exceeds a documented maximum */
 } bcm_status;
 
@@ -155,6 +155,21 @@ bcm_status bcm_reset_time(bcm_grid *grid);
  * stats: host array [n_sims] or NULL (then nothing is synchronised). */
 bcm_status bcm_step(bcm_grid *grid, int n_steps, double rtol, int max_iter, bcm_stats *stats);
 
+/* Solver controls (defaults in brackets): inner_rtol, the relative reduction of the
+ * FP32 inner PCG per defect-correction cycle in mixed mode [1e-5]; max_cycles, the
+ * cap on FP64 residual evaluations per solve [30]; check_every, PCG iterations
+ * between two reads of the device convergence flags by the host [8].  A value <= 0
+ * keeps the current setting. */
+bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int check_every);
+
+/* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
+ * whose blocks loop over the iterations with grid-wide barriers (default in mixed
+ * mode for grids of at most 256 sims); slabs_a = z-slabs per cube of its work items (1, 2 or 4;
+ * 16^3 cubes only for 2 and 4).  persistent = 0: two launches per iteration (the FP64
+ * default), one CTA per z-slab, slabs_a / slabs_b slabs per cube for pass A / pass B.  Results do
+ * not depend on the shape beyond the summation order of the dot products. */
+bcm_status bcm_set_launch(bcm_grid *grid, int persistent, int slabs_a, int slabs_b);
+
 /* Solve the pressure Poisson equation (Eq. poisson) for the current BCM_RHS into
  * BCM_P (warm start from BCM_P).  stats as in bcm_step. */
 bcm_status bcm_solve_pressure(bcm_grid *grid, double rtol, int max_iter, bcm_stats *stats);
@@ -182,7 +197,8 @@ enum {
     BCM_K_ADD_CORRECTION = 6, /* mixed: x += e */
     BCM_K_CORRECT = 7,        /* projection + FP64 divergence check */
     BCM_K_MISC = 8,           /* bookkeeping and test-path kernels */
-    BCM_NKERNELS = 9
+    BCM_K_PCG = 9,            /* persistent PCG: all iterations of one solve */
+    BCM_NKERNELS = 10
 };
 
 /* Timing of the library's own kernels: while enabled, every kernel the grid launches

@@ -1,0 +1,72 @@
+"""Launch-shape autotuner of the PCG: the persistent cooperative solver with 1, 2
+or 4 z-slabs per work item, or two launches per iteration with z-slabs per pass.
+
+Times a fixed number of PCG iterations on the grid's current right-hand side for
+every shape with the library's own CUDA-event kernel timing, restores the pressure,
+and keeps the fastest shape.  Results are cached in a JSON file keyed by device,
+cube size, precision and cube count.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import bcm
+
+# (persistent, slabs_a, slabs_b)
+SHAPES = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (0, 1, 1), (0, 1, 2), (0, 2, 2)]
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "bcm_gb300_launch.json")
+
+
+def _key(grid) -> str:
+    import torch
+    name = torch.cuda.get_device_name(grid.device)
+    return f"{name}|B{grid.spec.B}|prec{grid.precision}|cubes{grid.spec.n_cubes}"
+
+
+def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
+    """Pick and set the fastest (slabs_a, slabs_b); returns {shape: us per iteration}."""
+    key = _key(grid)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            with open(CACHE) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        pe, sa, sb = cache[key]["best"]
+        grid.set_launch(sa, sb, persistent=bool(pe))
+        return cache[key]["times"]
+    p = grid.field(bcm.P)
+    saved = p.clone()
+    times = {}
+    grid.set_solver(max_cycles=1)  # mixed mode: one inner solve per timing run
+    for pe, sa, sb in SHAPES:
+        if pe and sa > 1 and grid.spec.B != 16:
+            continue
+        grid.set_launch(sa, sb, persistent=bool(pe))
+        for rep in range(2):  # the first pass warms up the shape
+            p.copy_(saved)
+            grid.profile(True)
+            grid.solve_pressure_iters(iters)
+            prof, _ = grid.profile_read(reset=True)
+            grid.profile(False)
+        ta, na = prof["cg_a"]
+        tb, nb = prof["cg_b"]
+        tp, npc = prof["pcg"]
+        if pe and npc:
+            times[f"{pe},{sa},{sb}"] = 1e3 * tp / (npc * iters)
+        elif na and nb:
+            times[f"{pe},{sa},{sb}"] = 1e3 * (ta / na + tb / nb)
+    p.copy_(saved)
+    grid.set_solver(max_cycles=30)
+    best = min(times, key=times.get)
+    pe, sa, sb = map(int, best.split(","))
+    grid.set_launch(sa, sb, persistent=bool(pe))
+    if use_cache:
+        cache[key] = {"best": [pe, sa, sb], "times": times}
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return times

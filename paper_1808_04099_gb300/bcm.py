@@ -21,11 +21,11 @@ PREC_F64, PREC_F32_REFINE = 0, 1
 (U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
-            "bcm_set_geometry", "bcm_reset_time", "bcm_step", "bcm_solve_pressure",
+            "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch", "bcm_step", "bcm_solve_pressure",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_profile", "bcm_profile_read",
             "bcm_last_error"]
 KERNEL_NAMES = ["solid_fraction", "momentum", "rhs", "residual", "cg_a", "cg_b",
-                "add_correction", "correct", "misc"]
+                "add_correction", "correct", "misc", "pcg"]
 
 
 class GridDesc(C.Structure):
@@ -81,6 +81,8 @@ def lib(build: bool = True):
                                 C.POINTER(C.c_int32)]
         L.bcm_set_geometry.argtypes = [P, C.c_int, P, C.c_int, P]
         L.bcm_reset_time.argtypes = [P]
+        L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int]
+        L.bcm_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
         L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
         L.bcm_solve_pressure.argtypes = [P, C.c_double, C.c_int, P]
         L.bcm_fill_halo.argtypes = [P, C.c_int, C.c_int, P]
@@ -201,6 +203,12 @@ class Grid:
         _check(lib().bcm_set_geometry(self._h, sim, arr if bodies else None, len(bodies),
                                       m.ctypes.data if m is not None else None))
 
+    def set_solver(self, inner_rtol: float = 0.0, max_cycles: int = 0, check_every: int = 0):
+        _check(lib().bcm_set_solver(self._h, inner_rtol, max_cycles, check_every))
+
+    def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: bool = True):
+        _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
+
     def reset_time(self):
         _check(lib().bcm_reset_time(self._h))
 
@@ -226,6 +234,13 @@ class Grid:
         total = C.c_int64()
         _check(lib().bcm_profile_read(self._h, ms, n, C.byref(total), int(reset)))
         return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_NAMES)}, total.value
+
+    def solve_pressure_iters(self, iters: int):
+        """Run exactly `iters` PCG iterations on the current right-hand side (timing aid:
+        the tolerance is set out of reach, the not-converged status is expected)."""
+        st = (Stats * self.spec.n_sims)()
+        _check(lib().bcm_solve_pressure(self._h, 1e-300, iters, st), (BCM_E_NOT_CONVERGED,))
+        return [s.as_dict() for s in st]
 
     def fill_halo(self, fid: int, kind: int):
         import torch

@@ -49,13 +49,13 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t u, v, w, us, vs, ws, nx, ny, nz, phi, ub, p, b, bid, near_, r, p0, p1, q, e;
-  size_t nb, aux, sim, lvl, ijk, w3, slot, sp, ss, counter, flags, guard;
+  size_t nb, aux, sim, lvl, ijk, w3, nbw3, slot, sp, ss, counter, flags, guard, bar, err;
   size_t total;
   size_t n_slots;
 };
 
 struct HostTables {
-  std::vector<int> nb, aux, sim, lvl, ijk, w3, slot;
+  std::vector<int> nb, aux, sim, lvl, ijk, w3, nbw3, slot;
   std::vector<SimParams> sp;
   int n_slots = 0;
   int two_level = 0;
@@ -200,6 +200,13 @@ bcm_status build_tables(const bcm_grid_desc* d, HostTables& T) {
     }
   }
   T.n_slots = slots;
+  T.nbw3.assign(36 * (size_t)n, 3);
+  for (int c = 0; c < n; ++c)
+    for (int f = 0; f < 6; ++f) {
+      const int m = T.nb[6 * c + f];
+      if (m >= 0)
+        for (int e = 0; e < 6; ++e) T.nbw3[36 * c + 6 * f + e] = T.w3[6 * m + e];
+    }
   // per-sim constants
   T.sp.assign(d->n_sims, SimParams{});
   for (int s = 0; s < d->n_sims; ++s) {
@@ -258,12 +265,15 @@ Layout plan(const bcm_grid_desc* d, int n_slots) {
   L.lvl = take(sizeof(int) * d->n_cubes);
   L.ijk = take(3 * sizeof(int) * d->n_cubes);
   L.w3 = take(6 * sizeof(int) * d->n_cubes);
+  L.nbw3 = take(36 * sizeof(int) * d->n_cubes);
   L.slot = take(6 * sizeof(int) * d->n_cubes);
   L.sp = take(sizeof(SimParams) * d->n_sims);
   L.ss = take(sizeof(SimState) * d->n_sims);
-  L.counter = take(64);
+  L.counter = take(sizeof(unsigned int) * kTicketWords);
   L.flags = take(64);
   L.guard = take(64);
+  L.bar = take(sizeof(unsigned int) * (kTicketWords + 32));
+  L.err = take(64);
   L.total = off;
   L.n_slots = n_slots;
   return L;
@@ -282,6 +292,9 @@ struct KernelTimer {
 
 struct bcm_grid {
   bcm_grid_desc desc;
+  double inner_rtol = 1e-5;  // mixed: inner FP32 PCG reduction per cycle
+  int max_cycles = 30;       // mixed: FP64 residual evaluations per solve
+  int check_every = 8;       // host-driven loops: iterations between flag reads
   KernelTimer timer;
   long long launch_count = 0;
   HostTables T;
@@ -408,6 +421,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   UP(L.lvl, g->T.lvl.data(), sizeof(int) * n);
   UP(L.ijk, g->T.ijk.data(), sizeof(int) * 3 * n);
   UP(L.w3, g->T.w3.data(), sizeof(int) * 6 * n);
+  UP(L.nbw3, g->T.nbw3.data(), sizeof(int) * 36 * n);
   UP(L.slot, g->T.slot.data(), sizeof(int) * 6 * n);
   UP(L.sp, g->T.sp.data(), sizeof(SimParams) * desc->n_sims);
 #undef UP
@@ -418,6 +432,12 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   Ctx& x = g->ctx;
   x.B = g->B;
   x.f64 = g->f64;
+  x.slabs_a = 1;
+  x.slabs_b = 1;
+  x.slabs_p = (g->B == 16 && g->f64) ? 2 : 1;
+  // measured on GB300 at 4.2M cells: the persistent solver is on par in FP32 and
+  // slower in FP64 (ALU-bound passes), so FP64 defaults to two launches per iteration
+  x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
   x.stream = s;
   DevGrid& G = x.g;
   G.n_cubes = n;
@@ -430,6 +450,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   G.lvl = (const int*)(W + L.lvl);
   G.ijk = (const int*)(W + L.ijk);
   G.w3 = (const int*)(W + L.w3);
+  G.nbw3 = (const int*)(W + L.nbw3);
   G.slot = (const int*)(W + L.slot);
   G.near = (const unsigned char*)(W + L.near_);
   G.sp = (const SimParams*)(W + L.sp);
@@ -446,6 +467,8 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.r = W + L.r; F.p0 = W + L.p0; F.p1 = W + L.p1; F.q = W + L.q;
   F.e = g->f64 ? nullptr : (float*)(W + L.e);
   F.guard = (unsigned int*)(W + L.guard);
+  F.bar = (unsigned int*)(W + L.bar);
+  F.err = (int*)(W + L.err);
   *out = g;
   return BCM_OK;
 }
@@ -536,10 +559,6 @@ extern "C" bcm_status bcm_reset_time(bcm_grid* g) {
 namespace {
 
 
-constexpr int kCheckEvery = 8;       // host-driven loops: iterations between flag reads
-constexpr int kMaxCycles = 30;       // mixed: defect-correction cycles
-constexpr double kInnerRtol = 1e-3;  // mixed: inner FP32 PCG reduction per cycle
-
 bcm_status read_flags(bcm_grid* g, int flags[2]) {
   CUDA_TRY(cudaMemcpyAsync(flags, g->ws + g->L.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                            g->stream));
@@ -548,30 +567,63 @@ bcm_status read_flags(bcm_grid* g, int flags[2]) {
 }
 
 // Jacobi-PCG on K p = -V (b - mean), warm start p (Saad Alg. 9.1); FP64 vectors, or
-// FP32 inner PCG inside FP64 defect correction (mixed).  Loop control is read from
-// device flags every kCheckEvery iterations; finished sims skip their cubes.
+// FP32 inner PCG inside FP64 defect correction (mixed).  Persistent mode runs each
+// PCG solve as one cooperative launch; the two-launch mode reads the device
+// convergence flags every check_every iterations.  Finished sims skip their cubes.
+bcm_status read_err(bcm_grid* g) {
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, g->ws + g->L.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (err) {
+    CUDA_TRY(cudaMemsetAsync(g->ws + g->L.err, 0, sizeof(int), g->stream));
+    return fail(BCM_E_TIMEOUT, "a grid barrier of the persistent PCG timed out");
+  }
+  return BCM_OK;
+}
+
 bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   if (g->T.two_level)
     return fail(BCM_E_INVALID, "the flux-form 2:1 Poisson kernels are not available");
   Ctx& x = g->ctx;
   SolveParams prm{};
   prm.rtol = rtol;
-  prm.inner_rtol = kInnerRtol;
+  prm.inner_rtol = g->inner_rtol;
   prm.max_iter = max_iter;
   prm.inner_max_iter = max_iter;
-  prm.max_cycles = kMaxCycles;
+  prm.max_cycles = g->max_cycles;
   prm.mixed = g->f64 ? 0 : 1;
   prm.guard = x.f.guard;
   prm.guard_limit = 0;
+  prm.barrier_timeout_ns = 2000000000ull;
   RUN(BCM_K_MISC, launch_solve_begin(x));
   RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
   int flags[2] = {0, 0};
-  bcm_status st = read_flags(g, flags);
-  if (st != BCM_OK) return st;
+  bcm_status st;
+  if (x.persistent) {
+    if (g->f64) {
+      RUN(BCM_K_PCG, launch_pcg(x, prm));
+      return BCM_OK;
+    }
+    // defect correction: cycles are issued in batches; a finished sim makes every
+    // kernel of a later cycle return at once, so the host reads the flags rarely
+    int cycles = 0, batch = 2;
+    while (cycles < g->max_cycles) {
+      for (int b = 0; b < batch && cycles < g->max_cycles; ++b, ++cycles) {
+        RUN(BCM_K_PCG, launch_pcg(x, prm));
+        RUN(BCM_K_ADD_CORRECTION, launch_add_correction(x));
+        RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
+      }
+      if ((st = read_flags(g, flags)) != BCM_OK) return st;
+      if (flags[1]) break;
+      batch = 1;
+    }
+    return BCM_OK;
+  }
+  if ((st = read_flags(g, flags)) != BCM_OK) return st;
   if (g->f64) {
     int it = 0;
     while (!flags[0] && it < max_iter) {
-      for (int m = 0; m < kCheckEvery && it < max_iter; ++m, ++it)
+      for (int m = 0; m < g->check_every && it < max_iter; ++m, ++it)
       {
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
         RUN(BCM_K_CG_B, launch_cg_b(x, prm));
@@ -581,10 +633,10 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     return BCM_OK;
   }
   int cycles = 0;
-  while (!flags[1] && cycles <= kMaxCycles) {
+  while (!flags[1] && cycles <= g->max_cycles) {
     int it = 0;
     while (!flags[0] && it < max_iter) {
-      for (int m = 0; m < kCheckEvery && it < max_iter; ++m, ++it)
+      for (int m = 0; m < g->check_every && it < max_iter; ++m, ++it)
       {
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
         RUN(BCM_K_CG_B, launch_cg_b(x, prm));
@@ -600,6 +652,8 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
 }
 
 bcm_status collect(bcm_grid* g, bcm_stats* out) {
+  bcm_status est = read_err(g);
+  if (est != BCM_OK) return est;
   std::vector<SimState> ss(g->desc.n_sims);
   CUDA_TRY(cudaMemcpyAsync(ss.data(), g->ws + g->L.ss, sizeof(SimState) * ss.size(),
                            cudaMemcpyDeviceToHost, g->stream));
@@ -674,6 +728,37 @@ extern "C" bcm_status bcm_profile_read(bcm_grid* g, double* total_ms, int64_t* l
       g->timer.launches[k] = 0;
     }
     g->launch_count = 0;
+  }
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_set_solver(bcm_grid* g, double inner_rtol, int max_cycles,
+                                     int check_every) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (inner_rtol > 0) {
+    if (!(inner_rtol < 1.0)) return fail(BCM_E_INVALID, "inner_rtol must be < 1");
+    g->inner_rtol = inner_rtol;
+  }
+  if (max_cycles > 0) g->max_cycles = max_cycles;
+  if (check_every > 0) g->check_every = check_every;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, int slabs_b) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  auto ok = [&](int ns) { return ns == 1 || ns == 2 || ns == 4; };
+  if (!ok(slabs_a) || !ok(slabs_b)) return fail(BCM_E_INVALID, "slabs per cube must be 1, 2 or 4");
+  if (persistent && g->desc.n_sims > 256)
+    return fail(BCM_E_BOUNDS, "the persistent PCG handles at most 256 sims per grid");
+  if (g->B / slabs_a < 1 || g->B / slabs_b < 1 || (g->B * g->B / 4) * (g->B / slabs_b) < 1)
+    return fail(BCM_E_INVALID, "slab too thin for this cube size");
+  g->ctx.persistent = persistent ? 1 : 0;
+  if (persistent) {
+    if (g->B != 16 && slabs_a != 1) return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
+    g->ctx.slabs_p = slabs_a;
+  } else {
+    g->ctx.slabs_a = slabs_a;
+    g->ctx.slabs_b = slabs_b;
   }
   return BCM_OK;
 }

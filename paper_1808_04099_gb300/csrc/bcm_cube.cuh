@@ -1,0 +1,198 @@
+// bcm_cube.cuh -- block-level helpers of the whole-cube stencil kernels:
+// per-cube constants in shared memory, 4-wide vector access along x, and staging
+// of a pressure-like field (Neumann / outflow-Dirichlet ghosts) with its face halo.
+#pragma once
+
+#include "bcm_internal.cuh"
+
+namespace bcm {
+
+// ---- four consecutive values along x: one float4, or two double2 (16-byte accesses)
+__device__ __forceinline__ void ld4(const float* __restrict__ p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* __restrict__ p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* __restrict__ p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// ---- per-cube constants shared by a block
+template <class TV>
+struct CubeSh {
+  int nb[6];        // face neighbours / NB_* codes
+  int w3[6];        // Jacobi face weights (thirds) of this cube
+  int nbw3[6][6];   // ... of each same-level neighbour
+  int bc[6];        // the sim's domain-face conditions
+  TV invtab[kW3];   // 1 / diag(K) by face-weight sum
+};
+
+// Needs blockDim.x >= 37; the caller synchronises afterwards.
+template <class TV>
+__device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int c) {
+  const int t = threadIdx.x;
+  const SimParams& sp = g.sp[g.sim[c]];
+  if (t < 6) {
+    cs.nb[t] = g.nb[6 * c + t];
+    cs.w3[t] = g.w3[6 * c + t];
+    cs.bc[t] = sp.bc[t];
+  }
+  if (t < 36) cs.nbw3[t / 6][t - 6 * (t / 6)] = g.nbw3[36 * c + t];
+  if (t < kW3) cs.invtab[t] = TV(sp.invdiag[g.lvl[c]][t]);
+}
+
+// Face-weight sum (thirds) of cell (i, j, k) of a cube with face weights w3.
+template <int B>
+__device__ __forceinline__ int s3_of(const int* w3, int i, int j, int k) {
+  return 18 + (i == 0 ? w3[0] - 3 : 0) + (i == B - 1 ? w3[1] - 3 : 0) +
+         (j == 0 ? w3[2] - 3 : 0) + (j == B - 1 ? w3[3] - 3 : 0) +
+         (k == 0 ? w3[4] - 3 : 0) + (k == B - 1 ? w3[5] - 3 : 0);
+}
+
+// Tile positions of face f's ghost cell and of its mirror interior cell at (a, b).
+template <int B>
+__device__ __forceinline__ int ghost_pos(int f, int a, int b) {
+  using SL = Slab<B, B>;
+  switch (f) {
+    case 0: return SL::at(-1, a, b + 1);
+    case 1: return SL::at(B, a, b + 1);
+    case 2: return SL::at(a, -1, b + 1);
+    case 3: return SL::at(a, B, b + 1);
+    case 4: return SL::at(a, b, 0);
+    default: return SL::at(a, b, B + 1);
+  }
+}
+template <int B>
+__device__ __forceinline__ int mirror_pos(int f, int a, int b) {
+  using SL = Slab<B, B>;
+  switch (f) {
+    case 0: return SL::at(0, a, b + 1);
+    case 1: return SL::at(B - 1, a, b + 1);
+    case 2: return SL::at(a, 0, b + 1);
+    case 3: return SL::at(a, B - 1, b + 1);
+    case 4: return SL::at(a, b, 1);
+    default: return SL::at(a, b, B);
+  }
+}
+
+// Stage a pressure-like field of a whole cube into the (B+2)^3 tile S:
+//   own4(q4, i0, j, k, v[4]) -> the 4 cells starting at cell 4*q4 of this cube;
+//   nbv(f, n, cell)          -> a cell of same-level neighbour n across face f;
+// domain faces get the pressure ghost (mirror, or minus the mirror at outflow).
+// Ends with the tile complete and the block synchronised.
+template <int B, int NT, class TV, class Own, class Nbv>
+__device__ __forceinline__ void stage_pressure_cube(TV* __restrict__ S, const CubeSh<TV>& cs,
+                                                    const Own& own4, const Nbv& nbv) {
+  using SL = Slab<B, B>;
+  constexpr int B3 = B * B * B, BB = B * B;
+  for (int q4 = threadIdx.x; q4 < B3 / 4; q4 += NT) {
+    const int cell = 4 * q4, i0 = cell % B, j = (cell / B) % B, k = cell / BB;
+    TV v[4];
+    own4(q4, i0, j, k, v);
+    const int o = SL::at(i0, j, k + 1);
+    S[o] = v[0];
+    S[o + 1] = v[1];
+    S[o + 2] = v[2];
+    S[o + 3] = v[3];
+  }
+  for (int idx = threadIdx.x; idx < 6 * BB; idx += NT) {
+    const int f = idx / BB, t = idx - f * BB, b = t / B, a = t - b * B;
+    const int n = cs.nb[f];
+    if (n >= 0) S[ghost_pos<B>(f, a, b)] = nbv(f, n, cell_of<B>(f >> 1, (f & 1) ? 0 : B - 1, a, b));
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 6 * BB; idx += NT) {
+    const int f = idx / BB, t = idx - f * BB, b = t / B, a = t - b * B;
+    if (cs.nb[f] == NB_BOUNDARY) {
+      const TV m = S[mirror_pos<B>(f, a, b)];
+      S[ghost_pos<B>(f, a, b)] = cs.bc[f] == BC_OUTFLOW ? -m : m;
+    }
+  }
+  __syncthreads();
+}
+
+// Stage planes z0-1 .. z0+KS of a pressure-like field into the (KS+2)(B+2)^2 tile S,
+// with the x/y face ring on the KS own planes:
+//   val4(cube, cell0, face, v[4]) -> cells cell0..cell0+3 of `cube` (face = -1 for this
+//                                    cube, else the face across which it lies);
+//   val1(face, n, cell)          -> one cell of same-level neighbour n across face;
+// domain faces get the pressure ghost (mirror, or minus the mirror at outflow).
+// Ends with the tile complete and the block synchronised.
+template <int B, int KS, int NT, class TV, class Val4, class Val1>
+__device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const CubeSh<TV>& cs,
+                                                    int c, int z0, const Val4& val4,
+                                                    const Val1& val1) {
+  using SL = Slab<B, KS>;
+  constexpr int BB = B * B, Q = BB / 4;
+  for (int idx = threadIdx.x; idx < (KS + 2) * Q; idx += NT) {
+    const int kk = idx / Q, q = idx - kk * Q;
+    const int j = (4 * q) / B, i0 = 4 * q - j * B;
+    const int k = z0 - 1 + kk;
+    TV v[4];
+    bool have = true;
+    if (k >= 0 && k < B) {
+      val4(c, k * BB + 4 * q, -1, v);
+    } else {
+      const int f = k < 0 ? 4 : 5, n = cs.nb[f];
+      if (n >= 0) val4(n, (k < 0 ? B - 1 : 0) * BB + 4 * q, f, v);
+      else have = false;
+    }
+    if (have) {
+      const int o = SL::at(i0, j, kk);
+      S[o] = v[0];
+      S[o + 1] = v[1];
+      S[o + 2] = v[2];
+      S[o + 3] = v[3];
+    }
+  }
+  for (int idx = threadIdx.x; idx < 4 * KS * B; idx += NT) {
+    const int f = idx / (KS * B), rem = idx - f * (KS * B), kk = rem / B, t = rem - kk * B;
+    const int n = cs.nb[f];
+    if (n >= 0) {
+      const TV v = val1(f, n, cell_of<B>(f >> 1, (f & 1) ? 0 : B - 1, t, z0 + kk));
+      S[f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1)] = v;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 4 * KS * B; idx += NT) {
+    const int f = idx / (KS * B), rem = idx - f * (KS * B), kk = rem / B, t = rem - kk * B;
+    if (cs.nb[f] == NB_BOUNDARY) {
+      const int gpos = f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1);
+      const int mpos = f < 2 ? SL::at(f == 0 ? 0 : B - 1, t, kk + 1)
+                             : SL::at(t, f == 2 ? 0 : B - 1, kk + 1);
+      const TV m = S[mpos];
+      S[gpos] = cs.bc[f] == BC_OUTFLOW ? -m : m;
+    }
+  }
+  const bool lo = (z0 == 0 && cs.nb[4] == NB_BOUNDARY);
+  const bool hi = (z0 + KS == B && cs.nb[5] == NB_BOUNDARY);
+  if (lo || hi) {
+    for (int idx = threadIdx.x; idx < 2 * BB; idx += NT) {
+      const int top = idx / BB, t = idx - top * BB, j = t / B, i = t - j * B;
+      if (top ? hi : lo) {
+        const TV m = S[SL::at(i, j, top ? KS : 1)];
+        S[SL::at(i, j, top ? KS + 1 : 0)] = cs.bc[top ? 5 : 4] == BC_OUTFLOW ? -m : m;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// sum over the six faces of (p_c - p_nb) at tile position o (the 7-point K stencil / h)
+template <int B, class TV, int KS = B>
+__device__ __forceinline__ TV stencil_sum(const TV* __restrict__ S, int o) {
+  using SL = Slab<B, KS>;
+  const TV pc = S[o];
+  return (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) + (pc - S[o + SL::P]) +
+         (pc - S[o - SL::P * SL::P]) + (pc - S[o + SL::P * SL::P]);
+}
+
+}  // namespace bcm

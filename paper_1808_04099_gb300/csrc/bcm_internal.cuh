@@ -43,9 +43,14 @@ struct SimParams {
   int pad;
 };
 
+// Accumulators are striped over kStripes cache lines (block index mod kStripes) so
+// that thousands of blocks adding into one sim do not serialise on one address.
+constexpr int kStripes = 8;
+constexpr int kAccPad = 24;  // doubles per stripe (192 bytes)
+
 // Per-sim mutable state (solver scalars and atomic accumulators).
 struct SimState {
-  double acc[8];       // atomics: see ACC_* below
+  double acc[kStripes][kAccPad];  // atomics: see ACC_* below
   double drag_acc[3];
   double drag[3];
   double bb;           // ||rhs||^2
@@ -69,7 +74,9 @@ struct SimState {
 };
 
 enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 5,
-       ACC_DIVN = 6, ACC_DIVD = 7 };
+       ACC_DIVN = 6, ACC_DIVD = 7,
+       // persistent PCG: three rotating slots (iteration mod 3) per dot product
+       ACC_SLOT_PQ = 8, ACC_SLOT_RZ = 11, ACC_SLOT_RR = 14 };
 
 // Device view of the grid tables, passed by value to every kernel.
 struct DevGrid {
@@ -80,6 +87,7 @@ struct DevGrid {
   const int* __restrict__ lvl;    // [n]
   const int* __restrict__ ijk;    // [3n]
   const int* __restrict__ w3;     // [6n] Jacobi face weight in thirds (0,2,3,4,6)
+  const int* __restrict__ nbw3;   // [36n] w3 of each same-level neighbour (3 elsewhere)
   const int* __restrict__ slot;   // [6n] outflow slot or -1
   const unsigned char* __restrict__ near;  // [n] cube may hold phi != 0
   const SimParams* __restrict__ sp;
@@ -247,21 +255,59 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   }
 }
 
-// Last-block election: every block must call this exactly once per launch.
+// Last-block election: every block must call this exactly once per launch, after its
+// thread 0 has issued the block's accumulator atomics.  The ticket is two-level: a
+// block takes a ticket on one of kTickets striped counters (block index mod
+// kTickets), the last block of each stripe takes one on the top counter, and the
+// last of those is the last block.  One shared counter would serialise every block
+// of the launch on a single L2 address.  Counters reset themselves.  Only thread 0
+// fences: the last block reads nothing but the accumulators, so the other threads'
+// stores need not be visible to it (the next kernel sees them at the launch boundary).
+constexpr int kTickets = 32;
+constexpr int kTicketWords = 32 * (1 + kTickets);  // one 128-byte line per counter
+
 __device__ __forceinline__ bool last_block(unsigned int* counter) {
   __shared__ int is_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int total = gridDim.x * gridDim.y;
-    const unsigned int t = atomicAdd(counter, 1u);
-    is_last = (t == total - 1);
+    __threadfence();
+    const unsigned int nblk = gridDim.x;
+    const unsigned int stripe = blockIdx.x % kTickets;
+    const unsigned int in_stripe = (nblk - stripe + kTickets - 1) / kTickets;
+    const unsigned int t = atomicAdd(&counter[32 * (1 + stripe)], 1u);
+    int last = 0;
+    if (t == in_stripe - 1) {
+      counter[32 * (1 + stripe)] = 0u;
+      __threadfence();
+      const unsigned int stripes = nblk < (unsigned)kTickets ? nblk : (unsigned)kTickets;
+      const unsigned int u = atomicAdd(&counter[0], 1u);
+      if (u == stripes - 1) {
+        counter[0] = 0u;
+        last = 1;
+        __threadfence();
+      }
+    }
+    is_last = last;
   }
   __syncthreads();
-  if (is_last) __threadfence();
   return is_last != 0;
 }
 
 __device__ __forceinline__ double ld_acc(const double* p) { return __ldcg(p); }
+
+// Add v to accumulator idx of a sim (this block's stripe).
+__device__ __forceinline__ void acc_add(SimState& st, int idx, double v) {
+  atomicAdd(&st.acc[blockIdx.x % kStripes][idx], v);
+}
+// Sum of accumulator idx over the stripes, which are reset to zero (last block only).
+__device__ __forceinline__ double acc_take(SimState& st, int idx) {
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < kStripes; ++q) {
+    s += ld_acc(&st.acc[q][idx]);
+    st.acc[q][idx] = 0.0;
+  }
+  return s;
+}
 
 }  // namespace bcm

@@ -77,14 +77,7 @@ struct FieldVal {
   }
 };
 
-__device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v) {
-  atomicMax(p, (unsigned long long)__double_as_longlong(v));
-}
 
-// Device-side loop control for CUDA-graph while nodes (0 handle = host-driven loop).
-__device__ __forceinline__ void set_cond(unsigned long long handle, unsigned int v) {
-  if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, v);
-}
 
 // ------------------------------------------------------------- body geometry
 
@@ -407,381 +400,13 @@ __global__ __launch_bounds__(NT) void k_rhs(DevGrid g, const T* __restrict__ us,
   }
   double vals[1] = {bsum};
   block_sum<NT, 1>(vals, red);
-  if (threadIdx.x == 0 && sp.all_neumann) atomicAdd(&g.ss[s].acc[ACC_BSUM], vals[0]);
+  if (threadIdx.x == 0 && sp.all_neumann) acc_add(g.ss[s], ACC_BSUM, vals[0]);
   if (last_block(g.counter)) {
     for (int q = threadIdx.x; q < g.n_sims; q += NT) {
       SimState& st = g.ss[q];
-      st.bmean = g.sp[q].all_neumann ? ld_acc(&st.acc[ACC_BSUM]) / g.sp[q].n_cells : 0.0;
-      st.acc[ACC_BSUM] = 0.0;
+      const double bs = acc_take(st, ACC_BSUM);
+      st.bmean = g.sp[q].all_neumann ? bs / g.sp[q].n_cells : 0.0;
     }
-    if (threadIdx.x == 0) *g.counter = 0;
-  }
-}
-
-// ===========================================================================
-// (a9, a10) residual r = rhs - K x of the FP64 iterate x = p, rhs = -V (b - mean).
-// FP64 mode: r starts the PCG.  Mixed mode: one defect-correction cycle; r is
-// stored in FP32 as the inner right-hand side and the inner iterate e is zeroed.
-// ===========================================================================
-template <int B, int NT, class TV, bool MIXED>
-__global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __restrict__ b,
-                                                 const double* __restrict__ x,
-                                                 TV* __restrict__ r, float* __restrict__ e,
-                                                 SolveParams prm) {
-  using SL = Slab<B, B>;
-  constexpr int B3 = B * B * B;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* S = reinterpret_cast<double*>(smem_raw);
-  __shared__ double red[4 * 32];
-  const int c = blockIdx.x;
-  const int s = g.sim[c];
-  const SimParams& sp = g.sp[s];
-  SimState& st = g.ss[s];
-  const bool skip = MIXED ? (st.outer_done != 0) : false;
-  double acc4[4] = {0, 0, 0, 0};  // bb, rr64, rz, rr (inner, mixed)
-  if (!skip) {
-    stage_slab<B, B, NT>(S, g, c, 0, FieldVal<double>{x, B3}, PressureBC{&sp});
-    __syncthreads();
-    const double hd = cell_h<B>(g, c), V = hd * hd * hd, mean = st.bmean;
-    float rz32 = 0.f, rr32 = 0.f;
-    for (int q = threadIdx.x; q < B3; q += NT) {
-      const int k = q / (B * B), rem = q - k * B * B, j = rem / B, i = rem - j * B;
-      const int o = SL::at(i, j, k + 1);
-      const double pc = S[o];
-      const double acc = (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) +
-                         (pc - S[o + SL::P]) + (pc - S[o - SL::P * SL::P]) +
-                         (pc - S[o + SL::P * SL::P]);
-      const size_t gi = (size_t)c * B3 + q;
-      const double rhs = -V * (b[gi] - mean);
-      const double rv = rhs - hd * acc;
-      acc4[0] += rhs * rhs;
-      if (MIXED) {
-        const float r32 = float(rv);
-        r[gi] = TV(r32);
-        e[gi] = 0.f;
-        const float z32 = r32 * float(inv_diag<B>(g, c, q));
-        rz32 += r32 * z32;
-        rr32 += r32 * r32;
-        acc4[1] += rv * rv;
-      } else {
-        r[gi] = TV(rv);
-        const double z = rv * inv_diag<B>(g, c, q);
-        acc4[2] += rv * z;
-        acc4[3] += rv * rv;
-      }
-    }
-    if (MIXED) {
-      acc4[2] = rz32;
-      acc4[3] = rr32;
-    }
-  }
-  block_sum<NT, 4>(acc4, red);
-  if (threadIdx.x == 0 && !skip) {
-    atomicAdd(&st.acc[ACC_BB], acc4[0]);
-    if (MIXED) atomicAdd(&st.acc[ACC_RR64], acc4[1]);
-    atomicAdd(&st.acc[ACC_RZ], acc4[2]);
-    atomicAdd(&st.acc[ACC_RR], acc4[3]);
-  }
-  if (last_block(g.counter)) {
-    int alive = 0;
-    for (int q = threadIdx.x; q < g.n_sims; q += NT) {
-      SimState& t = g.ss[q];
-      const double bb = ld_acc(&t.acc[ACC_BB]), rr64 = ld_acc(&t.acc[ACC_RR64]);
-      const double rz = ld_acc(&t.acc[ACC_RZ]), rr = ld_acc(&t.acc[ACC_RR]);
-      t.acc[ACC_BB] = t.acc[ACC_RR64] = t.acc[ACC_RZ] = t.acc[ACC_RR] = 0.0;
-      if (MIXED && t.outer_done) continue;
-      if (MIXED) {
-        t.cycles += 1;
-        if (t.cycles == 1) {
-          t.bb = bb;
-          t.tol2 = prm.rtol * prm.rtol * bb;
-          t.zero_rhs = (bb == 0.0);
-        }
-        t.rr64 = rr64;
-        const bool ok = t.zero_rhs || rr64 <= t.tol2;
-        if (!isfinite(rr64)) t.nonfinite = 1;
-        if (ok || t.cycles > prm.max_cycles || t.nonfinite) {
-          t.outer_done = 1;
-          t.done = 1;
-          t.converged = ok;
-        } else {
-          t.rz = rz;
-          t.rr = rr;
-          t.inner_tol2 = prm.inner_rtol * prm.inner_rtol * rr;
-          t.iter = 0;
-          t.beta = 0.0;
-          t.done = (rr == 0.0);
-          alive |= !t.done;
-        }
-      } else {
-        t.bb = bb;
-        t.tol2 = prm.rtol * prm.rtol * bb;
-        t.zero_rhs = (bb == 0.0);
-        t.rz = rz;
-        t.rr = rr;
-        t.rr64 = rr;
-        t.iter = 0;
-        t.total_iters = 0;
-        t.beta = 0.0;
-        if (!isfinite(rr)) t.nonfinite = 1;
-        t.done = t.zero_rhs || rr <= t.tol2 || t.nonfinite;
-        t.converged = t.zero_rhs || rr <= t.tol2;
-        alive |= !t.done;
-      }
-    }
-    int outer_alive = 0;
-    if (MIXED)
-      for (int q = threadIdx.x; q < g.n_sims; q += NT) outer_alive |= !g.ss[q].outer_done;
-    alive = __syncthreads_or(alive);
-    outer_alive = __syncthreads_or(outer_alive);
-    if (threadIdx.x == 0) {
-      *g.counter = 0;
-      g.flags[0] = !alive;
-      g.flags[1] = MIXED ? !outer_alive : 1;
-      set_cond(prm.cond_inner, alive ? 1u : 0u);
-      if (MIXED) set_cond(prm.cond_outer, outer_alive ? 1u : 0u);
-    }
-  }
-}
-
-// ===========================================================================
-// (a9) PCG pass A:  p_new = z + beta p_old (z = r / diag, staged with halo),
-//                   q = K p_new,  <p_new, q>;  then alpha = rz / <p, q> per sim.
-// ===========================================================================
-template <int B, int NT, class TV>
-__global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r,
-                                             TV* __restrict__ p0, TV* __restrict__ p1,
-                                             TV* __restrict__ q, SolveParams prm) {
-  using SL = Slab<B, B>;
-  constexpr int B3 = B * B * B;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TV* S = reinterpret_cast<TV*>(smem_raw);
-  __shared__ double red[32];
-  const int c = blockIdx.x;
-  const int s = g.sim[c];
-  const SimParams& sp = g.sp[s];
-  SimState& st = g.ss[s];
-  double pq = 0.0;
-  if (!st.done) {
-    const int it = st.iter;
-    const TV* pold = (it & 1) ? p1 : p0;
-    TV* pnew = (it & 1) ? p0 : p1;
-    const TV beta = TV(st.beta);
-    const bool first = (it == 0);
-    struct PVal {
-      const DevGrid* g;
-      const TV* r;
-      const TV* po;
-      TV beta;
-      bool first;
-      __device__ __forceinline__ TV operator()(int cc, int cell) const {
-        const size_t gi = (size_t)cc * B3 + cell;
-        const TV z = r[gi] * TV(inv_diag<B>(*g, cc, cell));
-        return first ? z : z + beta * po[gi];
-      }
-    } val{&g, r, pold, beta, first};
-    stage_slab<B, B, NT>(S, g, c, 0, val, PressureBC{&sp});
-    __syncthreads();
-    const TV h = TV(cell_h<B>(g, c));
-    TV part = TV(0);
-    for (int qq = threadIdx.x; qq < B3; qq += NT) {
-      const int k = qq / (B * B), rem = qq - k * B * B, j = rem / B, i = rem - j * B;
-      const int o = SL::at(i, j, k + 1);
-      const TV pc = S[o];
-      const TV acc = (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) +
-                     (pc - S[o + SL::P]) + (pc - S[o - SL::P * SL::P]) +
-                     (pc - S[o + SL::P * SL::P]);
-      const TV qv = h * acc;
-      const size_t gi = (size_t)c * B3 + qq;
-      pnew[gi] = pc;
-      q[gi] = qv;
-      part += pc * qv;
-    }
-    pq = double(part);
-  }
-  double vals[1] = {pq};
-  block_sum<NT, 1>(vals, red);
-  if (threadIdx.x == 0 && !st.done) atomicAdd(&st.acc[ACC_PQ], vals[0]);
-  if (last_block(g.counter)) {
-    for (int qq = threadIdx.x; qq < g.n_sims; qq += NT) {
-      SimState& t = g.ss[qq];
-      const double pqs = ld_acc(&t.acc[ACC_PQ]);
-      t.acc[ACC_PQ] = 0.0;
-      if (t.done) continue;
-      t.alpha = (pqs != 0.0) ? t.rz / pqs : 0.0;
-      if (!isfinite(pqs)) {
-        t.nonfinite = 1;
-        t.alpha = 0.0;
-      }
-    }
-    if (threadIdx.x == 0) *g.counter = 0;
-  }
-}
-
-// ===========================================================================
-// (a9) PCG pass B:  x += alpha p,  r -= alpha q,  z = r / diag,  <r,z>, <r,r>;
-// then beta, convergence test and loop control per sim.
-// ===========================================================================
-template <int B, int NT, class TV, class TX>
-__global__ __launch_bounds__(NT) void k_cg_b(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
-                                             const TV* __restrict__ p0,
-                                             const TV* __restrict__ p1,
-                                             const TV* __restrict__ q, SolveParams prm) {
-  constexpr int B3 = B * B * B;
-  __shared__ double red[2 * 32];
-  const int c = blockIdx.x;
-  const int s = g.sim[c];
-  SimState& st = g.ss[s];
-  double vals[2] = {0.0, 0.0};
-  const bool active = !st.done && !st.nonfinite;
-  if (active) {
-    const TV* pn = (st.iter & 1) ? p0 : p1;
-    const TV alpha = TV(st.alpha);
-    TV rz = TV(0), rr = TV(0);
-    for (int qq = threadIdx.x; qq < B3; qq += NT) {
-      const size_t gi = (size_t)c * B3 + qq;
-      const TV pv = pn[gi];
-      x[gi] = TX(x[gi] + alpha * pv);
-      const TV rv = r[gi] - alpha * q[gi];
-      r[gi] = rv;
-      const TV z = rv * TV(inv_diag<B>(g, c, qq));
-      rz += rv * z;
-      rr += rv * rv;
-    }
-    vals[0] = double(rz);
-    vals[1] = double(rr);
-  }
-  block_sum<NT, 2>(vals, red);
-  if (threadIdx.x == 0 && active) {
-    atomicAdd(&st.acc[ACC_RZ], vals[0]);
-    atomicAdd(&st.acc[ACC_RR], vals[1]);
-  }
-  if (last_block(g.counter)) {
-    int alive = 0;
-    for (int qq = threadIdx.x; qq < g.n_sims; qq += NT) {
-      SimState& t = g.ss[qq];
-      const double rz = ld_acc(&t.acc[ACC_RZ]), rr = ld_acc(&t.acc[ACC_RR]);
-      t.acc[ACC_RZ] = t.acc[ACC_RR] = 0.0;
-      if (t.done) continue;
-      if (t.nonfinite || !isfinite(rr)) {
-        t.nonfinite = 1;
-        t.done = 1;
-        continue;
-      }
-      t.beta = (t.rz != 0.0) ? rz / t.rz : 0.0;
-      t.rz = rz;
-      t.rr = rr;
-      t.iter += 1;
-      t.total_iters += 1;
-      const bool inner = prm.mixed != 0;
-      const double tol2 = inner ? t.inner_tol2 : t.tol2;
-      const bool ok = rr <= tol2;
-      if (!inner) {
-        t.rr64 = rr;
-        t.converged = ok;
-      }
-      if (ok || t.iter >= (inner ? prm.inner_max_iter : prm.max_iter)) t.done = 1;
-      alive |= !t.done;
-    }
-    alive = __syncthreads_or(alive);
-    if (threadIdx.x == 0) {
-      *g.counter = 0;
-      g.flags[0] = !alive;
-      set_cond(prm.cond_inner, alive ? 1u : 0u);
-    }
-  }
-  // independent guard on the graph loop: a bounded number of body executions
-  if (prm.cond_inner && blockIdx.x == 0 && threadIdx.x == 0) {
-    const unsigned int n = atomicAdd(prm.guard, 1u) + 1u;
-    if (n >= (unsigned int)prm.guard_limit) cudaGraphSetConditional(
-        (cudaGraphConditionalHandle)prm.cond_inner, 0u);
-  }
-}
-
-// Mixed mode: x64 += e32 after an inner solve (sims still correcting).
-template <int B, int NT>
-__global__ __launch_bounds__(NT) void k_add_correction(DevGrid g, double* __restrict__ x,
-                                                       const float* __restrict__ e) {
-  constexpr int B3 = B * B * B;
-  const int c = blockIdx.x;
-  if (g.ss[g.sim[c]].outer_done) return;
-  for (int q = threadIdx.x; q < B3; q += NT) {
-    const size_t gi = (size_t)c * B3 + q;
-    x[gi] += double(e[gi]);
-  }
-}
-
-// ===========================================================================
-// (a11) projection: u = u* - dt * (mean of the two face gradients of p) (R1, R2),
-// plus the FP64 divergence check ||b - A p|| / ||b|| = ||D U^{n+1}|| / ||D U*||
-// and max |u|.
-// ===========================================================================
-template <int B, int NT, class T>
-__global__ __launch_bounds__(NT) void k_correct(DevGrid g, double* __restrict__ p,
-                                                const double* __restrict__ b,
-                                                const T* __restrict__ us,
-                                                const T* __restrict__ vs,
-                                                const T* __restrict__ ws, T* __restrict__ u,
-                                                T* __restrict__ v, T* __restrict__ w) {
-  using SL = Slab<B, B>;
-  constexpr int B3 = B * B * B;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* S = reinterpret_cast<double*>(smem_raw);
-  __shared__ double red[2 * 32];
-  const int c = blockIdx.x;
-  const int s = g.sim[c];
-  const SimParams& sp = g.sp[s];
-  SimState& st = g.ss[s];
-  const bool zero = st.zero_rhs != 0;
-  struct PV {
-    const double* p;
-    bool zero;
-    __device__ __forceinline__ double operator()(int cc, int cell) const {
-      return zero ? 0.0 : p[(size_t)cc * B3 + cell];
-    }
-  } val{p, zero};
-  stage_slab<B, B, NT>(S, g, c, 0, val, PressureBC{&sp});
-  __syncthreads();
-  const double hd = cell_h<B>(g, c);
-  const double ih = 1.0 / hd, ih2 = ih * ih;
-  const T cdt = T(0.5 * sp.dt);
-  const T* stars[3] = {us, vs, ws};
-  T* outs[3] = {u, v, w};
-  double dn = 0.0, dd = 0.0;
-  float umax = 0.f;
-  for (int q = threadIdx.x; q < B3; q += NT) {
-    const int k = q / (B * B), rem = q - k * B * B, j = rem / B, i = rem - j * B;
-    const int o = SL::at(i, j, k + 1);
-    const int off[3] = {1, SL::P, SL::P * SL::P};
-    const size_t gi = (size_t)c * B3 + q;
-    const double pc = S[o];
-    double lap = 0.0;
-    double m2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const double dm = pc - S[o - off[d]], dp = S[o + off[d]] - pc;
-      lap += dp - dm;
-      const T grad = T((dm + dp) * ih);  // (gm + gp) with gm, gp the face gradients
-      const T nv = stars[d][gi] - cdt * grad;
-      outs[d][gi] = nv;
-      m2 += double(nv) * double(nv);
-    }
-    if (zero) p[gi] = 0.0;
-    const double bv = b[gi];
-    const double res = bv - lap * ih2;  // b - A p
-    dn += res * res;
-    dd += bv * bv;
-    umax = fmaxf(umax, float(sqrt(m2)));
-  }
-  double vals[2] = {dn, dd};
-  block_sum<NT, 2>(vals, red);
-  // max |u|
-  float um = umax;
-  for (int o2 = 16; o2 > 0; o2 >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o2));
-  if ((threadIdx.x & 31) == 0) atomic_max_pos(&st.umax_bits, double(um));
-  if (threadIdx.x == 0) {
-    atomicAdd(&st.acc[ACC_DIVN], vals[0]);
-    atomicAdd(&st.acc[ACC_DIVD], vals[1]);
   }
 }
 
@@ -793,10 +418,9 @@ __global__ void k_step_end(DevGrid g) {
       t.drag[e] = t.drag_acc[e];
       t.drag_acc[e] = 0.0;
     }
-    const double dn = t.acc[ACC_DIVN], dd = t.acc[ACC_DIVD];
+    const double dn = acc_take(t, ACC_DIVN), dd = acc_take(t, ACC_DIVD);
     t.div_num = dn;
     t.div_den = dd;
-    t.acc[ACC_DIVN] = t.acc[ACC_DIVD] = 0.0;
     t.step += 1;
   }
 }
@@ -812,14 +436,13 @@ __global__ __launch_bounds__(NT) void k_bmean(DevGrid g, const double* __restric
   for (int q = threadIdx.x; q < B3; q += NT) acc += b[(size_t)c * B3 + q];
   double vals[1] = {acc};
   block_sum<NT, 1>(vals, red);
-  if (threadIdx.x == 0 && g.sp[s].all_neumann) atomicAdd(&g.ss[s].acc[ACC_BSUM], vals[0]);
+  if (threadIdx.x == 0 && g.sp[s].all_neumann) acc_add(g.ss[s], ACC_BSUM, vals[0]);
   if (last_block(g.counter)) {
     for (int q = threadIdx.x; q < g.n_sims; q += NT) {
       SimState& st = g.ss[q];
-      st.bmean = g.sp[q].all_neumann ? ld_acc(&st.acc[ACC_BSUM]) / g.sp[q].n_cells : 0.0;
-      st.acc[ACC_BSUM] = 0.0;
+      const double bs = acc_take(st, ACC_BSUM);
+      st.bmean = g.sp[q].all_neumann ? bs / g.sp[q].n_cells : 0.0;
     }
-    if (threadIdx.x == 0) *g.counter = 0;
   }
 }
 
@@ -888,29 +511,6 @@ __global__ __launch_bounds__(NT) void k_fill_halo(DevGrid g, const T* __restrict
       }
     }
     o[q] = vv;
-  }
-}
-
-template <int B, int NT>
-__global__ __launch_bounds__(NT) void k_apply_poisson(DevGrid g, const double* __restrict__ x,
-                                                      double* __restrict__ y) {
-  using SL = Slab<B, B>;
-  constexpr int B3 = B * B * B;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* S = reinterpret_cast<double*>(smem_raw);
-  const int c = blockIdx.x;
-  const SimParams& sp = g.sp[g.sim[c]];
-  stage_slab<B, B, NT>(S, g, c, 0, FieldVal<double>{x, B3}, PressureBC{&sp});
-  __syncthreads();
-  const double h = cell_h<B>(g, c);
-  for (int q = threadIdx.x; q < B3; q += NT) {
-    const int k = q / (B * B), rem = q - k * B * B, j = rem / B, i = rem - j * B;
-    const int o = SL::at(i, j, k + 1);
-    const double pc = S[o];
-    const double acc = (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) +
-                       (pc - S[o + SL::P]) + (pc - S[o - SL::P * SL::P]) +
-                       (pc - S[o + SL::P * SL::P]);
-    y[(size_t)c * B3 + q] = h * acc;
   }
 }
 
@@ -998,80 +598,6 @@ cudaError_t launch_solve_begin(const Ctx& x) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const Ctx& x, const SolveParams& prm) {
-  BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>();
-    const size_t sm = sizeof(double) * Slab<B, B>::N;
-    if (x.f64) {
-      auto kern = k_residual<B, NT, double, false>;
-      cudaError_t e = allow_smem(kern, sm);
-      if (e != cudaSuccess) return e;
-      kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, x.f.b, x.f.p, (double*)x.f.r, nullptr, prm);
-    } else {
-      auto kern = k_residual<B, NT, float, true>;
-      cudaError_t e = allow_smem(kern, sm);
-      if (e != cudaSuccess) return e;
-      kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, x.f.b, x.f.p, (float*)x.f.r, x.f.e, prm);
-    }
-  });
-  return cudaGetLastError();
-}
-
-template <class TV>
-static cudaError_t cg_a_t(const Ctx& x, const SolveParams& prm) {
-  BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>();
-    const size_t sm = sizeof(TV) * Slab<B, B>::N;
-    auto ka = k_cg_a<B, NT, TV>;
-    cudaError_t e = allow_smem(ka, sm);
-    if (e != cudaSuccess) return e;
-    ka<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, (const TV*)x.f.r, (TV*)x.f.p0, (TV*)x.f.p1,
-                                          (TV*)x.f.q, prm);
-  });
-  return cudaGetLastError();
-}
-template <class TV, class TX>
-static cudaError_t cg_b_t(const Ctx& x, const SolveParams& prm, TX* xv) {
-  BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>();
-    k_cg_b<B, NT, TV, TX><<<x.g.n_cubes, NT, 0, x.stream>>>(
-        x.g, xv, (TV*)x.f.r, (const TV*)x.f.p0, (const TV*)x.f.p1, (const TV*)x.f.q, prm);
-  });
-  return cudaGetLastError();
-}
-cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm) {
-  return x.f64 ? cg_a_t<double>(x, prm) : cg_a_t<float>(x, prm);
-}
-cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm) {
-  return x.f64 ? cg_b_t<double, double>(x, prm, x.f.p) : cg_b_t<float, float>(x, prm, x.f.e);
-}
-
-cudaError_t launch_add_correction(const Ctx& x) {
-  BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>();
-    k_add_correction<B, NT><<<x.g.n_cubes, NT, 0, x.stream>>>(x.g, x.f.p, x.f.e);
-  });
-  return cudaGetLastError();
-}
-
-template <class T>
-static cudaError_t correct_t(const Ctx& x) {
-  BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>();
-    const size_t sm = sizeof(double) * Slab<B, B>::N;
-    auto kern = k_correct<B, NT, T>;
-    cudaError_t e = allow_smem(kern, sm);
-    if (e != cudaSuccess) return e;
-    kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, x.f.p, x.f.b, (const T*)x.f.us,
-                                            (const T*)x.f.vs, (const T*)x.f.ws, (T*)x.f.u,
-                                            (T*)x.f.v, (T*)x.f.w);
-  });
-  return cudaGetLastError();
-}
-cudaError_t launch_correct(const Ctx& x) {
-  return x.f64 ? correct_t<double>(x) : correct_t<float>(x);
-}
-
 cudaError_t launch_step_end(const Ctx& x) {
   k_step_end<<<1, 128, 0, x.stream>>>(x.g);
   return cudaGetLastError();
@@ -1088,18 +614,6 @@ static cudaError_t fill_halo_t(const Ctx& x, const void* f, int kind, double* ou
 }
 cudaError_t launch_fill_halo(const Ctx& x, const void* f, int f64_field, int kind, double* out) {
   return f64_field ? fill_halo_t<double>(x, f, kind, out) : fill_halo_t<float>(x, f, kind, out);
-}
-
-cudaError_t launch_apply_poisson(const Ctx& x, const double* in, double* out) {
-  BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>();
-    const size_t sm = sizeof(double) * Slab<B, B>::N;
-    auto kern = k_apply_poisson<B, NT>;
-    cudaError_t e = allow_smem(kern, sm);
-    if (e != cudaSuccess) return e;
-    kern<<<x.g.n_cubes, NT, sm, x.stream>>>(x.g, in, out);
-  });
-  return cudaGetLastError();
 }
 
 }  // namespace bcm

@@ -16,6 +16,8 @@ struct Fields {
   void *r, *p0, *p1, *q;  // PCG vectors: FP64 (plain) or FP32 (mixed inner)
   float *e;               // mixed: inner iterate (correction of p)
   unsigned int* guard;    // graph-loop body counter
+  unsigned int* bar;      // persistent PCG grid barrier words
+  int* err;               // persistent PCG: a barrier wait timed out
 };
 
 struct SolveParams {
@@ -29,13 +31,18 @@ struct SolveParams {
   unsigned int* guard;
   int guard_limit;
   int pad;
+  unsigned long long barrier_timeout_ns;  // persistent PCG: longest wait at a grid barrier
 };
 
 struct Ctx {
   DevGrid g;
   Fields f;
   int B;
-  int f64;  // state in FP64 (plain mode) or FP32 (mixed mode)
+  int f64;      // state in FP64 (plain mode) or FP32 (mixed mode)
+  int slabs_a;  // PCG pass A: z-slabs per cube (1, 2 or 4)
+  int slabs_b;  // PCG pass B: z-slabs per cube (1, 2 or 4)
+  int slabs_p;  // persistent PCG: z-slabs per cube (1, 2 or 4)
+  int persistent;  // 1: one cooperative launch per PCG solve; 0: two launches per iteration
   cudaStream_t stream;
 };
 
@@ -47,6 +54,7 @@ cudaError_t launch_solve_begin(const Ctx& x);
 cudaError_t launch_residual(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm);
+cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_add_correction(const Ctx& x);
 cudaError_t launch_correct(const Ctx& x);
 cudaError_t launch_step_end(const Ctx& x);

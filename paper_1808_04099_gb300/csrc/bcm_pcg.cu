@@ -1,0 +1,353 @@
+// bcm_pcg.cu -- persistent Jacobi-PCG solver kernel (Eq. poisson; Saad, Alg. 9.1).
+//
+// One cooperative launch runs all PCG iterations of a solve.  Work items are
+// z-slabs of cubes; block p owns a contiguous run of items by the paper's
+// load-balanced linear distribution (Eq. loaddist: L = floor(N/P), R = N mod P,
+// n_p = floor((N + P - p - 1) / P)), so Z-ordered neighbours mostly share a block.
+// Each iteration is pass A (p = z + beta p, q = K p, <p,q>), a grid barrier, pass B
+// (x += alpha p, r -= alpha q, <r,z>, <r,r>), and a second grid barrier.
+//
+// The per-sim scalars never need a single writer: the dot products go to striped
+// accumulators in three rotating slots (iteration k mod 3), and after each barrier
+// every block derives alpha, beta and the convergence decision from the same sums.
+// Block 0 clears the slot that iteration k+1 will fill.  Grid barriers are
+// two-level tickets (32 striped counters, then one) with a generation word; every
+// wait is bounded by %globaltimer and a timeout sets an error flag and ends the
+// kernel (reported to the host as BCM_E_TIMEOUT), so a fault never hangs the GPU.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bcm_cube.cuh"
+#include "bcm_internal.cuh"
+#include "bcm_kernels.h"
+
+namespace bcm {
+
+constexpr int kMaxPersistentSims = 256;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  bar: [0] generation, [32 (1+s)] stripe
+// counters, [32 (1+kTickets)] top counter (one 128-byte line each).  Returns false
+// (and sets *err) when the wait exceeded limit_ns or another block reported an error.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err,
+                                             unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    const unsigned int nblk = gridDim.x;
+    const unsigned int stripe = blockIdx.x % kTickets;
+    const unsigned int in_stripe = (nblk - stripe + kTickets - 1) / kTickets;
+    const unsigned int t = atomicAdd(&bar[32 * (1 + stripe)], 1u);
+    bool released = false;
+    if (t == in_stripe - 1) {
+      bar[32 * (1 + stripe)] = 0u;
+      __threadfence();
+      const unsigned int stripes = nblk < (unsigned)kTickets ? nblk : (unsigned)kTickets;
+      const unsigned int u = atomicAdd(&bar[32 * (1 + kTickets)], 1u);
+      if (u == stripes - 1) {
+        bar[32 * (1 + kTickets)] = 0u;
+        __threadfence();
+        atomicAdd(&bar[0], 1u);
+        released = true;
+      }
+    }
+    int good = 1;
+    if (!released) {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g0) {
+        if (*(volatile int*)err) {
+          good = 0;
+          break;
+        }
+        if (global_ns() - t0 > limit_ns) {
+          atomicExch(err, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double slot_sum(SimState& st, int idx) {
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < kStripes; ++q) s += ld_acc(&st.acc[q][idx]);
+  return s;
+}
+
+template <int B, int KS, int NT, class TV, class TX>
+__global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
+                                            TV* __restrict__ p0, TV* __restrict__ p1,
+                                            TV* __restrict__ q, SolveParams prm,
+                                            unsigned int* bar, int* err) {
+  using SL = Slab<B, KS>;
+  constexpr int B3 = B * B * B, BB = B * B, NSL = B / KS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* S = reinterpret_cast<TV*>(smem_raw);
+  __shared__ CubeSh<TV> cs;
+  __shared__ int cs_cube;
+  __shared__ double red[2 * 32];
+  const int nsim = g.n_sims;
+  // per-sim scalars after the tile (dynamic shared memory, see pcg_smem)
+  double* s_alpha = reinterpret_cast<double*>(smem_raw + (sizeof(TV) * SL::N + 15) / 16 * 16);
+  double* s_beta = s_alpha + nsim;
+  double* s_rz = s_beta + nsim;
+  double* s_rzprev = s_rz + nsim;
+  unsigned char* s_done = reinterpret_cast<unsigned char*>(s_rzprev + nsim);
+  const bool inner = prm.mixed != 0;
+  const int kmax = inner ? prm.inner_max_iter : prm.max_iter;
+  // my items by the linear load-balanced distribution
+  const int N = g.n_cubes * NSL, P = gridDim.x, p = blockIdx.x;
+  const int Lq = N / P, Rq = N % P;
+  const int item0 = p * Lq + min(p, Rq), nitems = (N + P - p - 1) / P;
+  if (threadIdx.x == 0) cs_cube = -1;
+  // the state at entry: iteration 0 uses the residual kernel's scalars
+  for (int s = threadIdx.x; s < nsim; s += NT) {
+    SimState& st = g.ss[s];
+    s_rz[s] = st.rz;
+    s_rzprev[s] = st.rz;
+    s_done[s] = st.done ? 1 : 0;
+  }
+  __syncthreads();
+  const unsigned long long limit = prm.barrier_timeout_ns;
+  int k = 0;
+  for (;; ++k) {
+    // ---- decisions for iteration k (identical in every block)
+    int alive = 0;
+    for (int s = threadIdx.x; s < nsim; s += NT) {
+      SimState& st = g.ss[s];
+      if (s_done[s]) continue;
+      double rz, rr;
+      if (k == 0) {
+        rz = st.rz;
+        rr = st.rr;
+      } else {
+        rz = slot_sum(st, ACC_SLOT_RZ + k % 3);
+        rr = slot_sum(st, ACC_SLOT_RR + k % 3);
+      }
+      const double tol2 = inner ? st.inner_tol2 : st.tol2;
+      const bool bad = !isfinite(rr) || !isfinite(rz);
+      if (bad || rr <= tol2 || k >= kmax) {
+        s_done[s] = 1;
+        if (blockIdx.x == 0) {  // single writer of the solve's results
+          st.iter = k;
+          st.total_iters += k;
+          st.rr = rr;
+          st.done = 1;
+          if (bad) st.nonfinite = 1;
+          if (!inner) {
+            st.rr64 = rr;
+            st.converged = !bad && rr <= tol2;
+          }
+        }
+        continue;
+      }
+      s_beta[s] = (k == 0 || s_rz[s] == 0.0) ? 0.0 : rz / s_rz[s];
+      s_rzprev[s] = s_rz[s];
+      s_rz[s] = rz;
+      alive = 1;
+    }
+    alive = __syncthreads_or(alive);
+    if (!alive) break;
+    if (blockIdx.x == 0)  // clear the slots iteration k+1 fills (held iteration k-2's sums)
+      for (int i = threadIdx.x; i < nsim * kStripes; i += NT) {
+        SimState& st = g.ss[i / kStripes];
+        const int sp = i % kStripes, sl = (k + 1) % 3;
+        st.acc[sp][ACC_SLOT_RZ + sl] = 0.0;
+        st.acc[sp][ACC_SLOT_RR + sl] = 0.0;
+        st.acc[sp][ACC_SLOT_PQ + sl] = 0.0;
+      }
+    const TV* __restrict__ pold = (k & 1) ? p1 : p0;
+    TV* __restrict__ pnew = (k & 1) ? p0 : p1;
+    // ---- pass A over my items
+    for (int it = 0; it < nitems; ++it) {
+      const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
+      const int s = g.sim[c];
+      if (s_done[s]) continue;
+      if (cs_cube != c) {
+        __syncthreads();
+        load_cube(cs, g, c);
+        if (threadIdx.x == 0) cs_cube = c;
+        __syncthreads();
+      }
+      const TV beta = TV(s_beta[s]);
+      const bool first = (k == 0);
+      auto val4 = [&](int cube, int cell0, int face, TV (&v)[4]) {
+        const size_t gi = (size_t)cube * B3 + cell0;
+        TV rr4[4], pp[4] = {TV(0), TV(0), TV(0), TV(0)};
+        ld4(r + gi, rr4);
+        if (!first) ld4(pold + gi, pp);
+        const int* w3 = face < 0 ? cs.w3 : cs.nbw3[face];
+        const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const TV z = rr4[m] * cs.invtab[s3_of<B>(w3, i0 + m, j, kz)];
+          v[m] = first ? z : z + beta * pp[m];
+        }
+      };
+      auto val1 = [&](int f, int n, int cell) {
+        const int i = cell % B, j = (cell / B) % B, kz = cell / BB;
+        const size_t gi = (size_t)n * B3 + cell;
+        const TV z = r[gi] * cs.invtab[s3_of<B>(cs.nbw3[f], i, j, kz)];
+        return first ? z : z + beta * pold[gi];
+      };
+      stage_pressure_slab<B, KS, NT, TV>(S, cs, c, z0, val4, val1);
+      const TV h = TV(cell_h<B>(g, c));
+      const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
+      TV part = TV(0);
+      for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
+        const int cell = 4 * q4, kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
+        const int o = SL::at(i0, j, kk + 1);
+        TV pc[4], qv[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          pc[m] = S[o + m];
+          qv[m] = h * stencil_sum<B, TV, KS>(S, o + m);
+          part += pc[m] * qv[m];
+        }
+        st4(pnew + base + cell, pc);
+        st4(q + base + cell, qv);
+      }
+      double vals[1] = {double(part)};
+      block_sum<NT, 1>(vals, red);
+      if (threadIdx.x == 0) acc_add(g.ss[s], ACC_SLOT_PQ + k % 3, vals[0]);
+    }
+    if (!grid_barrier(bar, err, limit)) break;
+    // ---- alpha per sim from the completed <p, q>
+    for (int s = threadIdx.x; s < nsim; s += NT) {
+      if (s_done[s]) continue;
+      const double pq = slot_sum(g.ss[s], ACC_SLOT_PQ + k % 3);
+      s_alpha[s] = (pq != 0.0 && isfinite(pq)) ? s_rz[s] / pq : 0.0;
+    }
+    __syncthreads();
+    // ---- pass B over my items (pointwise)
+    for (int it = 0; it < nitems; ++it) {
+      const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
+      const int s = g.sim[c];
+      if (s_done[s]) continue;
+      if (cs_cube != c) {
+        __syncthreads();
+        load_cube(cs, g, c);
+        if (threadIdx.x == 0) cs_cube = c;
+        __syncthreads();
+      }
+      const TV alpha = TV(s_alpha[s]);
+      const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
+      TV rz = TV(0), rr = TV(0);
+      for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
+        const int cell = 4 * q4;
+        TV xv[4], pv[4], rv[4], qv[4];
+        ld4(x + base + cell, xv);
+        ld4(pnew + base + cell, pv);
+        ld4(r + base + cell, rv);
+        ld4(q + base + cell, qv);
+        const int kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xv[e] = xv[e] + alpha * pv[e];
+          rv[e] = rv[e] - alpha * qv[e];
+          const TV z = rv[e] * cs.invtab[s3_of<B>(cs.w3, i0 + e, j, z0 + kk)];
+          rz += rv[e] * z;
+          rr += rv[e] * rv[e];
+        }
+        st4(x + base + cell, xv);
+        st4(r + base + cell, rv);
+      }
+      double vals[2] = {double(rz), double(rr)};
+      block_sum<NT, 2>(vals, red);
+      if (threadIdx.x == 0) {
+        acc_add(g.ss[s], ACC_SLOT_RZ + (k + 1) % 3, vals[0]);
+        acc_add(g.ss[s], ACC_SLOT_RR + (k + 1) % 3, vals[1]);
+      }
+    }
+    if (!grid_barrier(bar, err, limit)) break;
+  }
+  // the generation word keeps counting across launches: a block reads it before it
+  // arrives, so any start value works
+  if (blockIdx.x == 0 && threadIdx.x == 0) g.flags[0] = 1;
+}
+
+// ---------------------------------------------------------------- launcher
+
+template <int B>
+constexpr int pcg_threads() { return B == 16 ? 256 : (B == 8 ? 128 : 64); }
+
+// Largest co-resident grid for one kernel configuration.
+template <class K>
+static int max_coresident(K kern, int nt, size_t smem, int* out) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, nt, smem);
+  if (e != cudaSuccess) return (int)e;
+  *out = per * nsm;
+  return 0;
+}
+
+template <int B, int KS, class TV, class TX>
+static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
+  constexpr int NT = pcg_threads<B>();
+  // tile (16-byte multiple) + alpha, beta, rz, rz_prev (FP64) and done (byte) per sim
+  const size_t tile = (sizeof(TV) * Slab<B, KS>::N + 15) / 16 * 16;
+  const size_t sm = tile + (size_t)x.g.n_sims * (4 * sizeof(double) + 1);
+  auto kern = k_pcg<B, KS, NT, TV, TX>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  int maxg = 0;
+  int rc = max_coresident(kern, NT, sm, &maxg);
+  if (rc) return (cudaError_t)rc;
+  if (maxg < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int items = x.g.n_cubes * (B / KS);
+  const int per = (items + maxg - 1) / maxg;
+  const int grid = (items + per - 1) / per;
+  DevGrid gg = x.g;
+  TX* xp = xv;
+  TV* rp = (TV*)x.f.r;
+  TV* p0 = (TV*)x.f.p0;
+  TV* p1 = (TV*)x.f.p1;
+  TV* qp = (TV*)x.f.q;
+  SolveParams pp = prm;
+  unsigned int* bar = x.f.bar;
+  int* err = x.f.err;
+  void* args[] = {&gg, &xp, &rp, &p0, &p1, &qp, &pp, &bar, &err};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(NT), args, sm, x.stream);
+}
+
+template <class TV, class TX>
+static cudaError_t pcg_dispatch(const Ctx& x, const SolveParams& prm, TX* xv) {
+  // slab depth: whole cubes in FP32; half cubes in FP64 (smaller tiles, more blocks)
+  switch (x.B) {
+    case 4: return pcg_t<4, 4, TV, TX>(x, prm, xv);
+    case 8: return pcg_t<8, 8, TV, TX>(x, prm, xv);
+    case 16:
+      if (x.slabs_p == 2) return pcg_t<16, 8, TV, TX>(x, prm, xv);
+      if (x.slabs_p == 4) return pcg_t<16, 4, TV, TX>(x, prm, xv);
+      return pcg_t<16, 16, TV, TX>(x, prm, xv);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm) {
+  if (x.g.n_sims > kMaxPersistentSims) return cudaErrorInvalidValue;
+  return x.f64 ? pcg_dispatch<double, double>(x, prm, x.f.p)
+               : pcg_dispatch<float, float>(x, prm, x.f.e);
+}
+
+}  // namespace bcm

@@ -142,7 +142,7 @@ def test_step_mixed(name):
 def test_batched_ragged_sims():
     """Several sims of different sizes and kinds in one flattened cube list."""
     specs = [W.cavity(2, 8, re=400.0), W.sphere_channel(4, 2, 2, 8, radius=0.3),
-             W.cavity(3, 4, re=150.0), W.sphere_channel(2, 1, 1, 8, length=(2.0, 1.0, 1.0),
+             W.cavity(3, 8, re=150.0), W.sphere_channel(2, 1, 1, 8, length=(2.0, 1.0, 1.0),
                                                         radius=0.2, center=(0.6, 0.5, 0.5))]
     spec = W.concat(specs)
     state = W.initial_state(spec, seed=13, noise=1e-3)
@@ -172,7 +172,7 @@ def test_rotating_ellipsoids():
     compare_fields(g, ost, spec, TOL64)
     for e in range(3):
         assert abs(gst[0]["drag"][e] - ostats[0]["drag"][e]) <= 1e-8 * abs(ostats[0]["drag"][0])
-    phi_o = O.Oracle(spec).solid_fraction([3 * spec.sim_dt[0]])[0]
+    phi_o = O.Oracle(spec).solid_fraction([2 * spec.sim_dt[0]])[0]  # phi of the last step start
     assert rel_l2(g.numpy(bcm.PHI), phi_o) < 1e-12
 
 
@@ -235,3 +235,38 @@ def test_full_size_sphere_mixed_properties():
     vel64 = np.concatenate([g64.numpy(f) for f in (bcm.U, bcm.V, bcm.W)])
     assert rel_l2(vel32, vel64) <= TOL32
     assert rel_l2(g32.numpy(bcm.P), g64.numpy(bcm.P)) <= TOL32
+
+
+@pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
+def test_launch_shapes_agree(prec):
+    """Every PCG launch shape gives the oracle's result: the persistent cooperative
+    solver with 1, 2 or 4 z-slabs per work item, and the two-launch iteration with
+    its slab counts per pass.  Shapes differ only in the order of the dot sums."""
+    spec = W.sphere_channel(2, 1, 1, 16, length=(2.0, 1.0, 1.0), radius=0.2,
+                            center=(0.6, 0.5, 0.5))
+    state = W.initial_state(spec, seed=21, noise=1e-3)
+    ost, ostats = oracle_run(spec, state, 2, 1e-13)
+    tol = TOL64 if prec == bcm.PREC_F64 else TOL32
+    shapes = [(True, 1, 1), (True, 2, 1), (True, 4, 1),
+              (False, 1, 1), (False, 2, 4), (False, 4, 2), (False, 4, 4)]
+    for persistent, sa, sb in shapes:
+        g = gpu_grid(spec, prec, state)
+        g.set_launch(sa, sb, persistent=persistent)
+        st = g.step(2, rtol=1e-13 if prec == bcm.PREC_F64 else 1e-12)
+        compare_fields(g, ost, spec, tol, per_component=(prec == bcm.PREC_F64))
+        if prec == bcm.PREC_F64:
+            assert abs(st[0]["cg_iters"] - ostats[0]["cg_iters"]) <= 2
+
+
+def test_persistent_many_sims_and_fallback():
+    """Batched sims through the persistent solver, and the two-launch path that
+    grids with more sims than the persistent kernel holds fall back to."""
+    specs = [W.cavity(2, 8, re=200.0 + 50 * i) for i in range(5)]
+    spec = W.concat(specs)
+    state = W.initial_state(spec, seed=22, noise=1e-3)
+    ost, _ = oracle_run(spec, state, 2, 1e-13)
+    for persistent in (True, False):
+        g = gpu_grid(spec, bcm.PREC_F64, state)
+        g.set_launch(1, 1, persistent=persistent)
+        g.step(2, rtol=1e-13)
+        compare_fields(g, ost, spec, TOL64)
