@@ -393,8 +393,15 @@ def ncu_case(args):
     prec = bcm.PREC_F64 if args.ncu_fp64 else bcm.PREC_F32_REFINE
     g = bcm.Grid(spec, prec)
     g.set_solver(inner_rtol=args.inner_rtol)
+    if args.ncu_two_launch:
+        g.set_launch(1, 1, persistent=False)
     g.load_state(W.initial_state(spec))
-    st = g.step(2, rtol=RTOL)
+    if args.ncu_iters:
+        st = g.step(1, rtol=RTOL)
+        g.set_solver(max_cycles=1)
+        st = g.solve_pressure_iters(args.ncu_iters)
+    else:
+        st = g.step(2, rtol=RTOL)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": spec.name, "precision": prec, "stats": st[0]}))
 
@@ -410,6 +417,11 @@ def main():
                     help="run two mixed steps of the workload and exit (for ncu captures)")
     ap.add_argument("--ncu-fp64", action="store_true",
                     help="with --ncu-case: run the FP64 path instead")
+    ap.add_argument("--ncu-iters", type=int, default=0,
+                    help="with --ncu-case: after one warm step run exactly this many PCG "
+                         "iterations as one solve (one persistent PCG launch)")
+    ap.add_argument("--ncu-two-launch", action="store_true",
+                    help="with --ncu-case: two launches per PCG iteration")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="mixed mode: inner FP32 PCG reduction per cycle (0 = library default)")
     args = ap.parse_args()

@@ -158,9 +158,12 @@ bcm_status bcm_step(bcm_grid *grid, int n_steps, double rtol, int max_iter, bcm_
 /* Solver controls (defaults in brackets): inner_rtol, the relative reduction of the
  * FP32 inner PCG per defect-correction cycle in mixed mode [1e-5]; max_cycles, the
  * cap on FP64 residual evaluations per solve [30]; check_every, PCG iterations
- * between two reads of the device convergence flags by the host [8].  A value <= 0
+ * between two reads of the device convergence flags by the host [8];
+ * barrier_timeout_s, the longest wait of a block at a grid barrier of the
+ * persistent PCG before the solve gives up with BCM_E_TIMEOUT [2 s].  A value <= 0
  * keeps the current setting. */
-bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int check_every);
+bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int check_every,
+                          double barrier_timeout_s);
 
 /* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
  * whose blocks loop over the iterations with grid-wide barriers (default in mixed

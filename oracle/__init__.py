@@ -24,14 +24,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so next to its source (gcc, OpenMP, -O2)."""
+    """Compile liboracle.so next to its source (gcc, OpenMP, -O2, no FMA contraction)."""
     with _lock:
         if force or not os.path.exists(_LIB_PATH) or \
                 os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
                                                   os.path.getmtime(_SRC[:-2] + ".h")):
             tmp = _LIB_PATH + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",
-                                   "-o", tmp, _SRC, "-lm"])
+            # no FMA contraction: the same arithmetic on x86 and Arm hosts
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp",
+                                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -295,6 +295,7 @@ struct bcm_grid {
   double inner_rtol = 1e-5;  // mixed: inner FP32 PCG reduction per cycle
   int max_cycles = 30;       // mixed: FP64 residual evaluations per solve
   int check_every = 8;       // host-driven loops: iterations between flag reads
+  double barrier_timeout_s = 2.0;  // persistent PCG: longest grid-barrier wait
   KernelTimer timer;
   long long launch_count = 0;
   HostTables T;
@@ -575,7 +576,13 @@ bcm_status read_err(bcm_grid* g) {
   CUDA_TRY(cudaMemcpyAsync(&err, g->ws + g->L.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (err) {
+    // a timed-out solve leaves barrier and ticket counters mid-count: start them afresh
     CUDA_TRY(cudaMemsetAsync(g->ws + g->L.err, 0, sizeof(int), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->ws + g->L.bar, 0, sizeof(unsigned int) * (kTicketWords + 32),
+                             g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->ws + g->L.counter, 0, sizeof(unsigned int) * kTicketWords,
+                             g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
     return fail(BCM_E_TIMEOUT, "a grid barrier of the persistent PCG timed out");
   }
   return BCM_OK;
@@ -594,7 +601,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   prm.mixed = g->f64 ? 0 : 1;
   prm.guard = x.f.guard;
   prm.guard_limit = 0;
-  prm.barrier_timeout_ns = 2000000000ull;
+  prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
   RUN(BCM_K_MISC, launch_solve_begin(x));
   RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
   int flags[2] = {0, 0};
@@ -602,7 +609,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   if (x.persistent) {
     if (g->f64) {
       RUN(BCM_K_PCG, launch_pcg(x, prm));
-      return BCM_OK;
+      return read_err(g);
     }
     // defect correction: cycles are issued in batches; a finished sim makes every
     // kernel of a later cycle return at once, so the host reads the flags rarely
@@ -614,6 +621,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
         RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
       }
       if ((st = read_flags(g, flags)) != BCM_OK) return st;
+      if ((st = read_err(g)) != BCM_OK) return st;
       if (flags[1]) break;
       batch = 1;
     }
@@ -733,7 +741,7 @@ extern "C" bcm_status bcm_profile_read(bcm_grid* g, double* total_ms, int64_t* l
 }
 
 extern "C" bcm_status bcm_set_solver(bcm_grid* g, double inner_rtol, int max_cycles,
-                                     int check_every) {
+                                     int check_every, double barrier_timeout_s) {
   if (!g) return fail(BCM_E_INVALID, "grid is NULL");
   if (inner_rtol > 0) {
     if (!(inner_rtol < 1.0)) return fail(BCM_E_INVALID, "inner_rtol must be < 1");
@@ -741,6 +749,7 @@ extern "C" bcm_status bcm_set_solver(bcm_grid* g, double inner_rtol, int max_cyc
   }
   if (max_cycles > 0) g->max_cycles = max_cycles;
   if (check_every > 0) g->check_every = check_every;
+  if (barrier_timeout_s > 0) g->barrier_timeout_s = barrier_timeout_s;
   return BCM_OK;
 }
 

@@ -270,3 +270,21 @@ def test_persistent_many_sims_and_fallback():
         g.set_launch(1, 1, persistent=persistent)
         g.step(2, rtol=1e-13)
         compare_fields(g, ost, spec, TOL64)
+
+
+def test_barrier_timeout_reported_and_recovered():
+    """A grid-barrier wait that runs out (a 1 ns limit) ends the persistent solve with
+    BCM_E_TIMEOUT instead of waiting; the next solve with the normal limit is exact."""
+    spec = W.cavity(2, 8)
+    state = W.initial_state(spec, 5, 1e-2)
+    g = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
+    g.set_launch(1, 1, persistent=True)
+    g.set_solver(barrier_timeout_s=1e-9)
+    with pytest.raises(bcm.BCMError) as ei:
+        g.step(1, rtol=1e-12)
+    assert ei.value.status == bcm.BCM_E_TIMEOUT
+    g.set_solver(barrier_timeout_s=2.0)
+    g.load_state(state)
+    g.step(2, rtol=1e-12)
+    ost, _ = oracle_run(spec, state, 2, 1e-13)
+    compare_fields(g, ost, spec, TOL32, per_component=False)
