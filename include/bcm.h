@@ -186,6 +186,25 @@ bcm_status bcm_solve_pressure(bcm_grid *grid, double rtol, int max_iter, bcm_sta
  * The field is converted to FP64. */
 bcm_status bcm_fill_halo(bcm_grid *grid, int field, int kind, double *dev_out);
 
+/* Pressure solve that allocates no memory, for callers that cannot allocate device
+ * memory at the moment they solve: code running while a CUDA graph is captured, an
+ * application that reserves all GPU memory up front for its own pool, or a plugin
+ * that must not call the allocator.  There is no counterpart in the paper: it is the
+ * FP64 Jacobi-PCG of bcm_solve_pressure with its working memory (CG vectors, per-sim
+ * solver state, block counters) in one fixed 32 MiB array inside the library's
+ * device image instead of the grid workspace.  dev_b: right-hand side (FP64, grid
+ * layout, read); dev_p: start value in, solution out (FP64, grid layout); the
+ * grid's own fields are not touched.  The grid's device must be current.
+ * Limits and sharing: grids needing more than 32 MiB (4 FP64 vectors, i.e. about
+ * 1M cells, plus per-sim state) are rejected with BCM_E_BOUNDS; single-level grids
+ * only.  The array stays allocated on every GPU that loads the library until the
+ * process exits, and every call reuses it: calls that overlap on the GPU (other
+ * streams or host threads on the same device) race.  The first call on each device
+ * looks up the array's device address; make that first call before any stream
+ * capture.  Synchronises the grid's stream; stats as in bcm_solve_pressure. */
+bcm_status bcm_solve_pressure_static(bcm_grid *grid, const double *dev_b, double *dev_p,
+                                     double rtol, int max_iter, bcm_stats *stats);
+
 /* y = K x with K = -V A the flux-form pressure operator of Eq. poisson (FP64). */
 bcm_status bcm_apply_poisson(bcm_grid *grid, const double *dev_x, double *dev_y);
 

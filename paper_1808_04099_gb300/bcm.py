@@ -22,7 +22,8 @@ PREC_F64, PREC_F32_REFINE = 0, 1
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
             "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch", "bcm_step", "bcm_solve_pressure",
-            "bcm_fill_halo", "bcm_apply_poisson", "bcm_profile", "bcm_profile_read",
+            "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
+            "bcm_profile", "bcm_profile_read",
             "bcm_last_error"]
 KERNEL_NAMES = ["solid_fraction", "momentum", "rhs", "residual", "cg_a", "cg_b",
                 "add_correction", "correct", "misc", "pcg"]
@@ -87,6 +88,7 @@ def lib(build: bool = True):
         L.bcm_solve_pressure.argtypes = [P, C.c_double, C.c_int, P]
         L.bcm_fill_halo.argtypes = [P, C.c_int, C.c_int, P]
         L.bcm_apply_poisson.argtypes = [P, P, P]
+        L.bcm_solve_pressure_static.argtypes = [P, P, P, C.c_double, C.c_int, P]
         L.bcm_profile.argtypes = [P, C.c_int]
         L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
         L.bcm_last_error.restype = C.c_char_p

@@ -358,6 +358,15 @@ bcm_status drain_timer(bcm_grid* g) {
 
 }  // namespace
 
+// Read-only views of a grid for other translation units of the library.
+namespace bcm {
+const Ctx* grid_ctx(const bcm_grid* g) { return &g->ctx; }
+int grid_two_level(const bcm_grid* g) { return g->T.two_level; }
+int grid_device(const bcm_grid* g) { return g->device; }
+cudaStream_t grid_stream(const bcm_grid* g) { return g->stream; }
+bcm_status grid_fail(bcm_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace bcm
+
 // ------------------------------------------------------------------ ABI
 
 extern "C" const char* bcm_last_error(void) { return g_last_error.c_str(); }
