@@ -598,8 +598,6 @@ bcm_status read_err(bcm_grid* g) {
 }
 
 bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
-  if (g->T.two_level)
-    return fail(BCM_E_INVALID, "the flux-form 2:1 Poisson kernels are not available");
   Ctx& x = g->ctx;
   SolveParams prm{};
   prm.rtol = rtol;
@@ -806,7 +804,6 @@ extern "C" bcm_status bcm_fill_halo(bcm_grid* g, int field, int kind, double* de
 
 extern "C" bcm_status bcm_apply_poisson(bcm_grid* g, const double* x, double* y) {
   if (!g || !x || !y) return fail(BCM_E_INVALID, "NULL argument");
-  if (g->T.two_level) return fail(BCM_E_INVALID, "the flux-form 2:1 operator is not available");
   RUN(BCM_K_MISC, launch_apply_poisson(g->ctx, x, y));
   return BCM_OK;
 }

@@ -32,6 +32,8 @@ struct CubeSh {
   int w3[6];        // Jacobi face weights (thirds) of this cube
   int nbw3[6][6];   // ... of each same-level neighbour
   int bc[6];        // the sim's domain-face conditions
+  int has21;        // some face of this cube is a 2:1 level interface
+  TV wt[6];         // flux weight of a face relative to a same-level face: 1, 2/3, 4/3
   TV invtab[kW3];   // 1 / diag(K) by face-weight sum
 };
 
@@ -41,9 +43,18 @@ __device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int 
   const int t = threadIdx.x;
   const SimParams& sp = g.sp[g.sim[c]];
   if (t < 6) {
-    cs.nb[t] = g.nb[6 * c + t];
+    const int n = g.nb[6 * c + t];
+    cs.nb[t] = n;
     cs.w3[t] = g.w3[6 * c + t];
     cs.bc[t] = sp.bc[t];
+    // R7: a fine face towards a coarse cube carries A/d = h_f / 1.5, a coarse face
+    // towards four fine cubes 4 (h_f^2 / 0.75 h_c) = (4/3) h_c
+    cs.wt[t] = n == NB_COARSE ? TV(2.0 / 3.0) : (n == NB_FINE ? TV(4.0 / 3.0) : TV(1));
+  }
+  if (t == 0) {
+    int any = 0;
+    for (int f = 0; f < 6; ++f) any |= g.nb[6 * c + f] < NB_BOUNDARY;
+    cs.has21 = any;
   }
   if (t < 36) cs.nbw3[t / 6][t - 6 * (t / 6)] = g.nbw3[36 * c + t];
   if (t < kW3) cs.invtab[t] = TV(sp.invdiag[g.lvl[c]][t]);
@@ -55,6 +66,36 @@ __device__ __forceinline__ int s3_of(const int* w3, int i, int j, int k) {
   return 18 + (i == 0 ? w3[0] - 3 : 0) + (i == B - 1 ? w3[1] - 3 : 0) +
          (j == 0 ? w3[2] - 3 : 0) + (j == B - 1 ? w3[3] - 3 : 0) +
          (k == 0 ? w3[4] - 3 : 0) + (k == B - 1 ? w3[5] - 3 : 0);
+}
+
+// 1 / diag(K) of a cell of any cube, from the global tables (2:1 neighbours).
+template <int B, class TV>
+__device__ __forceinline__ TV inv_diag_any(const DevGrid& g, int cube, int cell) {
+  const int i = cell % B, j = (cell / B) % B, k = cell / (B * B);
+  return TV(g.sp[g.sim[cube]].invdiag[g.lvl[cube]][s3_of<B>(g.w3 + 6 * cube, i, j, k)]);
+}
+
+// Poisson ghost across a 2:1 face f of cube c at tangential (a, b) (R7): the coarse
+// cell across the face (fine side), or the mean of the four fine cells that touch
+// the coarse face cell (coarse side).  valg(cube, cell) is the field value.
+template <int B, class TV, class ValG>
+__device__ __forceinline__ TV poisson_ghost_21(const DevGrid& g, int c, int f, int a, int b,
+                                               int code, const ValG& valg) {
+  const int d = f >> 1, side = f & 1;
+  if (code == NB_COARSE) {
+    const int C = g.aux[(6 * c + f) * 4];
+    const int sf = 1 << (g.max_level - g.lvl[c]), sc = 2 * sf;
+    const int A = (g.ijk[3 * c + tan1(d)] + a * sf - g.ijk[3 * C + tan1(d)]) / sc;
+    const int Bb = (g.ijk[3 * c + tan2(d)] + b * sf - g.ijk[3 * C + tan2(d)]) / sc;
+    return valg(C, cell_of<B>(d, side ? 0 : B - 1, A, Bb));
+  }
+  const int qa = (2 * a) / B, qb = (2 * b) / B;
+  const int F = g.aux[(6 * c + f) * 4 + qb * 2 + qa];
+  const int fa = 2 * a - qa * B, fb = 2 * b - qb * B;
+  TV sum = TV(0);
+  for (int bb = 0; bb < 2; ++bb)
+    for (int aa = 0; aa < 2; ++aa) sum += valg(F, cell_of<B>(d, side ? 0 : B - 1, fa + aa, fb + bb));
+  return TV(0.25) * sum;
 }
 
 // Tile positions of face f's ghost cell and of its mirror interior cell at (a, b).
@@ -88,9 +129,10 @@ __device__ __forceinline__ int mirror_pos(int f, int a, int b) {
 //   nbv(f, n, cell)          -> a cell of same-level neighbour n across face f;
 // domain faces get the pressure ghost (mirror, or minus the mirror at outflow).
 // Ends with the tile complete and the block synchronised.
-template <int B, int NT, class TV, class Own, class Nbv>
+template <int B, int NT, class TV, class Own, class Nbv, class ValG>
 __device__ __forceinline__ void stage_pressure_cube(TV* __restrict__ S, const CubeSh<TV>& cs,
-                                                    const Own& own4, const Nbv& nbv) {
+                                                    const DevGrid& g, int c, const Own& own4,
+                                                    const Nbv& nbv, const ValG& valg) {
   using SL = Slab<B, B>;
   constexpr int B3 = B * B * B, BB = B * B;
   for (int q4 = threadIdx.x; q4 < B3 / 4; q4 += NT) {
@@ -107,6 +149,7 @@ __device__ __forceinline__ void stage_pressure_cube(TV* __restrict__ S, const Cu
     const int f = idx / BB, t = idx - f * BB, b = t / B, a = t - b * B;
     const int n = cs.nb[f];
     if (n >= 0) S[ghost_pos<B>(f, a, b)] = nbv(f, n, cell_of<B>(f >> 1, (f & 1) ? 0 : B - 1, a, b));
+    else if (n < NB_BOUNDARY) S[ghost_pos<B>(f, a, b)] = poisson_ghost_21<B, TV>(g, c, f, a, b, n, valg);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < 6 * BB; idx += NT) {
@@ -126,10 +169,11 @@ __device__ __forceinline__ void stage_pressure_cube(TV* __restrict__ S, const Cu
 //   val1(face, n, cell)          -> one cell of same-level neighbour n across face;
 // domain faces get the pressure ghost (mirror, or minus the mirror at outflow).
 // Ends with the tile complete and the block synchronised.
-template <int B, int KS, int NT, class TV, class Val4, class Val1>
+template <int B, int KS, int NT, class TV, class Val4, class Val1, class ValG>
 __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const CubeSh<TV>& cs,
-                                                    int c, int z0, const Val4& val4,
-                                                    const Val1& val1) {
+                                                    const DevGrid& g, int c, int z0,
+                                                    const Val4& val4, const Val1& val1,
+                                                    const ValG& valg) {
   using SL = Slab<B, KS>;
   constexpr int BB = B * B, Q = BB / 4;
   for (int idx = threadIdx.x; idx < (KS + 2) * Q; idx += NT) {
@@ -142,8 +186,14 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
       val4(c, k * BB + 4 * q, -1, v);
     } else {
       const int f = k < 0 ? 4 : 5, n = cs.nb[f];
-      if (n >= 0) val4(n, (k < 0 ? B - 1 : 0) * BB + 4 * q, f, v);
-      else have = false;
+      if (n >= 0) {
+        val4(n, (k < 0 ? B - 1 : 0) * BB + 4 * q, f, v);
+      } else if (n < NB_BOUNDARY) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) v[m] = poisson_ghost_21<B, TV>(g, c, f, i0 + m, j, n, valg);
+      } else {
+        have = false;
+      }
     }
     if (have) {
       const int o = SL::at(i0, j, kk);
@@ -158,6 +208,9 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
     const int n = cs.nb[f];
     if (n >= 0) {
       const TV v = val1(f, n, cell_of<B>(f >> 1, (f & 1) ? 0 : B - 1, t, z0 + kk));
+      S[f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1)] = v;
+    } else if (n < NB_BOUNDARY) {
+      const TV v = poisson_ghost_21<B, TV>(g, c, f, t, z0 + kk, n, valg);
       S[f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1)] = v;
     }
   }
@@ -193,6 +246,25 @@ __device__ __forceinline__ TV stencil_sum(const TV* __restrict__ S, int o) {
   const TV pc = S[o];
   return (pc - S[o - 1]) + (pc - S[o + 1]) + (pc - S[o - SL::P]) + (pc - S[o + SL::P]) +
          (pc - S[o - SL::P * SL::P]) + (pc - S[o + SL::P * SL::P]);
+}
+
+// The K stencil sum with 2:1 faces weighted (R7): cell (i, j, k) of the cube (k is the
+// cube's plane index), tile position o.
+template <int B, class TV, int KS = B>
+__device__ __forceinline__ TV stencil_sum_w(const TV* __restrict__ S, int o, const CubeSh<TV>& cs,
+                                            int i, int j, int k) {
+  using SL = Slab<B, KS>;
+  TV acc = stencil_sum<B, TV, KS>(S, o);
+  if (cs.has21) {
+    const TV pc = S[o];
+    if (i == 0) acc += (cs.wt[0] - TV(1)) * (pc - S[o - 1]);
+    if (i == B - 1) acc += (cs.wt[1] - TV(1)) * (pc - S[o + 1]);
+    if (j == 0) acc += (cs.wt[2] - TV(1)) * (pc - S[o - SL::P]);
+    if (j == B - 1) acc += (cs.wt[3] - TV(1)) * (pc - S[o + SL::P]);
+    if (k == 0) acc += (cs.wt[4] - TV(1)) * (pc - S[o - SL::P * SL::P]);
+    if (k == B - 1) acc += (cs.wt[5] - TV(1)) * (pc - S[o + SL::P * SL::P]);
+  }
+  return acc;
 }
 
 }  // namespace bcm

@@ -9,6 +9,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "bcm_cube.cuh"
 #include "bcm_internal.cuh"
 #include "bcm_kernels.h"
 
@@ -359,8 +360,9 @@ __global__ __launch_bounds__(NT) void k_rhs(DevGrid g, const T* __restrict__ us,
   const T* Sf[3] = {S0, S1, S2};
   const double hd = cell_h<B>(g, c);
   const double scale = 1.0 / (hd * sp.dt);
-  bool bnd[6];
-  for (int f = 0; f < 6; ++f) bnd[f] = g.nb[6 * c + f] == NB_BOUNDARY;
+  int code[6];
+  for (int f = 0; f < 6; ++f) code[f] = g.nb[6 * c + f];
+  const T* const comps[3] = {us, vs, ws};
   double bsum = 0.0;
   for (int q = threadIdx.x; q < KS * B * B; q += NT) {
     const int kk = q / (B * B), rem = q - kk * B * B, j = rem / B, i = rem - j * B;
@@ -374,23 +376,33 @@ __global__ __launch_bounds__(NT) void k_rhs(DevGrid g, const T* __restrict__ us,
       const T* Sd = Sf[d];
       const int e = off[d];
       const int a = ii[tan1(d)], bb = ii[tan2(d)];
-      T Um, Up;
-      if (ii[d] == 0 && bnd[2 * d]) {
-        const int f = 2 * d, bc = sp.bc[f];
-        Um = bc == BC_SLIP ? T(0)
-             : bc == BC_OUTFLOW ? ub[((size_t)(g.slot[6 * c + f] * 3 + d) * B + bb) * B + a]
-                                : T(face_velocity<B>(g, c, f, d, a, bb));
-      } else {
-        Um = T(0.5) * (Sd[o - e] + Sd[o]);
+      // normal velocity through the low (side 0) and high (side 1) face of the cell
+      T U2[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * d + side;
+        const bool on_face = side ? (ii[d] == B - 1) : (ii[d] == 0);
+        const T other = side ? Sd[o + e] : Sd[o - e];
+        if (on_face && code[f] == NB_BOUNDARY) {
+          const int bc = sp.bc[f];
+          U2[side] = bc == BC_SLIP ? T(0)
+                     : bc == BC_OUTFLOW ? ub[((size_t)(g.slot[6 * c + f] * 3 + d) * B + bb) * B + a]
+                                        : T(face_velocity<B>(g, c, f, d, a, bb));
+        } else if (on_face && code[f] == NB_COARSE) {
+          // fine cell, coarse neighbour: linear between the two centres (R7), the
+          // staged halo holds the coarse cell
+          U2[side] = (T(2) * Sd[o] + other) / T(3);
+        } else if (on_face && code[f] == NB_FINE) {
+          // coarse cell, four fine neighbours: area mean of the four sub-face values
+          const T* comp = comps[d];
+          auto valg = [&](int cube, int cell) { return comp[(size_t)cube * B3 + cell]; };
+          const T m4 = poisson_ghost_21<B, T>(g, c, f, a, bb, NB_FINE, valg);
+          U2[side] = (T(2) * m4 + Sd[o]) / T(3);
+        } else {
+          U2[side] = side ? T(0.5) * (Sd[o] + other) : T(0.5) * (other + Sd[o]);
+        }
       }
-      if (ii[d] == B - 1 && bnd[2 * d + 1]) {
-        const int f = 2 * d + 1, bc = sp.bc[f];
-        Up = bc == BC_SLIP ? T(0)
-             : bc == BC_OUTFLOW ? ub[((size_t)(g.slot[6 * c + f] * 3 + d) * B + bb) * B + a]
-                                : T(face_velocity<B>(g, c, f, d, a, bb));
-      } else {
-        Up = T(0.5) * (Sd[o] + Sd[o + e]);
-      }
+      const T Um = U2[0], Up = U2[1];
       div = div - Um;
       div = div + Up;
     }

@@ -206,7 +206,12 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
         const TV z = r[gi] * cs.invtab[s3_of<B>(cs.nbw3[f], i, j, kz)];
         return first ? z : z + beta * pold[gi];
       };
-      stage_pressure_slab<B, KS, NT, TV>(S, cs, c, z0, val4, val1);
+      auto valg = [&](int n, int cell) {
+        const size_t gi = (size_t)n * B3 + cell;
+        const TV z = r[gi] * inv_diag_any<B, TV>(g, n, cell);
+        return first ? z : z + beta * pold[gi];
+      };
+      stage_pressure_slab<B, KS, NT, TV>(S, cs, g, c, z0, val4, val1, valg);
       const TV h = TV(cell_h<B>(g, c));
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
       TV part = TV(0);
@@ -217,7 +222,7 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           pc[m] = S[o + m];
-          qv[m] = h * stencil_sum<B, TV, KS>(S, o + m);
+          qv[m] = h * stencil_sum_w<B, TV, KS>(S, o + m, cs, i0 + m, j, z0 + kk);
           part += pc[m] * qv[m];
         }
         st4(pnew + base + cell, pc);

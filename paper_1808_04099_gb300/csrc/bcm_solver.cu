@@ -52,7 +52,8 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
     const size_t base = (size_t)c * B3;
     auto own4 = [&](int q4, int, int, int, double (&v)[4]) { ld4(x + base + 4 * q4, v); };
     auto nbv = [&](int, int n, int cell) { return x[(size_t)n * B3 + cell]; };
-    stage_pressure_cube<B, NT, double>(S, cs, own4, nbv);
+    auto valg = [&](int n, int cell) { return x[(size_t)n * B3 + cell]; };
+    stage_pressure_cube<B, NT, double>(S, cs, g, c, own4, nbv, valg);
     const double hd = cell_h<B>(g, c), V = hd * hd * hd, mean = st.bmean;
     float rz32 = 0.f, rr32 = 0.f;
     for (int q4 = threadIdx.x; q4 < B3 / 4; q4 += NT) {
@@ -64,7 +65,7 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const double rhs = -V * (bv[m] - mean);
-        rv[m] = rhs - hd * stencil_sum<B>(S, o + m);
+        rv[m] = rhs - hd * stencil_sum_w<B>(S, o + m, cs, i0 + m, j, k);
         acc4[0] += rhs * rhs;
       }
       if (MIXED) {
@@ -209,7 +210,12 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
       const TV z = r[gi] * cs.invtab[s3_of<B>(cs.nbw3[f], i, j, k)];
       return first ? z : z + beta * pold[gi];
     };
-    stage_pressure_slab<B, KS, NT, TV>(S, cs, c, z0, val4, val1);
+    auto valg = [&](int n, int cell) {
+      const size_t gi = (size_t)n * B3 + cell;
+      const TV z = r[gi] * inv_diag_any<B, TV>(g, n, cell);
+      return first ? z : z + beta * pold[gi];
+    };
+    stage_pressure_slab<B, KS, NT, TV>(S, cs, g, c, z0, val4, val1, valg);
     const TV h = TV(cell_h<B>(g, c));
     const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
     TV part = TV(0);
@@ -220,7 +226,7 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         pc[m] = S[o + m];
-        qv[m] = h * stencil_sum<B, TV, KS>(S, o + m);
+        qv[m] = h * stencil_sum_w<B, TV, KS>(S, o + m, cs, i0 + m, j, z0 + kk);
         part += pc[m] * qv[m];
       }
       st4(pnew + base + cell, pc);
@@ -396,7 +402,8 @@ __global__ __launch_bounds__(NT) void k_correct(DevGrid g, double* __restrict__ 
     }
   };
   auto nbv = [&](int, int n, int cell) { return zero ? 0.0 : p[(size_t)n * B3 + cell]; };
-  stage_pressure_cube<B, NT, double>(S, cs, own4, nbv);
+  auto valg = [&](int n, int cell) { return zero ? 0.0 : p[(size_t)n * B3 + cell]; };
+  stage_pressure_cube<B, NT, double>(S, cs, g, c, own4, nbv, valg);
   const double hd = cell_h<B>(g, c);
   const double ih = 1.0 / hd, ih2 = ih * ih;
   const T cdt = T(0.5 * sp.dt);
@@ -418,9 +425,14 @@ __global__ __launch_bounds__(NT) void k_correct(DevGrid g, double* __restrict__ 
     for (int m = 0; m < 4; ++m) {
       const double pc = S[o + m];
       double lap = 0.0;
+      const int ii[3] = {i0 + m, j, k};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const double dm = pc - S[o + m - off[d]], dp = S[o + m + off[d]] - pc;
+        double dm = pc - S[o + m - off[d]], dp = S[o + m + off[d]] - pc;
+        if (cs.has21) {  // 2:1 faces: gradient over the distance 0.75 h_c (R7)
+          if (ii[d] == 0) dm *= double(cs.wt[2 * d]);
+          if (ii[d] == B - 1) dp *= double(cs.wt[2 * d + 1]);
+        }
         lap += dp - dm;
         const T nv = sv[d][m] - cdt * T((dm + dp) * ih);
         sv[d][m] = nv;
@@ -465,14 +477,15 @@ __global__ __launch_bounds__(NT) void k_apply_poisson(DevGrid g, const double* _
   const size_t base = (size_t)c * B3;
   auto own4 = [&](int q4, int, int, int, double (&v)[4]) { ld4(x + base + 4 * q4, v); };
   auto nbv = [&](int, int n, int cell) { return x[(size_t)n * B3 + cell]; };
-  stage_pressure_cube<B, NT, double>(S, cs, own4, nbv);
+  auto valg = [&](int n, int cell) { return x[(size_t)n * B3 + cell]; };
+  stage_pressure_cube<B, NT, double>(S, cs, g, c, own4, nbv, valg);
   const double h = cell_h<B>(g, c);
   for (int q4 = threadIdx.x; q4 < B3 / 4; q4 += NT) {
     const int cell = 4 * q4, i0 = cell % B, j = (cell / B) % B, k = cell / BB;
     const int o = SL::at(i0, j, k + 1);
     double yv[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) yv[m] = h * stencil_sum<B>(S, o + m);
+    for (int m = 0; m < 4; ++m) yv[m] = h * stencil_sum_w<B>(S, o + m, cs, i0 + m, j, k);
     st4(y + base + cell, yv);
   }
 }

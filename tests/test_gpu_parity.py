@@ -59,6 +59,7 @@ HALO_SPECS = {
     "channel": lambda: W.sphere_channel(4, 2, 2, 8),
     "two_level": lambda: W.two_level_channel(4, 2, 2, 8, (1, 0, 0), (3, 2, 2), 1 / 16., 0),
     "B16": lambda: W.sphere_channel(2, 1, 1, 16, length=(2.0, 1.0, 1.0)),
+    "two_level_3d": lambda: W.two_level_channel(4, 4, 4, 8, (1, 1, 1), (3, 3, 3), 1 / 16., 0),
 }
 
 
@@ -79,7 +80,8 @@ def test_halo_fill_bitwise(name):
         assert np.array_equal(got, want), (name, kind, np.abs(got - want).max())
 
 
-@pytest.mark.parametrize("name", ["periodic", "cavity", "channel", "B16"])
+@pytest.mark.parametrize("name", ["periodic", "cavity", "channel", "B16", "two_level",
+                                  "two_level_3d"])
 def test_poisson_operator(name):
     spec = HALO_SPECS[name]()
     x = np.random.default_rng(8).standard_normal(spec.n_cells)
@@ -88,7 +90,7 @@ def test_poisson_operator(name):
     assert rel_l2(y, O.Oracle(spec).apply_poisson(x)) < 1e-14
 
 
-@pytest.mark.parametrize("name", ["cavity", "channel", "B16"])
+@pytest.mark.parametrize("name", ["cavity", "channel", "B16", "two_level_3d"])
 def test_pressure_solve(name):
     spec = HALO_SPECS[name]()
     b = np.random.default_rng(9).standard_normal(spec.n_cells)
@@ -288,3 +290,34 @@ def test_barrier_timeout_reported_and_recovered():
     g.step(2, rtol=1e-12)
     ost, _ = oracle_run(spec, state, 2, 1e-13)
     compare_fields(g, ost, spec, TOL32, per_component=False)
+
+
+def two_level_with_bodies():
+    """A channel refined 2:1 in all three directions around a fixed sphere and a
+    rotating, translating ellipsoid (both inside the refined block)."""
+    spec = W.two_level_channel(4, 4, 4, 8, (1, 1, 1), (3, 3, 3), 1 / 16., 0)
+    spec.bodies = [[W.Body(W.BODY_SPHERE, np.array([0.9, 1.0, 1.0]), np.array([0.22] * 3)),
+                    W.Body(W.BODY_ELLIPSOID, np.array([1.25, 0.9, 1.1]),
+                           np.array([0.12, 0.07, 0.09]), np.array([0.9, 0.1, 0.3, 0.3]) /
+                           np.linalg.norm([0.9, 0.1, 0.3, 0.3]), np.array([0.4, -1.0, 0.6]),
+                           np.array([0.02, 0.0, 0.0]))]]
+    return spec
+
+
+@pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
+def test_two_level_step(prec):
+    """The full step on a two-level grid: paper halos for momentum, flux-form Poisson
+    at the 2:1 faces, bodies in the refined block, against the oracle."""
+    spec = two_level_with_bodies()
+    state = W.initial_state(spec, seed=23, noise=1e-3)
+    ost, ostats = oracle_run(spec, state, 3, 1e-13)
+    g = gpu_grid(spec, prec, state)
+    st = g.step(3, rtol=1e-13 if prec == bcm.PREC_F64 else 1e-12)
+    assert st[0]["converged"] == 1
+    if prec == bcm.PREC_F64:
+        compare_fields(g, ost, spec, TOL64)
+        assert abs(st[0]["cg_iters"] - ostats[0]["cg_iters"]) <= 2
+        for e in range(3):
+            assert abs(st[0]["drag"][e] - ostats[0]["drag"][e]) <= 1e-8 * abs(ostats[0]["drag"][0])
+    else:
+        compare_fields(g, ost, spec, TOL32, per_component=False)
