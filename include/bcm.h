@@ -155,6 +155,16 @@ bcm_status bcm_reset_time(bcm_grid *grid);
  * stats: host array [n_sims] or NULL (then nothing is synchronised). */
 bcm_status bcm_step(bcm_grid *grid, int n_steps, double rtol, int max_iter, bcm_stats *stats);
 
+/* bcm_step as a CUDA graph.  The first call (and any call whose rtol, max_iter or
+ * solver settings differ from the captured ones) captures one step on a library
+ * stream and instantiates it; every call then launches the graph n_steps times on
+ * the grid's stream, with no host synchronisation unless stats is non-NULL.  The
+ * captured step uses the persistent PCG (grids of at most 256 sims) and, in mixed
+ * mode, a fixed budget of 4 defect-correction cycles per solve (cycles after a sim
+ * has converged return at once; a sim needing more is reported not converged). */
+bcm_status bcm_step_graph(bcm_grid *grid, int n_steps, double rtol, int max_iter,
+                          bcm_stats *stats);
+
 /* Solver controls (defaults in brackets): inner_rtol, the relative reduction of the
  * FP32 inner PCG per defect-correction cycle in mixed mode [1e-5]; max_cycles, the
  * cap on FP64 residual evaluations per solve [30]; check_every, PCG iterations

@@ -21,7 +21,8 @@ PREC_F64, PREC_F32_REFINE = 0, 1
 (U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
-            "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch", "bcm_step", "bcm_solve_pressure",
+            "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch",
+            "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
             "bcm_last_error"]
@@ -85,6 +86,7 @@ def lib(build: bool = True):
         L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_double]
         L.bcm_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
         L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
+        L.bcm_step_graph.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
         L.bcm_solve_pressure.argtypes = [P, C.c_double, C.c_int, P]
         L.bcm_fill_halo.argtypes = [P, C.c_int, C.c_int, P]
         L.bcm_apply_poisson.argtypes = [P, P, P]
@@ -220,6 +222,14 @@ class Grid:
              allow_not_converged: bool = False) -> Optional[List[dict]]:
         st = (Stats * self.spec.n_sims)() if stats else None
         rc = lib().bcm_step(self._h, n, rtol, max_iter, st)
+        _check(rc, (BCM_E_NOT_CONVERGED,) if allow_not_converged else ())
+        return [s.as_dict() for s in st] if stats else None
+
+    def step_graph(self, n: int = 1, rtol: float = 1e-10, max_iter: int = 20000,
+                   stats: bool = True, allow_not_converged: bool = False):
+        """n steps by replaying a captured CUDA graph of one step."""
+        st = (Stats * self.spec.n_sims)() if stats else None
+        rc = lib().bcm_step_graph(self._h, n, rtol, max_iter, st)
         _check(rc, (BCM_E_NOT_CONVERGED,) if allow_not_converged else ())
         return [s.as_dict() for s in st] if stats else None
 

@@ -290,8 +290,20 @@ struct KernelTimer {
   long long launches[BCM_NKERNELS] = {};
 };
 
+struct StepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  double rtol = 0.0;
+  int max_iter = 0, cycles = 0;
+  double inner_rtol = 0.0;
+  int persistent_slabs = 0;
+};
+
 struct bcm_grid {
   bcm_grid_desc desc;
+  StepGraph sg;
+  int graph_cycles = 4;      // graph steps: defect-correction cycles per solve (mixed)
   double inner_rtol = 1e-5;  // mixed: inner FP32 PCG reduction per cycle
   int max_cycles = 30;       // mixed: FP64 residual evaluations per solve
   int check_every = 8;       // host-driven loops: iterations between flag reads
@@ -486,6 +498,9 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
 extern "C" bcm_status bcm_destroy_grid(bcm_grid* g) {
   if (g) {
     for (cudaEvent_t e : g->timer.pool) cudaEventDestroy(e);
+    if (g->sg.exec) cudaGraphExecDestroy(g->sg.exec);
+    if (g->sg.graph) cudaGraphDestroy(g->sg.graph);
+    if (g->sg.capture_stream) cudaStreamDestroy(g->sg.capture_stream);
   }
   delete g;
   return BCM_OK;
@@ -717,6 +732,85 @@ extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_it
   }
   if (stats) last = collect(g, stats);
   return last;
+}
+
+// One step as a CUDA graph: no host synchronisation inside.  The PCG is the
+// persistent kernel (one launch per solve); mixed mode issues a fixed budget of
+// defect-correction cycles whose kernels return at once for sims already converged.
+namespace {
+bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_iter, int cycles) {
+  Ctx x = g->ctx;
+  x.stream = s;
+  bool moving = false;
+  for (const auto& p : g->T.sp) moving |= (p.n_bodies > 0 && p.moving);
+  SolveParams prm{};
+  prm.rtol = rtol;
+  prm.inner_rtol = g->inner_rtol;
+  prm.max_iter = max_iter;
+  prm.inner_max_iter = max_iter;
+  prm.max_cycles = cycles;
+  prm.mixed = g->f64 ? 0 : 1;
+  prm.guard = x.f.guard;
+  prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
+  if (moving) CUDA_TRY(launch_solid_fraction(x, -2));
+  CUDA_TRY(launch_momentum(x));
+  CUDA_TRY(launch_rhs(x));
+  CUDA_TRY(launch_solve_begin(x));
+  CUDA_TRY(launch_residual(x, prm));
+  if (g->f64) {
+    CUDA_TRY(launch_pcg(x, prm));
+  } else {
+    for (int c = 0; c < cycles; ++c) {
+      CUDA_TRY(launch_pcg(x, prm));
+      CUDA_TRY(launch_add_correction(x));
+      CUDA_TRY(launch_residual(x, prm));
+    }
+  }
+  CUDA_TRY(launch_correct(x));
+  CUDA_TRY(launch_step_end(x));
+  return BCM_OK;
+}
+}  // namespace
+
+extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int max_iter,
+                                     bcm_stats* stats) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (n_steps < 0 || !(rtol > 0) || max_iter < 1)
+    return fail(BCM_E_INVALID, "need n_steps >= 0, rtol > 0, max_iter >= 1");
+  if (g->desc.n_sims > 256)
+    return fail(BCM_E_BOUNDS, "graph steps use the persistent PCG: at most 256 sims per grid");
+  StepGraph& sg = g->sg;
+  const int cycles = g->f64 ? 0 : g->graph_cycles;
+  if (!sg.exec || sg.rtol != rtol || sg.max_iter != max_iter || sg.cycles != cycles ||
+      sg.inner_rtol != g->inner_rtol) {
+    if (sg.exec) CUDA_TRY(cudaGraphExecDestroy(sg.exec));
+    if (sg.graph) CUDA_TRY(cudaGraphDestroy(sg.graph));
+    sg.exec = nullptr;
+    sg.graph = nullptr;
+    if (!sg.capture_stream)
+      CUDA_TRY(cudaStreamCreateWithFlags(&sg.capture_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamBeginCapture(sg.capture_stream, cudaStreamCaptureModeThreadLocal));
+    bcm_status st = issue_graph_step(g, sg.capture_stream, rtol, max_iter, cycles);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(sg.capture_stream, &graph);
+    if (st != BCM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(BCM_E_CUDA, "step capture: %s", cudaGetErrorString(e));
+    sg.graph = graph;
+    CUDA_TRY(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
+    sg.rtol = rtol;
+    sg.max_iter = max_iter;
+    sg.cycles = cycles;
+    sg.inner_rtol = g->inner_rtol;
+  }
+  for (int n = 0; n < n_steps; ++n) {
+    CUDA_TRY(cudaGraphLaunch(sg.exec, g->stream));
+    g->launch_count += 1;
+  }
+  if (stats) return collect(g, stats);
+  return BCM_OK;
 }
 
 extern "C" bcm_status bcm_profile(bcm_grid* g, int enable) {
