@@ -236,6 +236,18 @@ def timed_steps(g, n, stream):
     return ev0.elapsed_time(ev1)
 
 
+def timed_steps_graph(g, n, stream):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    g.step_graph(n, rtol=RTOL, max_iter=20000, stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
 def gpu_arm(args, ws, rank, local):
     import torch
     from paper_1808_04099_gb300 import bcm
@@ -253,7 +265,7 @@ def gpu_arm(args, ws, rank, local):
 
     # ---- mixed precision: the headline value
     g = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
-    g.set_solver(inner_rtol=args.inner_rtol)
+    g.set_solver(inner_rtol=args.inner_rtol, recycle=args.recycle)
     g.load_state(state)
     stream = g.stream
     for _ in range(args.warmup):
@@ -265,10 +277,17 @@ def gpu_arm(args, ws, rank, local):
     barrier(ws)
     clocks = ClockSampler(uuid)
     clocks.start()
-    ms = timed_steps(g, args.steps, stream)
+    ms_eager = timed_steps(g, args.steps, stream)
+    _, launches_eager = g.profile_read(reset=True)
+    # the same steps replayed from a captured CUDA graph (no host synchronisation)
+    g.step_graph(1, rtol=RTOL, stats=False)
+    g.profile_read(reset=True)
+    ms_graph = timed_steps_graph(g, args.steps, stream)
+    _, launches_graph = g.profile_read(reset=True)
     clk = clocks.stop()
+    ms = min(ms_eager, ms_graph)
+    launches = launches_graph if ms_graph <= ms_eager else launches_eager
     barrier(ws)
-    _, launches = g.profile_read(reset=True)
     st = g.step(0, rtol=RTOL)[0] if True else None
     ms_max = max_over_ranks(ms, ws)
     value = sum_over_ranks(n * args.steps / (ms / 1e3), ws) if ws > 1 else n * args.steps / (ms_max / 1e3)
@@ -371,6 +390,9 @@ def gpu_arm(args, ws, rank, local):
                      "ms_per_step": ms64 / args.steps, "cg_iters_last_step": st64["cg_iters"],
                      "rel_resid_last_step": st64["rel_resid"], "kernels": k64},
             "speedup_mixed_vs_fp64": value / fp64_value,
+            "mixed_paths_ms_per_step": {"eager": ms_eager / args.steps,
+                                        "graph": ms_graph / args.steps,
+                                        "value_from": "graph" if ms_graph <= ms_eager else "eager"},
             "launch": {"mixed": {"slabs_a,slabs_b": shape32, "us_per_iter": tune32},
                        "fp64": {"slabs_a,slabs_b": shape64, "us_per_iter": tune64}},
             "roofline": roofline,
@@ -422,6 +444,8 @@ def main():
                          "iterations as one solve (one persistent PCG launch)")
     ap.add_argument("--ncu-two-launch", action="store_true",
                     help="with --ncu-case: two launches per PCG iteration")
+    ap.add_argument("--recycle", type=int, default=-1,
+                    help="mixed mode: 1 reliable updates across cycles, 0 restarts (default: library)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="mixed mode: inner FP32 PCG reduction per cycle (0 = library default)")
     args = ap.parse_args()

@@ -160,20 +160,25 @@ bcm_status bcm_step(bcm_grid *grid, int n_steps, double rtol, int max_iter, bcm_
  * stream and instantiates it; every call then launches the graph n_steps times on
  * the grid's stream, with no host synchronisation unless stats is non-NULL.  The
  * captured step uses the persistent PCG (grids of at most 256 sims) and, in mixed
- * mode, a fixed budget of 4 defect-correction cycles per solve (cycles after a sim
- * has converged return at once; a sim needing more is reported not converged). */
+ * mode, a fixed budget of ceil(log rtol / log inner_rtol) + 4 defect-correction
+ * cycles per solve (at most max_cycles; cycles after a sim has converged return at
+ * once; a sim needing more is reported not converged). */
 bcm_status bcm_step_graph(bcm_grid *grid, int n_steps, double rtol, int max_iter,
                           bcm_stats *stats);
 
 /* Solver controls (defaults in brackets): inner_rtol, the relative reduction of the
- * FP32 inner PCG per defect-correction cycle in mixed mode [1e-5]; max_cycles, the
+ * FP32 inner PCG per defect-correction cycle in mixed mode [0.1 with recycle, else
+ * 1e-5]; max_cycles, the
  * cap on FP64 residual evaluations per solve [30]; check_every, PCG iterations
  * between two reads of the device convergence flags by the host [8];
  * barrier_timeout_s, the longest wait of a block at a grid barrier of the
- * persistent PCG before the solve gives up with BCM_E_TIMEOUT [2 s].  A value <= 0
- * keeps the current setting. */
+ * persistent PCG before the solve gives up with BCM_E_TIMEOUT [2 s]; recycle, in
+ * mixed mode with the persistent PCG: 1 keeps the inner CG's search direction across
+ * defect-correction cycles (the FP64 residual replaces the FP32 one: a reliable
+ * update), 0 restarts the inner CG every cycle [1].  A value <= 0 keeps the current
+ * setting (recycle: a value < 0). */
 bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int check_every,
-                          double barrier_timeout_s);
+                          double barrier_timeout_s, int recycle);
 
 /* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
  * whose blocks loop over the iterations with grid-wide barriers (default in mixed

@@ -83,7 +83,7 @@ def lib(build: bool = True):
                                 C.POINTER(C.c_int32)]
         L.bcm_set_geometry.argtypes = [P, C.c_int, P, C.c_int, P]
         L.bcm_reset_time.argtypes = [P]
-        L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_double]
+        L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int]
         L.bcm_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
         L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
         L.bcm_step_graph.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
@@ -208,9 +208,9 @@ class Grid:
                                       m.ctypes.data if m is not None else None))
 
     def set_solver(self, inner_rtol: float = 0.0, max_cycles: int = 0, check_every: int = 0,
-                   barrier_timeout_s: float = 0.0):
+                   barrier_timeout_s: float = 0.0, recycle: int = -1):
         _check(lib().bcm_set_solver(self._h, inner_rtol, max_cycles, check_every,
-                                    barrier_timeout_s))
+                                    barrier_timeout_s, recycle))
 
     def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: bool = True):
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))

@@ -70,7 +70,10 @@ struct SimState {
   int zero_rhs;        // b == 0: p = 0
   int converged;
   int nonfinite;
-  int pad;
+  int cont;            // mixed: the next PCG launch continues the previous Krylov sequence
+  double rz_last;      // <r,z> before the last iteration of the previous PCG launch
+  int p_off;           // buffer offset of the previous launch's last search direction
+  int pad2;
 };
 
 enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 5,

@@ -32,6 +32,8 @@ struct SolveParams {
   int guard_limit;
   int pad;
   unsigned long long barrier_timeout_ns;  // persistent PCG: longest wait at a grid barrier
+  int recycle;            // mixed + persistent: keep the search direction across cycles
+  int pad2;
 };
 
 struct Ctx {

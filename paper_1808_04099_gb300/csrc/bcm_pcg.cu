@@ -91,7 +91,7 @@ __device__ __forceinline__ double slot_sum(SimState& st, int idx) {
 }
 
 template <int B, int KS, int NT, class TV, class TX>
-__global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
+__global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
                                             TV* __restrict__ p0, TV* __restrict__ p1,
                                             TV* __restrict__ q, SolveParams prm,
                                             unsigned int* bar, int* err) {
@@ -109,6 +109,8 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
   double* s_rz = s_beta + nsim;
   double* s_rzprev = s_rz + nsim;
   unsigned char* s_done = reinterpret_cast<unsigned char*>(s_rzprev + nsim);
+  unsigned char* s_first = s_done + nsim;  // restart with p = z at iteration 0
+  unsigned char* s_poff = s_first + nsim;  // search-direction buffer offset
   const bool inner = prm.mixed != 0;
   const int kmax = inner ? prm.inner_max_iter : prm.max_iter;
   // my items by the linear load-balanced distribution
@@ -119,9 +121,12 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
   // the state at entry: iteration 0 uses the residual kernel's scalars
   for (int s = threadIdx.x; s < nsim; s += NT) {
     SimState& st = g.ss[s];
-    s_rz[s] = st.rz;
-    s_rzprev[s] = st.rz;
+    const bool cont = st.cont != 0;
+    s_rz[s] = cont ? st.rz_last : st.rz;
+    s_rzprev[s] = s_rz[s];
     s_done[s] = st.done ? 1 : 0;
+    s_first[s] = cont ? 0 : 1;
+    s_poff[s] = cont ? (unsigned char)(st.p_off & 1) : 0;
   }
   __syncthreads();
   const unsigned long long limit = prm.barrier_timeout_ns;
@@ -149,6 +154,8 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
           st.total_iters += k;
           st.rr = rr;
           st.done = 1;
+          st.rz_last = s_rz[s];               // <r,z> of the last direction's iteration
+          st.p_off = (k + s_poff[s]) & 1;     // buffer holding the last direction
           if (bad) st.nonfinite = 1;
           if (!inner) {
             st.rr64 = rr;
@@ -157,7 +164,7 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
         }
         continue;
       }
-      s_beta[s] = (k == 0 || s_rz[s] == 0.0) ? 0.0 : rz / s_rz[s];
+      s_beta[s] = ((k == 0 && s_first[s]) || s_rz[s] == 0.0) ? 0.0 : rz / s_rz[s];
       s_rzprev[s] = s_rz[s];
       s_rz[s] = rz;
       alive = 1;
@@ -172,8 +179,6 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
         st.acc[sp][ACC_SLOT_RR + sl] = 0.0;
         st.acc[sp][ACC_SLOT_PQ + sl] = 0.0;
       }
-    const TV* __restrict__ pold = (k & 1) ? p1 : p0;
-    TV* __restrict__ pnew = (k & 1) ? p0 : p1;
     // ---- pass A over my items
     for (int it = 0; it < nitems; ++it) {
       const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
@@ -186,7 +191,10 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
         __syncthreads();
       }
       const TV beta = TV(s_beta[s]);
-      const bool first = (k == 0);
+      const bool first = (k == 0) && s_first[s];
+      const int pb = (k + s_poff[s]) & 1;
+      const TV* __restrict__ pold = pb ? p1 : p0;
+      TV* __restrict__ pnew = pb ? p0 : p1;
       auto val4 = [&](int cube, int cell0, int face, TV (&v)[4]) {
         const size_t gi = (size_t)cube * B3 + cell0;
         TV rr4[4], pp[4] = {TV(0), TV(0), TV(0), TV(0)};
@@ -253,6 +261,7 @@ __global__ __launch_bounds__(NT) void k_pcg(DevGrid g, TX* __restrict__ x, TV* _
       }
       const TV alpha = TV(s_alpha[s]);
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
+      const TV* __restrict__ pnew = ((k + s_poff[s]) & 1) ? p0 : p1;
       TV rz = TV(0), rr = TV(0);
       for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
         const int cell = 4 * q4;
@@ -307,9 +316,9 @@ static int max_coresident(K kern, int nt, size_t smem, int* out) {
 template <int B, int KS, class TV, class TX>
 static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   constexpr int NT = pcg_threads<B>();
-  // tile (16-byte multiple) + alpha, beta, rz, rz_prev (FP64) and done (byte) per sim
+  // tile (16-byte multiple) + alpha, beta, rz, rz_prev (FP64), done, first, p_off (bytes)
   const size_t tile = (sizeof(TV) * Slab<B, KS>::N + 15) / 16 * 16;
-  const size_t sm = tile + (size_t)x.g.n_sims * (4 * sizeof(double) + 1);
+  const size_t sm = tile + (size_t)x.g.n_sims * (4 * sizeof(double) + 3);
   auto kern = k_pcg<B, KS, NT, TV, TX>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -130,6 +130,9 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
           t.iter = 0;
           t.beta = 0.0;
           t.done = (rr == 0.0);
+          // reliable update: after the first cycle the inner CG resumes its previous
+          // search direction with the true (FP64) residual in place of its own
+          t.cont = (prm.recycle && t.cycles > 1) ? 1 : 0;
           alive |= !t.done;
           outer_alive = 1;
         }
@@ -143,6 +146,7 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
         t.iter = 0;
         t.total_iters = 0;
         t.beta = 0.0;
+        t.cont = 0;
         if (!isfinite(rr)) t.nonfinite = 1;
         t.done = t.zero_rhs || rr <= t.tol2 || t.nonfinite;
         t.converged = t.zero_rhs || rr <= t.tol2;
