@@ -33,11 +33,14 @@ struct CubeSh {
   int nbw3[6][6];   // ... of each same-level neighbour
   int bc[6];        // the sim's domain-face conditions
   int has21;        // some face of this cube is a 2:1 level interface
+  int smask;        // bit f set: face f's Jacobi weight is not the same-level 3 (thirds)
+  int nbmask[6];    // ... of each same-level neighbour
   TV wt[6];         // flux weight of a face relative to a same-level face: 1, 2/3, 4/3
   TV invtab[kW3];   // 1 / diag(K) by face-weight sum
 };
 
-// Needs blockDim.x >= 37; the caller synchronises afterwards.
+// Needs blockDim.x >= 37 (neighbour masks need 70; smaller blocks compute them in a
+// loop below); the caller synchronises afterwards.
 template <class TV>
 __device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int c) {
   const int t = threadIdx.x;
@@ -52,9 +55,21 @@ __device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int 
     cs.wt[t] = n == NB_COARSE ? TV(2.0 / 3.0) : (n == NB_FINE ? TV(4.0 / 3.0) : TV(1));
   }
   if (t == 0) {
-    int any = 0;
-    for (int f = 0; f < 6; ++f) any |= g.nb[6 * c + f] < NB_BOUNDARY;
+    int any = 0, m = 0;
+    for (int f = 0; f < 6; ++f) {
+      any |= g.nb[6 * c + f] < NB_BOUNDARY;
+      m |= (g.w3[6 * c + f] != 3) << f;
+    }
     cs.has21 = any;
+    cs.smask = m;
+  }
+  if (blockDim.x >= 70 ? (t >= 64 && t < 70) : (t == 1)) {
+    const int f0 = blockDim.x >= 70 ? t - 64 : 0, f1 = blockDim.x >= 70 ? f0 + 1 : 6;
+    for (int f = f0; f < f1; ++f) {
+      int m = 0;
+      for (int e = 0; e < 6; ++e) m |= (g.nbw3[36 * c + 6 * f + e] != 3) << e;
+      cs.nbmask[f] = m;
+    }
   }
   if (t < 36) cs.nbw3[t / 6][t - 6 * (t / 6)] = g.nbw3[36 * c + t];
   if (t < kW3) cs.invtab[t] = TV(sp.invdiag[g.lvl[c]][t]);

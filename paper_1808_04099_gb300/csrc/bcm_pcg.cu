@@ -200,18 +200,34 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         TV rr4[4], pp[4] = {TV(0), TV(0), TV(0), TV(0)};
         ld4(r + gi, rr4);
         if (!first) ld4(pold + gi, pp);
-        const int* w3 = face < 0 ? cs.w3 : cs.nbw3[face];
-        const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
+        const int mask = face < 0 ? cs.smask : cs.nbmask[face];
+        if (mask == 0) {  // every face of that cube has the same-level weight
+          const TV inv = cs.invtab[18];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const TV z = rr4[m] * cs.invtab[s3_of<B>(w3, i0 + m, j, kz)];
-          v[m] = first ? z : z + beta * pp[m];
+          for (int m = 0; m < 4; ++m) {
+            const TV z = rr4[m] * inv;
+            v[m] = first ? z : z + beta * pp[m];
+          }
+        } else {
+          const int* w3 = face < 0 ? cs.w3 : cs.nbw3[face];
+          const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const TV z = rr4[m] * cs.invtab[s3_of<B>(w3, i0 + m, j, kz)];
+            v[m] = first ? z : z + beta * pp[m];
+          }
         }
       };
       auto val1 = [&](int f, int n, int cell) {
-        const int i = cell % B, j = (cell / B) % B, kz = cell / BB;
         const size_t gi = (size_t)n * B3 + cell;
-        const TV z = r[gi] * cs.invtab[s3_of<B>(cs.nbw3[f], i, j, kz)];
+        TV inv;
+        if (cs.nbmask[f] == 0) {
+          inv = cs.invtab[18];
+        } else {
+          const int i = cell % B, j = (cell / B) % B, kz = cell / BB;
+          inv = cs.invtab[s3_of<B>(cs.nbw3[f], i, j, kz)];
+        }
+        const TV z = r[gi] * inv;
         return first ? z : z + beta * pold[gi];
       };
       auto valg = [&](int n, int cell) {
@@ -223,18 +239,42 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       const TV h = TV(cell_h<B>(g, c));
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
       TV part = TV(0);
-      for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
-        const int cell = 4 * q4, kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
-        const int o = SL::at(i0, j, kk + 1);
-        TV pc[4], qv[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          pc[m] = S[o + m];
-          qv[m] = h * stencil_sum_w<B, TV, KS>(S, o + m, cs, i0 + m, j, z0 + kk);
-          part += pc[m] * qv[m];
+      if (NT == BB) {
+        // one thread per (i, j) column marching up the slab: the z neighbours roll
+        // through registers, each plane costs five shared loads per cell
+        constexpr int PP = SL::P * SL::P;
+        const int i = threadIdx.x % B, j = threadIdx.x / B;
+        int o = SL::at(i, j, 1);
+        TV below = S[o - PP], cur = S[o];
+#pragma unroll 4
+        for (int kk = 0; kk < KS; ++kk) {
+          const TV above = S[o + PP];
+          TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
+                   (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+          if (cs.has21) acc = stencil_sum_w<B, TV, KS>(S, o, cs, i, j, z0 + kk);
+          const TV qv = h * acc;
+          const size_t gi = base + (size_t)kk * BB + j * B + i;
+          pnew[gi] = cur;
+          q[gi] = qv;
+          part += cur * qv;
+          below = cur;
+          cur = above;
+          o += PP;
         }
-        st4(pnew + base + cell, pc);
-        st4(q + base + cell, qv);
+      } else {
+        for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
+          const int cell = 4 * q4, kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
+          const int o = SL::at(i0, j, kk + 1);
+          TV pc[4], qv[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            pc[m] = S[o + m];
+            qv[m] = h * stencil_sum_w<B, TV, KS>(S, o + m, cs, i0 + m, j, z0 + kk);
+            part += pc[m] * qv[m];
+          }
+          st4(pnew + base + cell, pc);
+          st4(q + base + cell, qv);
+        }
       }
       double vals[1] = {double(part)};
       block_sum<NT, 1>(vals, red);
@@ -271,11 +311,13 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         ld4(r + base + cell, rv);
         ld4(q + base + cell, qv);
         const int kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
+        const bool plain = cs.smask == 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           xv[e] = xv[e] + alpha * pv[e];
           rv[e] = rv[e] - alpha * qv[e];
-          const TV z = rv[e] * cs.invtab[s3_of<B>(cs.w3, i0 + e, j, z0 + kk)];
+          const TV inv = plain ? cs.invtab[18] : cs.invtab[s3_of<B>(cs.w3, i0 + e, j, z0 + kk)];
+          const TV z = rv[e] * inv;
           rz += rv[e] * z;
           rr += rv[e] * rv[e];
         }
