@@ -148,6 +148,10 @@ bcm_status bcm_set_geometry(bcm_grid *grid, int sim, const bcm_body *bodies, int
 /* Reset step counters (time = 0) of all sims; the next step starts AB2 with Euler. */
 bcm_status bcm_reset_time(bcm_grid *grid);
 
+/* Set the step counter of every sim (time = step * dt), e.g. when restarting from a
+ * checkpoint; step 0 makes the next step the Euler start of AB2. */
+bcm_status bcm_set_step(bcm_grid *grid, int step);
+
 /* Advance every sim by n_steps fractional steps ("Numerical algorithm"):
  * solid fraction (moving bodies), momentum sub-step with halo staging, IB forcing,
  * Poisson right-hand side, Jacobi-PCG pressure solve to relative residual rtol
@@ -222,6 +226,28 @@ bcm_status bcm_solve_pressure_static(bcm_grid *grid, const double *dev_b, double
 
 /* y = K x with K = -V A the flux-form pressure operator of Eq. poisson (FP64). */
 bcm_status bcm_apply_poisson(bcm_grid *grid, const double *dev_x, double *dev_y);
+
+/* Discrete adjoint of the fractional step, for gradients of J = sum_n w_n F_x^n (F_x^n
+ * the drag of step n) with respect to the eight inflow-profile amplitudes a_m and the
+ * centre of a fixed sphere (body 0).  Every operator of the step is transposed exactly,
+ * boundary ghosts included; the adjoint Poisson solve is the same Jacobi-PCG (K is
+ * symmetric).  No counterpart in the paper, which has no adjoint; the step it reverses
+ * is the paper's ("Numerical algorithm").  FP64 single-level grids whose sims have an
+ * outflow face; bodies: fixed spheres.
+ *   bcm_adjoint_bytes:  bytes of the adjoint workspace (caller-owned device memory).
+ *   bcm_adjoint_init:   zero the adjoint state (lambda of the final state = 0).
+ *   bcm_adjoint_step:   reverse one step n.  state[7] = device pointers to the forward
+ *                       state at the start of step n: u, v, w, N^{n-1}_x, _y, _z (the
+ *                       BCM_NX.. fields before the step) and the outflow face values;
+ *                       first_step = 1 for step 0 (Euler start); drag_weight = w_n;
+ *                       rtol / max_iter of the adjoint Poisson solve.  dev_dJ: FP64
+ *                       device array [11] += dJ/d(a_1..a_8, c_x, c_y, c_z).
+ * Call bcm_adjoint_step for n = N-1 down to 0 with the same workspace. */
+size_t bcm_adjoint_bytes(const bcm_grid *grid);
+bcm_status bcm_adjoint_init(bcm_grid *grid, void *dev_adj, size_t bytes);
+bcm_status bcm_adjoint_step(bcm_grid *grid, void *dev_adj, size_t bytes, const void *const *state,
+                            int first_step, double drag_weight, double rtol, int max_iter,
+                            double *dev_dJ);
 
 /* Kernel classes for bcm_profile_read. */
 enum {

@@ -22,7 +22,8 @@ PREC_F64, PREC_F32_REFINE = 0, 1
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
             "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch",
-            "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
+            "bcm_set_step", "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
+            "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
             "bcm_last_error"]
@@ -83,6 +84,12 @@ def lib(build: bool = True):
                                 C.POINTER(C.c_int32)]
         L.bcm_set_geometry.argtypes = [P, C.c_int, P, C.c_int, P]
         L.bcm_reset_time.argtypes = [P]
+        L.bcm_set_step.argtypes = [P, C.c_int]
+        L.bcm_adjoint_bytes.restype = C.c_size_t
+        L.bcm_adjoint_bytes.argtypes = [P]
+        L.bcm_adjoint_init.argtypes = [P, P, C.c_size_t]
+        L.bcm_adjoint_step.argtypes = [P, P, C.c_size_t, P, C.c_int, C.c_double, C.c_double,
+                                       C.c_int, P]
         L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int]
         L.bcm_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
         L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
@@ -95,7 +102,8 @@ def lib(build: bool = True):
         L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
         L.bcm_last_error.restype = C.c_char_p
         for name in EXPORTED:
-            getattr(L, name).restype = getattr(L, name).restype or C.c_int
+            if name != "bcm_adjoint_bytes":
+                getattr(L, name).restype = getattr(L, name).restype or C.c_int
         _lib = L
     return _lib
 
@@ -214,6 +222,9 @@ class Grid:
 
     def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: bool = True):
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
+
+    def set_step(self, step: int):
+        _check(lib().bcm_set_step(self._h, step))
 
     def reset_time(self):
         _check(lib().bcm_reset_time(self._h))

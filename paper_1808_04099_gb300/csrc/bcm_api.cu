@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -569,6 +570,15 @@ extern "C" bcm_status bcm_set_geometry(bcm_grid* g, int sim, const bcm_body* bod
   // the host copy must stay valid until the copy has run
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(g->ctx, sim));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_set_step(bcm_grid* g, int step) {
+  if (!g || step < 0) return fail(BCM_E_INVALID, "bad grid or step");
+  for (int s = 0; s < g->desc.n_sims; ++s)
+    CUDA_TRY(cudaMemcpyAsync(g->ws + g->L.ss + sizeof(SimState) * s + offsetof(SimState, step),
+                             &step, sizeof(int), cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
   return BCM_OK;
 }
 
