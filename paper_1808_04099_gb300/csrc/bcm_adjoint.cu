@@ -215,7 +215,7 @@ __global__ __launch_bounds__(kNT) void k_adj_rhs(DevGrid g, AdjFields F) {
           if (bc == BC_OUTFLOW) {
             atomicAdd(&F.lub[((size_t)(g.slot[6 * x.c + f] * 3 + d) * B + b) * B + a],
                       sgn * lbj);
-          } else if (bc == BC_INFLOW && p.has_modes) {
+          } else if (bc == BC_INFLOW) {  // the amplitudes matter even where they are 0
             double dbeta[kModes];
             inflow_dbeta<B>(g, x.c, f, d, a, b, dbeta);
             for (int m = 0; m < kModes; ++m) ga[m] += sgn * lbj * 0.5 * dbeta[m];  // U = beta/2
@@ -388,7 +388,7 @@ __global__ __launch_bounds__(kNT) void k_adj_momentum(DevGrid g, AdjFields F, co
             if (bc == BC_OUTFLOW) {
               atomicAdd(&F.lub2[((size_t)(g.slot[6 * x.c + f] * 3 + e) * B + b) * B + a],
                         2.0 * lbeta);
-            } else if (bc == BC_INFLOW && p.has_modes) {
+            } else if (bc == BC_INFLOW) {
               double dbeta[kModes];
               inflow_dbeta<B>(g, x.c, f, e, a, b, dbeta);
               for (int m = 0; m < kModes; ++m) ga[m] += lbeta * dbeta[m];

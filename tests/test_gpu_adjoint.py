@@ -79,3 +79,23 @@ def test_adjoint_through_autograd_and_checkpoint_independence():
     # symmetry of the problem: no lateral force gradient in y at the symmetric point
     # (the inflow modes break it, so only the centre-y/z derivative is ~0 at a = 0)
     assert abs(c.grad[1].item()) <= 1e-8 * abs(c.grad[0].item()) + 1e-12
+
+
+def test_adjoint_amplitude_gradient_at_zero_amplitudes():
+    """At a = 0 the inflow profile is flat, yet dJ/da is not zero: the adjoint must
+    differentiate through the profile factor there too."""
+    modes = np.zeros(8)
+    center = np.array([1.0, 1.0, 1.0])
+    run = adjoint.AdjointRun(base_spec(), modes, center, RADIUS, STEPS, checkpoint_every=2,
+                             rtol=1e-13)
+    run.forward()
+    ga, gc = run.backward()
+    h = 1e-4
+    # modes (1,1) and (1,3) are symmetric about the channel centre (non-zero response);
+    # (2,2) is antisymmetric, so its first-order effect on the drag vanishes there
+    for m in (0, 4, 3):
+        tp = modes.copy()
+        tp[m] = h
+        fd = (oracle_J(tp, center) - oracle_J(-tp, center)) / (2 * h)
+        assert abs(ga[m] - fd) <= 1e-5 * abs(fd) + 1e-12, (m, ga[m], fd)
+    assert abs(ga[0]) > 1e-3
