@@ -416,7 +416,9 @@ def ncu_case(args):
     g = bcm.Grid(spec, prec)
     g.set_solver(inner_rtol=args.inner_rtol)
     if args.ncu_two_launch:
-        g.set_launch(1, 1, persistent=False)
+        g.set_launch(1, 1, persistent=0)
+    elif args.ncu_single_pass:
+        g.set_launch(1, 1, persistent=2)
     g.load_state(W.initial_state(spec))
     if args.ncu_iters:
         st = g.step(1, rtol=RTOL)
@@ -444,6 +446,8 @@ def main():
                          "iterations as one solve (one persistent PCG launch)")
     ap.add_argument("--ncu-two-launch", action="store_true",
                     help="with --ncu-case: two launches per PCG iteration")
+    ap.add_argument("--ncu-single-pass", action="store_true",
+                    help="with --ncu-case: the single-reduction persistent PCG")
     ap.add_argument("--recycle", type=int, default=-1,
                     help="mixed mode: 1 reliable updates across cycles, 0 restarts (default: library)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,

@@ -1,5 +1,6 @@
-"""Launch-shape autotuner of the PCG: the persistent cooperative solver with 1, 2
-or 4 z-slabs per work item, or two launches per iteration with z-slabs per pass.
+"""Launch-shape autotuner of the PCG: the persistent cooperative solver (two passes
+per iteration, or the single-reduction form with one) with 1, 2 or 4 z-slabs per work
+item, or two launches per iteration with z-slabs per pass.
 
 Times a fixed number of PCG iterations on the grid's current right-hand side for
 every shape with the library's own CUDA-event kernel timing, restores the pressure,
@@ -14,7 +15,8 @@ import os
 from . import bcm
 
 # (persistent, slabs_a, slabs_b)
-SHAPES = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (0, 1, 1), (0, 1, 2), (0, 2, 2)]
+SHAPES = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
+          (0, 1, 1), (0, 1, 2), (0, 2, 2)]
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "bcm_gb300_launch.json")
 
 
@@ -36,7 +38,7 @@ def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
             cache = {}
     if use_cache and key in cache:
         pe, sa, sb = cache[key]["best"]
-        grid.set_launch(sa, sb, persistent=bool(pe))
+        grid.set_launch(sa, sb, persistent=pe)
         return cache[key]["times"]
     p = grid.field(bcm.P)
     saved = p.clone()
@@ -45,7 +47,7 @@ def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
     for pe, sa, sb in SHAPES:
         if pe and sa > 1 and grid.spec.B != 16:
             continue
-        grid.set_launch(sa, sb, persistent=bool(pe))
+        grid.set_launch(sa, sb, persistent=pe)
         for rep in range(2):  # the first pass warms up the shape
             p.copy_(saved)
             grid.profile(True)
@@ -63,7 +65,7 @@ def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
     grid.set_solver(max_cycles=30)
     best = min(times, key=times.get)
     pe, sa, sb = map(int, best.split(","))
-    grid.set_launch(sa, sb, persistent=bool(pe))
+    grid.set_launch(sa, sb, persistent=pe)
     if use_cache:
         cache[key] = {"best": [pe, sa, sb], "times": times}
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)

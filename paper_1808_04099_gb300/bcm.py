@@ -220,7 +220,9 @@ class Grid:
         _check(lib().bcm_set_solver(self._h, inner_rtol, max_cycles, check_every,
                                     barrier_timeout_s, recycle))
 
-    def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: bool = True):
+    def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: int = 1):
+        """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG,
+        2 the persistent single-reduction PCG (bool values map to 0 and 1)."""
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
 
     def set_step(self, step: int):

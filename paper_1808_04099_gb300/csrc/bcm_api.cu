@@ -49,7 +49,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t u, v, w, us, vs, ws, nx, ny, nz, phi, ub, p, b, bid, near_, r, p0, p1, q, e;
+  size_t u, v, w, us, vs, ws, nx, ny, nz, phi, ub, p, b, bid, near_, r, p0, p1, q, e, w1, s0, s1;
   size_t nb, aux, sim, lvl, ijk, w3, nbw3, slot, sp, ss, counter, flags, guard, bar, err;
   size_t total;
   size_t n_slots;
@@ -260,6 +260,7 @@ Layout plan(const bcm_grid_desc* d, int n_slots) {
   L.bid = take(n); L.near_ = take(d->n_cubes);
   L.r = take(n * V); L.p0 = take(n * V); L.p1 = take(n * V); L.q = take(n * V);
   L.e = take(d->precision == BCM_PREC_F64 ? 0 : n * 4);
+  L.w1 = take(n * V); L.s0 = take(n * V); L.s1 = take(n * V);
   L.nb = take(6 * sizeof(int) * d->n_cubes);
   L.aux = take(24 * sizeof(int) * d->n_cubes);
   L.sim = take(sizeof(int) * d->n_cubes);
@@ -297,6 +298,7 @@ struct StepGraph {
   cudaStream_t capture_stream = nullptr;
   double rtol = 0.0;
   int max_iter = 0, cycles = 0;
+  int slabs_p = 0, single_pass = 0;  // the PCG launch shape captured
   double inner_rtol = 0.0;
   int persistent_slabs = 0;
   int recycle = -1;
@@ -464,6 +466,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   // measured on GB300 at 4.2M cells: the persistent solver is on par in FP32 and
   // slower in FP64 (ALU-bound passes), so FP64 defaults to two launches per iteration
   x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
+  x.single_pass = 0;
   x.stream = s;
   DevGrid& G = x.g;
   G.n_cubes = n;
@@ -492,6 +495,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.bid = W + L.bid; F.near = W + L.near_;
   F.r = W + L.r; F.p0 = W + L.p0; F.p1 = W + L.p1; F.q = W + L.q;
   F.e = g->f64 ? nullptr : (float*)(W + L.e);
+  F.w1 = W + L.w1; F.s0 = W + L.s0; F.s1 = W + L.s1;
   F.guard = (unsigned int*)(W + L.guard);
   F.bar = (unsigned int*)(W + L.bar);
   F.err = (int*)(W + L.err);
@@ -814,7 +818,8 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     if (cycles < 2) cycles = 2;
   }
   if (!sg.exec || sg.rtol != rtol || sg.max_iter != max_iter || sg.cycles != cycles ||
-      sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle) {
+      sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle ||
+      sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass) {
     if (sg.exec) CUDA_TRY(cudaGraphExecDestroy(sg.exec));
     if (sg.graph) CUDA_TRY(cudaGraphDestroy(sg.graph));
     sg.exec = nullptr;
@@ -847,6 +852,8 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     sg.cycles = cycles;
     sg.inner_rtol = g->inner_rtol;
     sg.recycle = g->recycle;
+    sg.slabs_p = g->ctx.slabs_p;
+    sg.single_pass = g->ctx.single_pass;
   }
   for (int n = 0; n < n_steps; ++n) {
     CUDA_TRY(cudaGraphLaunch(sg.exec, g->stream));
@@ -906,7 +913,9 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
     return fail(BCM_E_BOUNDS, "the persistent PCG handles at most 256 sims per grid");
   if (g->B / slabs_a < 1 || g->B / slabs_b < 1 || (g->B * g->B / 4) * (g->B / slabs_b) < 1)
     return fail(BCM_E_INVALID, "slab too thin for this cube size");
+  if (persistent < 0 || persistent > 2) return fail(BCM_E_INVALID, "persistent must be 0, 1 or 2");
   g->ctx.persistent = persistent ? 1 : 0;
+  g->ctx.single_pass = persistent == 2 ? 1 : 0;
   if (persistent) {
     if (g->B != 16 && slabs_a != 1) return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
     g->ctx.slabs_p = slabs_a;

@@ -73,13 +73,16 @@ struct SimState {
   int cont;            // mixed: the next PCG launch continues the previous Krylov sequence
   double rz_last;      // <r,z> before the last iteration of the previous PCG launch
   int p_off;           // buffer offset of the previous launch's last search direction
-  int pad2;
+  int s_off;           // single-pass PCG: buffer offset of the last A p
+  double phi_last;     // single-pass PCG: <p, A p> of the last direction
 };
 
 enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 5,
        ACC_DIVN = 6, ACC_DIVD = 7,
        // persistent PCG: three rotating slots (iteration mod 3) per dot product
-       ACC_SLOT_PQ = 8, ACC_SLOT_RZ = 11, ACC_SLOT_RR = 14 };
+       ACC_SLOT_PQ = 8, ACC_SLOT_RZ = 11, ACC_SLOT_RR = 14,
+       // single-pass PCG: <r,u>, <w,u>, <u,s_prev>, <r,r>
+       ACC_SLOT_G = 8, ACC_SLOT_D = 11, ACC_SLOT_E = 14, ACC_SLOT_R = 17, ACC_NSLOT = 12 };
 
 // Device view of the grid tables, passed by value to every kernel.
 struct DevGrid {

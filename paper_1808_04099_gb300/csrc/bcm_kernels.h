@@ -14,6 +14,7 @@ struct Fields {
   double *p, *b;                                              // FP64 always
   unsigned char *bid, *near;
   void *r, *p0, *p1, *q;  // PCG vectors: FP64 (plain) or FP32 (mixed inner)
+  void *w1, *s0, *s1;     // single-pass PCG: second A u buffer and the two A p buffers
   float *e;               // mixed: inner iterate (correction of p)
   unsigned int* guard;    // graph-loop body counter
   unsigned int* bar;      // persistent PCG grid barrier words
@@ -45,6 +46,7 @@ struct Ctx {
   int slabs_b;  // PCG pass B: z-slabs per cube (1, 2 or 4)
   int slabs_p;  // persistent PCG: z-slabs per cube (1, 2 or 4)
   int persistent;  // 1: one cooperative launch per PCG solve; 0: two launches per iteration
+  int single_pass; // persistent PCG: one pass and one grid barrier per iteration
   cudaStream_t stream;
 };
 
@@ -57,6 +59,7 @@ cudaError_t launch_residual(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm);
+cudaError_t launch_pcg1(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_add_correction(const Ctx& x);
 cudaError_t launch_correct(const Ctx& x);
 cudaError_t launch_step_end(const Ctx& x);

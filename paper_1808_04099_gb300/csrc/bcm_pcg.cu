@@ -21,74 +21,9 @@
 #include "bcm_cube.cuh"
 #include "bcm_internal.cuh"
 #include "bcm_kernels.h"
+#include "bcm_persist.cuh"
 
 namespace bcm {
-
-constexpr int kMaxPersistentSims = 256;
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier of a cooperative launch.  bar: [0] generation, [32 (1+s)] stripe
-// counters, [32 (1+kTickets)] top counter (one 128-byte line each).  Returns false
-// (and sets *err) when the wait exceeded limit_ns or another block reported an error.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err,
-                                             unsigned long long limit_ns) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar;
-    const unsigned int g0 = *gen;
-    __threadfence();
-    const unsigned int nblk = gridDim.x;
-    const unsigned int stripe = blockIdx.x % kTickets;
-    const unsigned int in_stripe = (nblk - stripe + kTickets - 1) / kTickets;
-    const unsigned int t = atomicAdd(&bar[32 * (1 + stripe)], 1u);
-    bool released = false;
-    if (t == in_stripe - 1) {
-      bar[32 * (1 + stripe)] = 0u;
-      __threadfence();
-      const unsigned int stripes = nblk < (unsigned)kTickets ? nblk : (unsigned)kTickets;
-      const unsigned int u = atomicAdd(&bar[32 * (1 + kTickets)], 1u);
-      if (u == stripes - 1) {
-        bar[32 * (1 + kTickets)] = 0u;
-        __threadfence();
-        atomicAdd(&bar[0], 1u);
-        released = true;
-      }
-    }
-    int good = 1;
-    if (!released) {
-      const unsigned long long t0 = global_ns();
-      while (*gen == g0) {
-        if (*(volatile int*)err) {
-          good = 0;
-          break;
-        }
-        if (global_ns() - t0 > limit_ns) {
-          atomicExch(err, 1);
-          good = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-__device__ __forceinline__ double slot_sum(SimState& st, int idx) {
-  double s = 0.0;
-#pragma unroll
-  for (int q = 0; q < kStripes; ++q) s += ld_acc(&st.acc[q][idx]);
-  return s;
-}
 
 template <int B, int KS, int NT, class TV, class TX>
 __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
@@ -340,21 +275,6 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
 
 // ---------------------------------------------------------------- launcher
 
-template <int B>
-constexpr int pcg_threads() { return B == 16 ? 256 : (B == 8 ? 128 : 64); }
-
-// Largest co-resident grid for one kernel configuration.
-template <class K>
-static int max_coresident(K kern, int nt, size_t smem, int* out) {
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, nt, smem);
-  if (e != cudaSuccess) return (int)e;
-  *out = per * nsm;
-  return 0;
-}
-
 template <int B, int KS, class TV, class TX>
 static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   constexpr int NT = pcg_threads<B>();
@@ -402,6 +322,7 @@ static cudaError_t pcg_dispatch(const Ctx& x, const SolveParams& prm, TX* xv) {
 
 cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm) {
   if (x.g.n_sims > kMaxPersistentSims) return cudaErrorInvalidValue;
+  if (x.single_pass) return launch_pcg1(x, prm);
   return x.f64 ? pcg_dispatch<double, double>(x, prm, x.f.p)
                : pcg_dispatch<float, float>(x, prm, x.f.e);
 }

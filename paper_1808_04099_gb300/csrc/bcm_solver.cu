@@ -156,7 +156,7 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
     // the persistent PCG's rotating dot-product slots start every solve at zero
     for (int i = threadIdx.x; i < g.n_sims * kStripes; i += NT) {
       SimState& t = g.ss[i / kStripes];
-      for (int sl = 0; sl < 9; ++sl) t.acc[i % kStripes][ACC_SLOT_PQ + sl] = 0.0;
+      for (int sl = 0; sl < ACC_NSLOT; ++sl) t.acc[i % kStripes][ACC_SLOT_PQ + sl] = 0.0;
     }
     alive = __syncthreads_or(alive);
     outer_alive = __syncthreads_or(outer_alive);

@@ -49,6 +49,20 @@ def test_graph_steps_match_oracle_and_eager(prec):
     assert abs(st[0]["drag"][0] - ostats[0]["drag"][0]) <= 1e-6 * abs(ostats[0]["drag"][0])
 
 
+@pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
+def test_graph_single_pass_pcg(prec):
+    """The captured step with the single-reduction persistent PCG."""
+    spec = W.sphere_channel(4, 2, 2, 8, radius=0.3)
+    state = W.initial_state(spec, seed=44)
+    ost, _ = oracle_run(spec, state, 3, 1e-13)
+    g = bcm.Grid(spec, prec)
+    g.load_state(state)
+    g.set_launch(1, 1, persistent=2)
+    st = g.step_graph(3, rtol=1e-13 if prec == bcm.PREC_F64 else 1e-12)
+    assert st[0]["converged"] == 1
+    check(g, ost, spec, TOL64 if prec == bcm.PREC_F64 else TOL32)
+
+
 def test_graph_batched_sims():
     """Independent cavity and sphere sims of uneven size in one captured step."""
     specs = [W.cavity(2, 8, re=250.0), W.sphere_channel(4, 2, 2, 8, radius=0.3, re=500.0),

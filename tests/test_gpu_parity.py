@@ -239,18 +239,39 @@ def test_full_size_sphere_mixed_properties():
     assert rel_l2(g32.numpy(bcm.P), g64.numpy(bcm.P)) <= TOL32
 
 
+def test_full_size_sphere_single_pass_mixed():
+    """The single-reduction persistent PCG at the benchmark's full size: two mixed steps
+    at residual 1e-10 meet the tolerance and agree with the two-pass solver."""
+    spec = W.config_sphere(2)
+    state = W.initial_state(spec)
+    runs = []
+    for persistent in (1, 2):
+        g = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
+        g.set_launch(1, 1, persistent=persistent)
+        st = g.step(2, rtol=1e-10)
+        assert st[0]["converged"] == 1 and st[0]["rel_resid"] <= 1e-10
+        assert st[0]["div_rel"] <= 1e-9
+        runs.append((np.concatenate([g.numpy(f) for f in (bcm.U, bcm.V, bcm.W)]),
+                     st[0]["cg_iters"]))
+        del g
+    assert rel_l2(runs[1][0], runs[0][0]) <= TOL32
+    # same iterates in exact arithmetic: iteration counts within a few percent
+    assert abs(runs[1][1] - runs[0][1]) <= 0.1 * runs[0][1]
+
+
 @pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
 def test_launch_shapes_agree(prec):
     """Every PCG launch shape gives the oracle's result: the persistent cooperative
-    solver with 1, 2 or 4 z-slabs per work item, and the two-launch iteration with
-    its slab counts per pass.  Shapes differ only in the order of the dot sums."""
+    solver (two passes per iteration, or the single-reduction form) with 1, 2 or 4
+    z-slabs per work item, and the two-launch iteration with its slab counts per pass.
+    Shapes differ only in rounding."""
     spec = W.sphere_channel(2, 1, 1, 16, length=(2.0, 1.0, 1.0), radius=0.2,
                             center=(0.6, 0.5, 0.5))
     state = W.initial_state(spec, seed=21, noise=1e-3)
     ost, ostats = oracle_run(spec, state, 2, 1e-13)
     tol = TOL64 if prec == bcm.PREC_F64 else TOL32
-    shapes = [(True, 1, 1), (True, 2, 1), (True, 4, 1),
-              (False, 1, 1), (False, 2, 4), (False, 4, 2), (False, 4, 4)]
+    shapes = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
+              (0, 1, 1), (0, 2, 4), (0, 4, 2), (0, 4, 4)]
     for persistent, sa, sb in shapes:
         g = gpu_grid(spec, prec, state)
         g.set_launch(sa, sb, persistent=persistent)
@@ -267,20 +288,21 @@ def test_persistent_many_sims_and_fallback():
     spec = W.concat(specs)
     state = W.initial_state(spec, seed=22, noise=1e-3)
     ost, _ = oracle_run(spec, state, 2, 1e-13)
-    for persistent in (True, False):
+    for persistent in (1, 2, 0):
         g = gpu_grid(spec, bcm.PREC_F64, state)
         g.set_launch(1, 1, persistent=persistent)
         g.step(2, rtol=1e-13)
         compare_fields(g, ost, spec, TOL64)
 
 
-def test_barrier_timeout_reported_and_recovered():
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_barrier_timeout_reported_and_recovered(persistent):
     """A grid-barrier wait that runs out (a 1 ns limit) ends the persistent solve with
     BCM_E_TIMEOUT instead of waiting; the next solve with the normal limit is exact."""
     spec = W.cavity(2, 8)
     state = W.initial_state(spec, 5, 1e-2)
     g = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
-    g.set_launch(1, 1, persistent=True)
+    g.set_launch(1, 1, persistent=persistent)
     g.set_solver(barrier_timeout_s=1e-9)
     with pytest.raises(bcm.BCMError) as ei:
         g.step(1, rtol=1e-12)
@@ -304,14 +326,18 @@ def two_level_with_bodies():
     return spec
 
 
+@pytest.mark.parametrize("persistent", [None, 2])
 @pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
-def test_two_level_step(prec):
+def test_two_level_step(prec, persistent):
     """The full step on a two-level grid: paper halos for momentum, flux-form Poisson
-    at the 2:1 faces, bodies in the refined block, against the oracle."""
+    at the 2:1 faces, bodies in the refined block, against the oracle (default launch
+    shape, and the single-reduction persistent PCG)."""
     spec = two_level_with_bodies()
     state = W.initial_state(spec, seed=23, noise=1e-3)
     ost, ostats = oracle_run(spec, state, 3, 1e-13)
     g = gpu_grid(spec, prec, state)
+    if persistent is not None:
+        g.set_launch(1, 1, persistent=persistent)
     st = g.step(3, rtol=1e-13 if prec == bcm.PREC_F64 else 1e-12)
     assert st[0]["converged"] == 1
     if prec == bcm.PREC_F64:
