@@ -116,6 +116,10 @@ typedef struct {
     double div_rel;        /* ||D U^{n+1}|| / ||D U*|| of the corrected face velocities */
     double drag[3];        /* force of the fluid on the bodies, last step */
     double umax;           /* max |u| after the last step */
+    int32_t pcg_form;      /* PCG of the last solve: 0 two launches per iteration,
+                              1 persistent streaming, 2 persistent single-reduction,
+                              3 persistent with the state on chip */
+    int32_t reserved;
 } bcm_stats;
 
 /* Bytes of device workspace the grid needs (fields, solver vectors, tables).
@@ -186,10 +190,13 @@ bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int
 
 /* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
  * whose blocks loop over the iterations with two grid-wide barriers each (default in
- * mixed mode for grids of at most 256 sims); persistent = 2: the same launch running the
- * single-reduction form of the iteration (Chronopoulos-Gear: one pass and one barrier
- * per iteration, three more vectors, the same iterates in exact arithmetic);
- * slabs_a = z-slabs per cube of the work items (1, 2 or 4; 16^3 cubes only for 2 and 4).
+ * mixed mode for grids of at most 256 sims); when every cube gets a co-resident block
+ * (FP32 inner solve, 16^3 or 8^3 cubes, slabs_a = 1) the launch keeps r and x in
+ * registers and p, q in shared memory, otherwise it streams the vectors through global
+ * memory.  persistent = 3: always the streaming form.  persistent = 2: the single-
+ * reduction form of the iteration (Chronopoulos-Gear: one pass and one barrier per
+ * iteration, three more vectors, the same iterates in exact arithmetic).  slabs_a =
+ * z-slabs per cube of the streaming work items (1, 2 or 4; 16^3 cubes only for 2 and 4).
  * persistent = 0: two launches per iteration (the FP64 default), one CTA per z-slab,
  * slabs_a / slabs_b slabs per cube for pass A / pass B.  Results do not depend on the
  * shape beyond rounding.  BCM_E_INVALID for other values. */

@@ -50,12 +50,14 @@ class Body(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("cg_iters", C.c_int32), ("refine_cycles", C.c_int32), ("steps", C.c_int32),
                 ("converged", C.c_int32), ("rel_resid", C.c_double), ("div_rel", C.c_double),
-                ("drag", C.c_double * 3), ("umax", C.c_double)]
+                ("drag", C.c_double * 3), ("umax", C.c_double), ("pcg_form", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {"cg_iters": self.cg_iters, "refine_cycles": self.refine_cycles,
                 "steps": self.steps, "converged": self.converged, "rel_resid": self.rel_resid,
-                "div_rel": self.div_rel, "drag": list(self.drag), "umax": self.umax}
+                "div_rel": self.div_rel, "drag": list(self.drag), "umax": self.umax,
+                "pcg_form": self.pcg_form}
 
 
 class BCMError(RuntimeError):
@@ -221,8 +223,10 @@ class Grid:
                                     barrier_timeout_s, recycle))
 
     def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: int = 1):
-        """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG,
-        2 the persistent single-reduction PCG (bool values map to 0 and 1)."""
+        """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG (state
+        on chip when every cube fits a co-resident block), 2 the persistent
+        single-reduction PCG, 3 the persistent two-pass PCG streaming its vectors
+        through global memory (bool values map to 0 and 1)."""
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
 
     def set_step(self, step: int):

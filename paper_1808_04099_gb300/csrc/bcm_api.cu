@@ -298,7 +298,7 @@ struct StepGraph {
   cudaStream_t capture_stream = nullptr;
   double rtol = 0.0;
   int max_iter = 0, cycles = 0;
-  int slabs_p = 0, single_pass = 0;  // the PCG launch shape captured
+  int slabs_p = 0, single_pass = 0, resident = 0;  // the PCG launch shape captured
   double inner_rtol = 0.0;
   int persistent_slabs = 0;
   int recycle = -1;
@@ -314,6 +314,7 @@ struct bcm_grid {
   int check_every = 8;       // host-driven loops: iterations between flag reads
   double barrier_timeout_s = 2.0;  // persistent PCG: longest grid-barrier wait
   int recycle = 1;           // mixed + persistent: reliable updates instead of restarts
+  int pcg_form = 0;          // PCG form of the last solve (PCG_*)
   KernelTimer timer;
   long long launch_count = 0;
   HostTables T;
@@ -467,6 +468,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   // slower in FP64 (ALU-bound passes), so FP64 defaults to two launches per iteration
   x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
   x.single_pass = 0;
+  x.resident = 1;
   x.stream = s;
   DevGrid& G = x.g;
   G.n_cubes = n;
@@ -654,11 +656,12 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
   RUN(BCM_K_MISC, launch_solve_begin(x));
   RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
+  g->pcg_form = PCG_TWO_LAUNCH;  // the persistent launches say which form they ran
   int flags[2] = {0, 0};
   bcm_status st;
   if (x.persistent) {
     if (g->f64) {
-      RUN(BCM_K_PCG, launch_pcg(x, prm));
+      RUN(BCM_K_PCG, launch_pcg(x, prm, &g->pcg_form));
       return read_err(g);
     }
     // defect correction: cycles are issued in batches; a finished sim makes every
@@ -666,7 +669,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     int cycles = 0, batch = 2;
     while (cycles < g->max_cycles) {
       for (int b = 0; b < batch && cycles < g->max_cycles; ++b, ++cycles) {
-        RUN(BCM_K_PCG, launch_pcg(x, prm));
+        RUN(BCM_K_PCG, launch_pcg(x, prm, &g->pcg_form));
         RUN(BCM_K_ADD_CORRECTION, launch_add_correction(x));
         RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
       }
@@ -730,6 +733,7 @@ bcm_status collect(bcm_grid* g, bcm_stats* out) {
     double um;
     memcpy(&um, &t.umax_bits, sizeof um);
     o.umax = um;
+    o.pcg_form = g->pcg_form;
     if (t.nonfinite) st = BCM_E_NONFINITE;
     else if (!t.converged && st == BCM_OK) st = BCM_E_NOT_CONVERGED;
   }
@@ -787,10 +791,10 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   CUDA_TRY(launch_solve_begin(x));
   CUDA_TRY(launch_residual(x, prm));
   if (g->f64) {
-    CUDA_TRY(launch_pcg(x, prm));
+    CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
   } else {
     for (int c = 0; c < cycles; ++c) {
-      CUDA_TRY(launch_pcg(x, prm));
+      CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
       CUDA_TRY(launch_add_correction(x));
       CUDA_TRY(launch_residual(x, prm));
     }
@@ -819,7 +823,8 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
   }
   if (!sg.exec || sg.rtol != rtol || sg.max_iter != max_iter || sg.cycles != cycles ||
       sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle ||
-      sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass) {
+      sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass ||
+      sg.resident != g->ctx.resident) {
     if (sg.exec) CUDA_TRY(cudaGraphExecDestroy(sg.exec));
     if (sg.graph) CUDA_TRY(cudaGraphDestroy(sg.graph));
     sg.exec = nullptr;
@@ -854,6 +859,7 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     sg.recycle = g->recycle;
     sg.slabs_p = g->ctx.slabs_p;
     sg.single_pass = g->ctx.single_pass;
+    sg.resident = g->ctx.resident;
   }
   for (int n = 0; n < n_steps; ++n) {
     CUDA_TRY(cudaGraphLaunch(sg.exec, g->stream));
@@ -913,9 +919,10 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
     return fail(BCM_E_BOUNDS, "the persistent PCG handles at most 256 sims per grid");
   if (g->B / slabs_a < 1 || g->B / slabs_b < 1 || (g->B * g->B / 4) * (g->B / slabs_b) < 1)
     return fail(BCM_E_INVALID, "slab too thin for this cube size");
-  if (persistent < 0 || persistent > 2) return fail(BCM_E_INVALID, "persistent must be 0, 1 or 2");
+  if (persistent < 0 || persistent > 3) return fail(BCM_E_INVALID, "persistent must be 0 .. 3");
   g->ctx.persistent = persistent ? 1 : 0;
   g->ctx.single_pass = persistent == 2 ? 1 : 0;
+  g->ctx.resident = persistent == 1 ? 1 : 0;
   if (persistent) {
     if (g->B != 16 && slabs_a != 1) return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
     g->ctx.slabs_p = slabs_a;

@@ -254,6 +254,16 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
   __syncthreads();
 }
 
+// Row j of the column that thread slot t (0 .. B*B-1, i = t % B) works on in the column
+// marches.  With B = 16 a warp covers two rows; rows w and w + 8 lie 8 (B+2) = 144
+// words apart in the tile (16 mod 32 banks), so the two half-warps never share a
+// bank, where rows w and w + 1 (18 words apart) would conflict on two banks.
+template <int B>
+__device__ __forceinline__ int column_row(int t) {
+  const int jj = t / B;
+  return B == 16 ? (jj >> 1) | ((jj & 1) << 3) : jj;
+}
+
 // sum over the six faces of (p_c - p_nb) at tile position o (the 7-point K stencil / h)
 template <int B, class TV, int KS = B>
 __device__ __forceinline__ TV stencil_sum(const TV* __restrict__ S, int o) {

@@ -47,6 +47,7 @@ struct Ctx {
   int slabs_p;  // persistent PCG: z-slabs per cube (1, 2 or 4)
   int persistent;  // 1: one cooperative launch per PCG solve; 0: two launches per iteration
   int single_pass; // persistent PCG: one pass and one grid barrier per iteration
+  int resident;    // persistent PCG: keep r, x, p, q on chip when every cube fits a block
   cudaStream_t stream;
 };
 
@@ -58,8 +59,12 @@ cudaError_t launch_solve_begin(const Ctx& x);
 cudaError_t launch_residual(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm);
-cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm);
+// PCG forms (reported in bcm_stats.pcg_form)
+enum { PCG_TWO_LAUNCH = 0, PCG_STREAMING = 1, PCG_SINGLE_PASS = 2, PCG_RESIDENT = 3 };
+// The persistent PCG in the form the launch shape and the grid select; *form gets it.
+cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form);
 cudaError_t launch_pcg1(const Ctx& x, const SolveParams& prm);
+cudaError_t launch_pcg_resident(const Ctx& x, const SolveParams& prm, bool* launched);
 cudaError_t launch_add_correction(const Ctx& x);
 cudaError_t launch_correct(const Ctx& x);
 cudaError_t launch_step_end(const Ctx& x);

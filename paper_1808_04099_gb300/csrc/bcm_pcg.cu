@@ -64,7 +64,8 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     s_poff[s] = cont ? (unsigned char)(st.p_off & 1) : 0;
   }
   __syncthreads();
-  const unsigned long long limit = prm.barrier_timeout_ns;
+  GridBarrier gb;
+  gb.init(bar, err, prm.barrier_timeout_ns);
   int k = 0;
   for (;; ++k) {
     // ---- decisions for iteration k (identical in every block)
@@ -178,7 +179,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         // one thread per (i, j) column marching up the slab: the z neighbours roll
         // through registers, each plane costs five shared loads per cell
         constexpr int PP = SL::P * SL::P;
-        const int i = threadIdx.x % B, j = threadIdx.x / B;
+        const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
         int o = SL::at(i, j, 1);
         TV below = S[o - PP], cur = S[o];
 #pragma unroll 4
@@ -215,7 +216,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       block_sum<NT, 1>(vals, red);
       if (threadIdx.x == 0) acc_add(g.ss[s], ACC_SLOT_PQ + k % 3, vals[0]);
     }
-    if (!grid_barrier(bar, err, limit)) break;
+    if (!gb.sync()) break;
     // ---- alpha per sim from the completed <p, q>
     for (int s = threadIdx.x; s < nsim; s += NT) {
       if (s_done[s]) continue;
@@ -238,15 +239,9 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
       const TV* __restrict__ pnew = ((k + s_poff[s]) & 1) ? p0 : p1;
       TV rz = TV(0), rr = TV(0);
-      for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
-        const int cell = 4 * q4;
-        TV xv[4], pv[4], rv[4], qv[4];
-        ld4(x + base + cell, xv);
-        ld4(pnew + base + cell, pv);
-        ld4(r + base + cell, rv);
-        ld4(q + base + cell, qv);
-        const int kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
-        const bool plain = cs.smask == 0;
+      const bool plain = cs.smask == 0;
+      auto update = [&](int q4, TV (&xv)[4], const TV (&pv)[4], TV (&rv)[4], const TV (&qv)[4]) {
+        const int cell = 4 * q4, kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           xv[e] = xv[e] + alpha * pv[e];
@@ -258,6 +253,27 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         }
         st4(x + base + cell, xv);
         st4(r + base + cell, rv);
+      };
+      // FP32: two quads per step, all eight loads in flight before any use
+      constexpr int NQ = KS * BB / 4, STEP = sizeof(TV) == 4 ? 2 : 1;
+      for (int q4 = threadIdx.x; q4 < NQ; q4 += STEP * NT) {
+        TV xa[4], pa[4], ra[4], qa[4];
+        ld4(x + base + 4 * q4, xa);
+        ld4(pnew + base + 4 * q4, pa);
+        ld4(r + base + 4 * q4, ra);
+        ld4(q + base + 4 * q4, qa);
+        if (STEP == 2 && q4 + NT < NQ) {
+          const int qb4 = q4 + NT;
+          TV xb[4], pbv[4], rb[4], qb[4];
+          ld4(x + base + 4 * qb4, xb);
+          ld4(pnew + base + 4 * qb4, pbv);
+          ld4(r + base + 4 * qb4, rb);
+          ld4(q + base + 4 * qb4, qb);
+          update(q4, xa, pa, ra, qa);
+          update(qb4, xb, pbv, rb, qb);
+        } else {
+          update(q4, xa, pa, ra, qa);
+        }
       }
       double vals[2] = {double(rz), double(rr)};
       block_sum<NT, 2>(vals, red);
@@ -266,7 +282,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         acc_add(g.ss[s], ACC_SLOT_RR + (k + 1) % 3, vals[1]);
       }
     }
-    if (!grid_barrier(bar, err, limit)) break;
+    if (!gb.sync()) break;
   }
   // the generation word keeps counting across launches: a block reads it before it
   // arrives, so any start value works
@@ -290,9 +306,10 @@ static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   int rc = max_coresident(kern, NT, sm, &maxg);
   if (rc) return (cudaError_t)rc;
   if (maxg < 1) return cudaErrorCooperativeLaunchTooLarge;
+  // every co-resident block takes part: the linear distribution then puts at most
+  // ceil(items / maxg) items on a block and evens out the items per SM
   const int items = x.g.n_cubes * (B / KS);
-  const int per = (items + maxg - 1) / maxg;
-  const int grid = (items + per - 1) / per;
+  const int grid = items < maxg ? items : maxg;
   DevGrid gg = x.g;
   TX* xp = xv;
   TV* rp = (TV*)x.f.r;
@@ -320,9 +337,21 @@ static cudaError_t pcg_dispatch(const Ctx& x, const SolveParams& prm, TX* xv) {
   }
 }
 
-cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm) {
+cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form) {
   if (x.g.n_sims > kMaxPersistentSims) return cudaErrorInvalidValue;
-  if (x.single_pass) return launch_pcg1(x, prm);
+  if (x.single_pass) {
+    *form = PCG_SINGLE_PASS;
+    return launch_pcg1(x, prm);
+  }
+  if (x.resident && x.slabs_p == 1) {
+    bool launched = false;
+    const cudaError_t e = launch_pcg_resident(x, prm, &launched);
+    if (e != cudaSuccess || launched) {
+      *form = PCG_RESIDENT;
+      return e;
+    }
+  }
+  *form = PCG_STREAMING;
   return x.f64 ? pcg_dispatch<double, double>(x, prm, x.f.p)
                : pcg_dispatch<float, float>(x, prm, x.f.e);
 }

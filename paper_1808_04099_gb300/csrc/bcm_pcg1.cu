@@ -85,7 +85,8 @@ __global__ __launch_bounds__(NT, 4) void k_pcg1(DevGrid g, TX* __restrict__ x,
     s_beta[s] = 0.0;
   }
   __syncthreads();
-  const unsigned long long limit = prm.barrier_timeout_ns;
+  GridBarrier gb;
+  gb.init(bar, err, prm.barrier_timeout_ns);
   // k = -1: the launch's first pass (w_0 and the dots of iteration 0)
   for (int k = -1;; ++k) {
     if (k >= 0) {
@@ -253,7 +254,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg1(DevGrid g, TX* __restrict__ x,
       TV de = TV(0);
       if (NT == BB) {
         constexpr int PP = SL::P * SL::P;
-        const int i = threadIdx.x % B, j = threadIdx.x / B;
+        const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
         int o = SL::at(i, j, 1);
         TV below = S[o - PP], cur = S[o];
 #pragma unroll 4
@@ -291,7 +292,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg1(DevGrid g, TX* __restrict__ x,
         acc_add(g.ss[s], ACC_SLOT_R + out, vals[3]);
       }
     }
-    if (!grid_barrier(bar, err, limit)) break;
+    if (!gb.sync()) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) g.flags[0] = 1;
 }

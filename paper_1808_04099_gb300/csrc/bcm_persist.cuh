@@ -18,55 +18,72 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier of a cooperative launch.  bar: [0] generation, [32 (1+s)] stripe
-// counters, [32 (1+kTickets)] top counter (one 128-byte line each).  Returns false
-// (and sets *err) when the wait exceeded limit_ns or another block reported an error.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err,
-                                             unsigned long long limit_ns) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar;
-    const unsigned int g0 = *gen;
-    __threadfence();
-    const unsigned int nblk = gridDim.x;
-    const unsigned int stripe = blockIdx.x % kTickets;
-    const unsigned int in_stripe = (nblk - stripe + kTickets - 1) / kTickets;
-    const unsigned int t = atomicAdd(&bar[32 * (1 + stripe)], 1u);
-    bool released = false;
-    if (t == in_stripe - 1) {
-      bar[32 * (1 + stripe)] = 0u;
-      __threadfence();
-      const unsigned int stripes = nblk < (unsigned)kTickets ? nblk : (unsigned)kTickets;
-      const unsigned int u = atomicAdd(&bar[32 * (1 + kTickets)], 1u);
-      if (u == stripes - 1) {
-        bar[32 * (1 + kTickets)] = 0u;
-        __threadfence();
-        atomicAdd(&bar[0], 1u);
-        released = true;
-      }
-    }
-    int good = 1;
-    if (!released) {
-      const unsigned long long t0 = global_ns();
-      while (*gen == g0) {
-        if (*(volatile int*)err) {
-          good = 0;
-          break;
-        }
-        if (global_ns() - t0 > limit_ns) {
-          atomicExch(err, 1);
-          good = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    ok = good;
+// counters, [32 (1+kTickets)] top counter (one 128-byte line each).  Thread 0 of each
+// block reads the generation once at the start of the kernel (init) and counts the
+// barriers it passes, so arriving costs no read of the generation: the generation
+// moves only when every block has arrived, hence never twice while one block waits.
+// sync() returns false (and sets *err) when the wait exceeded limit_ns or another
+// block reported an error.
+struct GridBarrier {
+  unsigned int* bar;
+  int* err;
+  unsigned long long limit_ns;
+  unsigned int gen;  // generation this block waits to see change (thread 0)
+
+  __device__ __forceinline__ void init(unsigned int* b, int* e, unsigned long long limit) {
+    bar = b;
+    err = e;
+    limit_ns = limit;
+    gen = threadIdx.x == 0 ? *(volatile unsigned int*)b : 0u;
   }
-  __syncthreads();
-  return ok != 0;
-}
+
+  __device__ __forceinline__ bool sync() {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      volatile unsigned int* g = bar;
+      __threadfence();  // this block's writes before its arrival
+      const unsigned int nblk = gridDim.x;
+      const unsigned int stripe = blockIdx.x % kTickets;
+      const unsigned int in_stripe = (nblk - stripe + kTickets - 1) / kTickets;
+      const unsigned int t = atomicAdd(&bar[32 * (1 + stripe)], 1u);
+      bool released = false;
+      if (t == in_stripe - 1) {
+        bar[32 * (1 + stripe)] = 0u;
+        __threadfence();
+        const unsigned int stripes = nblk < (unsigned)kTickets ? nblk : (unsigned)kTickets;
+        const unsigned int u = atomicAdd(&bar[32 * (1 + kTickets)], 1u);
+        if (u == stripes - 1) {
+          bar[32 * (1 + kTickets)] = 0u;
+          __threadfence();
+          atomicAdd(&bar[0], 1u);
+          released = true;
+        }
+      }
+      int good = 1;
+      if (!released) {
+        const unsigned long long t0 = global_ns();
+        while (*g == gen) {
+          if (*(volatile int*)err) {
+            good = 0;
+            break;
+          }
+          if (global_ns() - t0 > limit_ns) {
+            atomicExch(err, 1);
+            good = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      gen += 1;
+      __threadfence();
+      ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+  }
+};
 
 __device__ __forceinline__ double slot_sum(SimState& st, int idx) {
   double s = 0.0;

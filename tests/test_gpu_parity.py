@@ -239,43 +239,53 @@ def test_full_size_sphere_mixed_properties():
     assert rel_l2(g32.numpy(bcm.P), g64.numpy(bcm.P)) <= TOL32
 
 
-def test_full_size_sphere_single_pass_mixed():
-    """The single-reduction persistent PCG at the benchmark's full size: two mixed steps
-    at residual 1e-10 meet the tolerance and agree with the two-pass solver."""
+def test_full_size_sphere_persistent_forms_mixed():
+    """The persistent PCG forms at the benchmark's full size (16x8x8 cubes of 16^3):
+    two mixed steps at residual 1e-10 with the on-chip form (the default, one block per
+    cube), the single-reduction form and the streaming form meet the tolerance and agree."""
     spec = W.config_sphere(2)
     state = W.initial_state(spec)
     runs = []
-    for persistent in (1, 2):
+    for persistent in (1, 2, 3):
         g = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
         g.set_launch(1, 1, persistent=persistent)
         st = g.step(2, rtol=1e-10)
+        # 1024 cubes fit one co-resident wave of blocks of two 16^3 tiles (152 SMs x 4)
+        assert st[0]["pcg_form"] == {1: 3, 2: 2, 3: 1}[persistent]
         assert st[0]["converged"] == 1 and st[0]["rel_resid"] <= 1e-10
         assert st[0]["div_rel"] <= 1e-9
         runs.append((np.concatenate([g.numpy(f) for f in (bcm.U, bcm.V, bcm.W)]),
                      st[0]["cg_iters"]))
         del g
-    assert rel_l2(runs[1][0], runs[0][0]) <= TOL32
-    # same iterates in exact arithmetic: iteration counts within a few percent
-    assert abs(runs[1][1] - runs[0][1]) <= 0.1 * runs[0][1]
+    for vel, iters in runs[1:]:
+        assert rel_l2(vel, runs[0][0]) <= TOL32
+        # same iterates in exact arithmetic: iteration counts within a few percent
+        assert abs(iters - runs[0][1]) <= 0.1 * runs[0][1]
 
 
 @pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
 def test_launch_shapes_agree(prec):
     """Every PCG launch shape gives the oracle's result: the persistent cooperative
-    solver (two passes per iteration, or the single-reduction form) with 1, 2 or 4
-    z-slabs per work item, and the two-launch iteration with its slab counts per pass.
+    solver (two passes per iteration with the state on chip, or streamed with 1, 2 or
+    4 z-slabs per work item, or the single-reduction form), and the two-launch
+    iteration with its slab counts per pass.
     Shapes differ only in rounding."""
     spec = W.sphere_channel(2, 1, 1, 16, length=(2.0, 1.0, 1.0), radius=0.2,
                             center=(0.6, 0.5, 0.5))
     state = W.initial_state(spec, seed=21, noise=1e-3)
     ost, ostats = oracle_run(spec, state, 2, 1e-13)
     tol = TOL64 if prec == bcm.PREC_F64 else TOL32
-    shapes = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
+    shapes = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (3, 1, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
               (0, 1, 1), (0, 2, 4), (0, 4, 2), (0, 4, 4)]
     for persistent, sa, sb in shapes:
         g = gpu_grid(spec, prec, state)
         g.set_launch(sa, sb, persistent=persistent)
         st = g.step(2, rtol=1e-13 if prec == bcm.PREC_F64 else 1e-12)
+        if persistent:  # the form that ran: on chip only for the FP32 one-slab shape
+            on_chip = persistent == 1 and sa == 1 and prec == bcm.PREC_F32_REFINE
+            assert st[0]["pcg_form"] == (3 if on_chip else {1: 1, 2: 2, 3: 1}[persistent])
+        else:
+            assert st[0]["pcg_form"] == 0
         compare_fields(g, ost, spec, tol, per_component=(prec == bcm.PREC_F64))
         if prec == bcm.PREC_F64:
             assert abs(st[0]["cg_iters"] - ostats[0]["cg_iters"]) <= 2
@@ -288,14 +298,14 @@ def test_persistent_many_sims_and_fallback():
     spec = W.concat(specs)
     state = W.initial_state(spec, seed=22, noise=1e-3)
     ost, _ = oracle_run(spec, state, 2, 1e-13)
-    for persistent in (1, 2, 0):
+    for persistent in (1, 2, 3, 0):
         g = gpu_grid(spec, bcm.PREC_F64, state)
         g.set_launch(1, 1, persistent=persistent)
         g.step(2, rtol=1e-13)
         compare_fields(g, ost, spec, TOL64)
 
 
-@pytest.mark.parametrize("persistent", [1, 2])
+@pytest.mark.parametrize("persistent", [1, 2, 3])
 def test_barrier_timeout_reported_and_recovered(persistent):
     """A grid-barrier wait that runs out (a 1 ns limit) ends the persistent solve with
     BCM_E_TIMEOUT instead of waiting; the next solve with the normal limit is exact."""
@@ -326,12 +336,12 @@ def two_level_with_bodies():
     return spec
 
 
-@pytest.mark.parametrize("persistent", [None, 2])
+@pytest.mark.parametrize("persistent", [None, 2, 3])
 @pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
 def test_two_level_step(prec, persistent):
     """The full step on a two-level grid: paper halos for momentum, flux-form Poisson
     at the 2:1 faces, bodies in the refined block, against the oracle (default launch
-    shape, and the single-reduction persistent PCG)."""
+    shape, the single-reduction and the streaming persistent PCG)."""
     spec = two_level_with_bodies()
     state = W.initial_state(spec, seed=23, noise=1e-3)
     ost, ostats = oracle_run(spec, state, 3, 1e-13)
