@@ -189,17 +189,18 @@ bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int
                           double barrier_timeout_s, int recycle);
 
 /* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
- * whose blocks loop over the iterations with two grid-wide barriers each (default in
- * mixed mode for grids of at most 256 sims); when every cube gets a co-resident block
- * (FP32 inner solve, 16^3 or 8^3 cubes, slabs_a = 1) the launch keeps r and x in
- * registers and p, q in shared memory, otherwise it streams the vectors through global
- * memory.  persistent = 3: always the streaming form.  persistent = 2: the single-
- * reduction form of the iteration (Chronopoulos-Gear: one pass and one barrier per
- * iteration, three more vectors, the same iterates in exact arithmetic).  slabs_a =
- * z-slabs per cube of the streaming work items (1, 2 or 4; 16^3 cubes only for 2 and 4).
- * persistent = 0: two launches per iteration (the FP64 default), one CTA per z-slab,
- * slabs_a / slabs_b slabs per cube for pass A / pass B.  Results do not depend on the
- * shape beyond rounding.  BCM_E_INVALID for other values. */
+ * whose blocks loop over the iterations with two grid-wide barriers each, streaming
+ * the vectors through global memory (default in mixed mode for grids of at most 256
+ * sims); persistent = 3: the same iteration with each cube's search direction kept in
+ * shared memory, when every cube fits a co-resident block of at most two cubes (FP32
+ * inner solve, 16^3 or 8^3 cubes, slabs_a = 1), else the streaming form; persistent = 2:
+ * the single-reduction form of the iteration (Chronopoulos-Gear: one pass and one
+ * barrier per iteration, three more vectors, the same iterates in exact arithmetic).
+ * slabs_a = z-slabs per cube of the streaming work items (1, 2 or 4; 16^3 cubes only
+ * for 2 and 4).  persistent = 0: two launches per iteration (the FP64 default), one CTA
+ * per z-slab, slabs_a / slabs_b slabs per cube for pass A / pass B.  Results do not
+ * depend on the shape beyond rounding; bcm_stats.pcg_form says which form ran.
+ * BCM_E_INVALID for other values. */
 bcm_status bcm_set_launch(bcm_grid *grid, int persistent, int slabs_a, int slabs_b);
 
 /* Solve the pressure Poisson equation (Eq. poisson) for the current BCM_RHS into

@@ -1,7 +1,7 @@
 """Launch-shape autotuner of the PCG: the persistent cooperative solver (two passes
-per iteration with its state on chip where the grid allows, streaming with 1, 2 or 4
-z-slabs per work item, or the single-reduction form), or two launches per iteration
-with z-slabs per pass.
+per iteration streaming with 1, 2 or 4 z-slabs per work item or with the search
+direction in shared memory, or the single-reduction form), or two launches per
+iteration with z-slabs per pass.
 
 Times a fixed number of PCG iterations on the grid's current right-hand side for
 every shape with the library's own CUDA-event kernel timing, restores the pressure,
@@ -16,7 +16,7 @@ import os
 from . import bcm
 
 # (persistent, slabs_a, slabs_b)
-SHAPES = [(1, 1, 1), (3, 1, 1), (3, 2, 1), (3, 4, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
+SHAPES = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (3, 1, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
           (0, 1, 1), (0, 1, 2), (0, 2, 2)]
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "bcm_gb300_launch.json")
 

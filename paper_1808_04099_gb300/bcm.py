@@ -223,10 +223,10 @@ class Grid:
                                     barrier_timeout_s, recycle))
 
     def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: int = 1):
-        """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG (state
-        on chip when every cube fits a co-resident block), 2 the persistent
-        single-reduction PCG, 3 the persistent two-pass PCG streaming its vectors
-        through global memory (bool values map to 0 and 1)."""
+        """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG
+        streaming its vectors through global memory, 2 the persistent single-reduction
+        PCG, 3 the persistent two-pass PCG with the search direction in shared memory
+        where the grid fits one co-resident wave (bool values map to 0 and 1)."""
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
 
     def set_step(self, step: int):

@@ -468,7 +468,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   // slower in FP64 (ALU-bound passes), so FP64 defaults to two launches per iteration
   x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
   x.single_pass = 0;
-  x.resident = 1;
+  x.resident = 0;
   x.stream = s;
   DevGrid& G = x.g;
   G.n_cubes = n;
@@ -922,7 +922,7 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
   if (persistent < 0 || persistent > 3) return fail(BCM_E_INVALID, "persistent must be 0 .. 3");
   g->ctx.persistent = persistent ? 1 : 0;
   g->ctx.single_pass = persistent == 2 ? 1 : 0;
-  g->ctx.resident = persistent == 1 ? 1 : 0;
+  g->ctx.resident = persistent == 3 ? 1 : 0;
   if (persistent) {
     if (g->B != 16 && slabs_a != 1) return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
     g->ctx.slabs_p = slabs_a;

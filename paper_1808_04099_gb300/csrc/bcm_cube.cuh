@@ -230,28 +230,34 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 4 * KS * B; idx += NT) {
-    const int f = idx / (KS * B), rem = idx - f * (KS * B), kk = rem / B, t = rem - kk * B;
-    if (cs.nb[f] == NB_BOUNDARY) {
-      const int gpos = f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1);
-      const int mpos = f < 2 ? SL::at(f == 0 ? 0 : B - 1, t, kk + 1)
-                             : SL::at(t, f == 2 ? 0 : B - 1, kk + 1);
-      const TV m = S[mpos];
-      S[gpos] = cs.bc[f] == BC_OUTFLOW ? -m : m;
-    }
-  }
+  // domain faces: the ghost mirrors an own cell staged above (x/y ring and z planes
+  // touch disjoint ghosts); a cube without domain faces needs no second pass
   const bool lo = (z0 == 0 && cs.nb[4] == NB_BOUNDARY);
   const bool hi = (z0 + KS == B && cs.nb[5] == NB_BOUNDARY);
-  if (lo || hi) {
-    for (int idx = threadIdx.x; idx < 2 * BB; idx += NT) {
-      const int top = idx / BB, t = idx - top * BB, j = t / B, i = t - j * B;
-      if (top ? hi : lo) {
-        const TV m = S[SL::at(i, j, top ? KS : 1)];
-        S[SL::at(i, j, top ? KS + 1 : 0)] = cs.bc[top ? 5 : 4] == BC_OUTFLOW ? -m : m;
+  const bool ring = cs.nb[0] == NB_BOUNDARY || cs.nb[1] == NB_BOUNDARY ||
+                    cs.nb[2] == NB_BOUNDARY || cs.nb[3] == NB_BOUNDARY;
+  if (ring || lo || hi) {
+    if (ring)
+      for (int idx = threadIdx.x; idx < 4 * KS * B; idx += NT) {
+        const int f = idx / (KS * B), rem = idx - f * (KS * B), kk = rem / B, t = rem - kk * B;
+        if (cs.nb[f] == NB_BOUNDARY) {
+          const int gpos = f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1);
+          const int mpos = f < 2 ? SL::at(f == 0 ? 0 : B - 1, t, kk + 1)
+                                 : SL::at(t, f == 2 ? 0 : B - 1, kk + 1);
+          const TV m = S[mpos];
+          S[gpos] = cs.bc[f] == BC_OUTFLOW ? -m : m;
+        }
       }
-    }
+    if (lo || hi)
+      for (int idx = threadIdx.x; idx < 2 * BB; idx += NT) {
+        const int top = idx / BB, t = idx - top * BB, j = t / B, i = t - j * B;
+        if (top ? hi : lo) {
+          const TV m = S[SL::at(i, j, top ? KS : 1)];
+          S[SL::at(i, j, top ? KS + 1 : 0)] = cs.bc[top ? 5 : 4] == BC_OUTFLOW ? -m : m;
+        }
+      }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // Row j of the column that thread slot t (0 .. B*B-1, i = t % B) works on in the column

@@ -25,6 +25,8 @@
 
 namespace bcm {
 
+constexpr int kCubeCache = 4;  // cubes whose constants a block keeps for the whole solve
+
 template <int B, int KS, int NT, class TV, class TX>
 __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV* __restrict__ r,
                                             TV* __restrict__ p0, TV* __restrict__ p1,
@@ -34,7 +36,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
   constexpr int B3 = B * B * B, BB = B * B, NSL = B / KS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TV* S = reinterpret_cast<TV*>(smem_raw);
-  __shared__ CubeSh<TV> cs;
+  __shared__ CubeSh<TV> csa[kCubeCache];  // the block's cubes, or one reloaded per item
   __shared__ int cs_cube;
   __shared__ double red[2 * 32];
   const int nsim = g.n_sims;
@@ -63,6 +65,12 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     s_first[s] = cont ? 0 : 1;
     s_poff[s] = cont ? (unsigned char)(st.p_off & 1) : 0;
   }
+  // the block's items span cubes cA .. cB; their constants stay in shared memory
+  // when they fit the cache (every grid up to a few cubes per block)
+  const int cA = item0 / NSL, cB = (item0 + max(nitems, 1) - 1) / NSL;
+  const bool cached = cB - cA < kCubeCache;
+  if (cached)
+    for (int c = cA; c <= cB && c < g.n_cubes; ++c) load_cube(csa[c - cA], g, c);
   __syncthreads();
   GridBarrier gb;
   gb.init(bar, err, prm.barrier_timeout_ns);
@@ -115,17 +123,31 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         st.acc[sp][ACC_SLOT_RR + sl] = 0.0;
         st.acc[sp][ACC_SLOT_PQ + sl] = 0.0;
       }
-    // ---- pass A over my items
+    // ---- pass A over my items; <p, q> summed over the block's items of one sim
+    TV part = TV(0);
+    int psim = -1;
+    auto flush_pq = [&]() {
+      double vals[1] = {double(part)};
+      block_sum<NT, 1>(vals, red);
+      if (threadIdx.x == 0) acc_add(g.ss[psim], ACC_SLOT_PQ + k % 3, vals[0]);
+      part = TV(0);
+    };
     for (int it = 0; it < nitems; ++it) {
       const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
       const int s = g.sim[c];
       if (s_done[s]) continue;
-      if (cs_cube != c) {
+      if (psim >= 0) {
+        if (psim != s) flush_pq();
+        __syncthreads();  // the previous item's stencil has read the tile
+      }
+      psim = s;
+      if (!cached && cs_cube != c) {
         __syncthreads();
-        load_cube(cs, g, c);
+        load_cube(csa[0], g, c);
         if (threadIdx.x == 0) cs_cube = c;
         __syncthreads();
       }
+      const CubeSh<TV>& cs = csa[cached ? c - cA : 0];
       const TV beta = TV(s_beta[s]);
       const bool first = (k == 0) && s_first[s];
       const int pb = (k + s_poff[s]) & 1;
@@ -174,7 +196,6 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       stage_pressure_slab<B, KS, NT, TV>(S, cs, g, c, z0, val4, val1, valg);
       const TV h = TV(cell_h<B>(g, c));
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
-      TV part = TV(0);
       if (NT == BB) {
         // one thread per (i, j) column marching up the slab: the z neighbours roll
         // through registers, each plane costs five shared loads per cell
@@ -212,10 +233,8 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
           st4(q + base + cell, qv);
         }
       }
-      double vals[1] = {double(part)};
-      block_sum<NT, 1>(vals, red);
-      if (threadIdx.x == 0) acc_add(g.ss[s], ACC_SLOT_PQ + k % 3, vals[0]);
     }
+    if (psim >= 0) flush_pq();
     if (!gb.sync()) break;
     // ---- alpha per sim from the completed <p, q>
     for (int s = threadIdx.x; s < nsim; s += NT) {
@@ -224,21 +243,35 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       s_alpha[s] = (pq != 0.0 && isfinite(pq)) ? s_rz[s] / pq : 0.0;
     }
     __syncthreads();
-    // ---- pass B over my items (pointwise)
+    // ---- pass B over my items (pointwise); the dots summed per sim as in pass A
+    TV rz = TV(0), rr = TV(0);
+    psim = -1;
+    auto flush_rz = [&]() {
+      double vals[2] = {double(rz), double(rr)};
+      block_sum<NT, 2>(vals, red);
+      if (threadIdx.x == 0) {
+        acc_add(g.ss[psim], ACC_SLOT_RZ + (k + 1) % 3, vals[0]);
+        acc_add(g.ss[psim], ACC_SLOT_RR + (k + 1) % 3, vals[1]);
+      }
+      rz = TV(0);
+      rr = TV(0);
+    };
     for (int it = 0; it < nitems; ++it) {
       const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
       const int s = g.sim[c];
       if (s_done[s]) continue;
-      if (cs_cube != c) {
+      if (psim >= 0 && psim != s) flush_rz();
+      psim = s;
+      if (!cached && cs_cube != c) {
         __syncthreads();
-        load_cube(cs, g, c);
+        load_cube(csa[0], g, c);
         if (threadIdx.x == 0) cs_cube = c;
         __syncthreads();
       }
+      const CubeSh<TV>& cs = csa[cached ? c - cA : 0];
       const TV alpha = TV(s_alpha[s]);
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
       const TV* __restrict__ pnew = ((k + s_poff[s]) & 1) ? p0 : p1;
-      TV rz = TV(0), rr = TV(0);
       const bool plain = cs.smask == 0;
       auto update = [&](int q4, TV (&xv)[4], const TV (&pv)[4], TV (&rv)[4], const TV (&qv)[4]) {
         const int cell = 4 * q4, kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
@@ -275,13 +308,8 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
           update(q4, xa, pa, ra, qa);
         }
       }
-      double vals[2] = {double(rz), double(rr)};
-      block_sum<NT, 2>(vals, red);
-      if (threadIdx.x == 0) {
-        acc_add(g.ss[s], ACC_SLOT_RZ + (k + 1) % 3, vals[0]);
-        acc_add(g.ss[s], ACC_SLOT_RR + (k + 1) % 3, vals[1]);
-      }
     }
+    if (psim >= 0) flush_rz();
     if (!gb.sync()) break;
   }
   // the generation word keeps counting across launches: a block reads it before it
@@ -298,8 +326,8 @@ static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   const size_t tile = (sizeof(TV) * Slab<B, KS>::N + 15) / 16 * 16;
   const size_t sm = tile + (size_t)x.g.n_sims * (4 * sizeof(double) + 3);
   auto kern = k_pcg<B, KS, NT, TV, TX>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    const cudaError_t e = allow_dynamic_smem(kern, sm);
     if (e != cudaSuccess) return e;
   }
   int maxg = 0;

@@ -306,8 +306,8 @@ static cudaError_t pcg1_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   const size_t tile = (sizeof(TV) * Slab<B, KS>::N + 15) / 16 * 16;
   const size_t sm = tile + (size_t)x.g.n_sims * (4 * sizeof(double) + 3);
   auto kern = k_pcg1<B, KS, NT, TV, TX>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    const cudaError_t e = allow_dynamic_smem(kern, sm);
     if (e != cudaSuccess) return e;
   }
   int maxg = 0;

@@ -307,8 +307,8 @@ static cudaError_t pcg_res_t(const Ctx& x, const SolveParams& prm, bool* launche
   const size_t sm = sizeof(float) * (size_t)NC * ((SL::N + 3) / 4 * 4) +
                     (size_t)x.g.n_sims * (3 * sizeof(double) + 2);
   auto kern = k_pcg_res<B, NC>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    const cudaError_t e = allow_dynamic_smem(kern, sm);
     if (e != cudaSuccess) return e;
   }
   // the whole unified L1 as shared memory: four blocks of two 16^3 tiles need ~190 KB

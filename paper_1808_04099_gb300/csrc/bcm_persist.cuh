@@ -92,6 +92,18 @@ __device__ __forceinline__ double slot_sum(SimState& st, int idx) {
   return s;
 }
 
+// Dynamic shared memory beyond the default limit (48 KB minus the kernel's static
+// shared memory) needs the kernel's opt-in.
+template <class K>
+inline cudaError_t allow_dynamic_smem(K kern, size_t dyn) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if (fa.sharedSizeBytes + dyn > 48 * 1024)
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  return cudaSuccess;
+}
+
 template <int B>
 constexpr int pcg_threads() { return B == 16 ? 256 : (B == 8 ? 128 : 64); }
 

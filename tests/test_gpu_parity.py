@@ -241,8 +241,9 @@ def test_full_size_sphere_mixed_properties():
 
 def test_full_size_sphere_persistent_forms_mixed():
     """The persistent PCG forms at the benchmark's full size (16x8x8 cubes of 16^3):
-    two mixed steps at residual 1e-10 with the on-chip form (the default, one block per
-    cube), the single-reduction form and the streaming form meet the tolerance and agree."""
+    two mixed steps at residual 1e-10 with the streaming form (the default), the
+    single-reduction form and the shared-memory form (two cubes per block) meet the
+    tolerance and agree."""
     spec = W.config_sphere(2)
     state = W.initial_state(spec)
     runs = []
@@ -251,7 +252,7 @@ def test_full_size_sphere_persistent_forms_mixed():
         g.set_launch(1, 1, persistent=persistent)
         st = g.step(2, rtol=1e-10)
         # 1024 cubes fit one co-resident wave of blocks of two 16^3 tiles (152 SMs x 4)
-        assert st[0]["pcg_form"] == {1: 3, 2: 2, 3: 1}[persistent]
+        assert st[0]["pcg_form"] == persistent
         assert st[0]["converged"] == 1 and st[0]["rel_resid"] <= 1e-10
         assert st[0]["div_rel"] <= 1e-9
         runs.append((np.concatenate([g.numpy(f) for f in (bcm.U, bcm.V, bcm.W)]),
@@ -275,14 +276,14 @@ def test_launch_shapes_agree(prec):
     state = W.initial_state(spec, seed=21, noise=1e-3)
     ost, ostats = oracle_run(spec, state, 2, 1e-13)
     tol = TOL64 if prec == bcm.PREC_F64 else TOL32
-    shapes = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (3, 1, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1),
-              (0, 1, 1), (0, 2, 4), (0, 4, 2), (0, 4, 4)]
+    shapes = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (3, 1, 1), (3, 2, 1), (2, 1, 1), (2, 2, 1),
+              (2, 4, 1), (0, 1, 1), (0, 2, 4), (0, 4, 2), (0, 4, 4)]
     for persistent, sa, sb in shapes:
         g = gpu_grid(spec, prec, state)
         g.set_launch(sa, sb, persistent=persistent)
         st = g.step(2, rtol=1e-13 if prec == bcm.PREC_F64 else 1e-12)
         if persistent:  # the form that ran: on chip only for the FP32 one-slab shape
-            on_chip = persistent == 1 and sa == 1 and prec == bcm.PREC_F32_REFINE
+            on_chip = persistent == 3 and sa == 1 and prec == bcm.PREC_F32_REFINE
             assert st[0]["pcg_form"] == (3 if on_chip else {1: 1, 2: 2, 3: 1}[persistent])
         else:
             assert st[0]["pcg_form"] == 0
