@@ -1,19 +1,21 @@
 // bcm_pcg.cu -- persistent Jacobi-PCG solver kernel (Eq. poisson; Saad, Alg. 9.1).
 //
-// One cooperative launch runs all PCG iterations of a solve.  Work items are
-// z-slabs of cubes; block p owns a contiguous run of items by the paper's
-// load-balanced linear distribution (Eq. loaddist: L = floor(N/P), R = N mod P,
-// n_p = floor((N + P - p - 1) / P)), so Z-ordered neighbours mostly share a block.
-// Each iteration is pass A (p = z + beta p, q = K p, <p,q>), a grid barrier, pass B
+// One cooperative launch runs all PCG iterations of a solve on every co-resident block.
+// Work items are z-slabs of cubes; block p owns a contiguous run of items by the
+// paper's load-balanced linear distribution (Eq. loaddist: L = floor(N/P), R = N mod P,
+// n_p = floor((N + P - p - 1) / P)), so Z-ordered neighbours mostly share a block, and
+// keeps the constants of its cubes in shared memory for the whole solve.  Each
+// iteration is pass A (p = z + beta p, q = K p, <p,q>), a grid barrier, pass B
 // (x += alpha p, r -= alpha q, <r,z>, <r,r>), and a second grid barrier.
 //
 // The per-sim scalars never need a single writer: the dot products go to striped
 // accumulators in three rotating slots (iteration k mod 3), and after each barrier
 // every block derives alpha, beta and the convergence decision from the same sums.
-// Block 0 clears the slot that iteration k+1 will fill.  Grid barriers are
-// two-level tickets (32 striped counters, then one) with a generation word; every
-// wait is bounded by %globaltimer and a timeout sets an error flag and ends the
-// kernel (reported to the host as BCM_E_TIMEOUT), so a fault never hangs the GPU.
+// Block 0 clears the slot that iteration k+1 will fill.  A grid barrier counts the
+// arrivals on one counter (a reduction that returns nothing) and waits until it reaches
+// the grid size times the barriers passed; every wait is bounded by %globaltimer, and a
+// timeout sets an error flag and ends the kernel (reported to the host as
+// BCM_E_TIMEOUT), so a fault never hangs the GPU.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -312,8 +314,6 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     if (psim >= 0) flush_rz();
     if (!gb.sync()) break;
   }
-  // the generation word keeps counting across launches: a block reads it before it
-  // arrives, so any start value works
   if (blockIdx.x == 0 && threadIdx.x == 0) g.flags[0] = 1;
 }
 
@@ -367,6 +367,11 @@ static cudaError_t pcg_dispatch(const Ctx& x, const SolveParams& prm, TX* xv) {
 
 cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form) {
   if (x.g.n_sims > kMaxPersistentSims) return cudaErrorInvalidValue;
+  // every launch starts its grid barrier's arrival counter at zero
+  {
+    const cudaError_t e = cudaMemsetAsync(x.f.bar + 32, 0, 32 * sizeof(unsigned int), x.stream);
+    if (e != cudaSuccess) return e;
+  }
   if (x.single_pass) {
     *form = PCG_SINGLE_PASS;
     return launch_pcg1(x, prm);

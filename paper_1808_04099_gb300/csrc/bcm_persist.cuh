@@ -17,53 +17,39 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier of a cooperative launch.  bar: [0] generation, [32 (1+s)] stripe
-// counters, [32 (1+kTickets)] top counter (one 128-byte line each).  Thread 0 of each
-// block reads the generation once at the start of the kernel (init) and counts the
-// barriers it passes, so arriving costs no read of the generation: the generation
-// moves only when every block has arrived, hence never twice while one block waits.
+// Grid-wide barrier of a cooperative launch: one arrival counter, bar[32] (a 128-byte
+// line of its own), zeroed before every launch (launch_pcg).  A block arrives with a
+// reduction that returns nothing (thread 0, after a fence that publishes the block's
+// writes) and waits until the counter reaches gridDim.x times the number of barriers
+// it has passed, so the release costs one round trip after the last arrival.
 // sync() returns false (and sets *err) when the wait exceeded limit_ns or another
 // block reported an error.
 struct GridBarrier {
-  unsigned int* bar;
+  unsigned int* count;
   int* err;
   unsigned long long limit_ns;
-  unsigned int gen;  // generation this block waits to see change (thread 0)
+  unsigned int passed;  // barriers this block has passed (thread 0)
 
-  __device__ __forceinline__ void init(unsigned int* b, int* e, unsigned long long limit) {
-    bar = b;
+  __device__ __forceinline__ void init(unsigned int* bar, int* e, unsigned long long limit) {
+    count = bar + 32;
     err = e;
     limit_ns = limit;
-    gen = threadIdx.x == 0 ? *(volatile unsigned int*)b : 0u;
+    passed = 0u;
   }
 
   __device__ __forceinline__ bool sync() {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-      volatile unsigned int* g = bar;
       __threadfence();  // this block's writes before its arrival
-      const unsigned int nblk = gridDim.x;
-      const unsigned int stripe = blockIdx.x % kTickets;
-      const unsigned int in_stripe = (nblk - stripe + kTickets - 1) / kTickets;
-      const unsigned int t = atomicAdd(&bar[32 * (1 + stripe)], 1u);
-      bool released = false;
-      if (t == in_stripe - 1) {
-        bar[32 * (1 + stripe)] = 0u;
-        __threadfence();
-        const unsigned int stripes = nblk < (unsigned)kTickets ? nblk : (unsigned)kTickets;
-        const unsigned int u = atomicAdd(&bar[32 * (1 + kTickets)], 1u);
-        if (u == stripes - 1) {
-          bar[32 * (1 + kTickets)] = 0u;
-          __threadfence();
-          atomicAdd(&bar[0], 1u);
-          released = true;
-        }
-      }
+      atomicAdd(count, 1u);
+      passed += 1u;
+      const unsigned int target = passed * gridDim.x;
+      volatile unsigned int* c = count;
       int good = 1;
-      if (!released) {
+      if ((int)(*c - target) < 0) {
         const unsigned long long t0 = global_ns();
-        while (*g == gen) {
+        while ((int)(*c - target) < 0) {
           if (*(volatile int*)err) {
             good = 0;
             break;
@@ -76,7 +62,6 @@ struct GridBarrier {
           __nanosleep(32);
         }
       }
-      gen += 1;
       __threadfence();
       ok = good;
     }

@@ -309,8 +309,11 @@ def test_persistent_many_sims_and_fallback():
 @pytest.mark.parametrize("persistent", [1, 2, 3])
 def test_barrier_timeout_reported_and_recovered(persistent):
     """A grid-barrier wait that runs out (a 1 ns limit) ends the persistent solve with
-    BCM_E_TIMEOUT instead of waiting; the next solve with the normal limit is exact."""
-    spec = W.cavity(2, 8)
+    BCM_E_TIMEOUT instead of waiting; the next solve with the normal limit is exact.
+    64 cubes of 16^3: blocks wait microseconds at a barrier, many ticks of the device
+    timer, so the 1 ns limit runs out (a grid of a few small cubes can pass every
+    barrier within one tick)."""
+    spec = W.cavity(4, 16)
     state = W.initial_state(spec, 5, 1e-2)
     g = gpu_grid(spec, bcm.PREC_F32_REFINE, state)
     g.set_launch(1, 1, persistent=persistent)
