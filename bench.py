@@ -57,6 +57,32 @@ def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
     }[kernel]
 
 
+PROFILE = "profiles/pcg_sphere_16x8x8_B16_mixed.md"
+PCG_SOURCES = ["bcm_pcg.cu", "bcm_persist.cuh", "bcm_cube.cuh", "bcm_internal.cuh",
+               "bcm_kernels.h"]
+
+
+def profiled_pcg_traffic():
+    """DRAM bytes per PCG iteration from the committed ncu summary, or None when the
+    kernel sources changed since those counters were taken (hash recorded there)."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(here, PROFILE)).read()
+        h = hashlib.sha256()
+        for f in PCG_SOURCES:
+            with open(os.path.join(here, "paper_1808_04099_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    m_hash = re.search(r"= `([0-9a-f]{16})`", text)
+    m_bytes = re.search(r"dram bytes per PCG iteration: (\d+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != h.hexdigest()[:16]:
+        return None
+    return float(m_bytes.group(1))
+
+
 def kernel_table(prof, n, f64, phi_frac, pcg_iters):
     """Per kernel class: launches, time, algorithmic bytes and GB/s.  The persistent
     PCG moves 10 S bytes per cell per iteration; pcg_iters = iterations it ran."""
@@ -304,10 +330,16 @@ def gpu_arm(args, ws, rank, local):
     kern = kernel_table(prof, n, False, phi_frac, iters32)
     dom = max(kern, key=lambda k: kern[k]["total_ms"])
     d = kern[dom]
+    traffic = None
+    if dom == "pcg" and d.get("launches"):
+        per_iter = profiled_pcg_traffic()
+        if per_iter is not None:
+            traffic = per_iter * d["units"] / d["launches"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"], "peak": peak,
                 "unit": "GB/s", "frac": d["GBps"] / peak if d["GBps"] else None,
-                "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_launch": d["bytes_per_launch"]}
+                "traffic": traffic, "peak_kind": peak_kind,
+                "bytes_per_launch": d["bytes_per_launch"],
+                "traffic_source": PROFILE if traffic is not None else None}
     share = {k: kern[k]["total_ms"] / sum(v["total_ms"] for v in kern.values()) for k in kern}
 
     # ---- e2e through the C ABI with host buffers (pinned), mixed precision
