@@ -85,7 +85,8 @@ typedef struct {
     int32_t cells_per_edge;       /* B: 4, 8 or 16 */
     int32_t max_level;            /* 0 or 1 */
     int32_t precision;            /* BCM_PREC_* */
-    int32_t reserved;
+    int32_t lagged_bf16;          /* 1: BCM_PREC_F32_REFINE stores the lagged convection
+                                     N^{n-1} (BCM_NX..NZ) as bfloat16; else 0 */
     const int32_t *sim_cube_offset; /* [n_sims+1] */
     const int32_t *cube_ijk;        /* [n_cubes*3] base corners */
     const int8_t *cube_level;       /* [n_cubes] */

@@ -33,7 +33,7 @@ KERNEL_NAMES = ["solid_fraction", "momentum", "rhs", "residual", "cg_a", "cg_b",
 
 class GridDesc(C.Structure):
     _fields_ = [("n_sims", C.c_int32), ("n_cubes", C.c_int32), ("cells_per_edge", C.c_int32),
-                ("max_level", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("max_level", C.c_int32), ("precision", C.c_int32), ("lagged_bf16", C.c_int32),
                 ("sim_cube_offset", C.c_void_p), ("cube_ijk", C.c_void_p),
                 ("cube_level", C.c_void_p), ("sim_extent", C.c_void_p),
                 ("sim_origin", C.c_void_p), ("sim_h0", C.c_void_p), ("sim_bc", C.c_void_p),
@@ -130,7 +130,10 @@ def _body_struct(b) -> Body:
 class Grid:
     """One BCM grid (one or more independent sims) living in a torch-owned workspace."""
 
-    def __init__(self, spec, precision: int = PREC_F64, device=None, stream=None):
+    def __init__(self, spec, precision: int = PREC_F64, device=None, stream=None,
+                 lagged_bf16: bool = False):
+        """lagged_bf16: in mixed precision, store the lagged convection N^{n-1} (fields
+        NX, NY, NZ) as bfloat16."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the BCM library needs a CUDA device")
@@ -153,6 +156,7 @@ class Grid:
         d = GridDesc()
         d.n_sims, d.n_cubes, d.cells_per_edge = spec.n_sims, spec.n_cubes, spec.B
         d.max_level, d.precision = spec.max_level, precision
+        d.lagged_bf16 = 1 if lagged_bf16 else 0
         (d.sim_cube_offset, d.cube_ijk, d.cube_level, d.sim_extent, d.sim_origin, d.sim_h0,
          d.sim_bc, d.sim_bc_vel, d.sim_nu, d.sim_dt, d.sim_uconv) = \
             [a.ctypes.data for a in self._arrays]
@@ -188,7 +192,7 @@ class Grid:
         _check(lib().bcm_field(self._h, fid, C.byref(ptr), C.byref(cnt), C.byref(eb)))
         off = ptr.value - self.workspace.data_ptr()
         n = cnt.value * eb.value
-        dt = torch.float64 if eb.value == 8 else torch.float32
+        dt = {8: torch.float64, 4: torch.float32, 2: torch.bfloat16}[eb.value]
         return self.workspace[off:off + n].view(dt)
 
     def load_state(self, state):

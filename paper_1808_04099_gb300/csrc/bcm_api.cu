@@ -72,6 +72,8 @@ bcm_status validate(const bcm_grid_desc* d) {
   if (d->max_level < 0 || d->max_level > 1) return fail(BCM_E_INVALID, "max_level must be 0 or 1");
   if (d->precision != BCM_PREC_F64 && d->precision != BCM_PREC_F32_REFINE)
     return fail(BCM_E_INVALID, "unknown precision %d", d->precision);
+  if (d->lagged_bf16 != 0 && (d->lagged_bf16 != 1 || d->precision != BCM_PREC_F32_REFINE))
+    return fail(BCM_E_INVALID, "lagged_bf16 must be 0, or 1 with BCM_PREC_F32_REFINE");
   if (!d->sim_cube_offset || !d->cube_ijk || !d->cube_level || !d->sim_extent ||
       !d->sim_origin || !d->sim_h0 || !d->sim_bc || !d->sim_bc_vel || !d->sim_nu ||
       !d->sim_dt || !d->sim_uconv)
@@ -469,6 +471,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
   x.single_pass = 0;
   x.resident = 0;
+  x.lag_bf16 = desc->lagged_bf16;
   x.stream = s;
   DevGrid& G = x.g;
   G.n_cubes = n;
@@ -529,9 +532,9 @@ extern "C" bcm_status bcm_field(bcm_grid* g, int field, void** dev_ptr, size_t* 
     case BCM_W: off = L.w; break;
     case BCM_P: off = L.p; eb = 8; break;
     case BCM_PHI: off = L.phi; break;
-    case BCM_NX: off = L.nx; break;
-    case BCM_NY: off = L.ny; break;
-    case BCM_NZ: off = L.nz; break;
+    case BCM_NX: off = L.nx; eb = g->ctx.lag_bf16 ? 2 : S; break;
+    case BCM_NY: off = L.ny; eb = g->ctx.lag_bf16 ? 2 : S; break;
+    case BCM_NZ: off = L.nz; eb = g->ctx.lag_bf16 ? 2 : S; break;
     case BCM_USTAR: off = L.us; break;
     case BCM_VSTAR: off = L.vs; break;
     case BCM_WSTAR: off = L.ws; break;

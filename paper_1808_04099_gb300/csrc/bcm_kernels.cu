@@ -5,6 +5,7 @@
 // contraction, so no tensor cores): cube-major SoA rows are read coalesced, each
 // CTA stages its cube (or a z-slab) plus a one-cell face halo in shared memory, and
 // Krylov dot products are reduced with warp shuffles into FP64 per-sim atomics.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -221,11 +222,20 @@ __global__ __launch_bounds__(NT) void k_solid_fraction(DevGrid g, T* __restrict_
 //   u* = u~ + phi (u_s - u~),  drag -= phi (u_s - u~) V / dt   (R5)
 // and the convective outflow face update u_b^{n+1} (R8).
 // ===========================================================================
-template <int B, int KS, int NT, class T>
+// The lagged convection N^{n-1} in its storage type: the state type, or bfloat16
+// (round to nearest even) in mixed mode when the grid asks for it.
+__device__ __forceinline__ float lag_load(const float* p) { return *p; }
+__device__ __forceinline__ double lag_load(const double* p) { return *p; }
+__device__ __forceinline__ float lag_load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void lag_store(float* p, float v) { *p = v; }
+__device__ __forceinline__ void lag_store(double* p, double v) { *p = v; }
+__device__ __forceinline__ void lag_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <int B, int KS, int NT, class T, class TN>
 __global__ __launch_bounds__(NT) void k_momentum(
     DevGrid g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
-    T* __restrict__ us, T* __restrict__ vs, T* __restrict__ ws, T* __restrict__ nx,
-    T* __restrict__ ny, T* __restrict__ nz, const T* __restrict__ phi,
+    T* __restrict__ us, T* __restrict__ vs, T* __restrict__ ws, TN* __restrict__ nx,
+    TN* __restrict__ ny, TN* __restrict__ nz, const T* __restrict__ phi,
     const unsigned char* __restrict__ bid, T* __restrict__ ub) {
   using SL = Slab<B, KS>;
   constexpr int B3 = B * B * B, NSL = B / KS;
@@ -252,7 +262,7 @@ __global__ __launch_bounds__(NT) void k_momentum(
   const double t = g.ss[s].step * sp.dt;
   const T* Sf[3] = {S0, S1, S2};
   T* outs[3] = {us, vs, ws};
-  T* Ns[3] = {nx, ny, nz};
+  TN* Ns[3] = {nx, ny, nz};
   T fsum[3] = {T(0), T(0), T(0)};
   for (int q = threadIdx.x; q < KS * B * B; q += NT) {
     const int kk = q / (B * B), rem = q - kk * B * B, j = rem / B, i = rem - j * B;
@@ -290,11 +300,11 @@ __global__ __launch_bounds__(NT) void k_momentum(
       }
       N *= ih;
       L *= ih2;
-      const T Np = first ? N : Ns[comp][gi];
+      const T Np = first ? N : T(lag_load(Ns[comp] + gi));
       const T ut = u0 + dt * (-(T(1.5) * N - T(0.5) * Np) + nu * L);
       const T du = ph * (usb[comp] - ut);
       outs[comp][gi] = ut + du;
-      Ns[comp][gi] = N;
+      lag_store(Ns[comp] + gi, N);
       fsum[comp] += du;
     }
   }
@@ -563,23 +573,24 @@ cudaError_t launch_solid_fraction(const Ctx& x, int sim_filter) {
   return x.f64 ? solid_fraction_t<double>(x, sim_filter) : solid_fraction_t<float>(x, sim_filter);
 }
 
-template <class T>
+template <class T, class TN>
 static cudaError_t momentum_t(const Ctx& x) {
   BCM_DISPATCH_B(x.B, {
     constexpr int NT = threads_for<B>(), KS = slab3<B, T>();
     const size_t sm = 3 * sizeof(T) * Slab<B, KS>::N;
-    auto kern = k_momentum<B, KS, NT, T>;
+    auto kern = k_momentum<B, KS, NT, T, TN>;
     cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
     kern<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(
         x.g, (const T*)x.f.u, (const T*)x.f.v, (const T*)x.f.w, (T*)x.f.us, (T*)x.f.vs,
-        (T*)x.f.ws, (T*)x.f.nx, (T*)x.f.ny, (T*)x.f.nz, (const T*)x.f.phi, x.f.bid,
+        (T*)x.f.ws, (TN*)x.f.nx, (TN*)x.f.ny, (TN*)x.f.nz, (const T*)x.f.phi, x.f.bid,
         (T*)x.f.ub);
   });
   return cudaGetLastError();
 }
 cudaError_t launch_momentum(const Ctx& x) {
-  return x.f64 ? momentum_t<double>(x) : momentum_t<float>(x);
+  if (x.f64) return momentum_t<double, double>(x);
+  return x.lag_bf16 ? momentum_t<float, __nv_bfloat16>(x) : momentum_t<float, float>(x);
 }
 
 template <class T>

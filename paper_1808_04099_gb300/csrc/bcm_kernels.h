@@ -47,7 +47,8 @@ struct Ctx {
   int slabs_p;  // persistent PCG: z-slabs per cube (1, 2 or 4)
   int persistent;  // 1: one cooperative launch per PCG solve; 0: two launches per iteration
   int single_pass; // persistent PCG: one pass and one grid barrier per iteration
-  int resident;    // persistent PCG: keep r, x, p, q on chip when every cube fits a block
+  int resident;    // persistent PCG: search direction in shared memory where it fits
+  int lag_bf16;    // mixed mode: N^{n-1} stored as bfloat16
   cudaStream_t stream;
 };
 
