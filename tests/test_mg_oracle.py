@@ -1,0 +1,120 @@
+"""Pins of the oracle's multigrid preconditioner (oracle/mg_oracle.py) to things other
+than itself: the Galerkin operators of the per-cube levels against the closed form of
+the flux-form operator at the coarse spacing (built here from the geometry alone),
+symmetry and positive definiteness of M^-1, convergence of the V-cycle as an
+iteration, and PCG with M^-1 against a dense direct solve."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg  # noqa: F401  (spsolve)
+
+import oracle as O
+from oracle import mg_oracle as MGO
+from paper_1808_04099_gb300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+
+def closed_form_level(spec, l):
+    """Flux-form operator of a single-sim, single-level grid at level l (cells of
+    2^l h): a face between two cells of level l carries 4^l fine faces of coefficient
+    h (area h^2 over distance h), so its coefficient is 4^l h; an outflow face (p = 0
+    on the face) gives 2 x that on the diagonal, other domain faces nothing, and
+    periodic faces wrap."""
+    assert spec.n_sims == 1 and spec.max_level == 0
+    B = spec.B
+    bl = B >> l
+    h = spec.sim_h0[0]
+    coef = (4.0 ** l) * h
+    ext = np.asarray(spec.sim_extent[0]) // (1 << l)
+    cubes = np.asarray(spec.cube_ijk).reshape(-1, 3) // B
+    index = {}
+    n = 0
+    for c, cc in enumerate(cubes):
+        for k in range(bl):
+            for j in range(bl):
+                for i in range(bl):
+                    index[(cc[0] * bl + i, cc[1] * bl + j, cc[2] * bl + k)] = \
+                        (c * bl + k) * bl * bl + j * bl + i
+                    n += 1
+    rows, cols, vals = [], [], []
+    bc = list(spec.sim_bc[0])
+    for X, u in index.items():
+        diag = 0.0
+        for d in range(3):
+            for side, step in ((0, -1), (1, 1)):
+                Y = list(X)
+                Y[d] += step
+                f = 2 * d + side
+                if 0 <= Y[d] < ext[d]:
+                    v = index[tuple(Y)]
+                elif bc[f] == W.PERIODIC:
+                    Y[d] %= ext[d]
+                    v = index[tuple(Y)]
+                elif bc[f] == W.OUTFLOW:
+                    diag += 2.0 * coef
+                    continue
+                else:
+                    continue
+                if v == u:
+                    continue
+                diag += coef
+                rows.append(u)
+                cols.append(v)
+                vals.append(-coef)
+        rows.append(u)
+        cols.append(u)
+        vals.append(diag)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+GRIDS = {
+    "channel": lambda: W.sphere_channel(4, 2, 2, 4, length=(4.0, 2.0, 2.0), radius=0.3),
+    "cavity": lambda: W.cavity(2, 4),
+    "periodic": lambda: W.periodic_box(2, 4),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRIDS))
+def test_galerkin_levels_equal_closed_form(name):
+    spec = GRIDS[name]()
+    mg = MGO.MG(O.Oracle(spec))
+    L = int(round(math.log2(spec.B)))
+    for l in range(L + 1):
+        ref = closed_form_level(spec, l)
+        diff = abs(mg.Ks[l] - ref).max()
+        assert diff <= 1e-12 * abs(ref).max(), (l, diff)
+
+
+@pytest.mark.parametrize("name", ["channel", "cavity"])
+def test_preconditioner_symmetric_positive_definite(name):
+    spec = W.sphere_channel(2, 2, 2, 4, length=(2.0, 2.0, 2.0), radius=0.2,
+                            center=(0.5, 1.0, 1.0)) if name == "channel" else W.cavity(2, 4)
+    mg = MGO.MG(O.Oracle(spec))
+    M = mg.matrix()
+    assert np.abs(M - M.T).max() <= 1e-13 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0.0
+
+
+def test_vcycle_iteration_converges():
+    """x <- x + M^-1 (b - K x) is a convergent iteration: rho(I - M^-1 K) < 1."""
+    spec = W.sphere_channel(2, 2, 2, 4, length=(2.0, 2.0, 2.0), radius=0.2,
+                            center=(0.5, 1.0, 1.0))
+    mg = MGO.MG(O.Oracle(spec))
+    E = np.eye(mg.K.shape[0]) - mg.matrix() @ mg.K.toarray()
+    assert np.abs(np.linalg.eigvals(E)).max() < 0.9
+
+
+def test_mg_pcg_matches_direct_solve_in_fewer_iterations():
+    spec = W.sphere_channel(4, 2, 2, 8, radius=0.3)
+    mg = MGO.MG(O.Oracle(spec))
+    K = mg.K
+    b = np.random.default_rng(3).standard_normal(K.shape[0])
+    x, it = MGO.pcg(K, b, mg.apply, 1e-11)
+    xd = sp.linalg.spsolve(sp.csc_matrix(K), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    d = K.diagonal()
+    _, it_j = MGO.pcg(K, b, lambda r: r / d, 1e-11)
+    assert it * 3 < it_j, (it, it_j)
