@@ -18,7 +18,8 @@ Here the multigrid is the preconditioner of that CG, on single-level grids:
   transfer  P_l: level l+1 -> level l, piecewise constant (each fine unknown takes the
             value of the coarse unknown covering it); restriction P_l^T (sums).
   operators K_0 = K, K_{l+1} = P_l^T K_l P_l (Galerkin).
-  smoother  S_l = omega D_l^-1, D_l = diag(K_l) (a zero diagonal gives 0), omega = 0.8.
+  smoother  S_l = omega D_l^-1, D_l = diag(K_l) (a zero diagonal gives 0: the top node
+            of a sim without outflow faces, where K 1 = 0), omega = 0.8.
   V-cycle   V_l(r):  x = S_l r;  x += P_l V_{l+1}(P_l^T (r - K_l x));
                      x += S_l (r - K_l x);  return x
             V_top(r): x = 0; four times x += S (r - K x); return x
@@ -115,24 +116,35 @@ def galerkin(K, Ps):
     return Ks
 
 
-def _smooth(Kl, r):
-    d = Kl.diagonal()
-    inv = np.where(d != 0.0, 1.0 / np.where(d != 0.0, d, 1.0), 0.0)
-    return OMEGA * inv * r
+def inverse_diagonals(Ks, Ps) -> List[np.ndarray]:
+    """omega / diag(K_l) per level; a zero diagonal gives 0.  A Galerkin diagonal is a
+    sum of non-negative face coefficients; one that is zero in exact arithmetic (the top
+    node of a sim without an outflow face, where K 1 = 0) comes out of the
+    floating-point products as round-off, so a diagonal below 1e-12 of the diagonals it
+    aggregates (summed in absolute value down to the finest level) counts as zero."""
+    mass = np.abs(Ks[0].diagonal())
+    out = []
+    for l, Kl in enumerate(Ks):
+        if l:
+            mass = Ps[l - 1].T @ mass
+        d = Kl.diagonal()
+        zero = np.abs(d) <= 1e-12 * mass
+        out.append(np.where(zero, 0.0, OMEGA / np.where(zero, 1.0, d)))
+    return out
 
 
-def vcycle(Ks, Ps, r: np.ndarray, l: int = 0) -> np.ndarray:
-    """V_l(r) as defined in the module docstring."""
-    Kl = Ks[l]
+def vcycle(Ks, Ps, Ws, r: np.ndarray, l: int = 0) -> np.ndarray:
+    """V_l(r) as defined in the module docstring (Ws: the smoothers omega D_l^-1)."""
+    Kl, S = Ks[l], Ws[l]
     if l == len(Ps):  # top
         x = np.zeros_like(r)
         for _ in range(NU_TOP):
-            x = x + _smooth(Kl, r - Kl @ x)
+            x = x + S * (r - Kl @ x)
         return x
     P = Ps[l]
-    x = _smooth(Kl, r)
-    x = x + P @ vcycle(Ks, Ps, P.T @ (r - Kl @ x), l + 1)
-    x = x + _smooth(Kl, r - Kl @ x)
+    x = S * r
+    x = x + P @ vcycle(Ks, Ps, Ws, P.T @ (r - Kl @ x), l + 1)
+    x = x + S * (r - Kl @ x)
     return x
 
 
@@ -145,9 +157,10 @@ class MG:
         self.maps = parent_maps(oracle.spec)
         self.Ps = prolongators(self.maps)
         self.Ks = galerkin(self.K, self.Ps)
+        self.Ws = inverse_diagonals(self.Ks, self.Ps)
 
     def apply(self, r: np.ndarray) -> np.ndarray:
-        return vcycle(self.Ks, self.Ps, np.asarray(r, np.float64))
+        return vcycle(self.Ks, self.Ps, self.Ws, np.asarray(r, np.float64))
 
     def matrix(self) -> np.ndarray:
         """M^-1 as a dense matrix (one V-cycle per column)."""

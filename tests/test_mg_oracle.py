@@ -98,6 +98,20 @@ def test_preconditioner_symmetric_positive_definite(name):
     assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0.0
 
 
+@pytest.mark.parametrize("name", ["cavity", "periodic"])
+def test_singular_sims_keep_the_top_correction_at_zero(name):
+    """All-Neumann and all-periodic sims: K 1 = 0, so the single top node's Galerkin
+    diagonal is zero and its correction is zero; M^-1 stays bounded (no division by the
+    round-off of that diagonal) and symmetric."""
+    spec = GRIDS[name]()
+    mg = MGO.MG(O.Oracle(spec))
+    top = mg.Ks[-1].toarray()
+    assert top.shape == (1, 1) and abs(top[0, 0]) <= 1e-12 * abs(mg.Ks[0]).max()
+    r = np.random.default_rng(5).standard_normal(mg.K.shape[0])
+    z = mg.apply(r)
+    assert np.linalg.norm(z) <= 10.0 * np.linalg.norm(r / mg.K.diagonal())
+
+
 def test_vcycle_iteration_converges():
     """x <- x + M^-1 (b - K x) is a convergent iteration: rho(I - M^-1 K) < 1."""
     spec = W.sphere_channel(2, 2, 2, 4, length=(2.0, 2.0, 2.0), radius=0.2,
