@@ -119,7 +119,8 @@ typedef struct {
     double umax;           /* max |u| after the last step */
     int32_t pcg_form;      /* PCG of the last solve: 0 two launches per iteration,
                               1 persistent streaming, 2 persistent single-reduction,
-                              3 persistent with the state on chip */
+                              3 persistent with the state on chip, 4 multigrid-
+                              preconditioned (two launches and a V-cycle) */
     int32_t reserved;
 } bcm_stats;
 
@@ -204,6 +205,18 @@ bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int
  * BCM_E_INVALID for other values. */
 bcm_status bcm_set_launch(bcm_grid *grid, int persistent, int slabs_a, int slabs_b);
 
+/* Preconditioner of the pressure PCG.  BCM_PRECOND_JACOBI (the default): M = diag(K).
+ * BCM_PRECOND_MULTIGRID: one symmetric V-cycle of a geometric multigrid per iteration
+ * (the paper solves the pressure equation by multigrid on its cubes): every cube is
+ * coarsened 2:1 down to one cell, then the cubes of each sim are aggregated 2x2x2 up
+ * to one node; piecewise-constant transfers, Galerkin coarse operators, one damped
+ * Jacobi sweep (omega = 0.8) before and after each coarse correction, four on the top
+ * level.  Single-level grids only (BCM_E_INVALID otherwise).  With multigrid the solve
+ * runs two launches per iteration plus the V-cycle (no persistent form, no graph
+ * steps); results agree with the Jacobi solve to the solver tolerance. */
+enum { BCM_PRECOND_JACOBI = 0, BCM_PRECOND_MULTIGRID = 1 };
+bcm_status bcm_set_preconditioner(bcm_grid *grid, int kind);
+
 /* Solve the pressure Poisson equation (Eq. poisson) for the current BCM_RHS into
  * BCM_P (warm start from BCM_P).  stats as in bcm_step. */
 bcm_status bcm_solve_pressure(bcm_grid *grid, double rtol, int max_iter, bcm_stats *stats);
@@ -239,6 +252,11 @@ bcm_status bcm_solve_pressure_static(bcm_grid *grid, const double *dev_b, double
 /* y = K x with K = -V A the flux-form pressure operator of Eq. poisson (FP64). */
 bcm_status bcm_apply_poisson(bcm_grid *grid, const double *dev_x, double *dev_y);
 
+/* z = M^-1 r, one multigrid V-cycle (the preconditioner of BCM_PRECOND_MULTIGRID), on
+ * FP64 single-level grids: a test path.  It uses the grid's PCG residual buffer as
+ * scratch, so call it between solves.  BCM_E_INVALID for other grids. */
+bcm_status bcm_apply_preconditioner(bcm_grid *grid, const double *dev_r, double *dev_z);
+
 /* Discrete adjoint of the fractional step, for gradients of J = sum_n w_n F_x^n (F_x^n
  * the drag of step n) with respect to the eight inflow-profile amplitudes a_m and the
  * centre of a fixed sphere (body 0).  Every operator of the step is transposed exactly,
@@ -273,7 +291,8 @@ enum {
     BCM_K_CORRECT = 7,        /* projection + FP64 divergence check */
     BCM_K_MISC = 8,           /* bookkeeping and test-path kernels */
     BCM_K_PCG = 9,            /* persistent PCG: all iterations of one solve */
-    BCM_NKERNELS = 10
+    BCM_K_MG = 10,            /* multigrid V-cycle (BCM_PRECOND_MULTIGRID) */
+    BCM_NKERNELS = 11
 };
 
 /* Timing of the library's own kernels: while enabled, every kernel the grid launches

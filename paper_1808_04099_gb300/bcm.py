@@ -18,17 +18,19 @@ from . import _build
 BCM_OK, BCM_E_INVALID, BCM_E_CUDA, BCM_E_NOT_CONVERGED = 0, -1, -2, -3
 BCM_E_NONFINITE, BCM_E_TIMEOUT, BCM_E_BOUNDS = -4, -5, -6
 PREC_F64, PREC_F32_REFINE = 0, 1
+PRECOND_JACOBI, PRECOND_MULTIGRID = 0, 1
 (U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
             "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch",
+            "bcm_set_preconditioner", "bcm_apply_preconditioner",
             "bcm_set_step", "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
             "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
             "bcm_last_error"]
 KERNEL_NAMES = ["solid_fraction", "momentum", "rhs", "residual", "cg_a", "cg_b",
-                "add_correction", "correct", "misc", "pcg"]
+                "add_correction", "correct", "misc", "pcg", "mg"]
 
 
 class GridDesc(C.Structure):
@@ -99,6 +101,8 @@ def lib(build: bool = True):
         L.bcm_solve_pressure.argtypes = [P, C.c_double, C.c_int, P]
         L.bcm_fill_halo.argtypes = [P, C.c_int, C.c_int, P]
         L.bcm_apply_poisson.argtypes = [P, P, P]
+        L.bcm_set_preconditioner.argtypes = [P, C.c_int]
+        L.bcm_apply_preconditioner.argtypes = [P, P, P]
         L.bcm_solve_pressure_static.argtypes = [P, P, P, C.c_double, C.c_int, P]
         L.bcm_profile.argtypes = [P, C.c_int]
         L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
@@ -225,6 +229,19 @@ class Grid:
                    barrier_timeout_s: float = 0.0, recycle: int = -1):
         _check(lib().bcm_set_solver(self._h, inner_rtol, max_cycles, check_every,
                                     barrier_timeout_s, recycle))
+
+    def set_preconditioner(self, kind: int):
+        """PRECOND_JACOBI (default) or PRECOND_MULTIGRID (single-level grids)."""
+        _check(lib().bcm_set_preconditioner(self._h, int(kind)))
+
+    def apply_preconditioner(self, r):
+        """z = M^-1 r by one multigrid V-cycle (FP64 single-level grids; test path)."""
+        import torch
+        r = torch.as_tensor(r).to(self.device, torch.float64).contiguous()
+        z = torch.empty_like(r)
+        _check(lib().bcm_apply_preconditioner(self._h, C.c_void_p(r.data_ptr()),
+                                              C.c_void_p(z.data_ptr())))
+        return z
 
     def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: int = 1):
         """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG

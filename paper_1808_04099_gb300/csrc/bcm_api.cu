@@ -13,6 +13,8 @@
 #include <string.h>
 
 #include <string>
+#include <array>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -63,6 +65,25 @@ struct HostTables {
 };
 
 int face_axis(int f) { return f >> 1; }
+
+// Multigrid hierarchy of a single-level grid (see bcm_mg.cu): per-cube level sizes and
+// the cube-aggregate levels as CSR tables (Galerkin sums of the cube graph).
+struct MgAgg {
+  int n = 0;                          // nodes
+  std::vector<int> row, col, cptr, cidx, parent;
+  std::vector<double> val, diag;
+};
+struct MgHost {
+  bool ok = false;
+  int L = 0;
+  std::vector<size_t> n;  // per-cube level cells, l = 0 .. L
+  std::vector<MgAgg> agg;
+};
+struct MgLayout {
+  size_t x[kMgMaxL + 1], y[kMgMaxL + 1], r[kMgMaxL + 1], rr;
+  size_t ar[kMgMaxM], ax[kMgMaxM], at[kMgMaxM], diag[kMgMaxM], val[kMgMaxM];
+  size_t row[kMgMaxM], col[kMgMaxM], cptr[kMgMaxM], cidx[kMgMaxM], parent[kMgMaxM];
+};
 
 bcm_status validate(const bcm_grid_desc* d) {
   if (!d) return fail(BCM_E_INVALID, "desc is NULL");
@@ -238,11 +259,109 @@ bcm_status build_tables(const bcm_grid_desc* d, HostTables& T) {
       const double h = p.h0 / double(1 << l);
       for (int w = 0; w < kW3; ++w) p.invdiag[l][w] = w > 0 ? 3.0 / (h * w) : 0.0;
     }
+    for (int w = 0; w < kW3; ++w) p.invdiag32[w] = (float)p.invdiag[0][w];
+    p.h032 = (float)p.h0;
   }
   return BCM_OK;
 }
 
-Layout plan(const bcm_grid_desc* d, int n_slots) {
+// Aggregate levels: cubes of one sim whose cube coordinates shifted right by m agree
+// form one node of level m = k + 1; edge weights are the Galerkin sums of the cube
+// graph, whose faces carry B^2 h (4^L fine faces of coefficient h) and whose outflow
+// faces add 2 B^2 h to the diagonal.
+MgHost mg_build(const bcm_grid_desc* d, const HostTables& T) {
+  MgHost m;
+  if (d->max_level != 0) return m;
+  const int B = d->cells_per_edge, nc = d->n_cubes;
+  while ((1 << m.L) < B) ++m.L;
+  for (int l = 0; l <= m.L; ++l) m.n.push_back((size_t)nc * (B >> l) * (B >> l) * (B >> l));
+  int ext = 1;
+  for (int s = 0; s < d->n_sims; ++s) {
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+    for (int c = d->sim_cube_offset[s]; c < d->sim_cube_offset[s + 1]; ++c)
+      for (int e = 0; e < 3; ++e) {
+        const int x = d->cube_ijk[3 * c + e] / B;
+        lo[e] = lo[e] < x ? lo[e] : x;
+        hi[e] = hi[e] > x ? hi[e] : x;
+      }
+    for (int e = 0; e < 3; ++e) ext = ext > hi[e] - lo[e] + 1 ? ext : hi[e] - lo[e] + 1;
+  }
+  int M = 1;
+  while ((1 << M) < ext) ++M;
+  if (M > kMgMaxM) return m;
+  // level "k = -1": the cube graph
+  std::vector<std::array<int, 4>> key(nc);
+  std::vector<std::map<int, double>> edges(nc);
+  std::vector<double> bnd(nc, 0.0);
+  for (int c = 0; c < nc; ++c) {
+    const int s = T.sim[c];
+    const double a = double(B) * B * d->sim_h0[s];
+    key[c] = {s, d->cube_ijk[3 * c] / B, d->cube_ijk[3 * c + 1] / B, d->cube_ijk[3 * c + 2] / B};
+    for (int f = 0; f < 6; ++f) {
+      const int nb = T.nb[6 * c + f];
+      if (nb >= 0) {
+        if (nb != c) edges[c][nb] += a;
+      } else if (nb == NB_BOUNDARY && d->sim_bc[6 * s + f] == BC_OUTFLOW) {
+        bnd[c] += 2.0 * a;
+      }
+    }
+  }
+  for (int k = 0; k < M; ++k) {
+    MgAgg g;
+    std::map<std::array<int, 4>, int> ids;
+    const int np = (int)key.size();
+    g.parent.resize(np);
+    std::vector<std::array<int, 4>> nkey;
+    for (int u = 0; u < np; ++u) {
+      const std::array<int, 4> kk = {key[u][0], key[u][1] >> 1, key[u][2] >> 1, key[u][3] >> 1};
+      auto it = ids.find(kk);
+      int id;
+      if (it == ids.end()) {
+        id = (int)nkey.size();
+        ids.emplace(kk, id);
+        nkey.push_back(kk);
+      } else {
+        id = it->second;
+      }
+      g.parent[u] = id;
+    }
+    g.n = (int)nkey.size();
+    std::vector<std::map<int, double>> ne(g.n);
+    std::vector<double> nbnd(g.n, 0.0);
+    std::vector<std::vector<int>> kids(g.n);
+    for (int u = 0; u < np; ++u) {
+      const int U = g.parent[u];
+      kids[U].push_back(u);
+      nbnd[U] += bnd[u];
+      for (const auto& e : edges[u]) {
+        const int V = g.parent[e.first];
+        if (V != U) ne[U][V] += e.second;
+      }
+    }
+    g.row.push_back(0);
+    g.cptr.push_back(0);
+    for (int U = 0; U < g.n; ++U) {
+      double dsum = nbnd[U];
+      for (const auto& e : ne[U]) {
+        g.col.push_back(e.first);
+        g.val.push_back(e.second);
+        dsum += e.second;
+      }
+      g.diag.push_back(dsum);
+      g.row.push_back((int)g.col.size());
+      for (int u : kids[U]) g.cidx.push_back(u);
+      g.cptr.push_back((int)g.cidx.size());
+    }
+    m.agg.push_back(std::move(g));
+    key = std::move(nkey);
+    edges = std::move(ne);
+    bnd = std::move(nbnd);
+  }
+  m.ok = true;
+  return m;
+}
+
+Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml) {
   Layout L{};
   const size_t n = (size_t)d->n_cubes * d->cells_per_edge * d->cells_per_edge * d->cells_per_edge;
   const size_t S = d->precision == BCM_PREC_F64 ? 8 : 4;   // state storage
@@ -278,6 +397,29 @@ Layout plan(const bcm_grid_desc* d, int n_slots) {
   L.guard = take(64);
   L.bar = take(sizeof(unsigned int) * (kTicketWords + 32));
   L.err = take(64);
+  if (mg.ok && ml) {  // multigrid preconditioner (single-level grids)
+    for (int l = 0; l <= mg.L; ++l) {
+      ml->x[l] = take(mg.n[l] * V);
+      ml->y[l] = take(mg.n[l] * V);
+      ml->r[l] = l ? take(mg.n[l] * V) : 0;
+    }
+    ml->rr = take((size_t)d->n_cubes * V);
+    size_t prev = (size_t)d->n_cubes;
+    for (size_t k = 0; k < mg.agg.size(); ++k) {
+      const MgAgg& a = mg.agg[k];
+      ml->ar[k] = take(a.n * 8);
+      ml->ax[k] = take(a.n * 8);
+      ml->at[k] = take(a.n * 8);
+      ml->diag[k] = take(a.n * 8);
+      ml->val[k] = take(a.val.size() * 8);
+      ml->row[k] = take((a.n + 1) * sizeof(int));
+      ml->col[k] = take(a.col.size() * sizeof(int));
+      ml->cptr[k] = take((a.n + 1) * sizeof(int));
+      ml->cidx[k] = take(prev * sizeof(int));
+      ml->parent[k] = take(prev * sizeof(int));
+      prev = (size_t)a.n;
+    }
+  }
   L.total = off;
   L.n_slots = n_slots;
   return L;
@@ -317,6 +459,7 @@ struct bcm_grid {
   double barrier_timeout_s = 2.0;  // persistent PCG: longest grid-barrier wait
   int recycle = 1;           // mixed + persistent: reliable updates instead of restarts
   int pcg_form = 0;          // PCG form of the last solve (PCG_*)
+  int mg_ok = 0;             // the grid has a multigrid hierarchy (single-level)
   KernelTimer timer;
   long long launch_count = 0;
   HostTables T;
@@ -396,7 +539,8 @@ extern "C" size_t bcm_workspace_bytes(const bcm_grid_desc* desc) {
   if (validate(desc) != BCM_OK) return 0;
   HostTables T;
   if (build_tables(desc, T) != BCM_OK) return 0;
-  return plan(desc, T.n_slots).total;
+  MgLayout ml;
+  return plan(desc, T.n_slots, mg_build(desc, T), &ml).total;
 }
 
 extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_workspace, size_t bytes,
@@ -412,7 +556,10 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
     delete g;
     return st;
   }
-  g->L = plan(desc, g->T.n_slots);
+  const MgHost mgh = mg_build(desc, g->T);
+  MgLayout ml{};
+  g->L = plan(desc, g->T.n_slots, mgh, &ml);
+  g->mg_ok = mgh.ok ? 1 : 0;
   if (!dev_workspace || bytes < g->L.total) {
     size_t need = g->L.total;
     delete g;
@@ -455,6 +602,16 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   UP(L.nbw3, g->T.nbw3.data(), sizeof(int) * 36 * n);
   UP(L.slot, g->T.slot.data(), sizeof(int) * 6 * n);
   UP(L.sp, g->T.sp.data(), sizeof(SimParams) * desc->n_sims);
+  for (size_t k = 0; mgh.ok && k < mgh.agg.size(); ++k) {
+    const MgAgg& a = mgh.agg[k];
+    UP(ml.diag[k], a.diag.data(), a.diag.size() * sizeof(double));
+    if (!a.val.empty()) UP(ml.val[k], a.val.data(), a.val.size() * sizeof(double));
+    UP(ml.row[k], a.row.data(), a.row.size() * sizeof(int));
+    if (!a.col.empty()) UP(ml.col[k], a.col.data(), a.col.size() * sizeof(int));
+    UP(ml.cptr[k], a.cptr.data(), a.cptr.size() * sizeof(int));
+    UP(ml.cidx[k], a.cidx.data(), a.cidx.size() * sizeof(int));
+    UP(ml.parent[k], a.parent.data(), a.parent.size() * sizeof(int));
+  }
 #undef UP
   {
     cudaError_t e = cudaStreamSynchronize(s);
@@ -504,6 +661,32 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.guard = (unsigned int*)(W + L.guard);
   F.bar = (unsigned int*)(W + L.bar);
   F.err = (int*)(W + L.err);
+  x.use_mg = 0;
+  x.mg = MgDev{};
+  if (mgh.ok) {
+    MgDev& D = x.mg;
+    D.L = mgh.L;
+    D.M = (int)mgh.agg.size();
+    for (int l = 0; l <= mgh.L; ++l) {
+      D.x[l] = W + ml.x[l];
+      D.y[l] = W + ml.y[l];
+      D.r[l] = l ? (void*)(W + ml.r[l]) : F.r;
+    }
+    D.rr = W + ml.rr;
+    for (int k = 0; k < D.M; ++k) {
+      D.n[k] = mgh.agg[k].n;
+      D.ar[k] = (double*)(W + ml.ar[k]);
+      D.ax[k] = (double*)(W + ml.ax[k]);
+      D.at[k] = (double*)(W + ml.at[k]);
+      D.diag[k] = (double*)(W + ml.diag[k]);
+      D.val[k] = (double*)(W + ml.val[k]);
+      D.row[k] = (int*)(W + ml.row[k]);
+      D.col[k] = (int*)(W + ml.col[k]);
+      D.cptr[k] = (int*)(W + ml.cptr[k]);
+      D.cidx[k] = (int*)(W + ml.cidx[k]);
+      D.parent[k] = (int*)(W + ml.parent[k]);
+    }
+  }
   *out = g;
   return BCM_OK;
 }
@@ -646,9 +829,11 @@ double effective_inner_rtol(const bcm_grid* g, bool recycle) {
 
 bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   Ctx& x = g->ctx;
+  const bool mg = x.use_mg != 0;  // multigrid-preconditioned CG: two launches + V-cycle
   SolveParams prm{};
   prm.rtol = rtol;
-  prm.recycle = (g->recycle && x.persistent) ? 1 : 0;
+  prm.mg = mg ? 1 : 0;
+  prm.recycle = (g->recycle && x.persistent && !mg) ? 1 : 0;
   prm.inner_rtol = effective_inner_rtol(g, prm.recycle != 0);
   prm.max_iter = max_iter;
   prm.inner_max_iter = max_iter;
@@ -659,10 +844,13 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
   RUN(BCM_K_MISC, launch_solve_begin(x));
   RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
-  g->pcg_form = PCG_TWO_LAUNCH;  // the persistent launches say which form they ran
+  if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 0));
+  g->pcg_form = mg ? PCG_MULTIGRID : PCG_TWO_LAUNCH;  // persistent launches set theirs
   int flags[2] = {0, 0};
   bcm_status st;
-  if (x.persistent) {
+  // the multigrid iteration converges in a few iterations: read the flags more often
+  const int every = mg ? (g->check_every < 2 ? g->check_every : 2) : g->check_every;
+  if (x.persistent && !mg) {
     if (g->f64) {
       RUN(BCM_K_PCG, launch_pcg(x, prm, &g->pcg_form));
       return read_err(g);
@@ -687,10 +875,11 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   if (g->f64) {
     int it = 0;
     while (!flags[0] && it < max_iter) {
-      for (int m = 0; m < g->check_every && it < max_iter; ++m, ++it)
+      for (int m = 0; m < every && it < max_iter; ++m, ++it)
       {
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
         RUN(BCM_K_CG_B, launch_cg_b(x, prm));
+        if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));
       }
       if ((st = read_flags(g, flags)) != BCM_OK) return st;
     }
@@ -700,15 +889,17 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   while (!flags[1] && cycles <= g->max_cycles) {
     int it = 0;
     while (!flags[0] && it < max_iter) {
-      for (int m = 0; m < g->check_every && it < max_iter; ++m, ++it)
+      for (int m = 0; m < every && it < max_iter; ++m, ++it)
       {
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
         RUN(BCM_K_CG_B, launch_cg_b(x, prm));
+        if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));
       }
       if ((st = read_flags(g, flags)) != BCM_OK) return st;
     }
     RUN(BCM_K_ADD_CORRECTION, launch_add_correction(x));
     RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
+    if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 0));
     if ((st = read_flags(g, flags)) != BCM_OK) return st;
     ++cycles;
   }
@@ -815,6 +1006,8 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     return fail(BCM_E_INVALID, "need n_steps >= 0, rtol > 0, max_iter >= 1");
   if (g->desc.n_sims > 256)
     return fail(BCM_E_BOUNDS, "graph steps use the persistent PCG: at most 256 sims per grid");
+  if (g->ctx.use_mg)
+    return fail(BCM_E_INVALID, "graph steps use the persistent Jacobi PCG, not multigrid");
   StepGraph& sg = g->sg;
   int cycles = 0;
   if (!g->f64) {  // enough cycles for rtol at the inner reduction per cycle, plus margin
@@ -956,6 +1149,30 @@ extern "C" bcm_status bcm_fill_halo(bcm_grid* g, int field, int kind, double* de
   if (st != BCM_OK) return st;
   if (field == BCM_UB) return fail(BCM_E_INVALID, "BCM_UB is not a cell field");
   RUN(BCM_K_MISC, launch_fill_halo(g->ctx, ptr, eb == 8, kind, dev_out));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_set_preconditioner(bcm_grid* g, int kind) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (kind != BCM_PRECOND_JACOBI && kind != BCM_PRECOND_MULTIGRID)
+    return fail(BCM_E_INVALID, "unknown preconditioner %d", kind);
+  if (kind == BCM_PRECOND_MULTIGRID && !g->mg_ok)
+    return fail(BCM_E_INVALID, "the multigrid preconditioner needs a single-level grid");
+  g->ctx.use_mg = kind == BCM_PRECOND_MULTIGRID ? 1 : 0;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_apply_preconditioner(bcm_grid* g, const double* r, double* z) {
+  if (!g || !r || !z) return fail(BCM_E_INVALID, "NULL argument");
+  if (!g->f64 || !g->mg_ok)
+    return fail(BCM_E_INVALID, "the preconditioner test path needs an FP64 single-level grid");
+  const Ctx& x = g->ctx;
+  const size_t bytes = g->n_cells * sizeof(double);
+  CUDA_TRY(cudaMemcpyAsync(x.f.r, r, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  SolveParams prm{};
+  RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 2));
+  CUDA_TRY(cudaMemcpyAsync(z, x.mg.y[0], bytes, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
   return BCM_OK;
 }
 

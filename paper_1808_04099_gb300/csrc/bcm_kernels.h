@@ -31,10 +31,33 @@ struct SolveParams {
   unsigned long long cond_inner, cond_outer;  // graph conditional handles (0 = none)
   unsigned int* guard;
   int guard_limit;
-  int pad;
+  int mg;                 // 1: the multigrid preconditioner supplies z (pass A reads it;
+                          // the V-cycle's last launch takes the iteration's decisions)
   unsigned long long barrier_timeout_ns;  // persistent PCG: longest wait at a grid barrier
   int recycle;            // mixed + persistent: keep the search direction across cycles
   int pad2;
+};
+
+// Geometric multigrid preconditioner (single-level grids): per-cube levels
+// l = 0 .. L (cells per cube edge B >> l) and cube-aggregate levels k = 0 .. M-1
+// (aggregate level m = k + 1; k = 0 aggregates cubes).  Per-cube level arrays are in
+// the PCG vector type, aggregate arrays in FP64.
+constexpr int kMgMaxL = 4;   // log2 of the largest cube edge (16)
+constexpr int kMgMaxM = 20;  // aggregate levels
+constexpr double kMgOmega = 0.8;  // damped-Jacobi weight of the smoother
+constexpr int kMgNuTop = 4;       // Jacobi sweeps on the top aggregate level
+struct MgDev {
+  int L, M;
+  void* x[kMgMaxL + 1];  // pre-smoothed iterate of level l
+  void* y[kMgMaxL + 1];  // corrected iterate of level l (y[0] = z, the PCG's M^-1 r)
+  void* r[kMgMaxL + 1];  // residual of level l (r[0] is the PCG residual)
+  void* rr;              // level L: residual after pre-smoothing, one value per cube
+  int n[kMgMaxM];        // nodes of aggregate level k
+  double *ar[kMgMaxM], *ax[kMgMaxM], *at[kMgMaxM];  // residual, iterate, scratch
+  double *diag[kMgMaxM], *val[kMgMaxM];              // K: diagonal, -off-diagonal (CSR)
+  int *row[kMgMaxM], *col[kMgMaxM];
+  int *cptr[kMgMaxM], *cidx[kMgMaxM];  // children: level k-1 nodes (cubes for k = 0)
+  int *parent[kMgMaxM];                // parent at level k of each level k-1 node
 };
 
 struct Ctx {
@@ -49,6 +72,8 @@ struct Ctx {
   int single_pass; // persistent PCG: one pass and one grid barrier per iteration
   int resident;    // persistent PCG: search direction in shared memory where it fits
   int lag_bf16;    // mixed mode: N^{n-1} stored as bfloat16
+  int use_mg;      // PCG preconditioner: 0 Jacobi, 1 geometric multigrid
+  MgDev mg;
   cudaStream_t stream;
 };
 
@@ -61,7 +86,8 @@ cudaError_t launch_residual(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm);
 // PCG forms (reported in bcm_stats.pcg_form)
-enum { PCG_TWO_LAUNCH = 0, PCG_STREAMING = 1, PCG_SINGLE_PASS = 2, PCG_RESIDENT = 3 };
+enum { PCG_TWO_LAUNCH = 0, PCG_STREAMING = 1, PCG_SINGLE_PASS = 2, PCG_RESIDENT = 3,
+       PCG_MULTIGRID = 4 };
 // The persistent PCG in the form the launch shape and the grid select; *form gets it.
 cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form);
 cudaError_t launch_pcg1(const Ctx& x, const SolveParams& prm);
@@ -71,5 +97,9 @@ cudaError_t launch_correct(const Ctx& x);
 cudaError_t launch_step_end(const Ctx& x);
 cudaError_t launch_fill_halo(const Ctx& x, const void* f, int f64_field, int kind, double* out);
 cudaError_t launch_apply_poisson(const Ctx& x, const double* in, double* out);
+// One V-cycle z = M^-1 r on the PCG residual.  mode 0: after the residual kernel
+// (<r,z> becomes the PCG's rz); 1: after pass B (<r,z>, beta and the convergence
+// decision); 2: standalone (every sim, no dot products).
+cudaError_t launch_mg_vcycle(const Ctx& x, const SolveParams& prm, int mode);
 
 }  // namespace bcm

@@ -1,0 +1,564 @@
+// bcm_mg.cu -- geometric multigrid V-cycle, the preconditioner M^-1 of the pressure PCG
+// (Eq. poisson; the paper solves the pressure equation with a multigrid on its cubes).
+//
+// Single-level grids.  Per-cube levels l = 0 .. L coarsen every cube by two per level
+// (B, B/2, ..., 1 cells per edge); a level-l+1 cell covers 2x2x2 cells of level l of the
+// same cube.  Above level L (one cell per cube) the cubes of a sim are aggregated by
+// their cube coordinates shifted right by m (m = 1 .. M).  Transfers are piecewise
+// constant, restriction sums, and the coarse operators are the Galerkin products
+// P^T K P.  For the flux-form K these are again flux-form operators: on per-cube level
+// l a face carries 4^l fine faces, coefficient 4^l h, an outflow face twice that on the
+// diagonal, other domain faces nothing; the aggregate levels keep their Galerkin sums
+// as small CSR tables built on the host.  The smoother is damped Jacobi
+// S = omega D^-1 (omega = 0.8), one sweep before and one after the coarse correction,
+// so the V-cycle is symmetric positive definite and M^-1 suits CG:
+//   V_l(r) = x + S (r - K x),  x = S r + P V_{l+1}(P^T (r - K S r)),
+//   V_top(r) = four damped-Jacobi sweeps from zero.
+//
+// Launches per V-cycle: one per per-cube level on the way down (pre-smoothing with the
+// neighbours' values computed on the fly, residual, restriction), one single-block
+// launch for the aggregate levels, and one per per-cube level on the way up
+// (prolongation of the neighbours on the fly, post-smoothing).  The last launch also
+// forms <r, z> per sim and, after PCG pass B, takes the iteration's decisions (beta,
+// convergence) that pass B leaves to it.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bcm_cube.cuh"
+#include "bcm_internal.cuh"
+#include "bcm_kernels.h"
+#include "bcm_persist.cuh"
+
+namespace bcm {
+
+template <int BL>
+__device__ __forceinline__ int lcell(int i, int j, int k) { return (k * BL + j) * BL + i; }
+
+// Cell across direction f (0..5: -x, +x, -y, +y, -z, +z) of cell (i, j, k) of cube c on
+// a level with BL cells per edge.  Returns 1 with (nc, ni, nj, nk) for a cell of this
+// or a same-level neighbouring cube, 0 with the mirror sign of a domain face (+1: the
+// ghost equals the cell, Neumann; -1: minus the cell, p = 0 on an outflow face).
+template <int BL>
+__device__ __forceinline__ int level_nb(const DevGrid& g, int c, int i, int j, int k, int f,
+                                        int& nc, int& ni, int& nj, int& nk, int& sign) {
+  const int d = f >> 1, step = (f & 1) ? 1 : -1;
+  int q[3] = {i, j, k};
+  q[d] += step;
+  if (q[d] >= 0 && q[d] < BL) {
+    nc = c;
+  } else {
+    const int n = g.nb[6 * c + f];
+    if (n < 0) {
+      sign = g.sp[g.sim[c]].bc[f] == BC_OUTFLOW ? -1 : 1;
+      return 0;
+    }
+    nc = n;
+    q[d] = (f & 1) ? 0 : BL - 1;
+  }
+  ni = q[0];
+  nj = q[1];
+  nk = q[2];
+  return 1;
+}
+
+// Per-sim constants of a level in the vector type: the FP32 path does no FP64
+// arithmetic (FP64 runs at a small fraction of the FP32 rate on this GPU).
+template <class TV>
+__device__ __forceinline__ TV sim_inv(const SimParams& sp, int s3);
+template <>
+__device__ __forceinline__ float sim_inv<float>(const SimParams& sp, int s3) { return sp.invdiag32[s3]; }
+template <>
+__device__ __forceinline__ double sim_inv<double>(const SimParams& sp, int s3) { return sp.invdiag[0][s3]; }
+template <class TV>
+__device__ __forceinline__ TV sim_h(const SimParams& sp);
+template <>
+__device__ __forceinline__ float sim_h<float>(const SimParams& sp) { return sp.h032; }
+template <>
+__device__ __forceinline__ double sim_h<double>(const SimParams& sp) { return sp.h0; }
+
+// omega / diag(K_l) of cell (i, j, k) of cube c on per-cube level l (BL cells per edge):
+// diag(K_l) = 4^l diag(K) of a fine cell with the same boundary faces; wscale =
+// omega / 4^l.  Neighbouring cubes belong to the same sim, so sp serves them too.
+template <int BL, class TV>
+__device__ __forceinline__ TV smooth_w(const DevGrid& g, const SimParams& sp, int c, int i, int j,
+                                       int k, TV wscale) {
+  return wscale * sim_inv<TV>(sp, s3_of<BL>(g.w3 + 6 * c, i, j, k));
+}
+
+// ---- down: x = S r, rr = r - K x, restriction of rr (P^T: sums)
+// One thread per coarse cell (its 2x2x2 fine cells), or per cube on the level with one
+// cell per cube (its residual goes to `rc` per cube for the aggregate levels).
+template <int BL, class TV>
+__global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale,
+                                                 const TV* __restrict__ r,
+                                                 TV* __restrict__ x, TV* __restrict__ rc,
+                                                 int all) {
+  constexpr int CB = BL > 1 ? BL / 2 : 1, C3 = CB * CB * CB, B3 = BL * BL * BL;
+  constexpr int CH = BL > 1 ? 2 : 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.n_cubes * C3) return;
+  const int c = (int)(t / C3), ci = (int)(t - (long long)c * C3);
+  const int s = g.sim[c];
+  if (!all && g.ss[s].done) return;
+  const int I = ci % CB, J = (ci / CB) % CB, Kc = ci / (CB * CB);
+  const SimParams& sp = g.sp[s];
+  const TV coef = sim_h<TV>(sp) * cscale;  // 4^l h
+  TV sum = TV(0);
+#pragma unroll
+  for (int dk = 0; dk < CH; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < CH; ++dj)
+#pragma unroll
+      for (int di = 0; di < CH; ++di) {
+        const int i = CH * I + di, j = CH * J + dj, k = CH * Kc + dk;
+        const size_t gi = (size_t)c * B3 + lcell<BL>(i, j, k);
+        const TV rv = r[gi];
+        const TV xc = smooth_w<BL, TV>(g, sp, c, i, j, k, wscale) * rv;
+        TV acc = TV(0);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          int nc, ni, nj, nk, sign = 1;
+          TV xn;
+          if (level_nb<BL>(g, c, i, j, k, f, nc, ni, nj, nk, sign))
+            xn = smooth_w<BL, TV>(g, sp, nc, ni, nj, nk, wscale) *
+                 r[(size_t)nc * B3 + lcell<BL>(ni, nj, nk)];
+          else
+            xn = TV(sign) * xc;
+          acc += xc - xn;
+        }
+        x[gi] = xc;
+        sum += rv - coef * acc;
+      }
+  rc[t] = sum;
+}
+
+// ---- up: x~ = x + P y_coarse (on the fly for the cell and its neighbours), then
+// y = x~ + S (r - K x~).  One thread per cell.  On the level with one cell per cube the
+// coarse values come from aggregate level 0 (FP64, through the cube's parent).
+template <int BL, class TV>
+__device__ __forceinline__ TV up_value(const TV* __restrict__ x, const TV* __restrict__ yc,
+                                       const double* __restrict__ yagg,
+                                       const int* __restrict__ agg_parent, int c, int i, int j,
+                                       int k) {
+  constexpr int B3 = BL * BL * BL;
+  const TV xv = x[(size_t)c * B3 + lcell<BL>(i, j, k)];
+  if constexpr (BL == 1) {
+    return xv + TV(yagg[agg_parent[c]]);
+  } else {
+    constexpr int CB = BL / 2;
+    return xv + yc[(size_t)c * CB * CB * CB + lcell<CB>(i >> 1, j >> 1, k >> 1)];
+  }
+}
+
+template <int BL, class TV>
+__device__ __forceinline__ TV up_cell(const DevGrid& g, TV wscale, TV cscale,
+                                      const TV* __restrict__ r,
+                                      const TV* __restrict__ x, const TV* __restrict__ yc,
+                                      const double* __restrict__ yagg,
+                                      const int* __restrict__ agg_parent, int c, int i, int j,
+                                      int k, TV* rv_out) {
+  constexpr int B3 = BL * BL * BL;
+  const SimParams& sp = g.sp[g.sim[c]];
+  const TV coef = sim_h<TV>(sp) * cscale;
+  const TV xc = up_value<BL, TV>(x, yc, yagg, agg_parent, c, i, j, k);
+  TV acc = TV(0);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    int nc, ni, nj, nk, sign = 1;
+    const TV xn = level_nb<BL>(g, c, i, j, k, f, nc, ni, nj, nk, sign)
+                      ? up_value<BL, TV>(x, yc, yagg, agg_parent, nc, ni, nj, nk)
+                      : TV(sign) * xc;
+    acc += xc - xn;
+  }
+  const TV rv = r[(size_t)c * B3 + lcell<BL>(i, j, k)];
+  *rv_out = rv;
+  return xc + smooth_w<BL, TV>(g, sp, c, i, j, k, wscale) * (rv - coef * acc);
+}
+
+template <int BL, class TV>
+__global__ __launch_bounds__(256) void k_mg_up(DevGrid g, TV wscale, TV cscale,
+                                               const TV* __restrict__ r,
+                                               const TV* __restrict__ x,
+                                               const TV* __restrict__ yc,
+                                               const double* __restrict__ yagg,
+                                               const int* __restrict__ agg_parent,
+                                               TV* __restrict__ y, int all) {
+  constexpr int B3 = BL * BL * BL;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.n_cubes * B3) return;
+  const int c = (int)(t / B3), cell = (int)(t - (long long)c * B3);
+  if (!all && g.ss[g.sim[c]].done) return;
+  const int i = cell % BL, j = (cell / BL) % BL, k = cell / (BL * BL);
+  TV rv;
+  y[t] = up_cell<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
+}
+
+// The last block of the finest up launch: mode 0 (start of a solve) takes <r, z> as
+// the PCG's rz; mode 1 (after pass B) forms beta, counts the iteration and tests
+// convergence on the <r, r> that pass B accumulated.
+__device__ void mg_decide(const DevGrid& g, const SolveParams& prm, int mode, int nt) {
+  int alive = 0;
+  for (int q = threadIdx.x; q < g.n_sims; q += nt) {
+    SimState& t = g.ss[q];
+    const double rzs = acc_take(t, ACC_RZ);
+    if (mode == 0) {
+      if (!t.done) t.rz = rzs;
+      alive |= !t.done;
+      continue;
+    }
+    const double rr = acc_take(t, ACC_RR);
+    if (t.done) continue;
+    if (t.nonfinite || !isfinite(rr) || !isfinite(rzs)) {
+      t.nonfinite = 1;
+      t.done = 1;
+      continue;
+    }
+    t.beta = (t.rz != 0.0) ? rzs / t.rz : 0.0;
+    t.rz = rzs;
+    t.rr = rr;
+    t.iter += 1;
+    t.total_iters += 1;
+    const bool inner = prm.mixed != 0;
+    const double tol2 = inner ? t.inner_tol2 : t.tol2;
+    const bool ok = rr <= tol2;
+    if (!inner) {
+      t.rr64 = rr;
+      t.converged = ok;
+    }
+    if (ok || t.iter >= (inner ? prm.inner_max_iter : prm.max_iter)) t.done = 1;
+    alive |= !t.done;
+  }
+  alive = __syncthreads_or(alive);
+  if (threadIdx.x == 0 && mode == 1) g.flags[0] = !alive;
+}
+
+// ---- up on the finest level: z = y_0, <r, z> per sim, and the PCG's decisions.
+// Blocks of NT = min(256, B^3) threads lie inside one cube, hence one sim.
+template <int B, int NT, class TV>
+__global__ __launch_bounds__(NT) void k_mg_up0(DevGrid g, const TV* __restrict__ r,
+                                              const TV* __restrict__ x,
+                                              const TV* __restrict__ yc,
+                                              const double* __restrict__ yagg,
+                                              const int* __restrict__ agg_parent,
+                                              TV* __restrict__ z, SolveParams prm, int mode) {
+  constexpr int B3 = B * B * B, PER = B3 / NT;
+  __shared__ double red[32];
+  const int c = blockIdx.x / PER;
+  const int s = g.sim[c];
+  SimState& st = g.ss[s];
+  const bool all = mode == 2;
+  const bool active = all || !st.done;
+  double rz = 0.0;
+  if (active) {
+    const int cell = (blockIdx.x - c * PER) * NT + threadIdx.x;
+    const int i = cell % B, j = (cell / B) % B, k = cell / (B * B);
+    TV rv;
+    const TV zv = up_cell<B, TV>(g, TV(kMgOmega), TV(1), r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
+    z[(size_t)c * B3 + cell] = zv;
+    rz = double(rv * zv);
+  }
+  if (all) return;
+  double vals[1] = {rz};
+  block_sum<NT, 1>(vals, red);
+  if (threadIdx.x == 0 && active) acc_add(st, ACC_RZ, vals[0]);
+  if (last_block(g.counter)) mg_decide(g, prm, mode, NT);
+}
+
+// ---- finest level of 8^3 / 16^3 cubes, one block per cube with the (B+2)^3 tile of the
+// PCG passes: down stages x = S r with the face halo, marches each column for
+// rr = r - K x and sums the 2x2x2 children of rr into r_1; up stages x~ = x + P y_1, marches
+// for z = x~ + S (r - K x~) and forms <r, z>.  Same values as the per-cell kernels above.
+template <int B, class TV>
+__global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __restrict__ r,
+                                                         TV* __restrict__ x,
+                                                         TV* __restrict__ r1, int all) {
+  using SL = Slab<B, B>;
+  constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* S = reinterpret_cast<TV*>(smem_raw);
+  TV* RR = S + (SL::N + 3) / 4 * 4;
+  __shared__ CubeSh<TV> cs;
+  const int c = blockIdx.x;
+  if (!all && g.ss[g.sim[c]].done) return;
+  load_cube(cs, g, c);
+  __syncthreads();
+  const TV w = TV(kMgOmega);
+  auto val4 = [&](int cube, int cell0, int face, TV (&v)[4]) {
+    TV rr[4];
+    ld4(r + (size_t)cube * B3 + cell0, rr);
+    const int mask = face < 0 ? cs.smask : cs.nbmask[face];
+    const int* w3 = face < 0 ? cs.w3 : cs.nbw3[face];
+    const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      v[m] = w * rr[m] * (mask == 0 ? cs.invtab[18] : cs.invtab[s3_of<B>(w3, i0 + m, j, kz)]);
+  };
+  auto val1 = [&](int f, int n, int cell) {
+    const TV inv = cs.nbmask[f] == 0
+                       ? cs.invtab[18]
+                       : cs.invtab[s3_of<B>(cs.nbw3[f], cell % B, (cell / B) % B, cell / BB)];
+    return w * r[(size_t)n * B3 + cell] * inv;
+  };
+  auto valg = [&](int n, int cell) {
+    return w * r[(size_t)n * B3 + cell] * inv_diag_any<B, TV>(g, n, cell);
+  };
+  stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg);
+  const TV h = sim_h<TV>(g.sp[g.sim[c]]);
+  const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
+  int o = SL::at(i, j, 1);
+  TV below = S[o - PP], cur = S[o];
+#pragma unroll 4
+  for (int kk = 0; kk < B; ++kk) {
+    const TV above = S[o + PP];
+    const TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
+                   (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+    const int cell = (kk * B + j) * B + i;
+    const size_t gi = (size_t)c * B3 + cell;
+    x[gi] = cur;
+    RR[cell] = r[gi] - h * acc;
+    below = cur;
+    cur = above;
+    o += PP;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < CB * CB * CB; q += NT) {
+    const int I = q % CB, J = (q / CB) % CB, K = q / (CB * CB);
+    TV sum = TV(0);
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+      sum += RR[((2 * K + (d >> 2)) * B + 2 * J + ((d >> 1) & 1)) * B + 2 * I + (d & 1)];
+    r1[(size_t)c * CB * CB * CB + q] = sum;
+  }
+}
+
+template <int B, class TV>
+__global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __restrict__ r,
+                                                       const TV* __restrict__ x,
+                                                       const TV* __restrict__ y1,
+                                                       TV* __restrict__ z, SolveParams prm,
+                                                       int mode) {
+  using SL = Slab<B, B>;
+  constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TV* S = reinterpret_cast<TV*>(smem_raw);
+  __shared__ CubeSh<TV> cs;
+  __shared__ double red[32];
+  const int c = blockIdx.x, s = g.sim[c];
+  SimState& st = g.ss[s];
+  const bool all = mode == 2;
+  const bool active = all || !st.done;
+  double rz = 0.0;
+  if (active) {
+    load_cube(cs, g, c);
+    __syncthreads();
+    auto xt = [&](int cube, int cell) {
+      const int i = cell % B, j = (cell / B) % B, k = cell / BB;
+      return x[(size_t)cube * B3 + cell] +
+             y1[(size_t)cube * CB * CB * CB + ((k >> 1) * CB + (j >> 1)) * CB + (i >> 1)];
+    };
+    auto val4 = [&](int cube, int cell0, int, TV (&v)[4]) {
+      TV xv[4];
+      ld4(x + (size_t)cube * B3 + cell0, xv);
+      const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
+      const size_t pb = (size_t)cube * CB * CB * CB + ((kz >> 1) * CB + (j >> 1)) * CB + (i0 >> 1);
+      const TV ya = y1[pb], yb = y1[pb + 1];
+      v[0] = xv[0] + ya;
+      v[1] = xv[1] + ya;
+      v[2] = xv[2] + yb;
+      v[3] = xv[3] + yb;
+    };
+    auto val1 = [&](int, int n, int cell) { return xt(n, cell); };
+    auto valg = [&](int n, int cell) { return xt(n, cell); };
+    stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg);
+    const TV h = sim_h<TV>(g.sp[s]), w = TV(kMgOmega);
+    const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
+    int o = SL::at(i, j, 1);
+    TV below = S[o - PP], cur = S[o];
+    TV part = TV(0);
+#pragma unroll 4
+    for (int kk = 0; kk < B; ++kk) {
+      const TV above = S[o + PP];
+      const TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
+                     (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+      const size_t gi = (size_t)c * B3 + (kk * B + j) * B + i;
+      const TV inv = cs.smask == 0 ? cs.invtab[18] : cs.invtab[s3_of<B>(cs.w3, i, j, kk)];
+      const TV rv = r[gi];
+      const TV zv = cur + w * inv * (rv - h * acc);
+      z[gi] = zv;
+      part += rv * zv;
+      below = cur;
+      cur = above;
+      o += PP;
+    }
+    rz = double(part);
+  }
+  if (all) return;
+  double vals[1] = {rz};
+  block_sum<NT, 1>(vals, red);
+  if (threadIdx.x == 0 && active) acc_add(st, ACC_RZ, vals[0]);
+  if (last_block(g.counter)) mg_decide(g, prm, mode, NT);
+}
+
+// ---- the aggregate levels, in one block: gather of the cubes' residuals, the V-cycle
+// on the CSR levels k = 0 .. M-1 (k = M-1 the top), result y = ax[0].
+template <class TV>
+__global__ __launch_bounds__(1024) void k_mg_top(MgDev mg, const TV* __restrict__ rr) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const double w = kMgOmega;
+  auto dinv = [&](int k, int a) {
+    const double d = mg.diag[k][a];
+    return d > 0.0 ? 1.0 / d : 0.0;
+  };
+  // at = ar - K ax on level k
+  auto residual = [&](int k) {
+    for (int a = tid; a < mg.n[k]; a += NT) {
+      double kx = mg.diag[k][a] * mg.ax[k][a];
+      for (int e = mg.row[k][a]; e < mg.row[k][a + 1]; ++e) kx -= mg.val[k][e] * mg.ax[k][mg.col[k][e]];
+      mg.at[k][a] = mg.ar[k][a] - kx;
+    }
+    __syncthreads();
+  };
+  for (int a = tid; a < mg.n[0]; a += NT) {
+    double sum = 0.0;
+    for (int e = mg.cptr[0][a]; e < mg.cptr[0][a + 1]; ++e) sum += double(rr[mg.cidx[0][e]]);
+    mg.ar[0][a] = sum;
+  }
+  __syncthreads();
+  const int top = mg.M - 1;
+  for (int k = 0; k < top; ++k) {
+    for (int a = tid; a < mg.n[k]; a += NT) mg.ax[k][a] = w * dinv(k, a) * mg.ar[k][a];
+    __syncthreads();
+    residual(k);
+    for (int a = tid; a < mg.n[k + 1]; a += NT) {
+      double sum = 0.0;
+      for (int e = mg.cptr[k + 1][a]; e < mg.cptr[k + 1][a + 1]; ++e)
+        sum += mg.at[k][mg.cidx[k + 1][e]];
+      mg.ar[k + 1][a] = sum;
+    }
+    __syncthreads();
+  }
+  for (int a = tid; a < mg.n[top]; a += NT) mg.ax[top][a] = 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < kMgNuTop; ++sweep) {
+    residual(top);
+    for (int a = tid; a < mg.n[top]; a += NT) mg.ax[top][a] += w * dinv(top, a) * mg.at[top][a];
+    __syncthreads();
+  }
+  for (int k = top - 1; k >= 0; --k) {
+    for (int a = tid; a < mg.n[k]; a += NT) mg.ax[k][a] += mg.ax[k + 1][mg.parent[k + 1][a]];
+    __syncthreads();
+    residual(k);
+    for (int a = tid; a < mg.n[k]; a += NT) mg.ax[k][a] += w * dinv(k, a) * mg.at[k][a];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- launcher
+
+template <int BL, class TV>
+static cudaError_t down_t(const Ctx& x, int l, int all) {
+  constexpr int CB = BL > 1 ? BL / 2 : 1;
+  const long long n = (long long)x.g.n_cubes * CB * CB * CB;
+  const TV* r = (const TV*)x.mg.r[l];
+  TV* xv = (TV*)x.mg.x[l];
+  TV* rc = BL > 1 ? (TV*)x.mg.r[l + 1] : (TV*)x.mg.rr;
+  const double c4 = double(1 << (2 * l));
+  k_mg_down<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
+      x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+  return cudaGetLastError();
+}
+
+template <int BL, class TV>
+static cudaError_t up_t(const Ctx& x, int l, int all) {
+  const long long n = (long long)x.g.n_cubes * BL * BL * BL;
+  const TV* yc = BL > 1 ? (const TV*)x.mg.y[l + 1] : nullptr;
+  const double c4 = double(1 << (2 * l));
+  k_mg_up<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
+      x.g, TV(kMgOmega / c4), TV(c4), (const TV*)x.mg.r[l], (const TV*)x.mg.x[l], yc,
+      x.mg.ax[0], x.mg.parent[0], (TV*)x.mg.y[l], all);
+  return cudaGetLastError();
+}
+
+template <class TV>
+static cudaError_t level_t(const Ctx& x, int l, bool down, int all) {
+  const int BL = x.B >> l;
+#define BCM_MG_LEVEL(V) \
+  case V: return down ? down_t<V, TV>(x, l, all) : up_t<V, TV>(x, l, all);
+  switch (BL) {
+    BCM_MG_LEVEL(16)
+    BCM_MG_LEVEL(8)
+    BCM_MG_LEVEL(4)
+    BCM_MG_LEVEL(2)
+    BCM_MG_LEVEL(1)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BCM_MG_LEVEL
+}
+
+template <int B, class TV>
+static cudaError_t up0_t(const Ctx& x, const SolveParams& prm, int mode) {
+  constexpr int B3 = B * B * B, NT = B3 < 256 ? B3 : 256;
+  const TV* yc = (const TV*)x.mg.y[1];
+  k_mg_up0<B, NT, TV><<<x.g.n_cubes * (B3 / NT), NT, 0, x.stream>>>(
+      x.g, (const TV*)x.mg.r[0], (const TV*)x.mg.x[0], yc, x.mg.ax[0], x.mg.parent[0],
+      (TV*)x.mg.y[0], prm, mode);
+  return cudaGetLastError();
+}
+
+template <int B, class TV>
+static cudaError_t down0_tile_t(const Ctx& x, int all) {
+  using SL = Slab<B, B>;
+  const size_t sm = sizeof(TV) * ((SL::N + 3) / 4 * 4 + (size_t)B * B * B);
+  auto kern = k_mg_down0_tile<B, TV>;
+  cudaError_t e = allow_dynamic_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[0], (TV*)x.mg.x[0],
+                                            (TV*)x.mg.r[1], all);
+  return cudaGetLastError();
+}
+
+template <int B, class TV>
+static cudaError_t up0_tile_t(const Ctx& x, const SolveParams& prm, int mode) {
+  using SL = Slab<B, B>;
+  const size_t sm = sizeof(TV) * SL::N;
+  auto kern = k_mg_up0_tile<B, TV>;
+  cudaError_t e = allow_dynamic_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[0], (const TV*)x.mg.x[0],
+                                            (const TV*)x.mg.y[1], (TV*)x.mg.y[0], prm, mode);
+  return cudaGetLastError();
+}
+
+template <class TV>
+static cudaError_t vcycle_t(const Ctx& x, const SolveParams& prm, int mode) {
+  const int all = mode == 2 ? 1 : 0;
+  cudaError_t e;
+  // the finest level of 8^3 and 16^3 cubes through the shared-memory tile
+  const bool tile = x.B == 8 || x.B == 16;
+  for (int l = 0; l <= x.mg.L; ++l) {
+    if (l == 0 && tile) {
+      e = x.B == 16 ? down0_tile_t<16, TV>(x, all) : down0_tile_t<8, TV>(x, all);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    if ((e = level_t<TV>(x, l, true, all)) != cudaSuccess) return e;
+  }
+  k_mg_top<TV><<<1, 1024, 0, x.stream>>>(x.mg, (const TV*)x.mg.rr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int l = x.mg.L; l >= 1; --l)
+    if ((e = level_t<TV>(x, l, false, all)) != cudaSuccess) return e;
+  if (tile) return x.B == 16 ? up0_tile_t<16, TV>(x, prm, mode) : up0_tile_t<8, TV>(x, prm, mode);
+  switch (x.B) {
+    case 4: return up0_t<4, TV>(x, prm, mode);
+    case 8: return up0_t<8, TV>(x, prm, mode);
+    case 16: return up0_t<16, TV>(x, prm, mode);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_mg_vcycle(const Ctx& x, const SolveParams& prm, int mode) {
+  return x.f64 ? vcycle_t<double>(x, prm, mode) : vcycle_t<float>(x, prm, mode);
+}
+
+}  // namespace bcm

@@ -175,6 +175,7 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
 // ===========================================================================
 template <int B, int KS, int NT, class TV>
 __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r,
+                                             const TV* __restrict__ zv,
                                              TV* __restrict__ p0, TV* __restrict__ p1,
                                              TV* __restrict__ q, SolveParams prm) {
   using SL = Slab<B, KS>;
@@ -195,11 +196,18 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
     const TV beta = TV(st.beta);
     const bool first = (it == 0);
     __syncthreads();
+    // z = M^-1 r: the multigrid V-cycle's output, or the Jacobi scaling of r
     auto val4 = [&](int cube, int cell0, int face, TV (&v)[4]) {
       const size_t gi = (size_t)cube * B3 + cell0;
       TV rr[4], pp[4] = {TV(0), TV(0), TV(0), TV(0)};
-      ld4(r + gi, rr);
       if (!first) ld4(pold + gi, pp);
+      if (zv) {
+        ld4(zv + gi, rr);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) v[m] = first ? rr[m] : rr[m] + beta * pp[m];
+        return;
+      }
+      ld4(r + gi, rr);
       const int* w3 = face < 0 ? cs.w3 : cs.nbw3[face];
       const int k = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
 #pragma unroll
@@ -211,12 +219,12 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
     auto val1 = [&](int f, int n, int cell) {
       const int i = cell % B, j = (cell / B) % B, k = cell / BB;
       const size_t gi = (size_t)n * B3 + cell;
-      const TV z = r[gi] * cs.invtab[s3_of<B>(cs.nbw3[f], i, j, k)];
+      const TV z = zv ? zv[gi] : r[gi] * cs.invtab[s3_of<B>(cs.nbw3[f], i, j, k)];
       return first ? z : z + beta * pold[gi];
     };
     auto valg = [&](int n, int cell) {
       const size_t gi = (size_t)n * B3 + cell;
-      const TV z = r[gi] * inv_diag_any<B, TV>(g, n, cell);
+      const TV z = zv ? zv[gi] : r[gi] * inv_diag_any<B, TV>(g, n, cell);
       return first ? z : z + beta * pold[gi];
     };
     stage_pressure_slab<B, KS, NT, TV>(S, cs, g, c, z0, val4, val1, valg);
@@ -311,10 +319,12 @@ __global__ __launch_bounds__(NT) void k_cg_b(DevGrid g, TX* __restrict__ x, TV* 
   }
   block_sum<NT, 2>(vals, red);
   if (threadIdx.x == 0 && active) {
-    acc_add(st, ACC_RZ, vals[0]);
+    if (!prm.mg) acc_add(st, ACC_RZ, vals[0]);
     acc_add(st, ACC_RR, vals[1]);
   }
-  if (last_block(g.counter)) {
+  // with the multigrid preconditioner z = M^-1 r comes from the V-cycle that follows,
+  // whose last launch takes the decisions below
+  if (!prm.mg && last_block(g.counter)) {
     int alive = 0;
     for (int qq = threadIdx.x; qq < g.n_sims; qq += NT) {
       SimState& t = g.ss[qq];
@@ -552,7 +562,8 @@ static cudaError_t cg_a_t(const Ctx& x, const SolveParams& prm) {
       auto ka = k_cg_a<B, KS, NT, TV>;
       cudaError_t e = allow_smem(ka, sm);
       if (e != cudaSuccess) return e;
-      ka<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(x.g, (const TV*)x.f.r, (TV*)x.f.p0,
+      const TV* zv = prm.mg ? (const TV*)x.mg.y[0] : nullptr;
+      ka<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(x.g, (const TV*)x.f.r, zv, (TV*)x.f.p0,
                                                        (TV*)x.f.p1, (TV*)x.f.q, prm);
     });
   });

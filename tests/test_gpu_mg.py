@@ -1,0 +1,110 @@
+"""The multigrid preconditioner on the GPU (BCM_PRECOND_MULTIGRID) against the oracle:
+one V-cycle z = M^-1 r against the oracle's V-cycle built from its definition (Galerkin
+products of the oracle's own operator), and whole steps with the multigrid-preconditioned
+PCG against the oracle's steps (whose Jacobi-PCG reaches the same unique solution)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mg_oracle as MGO
+from paper_1808_04099_gb300 import workloads as W
+from _util import demean_per_sim, oracle_run, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1808_04099_gb300 import bcm  # noqa: E402
+
+TOL64, TOL32 = 1e-10, 1e-6
+
+GRIDS = {
+    "channel_B4": lambda: W.sphere_channel(4, 2, 2, 4, length=(4.0, 2.0, 2.0), radius=0.3),
+    "cavity_B8": lambda: W.cavity(2, 8),
+    "periodic_B4": lambda: W.periodic_box(2, 4),
+    "channel_B16": lambda: W.sphere_channel(2, 1, 1, 16, length=(2.0, 1.0, 1.0), radius=0.2,
+                                            center=(0.6, 0.5, 0.5)),
+    "batched": lambda: W.concat([W.cavity(2, 4, re=300.0),
+                                 W.sphere_channel(4, 2, 2, 4, radius=0.3),
+                                 W.cavity(3, 4, re=700.0)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRIDS))
+def test_vcycle_matches_oracle(name):
+    spec = GRIDS[name]()
+    g = bcm.Grid(spec, bcm.PREC_F64)
+    mg = MGO.MG(O.Oracle(spec))
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        r = rng.standard_normal(spec.n_cells)
+        z = g.apply_preconditioner(r).cpu().numpy()
+        ref = mg.apply(r)
+        assert rel_l2(z, ref) <= 1e-12
+
+
+def velocity(g):
+    return np.concatenate([g.numpy(f) for f in (bcm.U, bcm.V, bcm.W)])
+
+
+def check(g, ost, spec, tol):
+    ref = np.concatenate([ost[k] for k in ("u", "v", "w")])
+    assert rel_l2(velocity(g), ref) <= tol
+    assert rel_l2(demean_per_sim(g.numpy(bcm.P), spec), demean_per_sim(ost["p"], spec)) <= tol
+
+
+@pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
+def test_mg_steps_match_oracle(prec):
+    """Sphere flow (B = 8) and a batch of ragged sims: two steps with the multigrid PCG
+    against the oracle; fewer PCG iterations than the Jacobi PCG on the same step."""
+    for spec in (W.sphere_channel(4, 2, 2, 8, radius=0.3),
+                 W.concat([W.cavity(2, 8, re=250.0), W.sphere_channel(4, 2, 2, 8, radius=0.3)])):
+        state = W.initial_state(spec, seed=51, noise=1e-3)
+        ost, ostats = oracle_run(spec, state, 2, 1e-13)
+        rtol = 1e-13 if prec == bcm.PREC_F64 else 1e-12
+        g = bcm.Grid(spec, prec)
+        g.load_state(state)
+        g.set_preconditioner(bcm.PRECOND_MULTIGRID)
+        st = g.step(2, rtol=rtol)
+        assert all(s["converged"] == 1 and s["pcg_form"] == 4 for s in st)
+        check(g, ost, spec, TOL64 if prec == bcm.PREC_F64 else TOL32)
+        if prec == bcm.PREC_F64:
+            for s, o in zip(st, ostats):
+                assert s["cg_iters"] * 2 < o["cg_iters"], (s["cg_iters"], o["cg_iters"])
+
+
+def test_mg_full_size_sphere_mixed():
+    """The 4.19M-cell sphere flow, two mixed steps at residual 1e-10 with the multigrid
+    PCG: converged, divergence at the residual, and within 1e-6 of the Jacobi PCG."""
+    spec = W.config_sphere(2)
+    state = W.initial_state(spec)
+    runs = []
+    for kind in (bcm.PRECOND_MULTIGRID, bcm.PRECOND_JACOBI):
+        g = bcm.Grid(spec, bcm.PREC_F32_REFINE)
+        g.load_state(state)
+        g.set_preconditioner(kind)
+        st = g.step(2, rtol=1e-10)
+        assert st[0]["converged"] == 1 and st[0]["rel_resid"] <= 1e-10
+        assert st[0]["div_rel"] <= 1e-9
+        runs.append((velocity(g), st[0]["cg_iters"]))
+        del g
+        torch.cuda.empty_cache()
+    assert rel_l2(runs[0][0], runs[1][0]) <= TOL32
+    assert runs[0][1] * 4 < runs[1][1], (runs[0][1], runs[1][1])
+
+
+def test_mg_rejected_where_not_defined():
+    """Two-level grids have no multigrid hierarchy; graph steps keep the Jacobi PCG."""
+    spec = W.two_level_channel(4, 4, 4, 8, (1, 1, 1), (3, 3, 3), 1 / 16., 0)
+    g = bcm.Grid(spec, bcm.PREC_F64)
+    with pytest.raises(bcm.BCMError) as ei:
+        g.set_preconditioner(bcm.PRECOND_MULTIGRID)
+    assert ei.value.status == bcm.BCM_E_INVALID
+    g1 = bcm.Grid(W.cavity(2, 8), bcm.PREC_F32_REFINE)
+    g1.load_state(W.initial_state(W.cavity(2, 8), 1, 1e-3))
+    g1.set_preconditioner(bcm.PRECOND_MULTIGRID)
+    with pytest.raises(bcm.BCMError) as ei:
+        g1.step_graph(1, rtol=1e-8)
+    assert ei.value.status == bcm.BCM_E_INVALID
