@@ -9,6 +9,7 @@ pressure solve to relative residual 1e-8, projection + FP64 divergence check.
 
 value      FP32 sweeps inside FP64 defect correction (mixed), device-timed
 fp64       the plain FP64 path at the same residual, device-timed
+mg         the same steps with the multigrid-preconditioned PCG, mixed and FP64
 e2e        the mixed step through the C ABI with the state copied host->device
            from pinned memory before and device->host after every step
 roofline   the dominant kernel's algorithmic bytes / its CUDA-event time vs
@@ -53,6 +54,9 @@ def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
         "correct": 8 + 8 + 6 * S,               # p, b, u* in; u out
         "solid_fraction": S + 1,
         "pcg": 10 * S,                          # per iteration: pass A (4 S) + pass B (6 S)
+        # per V-cycle: finest level down (r in; x, r_1 out) and up (x, y_1, r in; z out),
+        # the coarser levels 1/7 of that
+        "mg": 6 * S,
         "misc": 0.0,
     }[kernel]
 
@@ -85,7 +89,8 @@ def profiled_pcg_traffic():
 
 def kernel_table(prof, n, f64, phi_frac, pcg_iters):
     """Per kernel class: launches, time, algorithmic bytes and GB/s.  The persistent
-    PCG moves 10 S bytes per cell per iteration; pcg_iters = iterations it ran."""
+    PCG moves 10 S bytes per cell per iteration; pcg_iters = iterations it ran.  The
+    library times each multigrid V-cycle (all its launches) as one unit."""
     out = {}
     for k, (tot, cnt) in prof.items():
         if not cnt:
@@ -99,6 +104,8 @@ def kernel_table(prof, n, f64, phi_frac, pcg_iters):
                   "GBps": (total_bytes / (tot / 1e3)) / 1e9 if bpc else None}
         if k == "pcg" and pcg_iters:
             out[k]["us_per_iter"] = 1e3 * tot / pcg_iters
+        if k == "mg":
+            out[k]["us_per_vcycle"] = 1e3 * tot / units
     return out
 
 
@@ -396,6 +403,32 @@ def gpu_arm(args, ws, rank, local):
     fp64_value = n * args.steps / (ms64 / 1e3) * (ws if ws > 1 else 1)
     k64 = kernel_table(prof64, n, True, phi_frac, iters64)
 
+    # ---- the same step with the multigrid-preconditioned PCG (per-cube geometric
+    # multigrid, one V-cycle per iteration), eager steps, both precisions
+    mg = {}
+    for name, prec in (("mixed", bcm.PREC_F32_REFINE), ("fp64", bcm.PREC_F64)):
+        gm = bcm.Grid(spec, prec, device=dev)
+        gm.load_state(state)
+        gm.set_preconditioner(bcm.PRECOND_MULTIGRID)
+        for _ in range(args.warmup):
+            gm.step(1, rtol=RTOL, stats=False)
+        msm = timed_steps(gm, args.steps, gm.stream)
+        stm = gm.step(0, rtol=RTOL)[0]
+        gm.profile(True)
+        itm = 0
+        for _ in range(kprof_steps):
+            itm += gm.step(1, rtol=RTOL)[0]["cg_iters"]
+        profm, _ = gm.profile_read(reset=True)
+        gm.profile(False)
+        del gm
+        msm = max_over_ranks(msm, ws)
+        mg[name] = {"value": n * args.steps / (msm / 1e3) * (ws if ws > 1 else 1),
+                    "unit": "cell-updates/s", "ms_per_step": msm / args.steps,
+                    "cg_iters_last_step": stm["cg_iters"],
+                    "refine_cycles_last_step": stm["refine_cycles"],
+                    "rel_resid_last_step": stm["rel_resid"],
+                    "kernels": kernel_table(profm, n, prec == bcm.PREC_F64, phi_frac, itm)}
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -422,6 +455,9 @@ def gpu_arm(args, ws, rank, local):
                      "ms_per_step": ms64 / args.steps, "cg_iters_last_step": st64["cg_iters"],
                      "rel_resid_last_step": st64["rel_resid"], "kernels": k64},
             "speedup_mixed_vs_fp64": value / fp64_value,
+            "mg": dict(mg, note="multigrid-preconditioned PCG (a NEXT row beyond the "
+                                "Jacobi-PCG hot path), eager steps, same workload and "
+                                "residual"),
             "mixed_paths_ms_per_step": {"eager": ms_eager / args.steps,
                                         "graph": ms_graph / args.steps,
                                         "value_from": "graph" if ms_graph <= ms_eager else "eager"},
