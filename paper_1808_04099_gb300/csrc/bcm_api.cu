@@ -449,9 +449,21 @@ struct StepGraph {
   size_t kernels = 0;  // kernel nodes in the captured step
 };
 
+// The multigrid PCG's iteration (pass A, pass B, V-cycle) as one CUDA graph, captured
+// once per set of solver parameters and launch shape and replayed between flag reads.
+struct MgIterGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  SolveParams key{};
+  int slabs_a = 0, slabs_b = 0, valid = 0;
+  long long kernels = 0;  // kernel nodes per replay
+};
+
 struct bcm_grid {
   bcm_grid_desc desc;
   StepGraph sg;
+  MgIterGraph mgg;
   int graph_cycles = 0;      // graph steps: defect-correction cycles per solve (0: from rtol)
   double inner_rtol = -1.0;  // mixed: inner FP32 PCG reduction per cycle (< 0: automatic)
   int max_cycles = 30;       // mixed: FP64 residual evaluations per solve
@@ -697,6 +709,9 @@ extern "C" bcm_status bcm_destroy_grid(bcm_grid* g) {
     if (g->sg.exec) cudaGraphExecDestroy(g->sg.exec);
     if (g->sg.graph) cudaGraphDestroy(g->sg.graph);
     if (g->sg.capture_stream) cudaStreamDestroy(g->sg.capture_stream);
+    if (g->mgg.exec) cudaGraphExecDestroy(g->mgg.exec);
+    if (g->mgg.graph) cudaGraphDestroy(g->mgg.graph);
+    if (g->mgg.capture_stream) cudaStreamDestroy(g->mgg.capture_stream);
   }
   delete g;
   return BCM_OK;
@@ -827,6 +842,52 @@ double effective_inner_rtol(const bcm_grid* g, bool recycle) {
   return recycle ? 0.1 : 1e-5;
 }
 
+bcm_status mg_iteration_graph(bcm_grid* g, const SolveParams& prm, cudaGraphExec_t* out) {
+  MgIterGraph& m = g->mgg;
+  if (m.valid && memcmp(&m.key, &prm, sizeof prm) == 0 && m.slabs_a == g->ctx.slabs_a &&
+      m.slabs_b == g->ctx.slabs_b) {
+    *out = m.exec;
+    return BCM_OK;
+  }
+  if (m.exec) CUDA_TRY(cudaGraphExecDestroy(m.exec));
+  if (m.graph) CUDA_TRY(cudaGraphDestroy(m.graph));
+  m.exec = nullptr;
+  m.graph = nullptr;
+  m.valid = 0;
+  if (!m.capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&m.capture_stream, cudaStreamNonBlocking));
+  Ctx x = g->ctx;
+  x.stream = m.capture_stream;
+  CUDA_TRY(cudaStreamBeginCapture(m.capture_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_cg_a(x, prm);
+  if (e == cudaSuccess) e = launch_cg_b(x, prm);
+  if (e == cudaSuccess) e = launch_mg_vcycle(x, prm, 1);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(m.capture_stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(BCM_E_CUDA, "multigrid iteration capture: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  m.graph = graph;
+  size_t nn = 0;
+  CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) CUDA_TRY(cudaGraphGetNodes(graph, nodes.data(), &nn));
+  m.kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+    m.kernels += ty == cudaGraphNodeTypeKernel;
+  }
+  CUDA_TRY(cudaGraphInstantiate(&m.exec, graph, 0));
+  m.key = prm;
+  m.slabs_a = g->ctx.slabs_a;
+  m.slabs_b = g->ctx.slabs_b;
+  m.valid = 1;
+  *out = m.exec;
+  return BCM_OK;
+}
+
 bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   Ctx& x = g->ctx;
   const bool mg = x.use_mg != 0;  // multigrid-preconditioned CG: two launches + V-cycle
@@ -850,6 +911,10 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   bcm_status st;
   // the multigrid iteration converges in a few iterations: read the flags more often
   const int every = mg ? (g->check_every < 2 ? g->check_every : 2) : g->check_every;
+  // with kernel timing off the multigrid iteration replays one captured graph
+  const bool mg_graph = mg && !g->timer.on;
+  cudaGraphExec_t mg_exec = nullptr;
+  if (mg_graph && (st = mg_iteration_graph(g, prm, &mg_exec)) != BCM_OK) return st;
   if (x.persistent && !mg) {
     if (g->f64) {
       RUN(BCM_K_PCG, launch_pcg(x, prm, &g->pcg_form));
@@ -877,6 +942,11 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     while (!flags[0] && it < max_iter) {
       for (int m = 0; m < every && it < max_iter; ++m, ++it)
       {
+        if (mg_graph) {  // pass A, pass B and the V-cycle as one graph
+          CUDA_TRY(cudaGraphLaunch(mg_exec, g->stream));
+          g->launch_count += g->mgg.kernels;
+          continue;
+        }
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
         RUN(BCM_K_CG_B, launch_cg_b(x, prm));
         if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));
@@ -891,6 +961,11 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     while (!flags[0] && it < max_iter) {
       for (int m = 0; m < every && it < max_iter; ++m, ++it)
       {
+        if (mg_graph) {  // pass A, pass B and the V-cycle as one graph
+          CUDA_TRY(cudaGraphLaunch(mg_exec, g->stream));
+          g->launch_count += g->mgg.kernels;
+          continue;
+        }
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
         RUN(BCM_K_CG_B, launch_cg_b(x, prm));
         if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));

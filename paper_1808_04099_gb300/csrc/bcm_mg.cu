@@ -90,14 +90,11 @@ __device__ __forceinline__ TV smooth_w(const DevGrid& g, const SimParams& sp, in
 // One thread per coarse cell (its 2x2x2 fine cells), or per cube on the level with one
 // cell per cube (its residual goes to `rc` per cube for the aggregate levels).
 template <int BL, class TV>
-__global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale,
-                                                 const TV* __restrict__ r,
-                                                 TV* __restrict__ x, TV* __restrict__ rc,
-                                                 int all) {
+__device__ __forceinline__ void mg_down_item(const DevGrid& g, TV wscale, TV cscale,
+                                             const TV* __restrict__ r, TV* __restrict__ x,
+                                             TV* __restrict__ rc, int all, long long t) {
   constexpr int CB = BL > 1 ? BL / 2 : 1, C3 = CB * CB * CB, B3 = BL * BL * BL;
   constexpr int CH = BL > 1 ? 2 : 1;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)g.n_cubes * C3) return;
   const int c = (int)(t / C3), ci = (int)(t - (long long)c * C3);
   const int s = g.sim[c];
   if (!all && g.ss[s].done) return;
@@ -131,6 +128,17 @@ __global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale
         sum += rv - coef * acc;
       }
   rc[t] = sum;
+}
+
+template <int BL, class TV>
+__global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale,
+                                                 const TV* __restrict__ r,
+                                                 TV* __restrict__ x, TV* __restrict__ rc,
+                                                 int all) {
+  constexpr int CB = BL > 1 ? BL / 2 : 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.n_cubes * CB * CB * CB) return;
+  mg_down_item<BL, TV>(g, wscale, cscale, r, x, rc, all, t);
 }
 
 // ---- up: x~ = x + P y_coarse (on the fly for the cell and its neighbours), then
@@ -177,6 +185,21 @@ __device__ __forceinline__ TV up_cell(const DevGrid& g, TV wscale, TV cscale,
 }
 
 template <int BL, class TV>
+__device__ __forceinline__ void mg_up_item(const DevGrid& g, TV wscale, TV cscale,
+                                           const TV* __restrict__ r, const TV* __restrict__ x,
+                                           const TV* __restrict__ yc,
+                                           const double* __restrict__ yagg,
+                                           const int* __restrict__ agg_parent,
+                                           TV* __restrict__ y, int all, long long t) {
+  constexpr int B3 = BL * BL * BL;
+  const int c = (int)(t / B3), cell = (int)(t - (long long)c * B3);
+  if (!all && g.ss[g.sim[c]].done) return;
+  const int i = cell % BL, j = (cell / BL) % BL, k = cell / (BL * BL);
+  TV rv;
+  y[t] = up_cell<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
+}
+
+template <int BL, class TV>
 __global__ __launch_bounds__(256) void k_mg_up(DevGrid g, TV wscale, TV cscale,
                                                const TV* __restrict__ r,
                                                const TV* __restrict__ x,
@@ -184,14 +207,9 @@ __global__ __launch_bounds__(256) void k_mg_up(DevGrid g, TV wscale, TV cscale,
                                                const double* __restrict__ yagg,
                                                const int* __restrict__ agg_parent,
                                                TV* __restrict__ y, int all) {
-  constexpr int B3 = BL * BL * BL;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)g.n_cubes * B3) return;
-  const int c = (int)(t / B3), cell = (int)(t - (long long)c * B3);
-  if (!all && g.ss[g.sim[c]].done) return;
-  const int i = cell % BL, j = (cell / BL) % BL, k = cell / (BL * BL);
-  TV rv;
-  y[t] = up_cell<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
+  if (t >= (long long)g.n_cubes * BL * BL * BL) return;
+  mg_up_item<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, y, all, t);
 }
 
 // The last block of the finest up launch: mode 0 (start of a solve) takes <r, z> as
@@ -401,57 +419,96 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
 }
 
 // ---- the aggregate levels, in one block: gather of the cubes' residuals, the V-cycle
-// on the CSR levels k = 0 .. M-1 (k = M-1 the top), result y = ax[0].
+// on the CSR levels k = 0 .. M-1 (k = M-1 the top), result y = ax[0].  The node vectors
+// live in shared memory when they fit (use_smem), else in the workspace; the CSR tables
+// are read from the workspace.
 template <class TV>
-__global__ __launch_bounds__(1024) void k_mg_top(MgDev mg, const TV* __restrict__ rr) {
+__device__ void mg_top(const MgDev& mg, const TV* __restrict__ rr, int use_smem, double* sm) {
+  __shared__ int offs[kMgMaxM + 1];
   const int tid = threadIdx.x, NT = blockDim.x;
   const double w = kMgOmega;
+  if (tid == 0) {
+    offs[0] = 0;
+    for (int k = 0; k < mg.M; ++k) offs[k + 1] = offs[k] + mg.n[k];
+  }
+  __syncthreads();
+  const int tot = offs[mg.M];
+  auto AR = [&](int k) { return use_smem ? sm + offs[k] : mg.ar[k]; };
+  auto AX = [&](int k) { return use_smem ? sm + tot + offs[k] : mg.ax[k]; };
+  auto AT = [&](int k) { return use_smem ? sm + 2 * tot + offs[k] : mg.at[k]; };
   auto dinv = [&](int k, int a) {
     const double d = mg.diag[k][a];
     return d > 0.0 ? 1.0 / d : 0.0;
   };
   // at = ar - K ax on level k
   auto residual = [&](int k) {
+    const double* ar = AR(k);
+    const double* ax = AX(k);
+    double* at = AT(k);
     for (int a = tid; a < mg.n[k]; a += NT) {
-      double kx = mg.diag[k][a] * mg.ax[k][a];
-      for (int e = mg.row[k][a]; e < mg.row[k][a + 1]; ++e) kx -= mg.val[k][e] * mg.ax[k][mg.col[k][e]];
-      mg.at[k][a] = mg.ar[k][a] - kx;
+      double kx = mg.diag[k][a] * ax[a];
+      for (int e = mg.row[k][a]; e < mg.row[k][a + 1]; ++e) kx -= mg.val[k][e] * ax[mg.col[k][e]];
+      at[a] = ar[a] - kx;
     }
     __syncthreads();
   };
-  for (int a = tid; a < mg.n[0]; a += NT) {
-    double sum = 0.0;
-    for (int e = mg.cptr[0][a]; e < mg.cptr[0][a + 1]; ++e) sum += double(rr[mg.cidx[0][e]]);
-    mg.ar[0][a] = sum;
+  {
+    double* ar = AR(0);
+    for (int a = tid; a < mg.n[0]; a += NT) {
+      double sum = 0.0;
+      for (int e = mg.cptr[0][a]; e < mg.cptr[0][a + 1]; ++e) sum += double(rr[mg.cidx[0][e]]);
+      ar[a] = sum;
+    }
   }
   __syncthreads();
   const int top = mg.M - 1;
   for (int k = 0; k < top; ++k) {
-    for (int a = tid; a < mg.n[k]; a += NT) mg.ax[k][a] = w * dinv(k, a) * mg.ar[k][a];
+    double* ax = AX(k);
+    const double* ar = AR(k);
+    for (int a = tid; a < mg.n[k]; a += NT) ax[a] = w * dinv(k, a) * ar[a];
     __syncthreads();
     residual(k);
+    const double* at = AT(k);
+    double* arn = AR(k + 1);
     for (int a = tid; a < mg.n[k + 1]; a += NT) {
       double sum = 0.0;
-      for (int e = mg.cptr[k + 1][a]; e < mg.cptr[k + 1][a + 1]; ++e)
-        sum += mg.at[k][mg.cidx[k + 1][e]];
-      mg.ar[k + 1][a] = sum;
+      for (int e = mg.cptr[k + 1][a]; e < mg.cptr[k + 1][a + 1]; ++e) sum += at[mg.cidx[k + 1][e]];
+      arn[a] = sum;
     }
     __syncthreads();
   }
-  for (int a = tid; a < mg.n[top]; a += NT) mg.ax[top][a] = 0.0;
-  __syncthreads();
-  for (int sweep = 0; sweep < kMgNuTop; ++sweep) {
-    residual(top);
-    for (int a = tid; a < mg.n[top]; a += NT) mg.ax[top][a] += w * dinv(top, a) * mg.at[top][a];
+  {
+    double* ax = AX(top);
+    for (int a = tid; a < mg.n[top]; a += NT) ax[a] = 0.0;
     __syncthreads();
+    for (int sweep = 0; sweep < kMgNuTop; ++sweep) {
+      residual(top);
+      const double* at = AT(top);
+      for (int a = tid; a < mg.n[top]; a += NT) ax[a] += w * dinv(top, a) * at[a];
+      __syncthreads();
+    }
   }
   for (int k = top - 1; k >= 0; --k) {
-    for (int a = tid; a < mg.n[k]; a += NT) mg.ax[k][a] += mg.ax[k + 1][mg.parent[k + 1][a]];
+    double* ax = AX(k);
+    const double* axc = AX(k + 1);
+    for (int a = tid; a < mg.n[k]; a += NT) ax[a] += axc[mg.parent[k + 1][a]];
     __syncthreads();
     residual(k);
-    for (int a = tid; a < mg.n[k]; a += NT) mg.ax[k][a] += w * dinv(k, a) * mg.at[k][a];
+    const double* at = AT(k);
+    for (int a = tid; a < mg.n[k]; a += NT) ax[a] += w * dinv(k, a) * at[a];
     __syncthreads();
   }
+  if (use_smem) {  // the level-0 result for the up launches
+    const double* ax = AX(0);
+    for (int a = tid; a < mg.n[0]; a += NT) mg.ax[0][a] = ax[a];
+  }
+}
+
+template <class TV>
+__global__ __launch_bounds__(1024) void k_mg_top(MgDev mg, const TV* __restrict__ rr,
+                                                 int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mg_top<TV>(mg, rr, use_smem, reinterpret_cast<double*>(smem_raw));
 }
 
 // ---------------------------------------------------------------- launcher
@@ -536,16 +593,21 @@ static cudaError_t vcycle_t(const Ctx& x, const SolveParams& prm, int mode) {
   cudaError_t e;
   // the finest level of 8^3 and 16^3 cubes through the shared-memory tile
   const bool tile = x.B == 8 || x.B == 16;
-  for (int l = 0; l <= x.mg.L; ++l) {
-    if (l == 0 && tile) {
-      e = x.B == 16 ? down0_tile_t<16, TV>(x, all) : down0_tile_t<8, TV>(x, all);
-      if (e != cudaSuccess) return e;
-      continue;
-    }
+  e = tile ? (x.B == 16 ? down0_tile_t<16, TV>(x, all) : down0_tile_t<8, TV>(x, all))
+           : level_t<TV>(x, 0, true, all);
+  if (e != cudaSuccess) return e;
+  for (int l = 1; l <= x.mg.L; ++l)
     if ((e = level_t<TV>(x, l, true, all)) != cudaSuccess) return e;
+  {
+    size_t nodes = 0;
+    for (int k = 0; k < x.mg.M; ++k) nodes += (size_t)x.mg.n[k];
+    const size_t sm = 3 * nodes * sizeof(double);
+    const int use_smem = sm <= 160 * 1024 ? 1 : 0;
+    auto kern = k_mg_top<TV>;
+    if (use_smem && (e = allow_dynamic_smem(kern, sm)) != cudaSuccess) return e;
+    kern<<<1, 1024, use_smem ? sm : 0, x.stream>>>(x.mg, (const TV*)x.mg.rr, use_smem);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_mg_top<TV><<<1, 1024, 0, x.stream>>>(x.mg, (const TV*)x.mg.rr);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = x.mg.L; l >= 1; --l)
     if ((e = level_t<TV>(x, l, false, all)) != cudaSuccess) return e;
   if (tile) return x.B == 16 ? up0_tile_t<16, TV>(x, prm, mode) : up0_tile_t<8, TV>(x, prm, mode);

@@ -108,3 +108,4 @@ def test_mg_rejected_where_not_defined():
     with pytest.raises(bcm.BCMError) as ei:
         g1.step_graph(1, rtol=1e-8)
     assert ei.value.status == bcm.BCM_E_INVALID
+
