@@ -177,8 +177,8 @@ bcm_status bcm_step_graph(bcm_grid *grid, int n_steps, double rtol, int max_iter
                           bcm_stats *stats);
 
 /* Solver controls (defaults in brackets): inner_rtol, the relative reduction of the
- * FP32 inner PCG per defect-correction cycle in mixed mode [0.1 with recycle, else
- * 1e-5]; max_cycles, the
+ * FP32 inner PCG per defect-correction cycle in mixed mode [0.1 with recycle, 1e-4 with
+ * the multigrid preconditioner, else 1e-5]; max_cycles, the
  * cap on FP64 residual evaluations per solve [30]; check_every, PCG iterations
  * between two reads of the device convergence flags by the host [8];
  * barrier_timeout_s, the longest wait of a block at a grid barrier of the
