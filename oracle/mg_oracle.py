@@ -20,14 +20,18 @@ Here the multigrid is the preconditioner of that CG, on single-level grids:
   operators K_0 = K, K_{l+1} = P_l^T K_l P_l (Galerkin).
   smoother  S_l = omega D_l^-1, D_l = diag(K_l) (a zero diagonal gives 0: the top node
             of a sim without outflow faces, where K 1 = 0), omega = 0.8.
-  V-cycle   V_l(r):  x = S_l r;  x += P_l V_{l+1}(P_l^T (r - K_l x));
+  V-cycle   V_l(r):  x = S_l r;  x += s P_l V_{l+1}(P_l^T (r - K_l x));
                      x += S_l (r - K_l x);  return x
+            with the coarse correction scaled by s = 1.75: piecewise-constant transfers
+            leave the Galerkin correction too weak, and the scale that minimises the
+            PCG iteration count on channel, cavity and batched grids is 1.5 - 2
             V_top(r): x = 0; four times x += S (r - K x); return x
   M^-1 r = V_0(r).
 
 The pre- and post-smoothers are the same symmetric S, so M^-1 is symmetric; with
 omega < 2 / lambda_max(D^-1 K) (lambda_max <= 2 for these diagonally dominant
-operators) it is positive definite.
+operators) its smoother part is positive definite and the scaled coarse part positive
+semidefinite, so M^-1 is positive definite for any s > 0.
 """
 from __future__ import annotations
 
@@ -39,6 +43,7 @@ import scipy.sparse as sp
 
 OMEGA = 0.8
 NU_TOP = 4
+OVER = 1.75  # scale of the coarse-grid correction
 
 
 def operator_matrix(oracle):
@@ -143,7 +148,7 @@ def vcycle(Ks, Ps, Ws, r: np.ndarray, l: int = 0) -> np.ndarray:
         return x
     P = Ps[l]
     x = S * r
-    x = x + P @ vcycle(Ks, Ps, Ws, P.T @ (r - Kl @ x), l + 1)
+    x = x + OVER * (P @ vcycle(Ks, Ps, Ws, P.T @ (r - Kl @ x), l + 1))
     x = x + S * (r - Kl @ x)
     return x
 
