@@ -46,6 +46,7 @@ constexpr int kMgMaxL = 4;   // log2 of the largest cube edge (16)
 constexpr int kMgMaxM = 20;  // aggregate levels
 constexpr double kMgOmega = 0.8;  // damped-Jacobi weight of the smoother
 constexpr int kMgNuTop = 4;       // Jacobi sweeps on the top aggregate level
+constexpr double kMgOver = 1.75;  // scale of the coarse-grid correction
 struct MgDev {
   int L, M;
   void* x[kMgMaxL + 1];  // pre-smoothed iterate of level l

@@ -11,8 +11,9 @@
 // diagonal, other domain faces nothing; the aggregate levels keep their Galerkin sums
 // as small CSR tables built on the host.  The smoother is damped Jacobi
 // S = omega D^-1 (omega = 0.8), one sweep before and one after the coarse correction,
-// so the V-cycle is symmetric positive definite and M^-1 suits CG:
-//   V_l(r) = x + S (r - K x),  x = S r + P V_{l+1}(P^T (r - K S r)),
+// which is scaled by s = 1.75 (piecewise-constant transfers leave it too weak), so the
+// V-cycle is symmetric positive definite and M^-1 suits CG:
+//   V_l(r) = x + S (r - K x),  x = S r + s P V_{l+1}(P^T (r - K S r)),
 //   V_top(r) = four damped-Jacobi sweeps from zero.
 //
 // Launches per V-cycle: one per per-cube level on the way down (pre-smoothing with the
@@ -152,10 +153,10 @@ __device__ __forceinline__ TV up_value(const TV* __restrict__ x, const TV* __res
   constexpr int B3 = BL * BL * BL;
   const TV xv = x[(size_t)c * B3 + lcell<BL>(i, j, k)];
   if constexpr (BL == 1) {
-    return xv + TV(yagg[agg_parent[c]]);
+    return xv + TV(kMgOver * yagg[agg_parent[c]]);
   } else {
     constexpr int CB = BL / 2;
-    return xv + yc[(size_t)c * CB * CB * CB + lcell<CB>(i >> 1, j >> 1, k >> 1)];
+    return xv + TV(kMgOver) * yc[(size_t)c * CB * CB * CB + lcell<CB>(i >> 1, j >> 1, k >> 1)];
   }
 }
 
@@ -373,14 +374,15 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
     auto xt = [&](int cube, int cell) {
       const int i = cell % B, j = (cell / B) % B, k = cell / BB;
       return x[(size_t)cube * B3 + cell] +
-             y1[(size_t)cube * CB * CB * CB + ((k >> 1) * CB + (j >> 1)) * CB + (i >> 1)];
+             TV(kMgOver) *
+                 y1[(size_t)cube * CB * CB * CB + ((k >> 1) * CB + (j >> 1)) * CB + (i >> 1)];
     };
     auto val4 = [&](int cube, int cell0, int, TV (&v)[4]) {
       TV xv[4];
       ld4(x + (size_t)cube * B3 + cell0, xv);
       const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
       const size_t pb = (size_t)cube * CB * CB * CB + ((kz >> 1) * CB + (j >> 1)) * CB + (i0 >> 1);
-      const TV ya = y1[pb], yb = y1[pb + 1];
+      const TV ya = TV(kMgOver) * y1[pb], yb = TV(kMgOver) * y1[pb + 1];
       v[0] = xv[0] + ya;
       v[1] = xv[1] + ya;
       v[2] = xv[2] + yb;
@@ -491,7 +493,7 @@ __device__ void mg_top(const MgDev& mg, const TV* __restrict__ rr, int use_smem,
   for (int k = top - 1; k >= 0; --k) {
     double* ax = AX(k);
     const double* axc = AX(k + 1);
-    for (int a = tid; a < mg.n[k]; a += NT) ax[a] += axc[mg.parent[k + 1][a]];
+    for (int a = tid; a < mg.n[k]; a += NT) ax[a] += kMgOver * axc[mg.parent[k + 1][a]];
     __syncthreads();
     residual(k);
     const double* at = AT(k);
