@@ -487,6 +487,8 @@ def ncu_case(args):
         g.set_launch(1, 1, persistent=0)
     elif args.ncu_single_pass:
         g.set_launch(1, 1, persistent=2)
+    if args.ncu_mg:
+        g.set_preconditioner(bcm.PRECOND_MULTIGRID)
     g.load_state(W.initial_state(spec))
     if args.ncu_iters:
         st = g.step(1, rtol=RTOL)
@@ -516,6 +518,8 @@ def main():
                     help="with --ncu-case: two launches per PCG iteration")
     ap.add_argument("--ncu-single-pass", action="store_true",
                     help="with --ncu-case: the single-reduction persistent PCG")
+    ap.add_argument("--ncu-mg", action="store_true",
+                    help="with --ncu-case: the multigrid-preconditioned PCG")
     ap.add_argument("--recycle", type=int, default=-1,
                     help="mixed mode: 1 reliable updates across cycles, 0 restarts (default: library)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
