@@ -54,9 +54,10 @@ def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
         "correct": 8 + 8 + 6 * S,               # p, b, u* in; u out
         "solid_fraction": S + 1,
         "pcg": 10 * S,                          # per iteration: pass A (4 S) + pass B (6 S)
-        # per V-cycle: finest level down (r in; x, r_1 out) and up (x, y_1, r in; z out),
-        # the coarser levels 1/7 of that
-        "mg": 6 * S,
+        # per V-cycle after pass A: finest level down with pass B (r, q, x, p in; x, r,
+        # x_0, r_1 out: 7.125 S) and up (x_0, y_1, r in; z out: 3.125 S), the coarser
+        # levels 1/7 of the V-cycle's part (0.75 S)
+        "mg": 11 * S,
         "misc": 0.0,
     }[kernel]
 

@@ -687,6 +687,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
     D.rr = W + ml.rr;
     for (int k = 0; k < D.M; ++k) {
       D.n[k] = mgh.agg[k].n;
+      D.nnz[k] = (int)mgh.agg[k].col.size();
       D.ar[k] = (double*)(W + ml.ar[k]);
       D.ax[k] = (double*)(W + ml.ax[k]);
       D.at[k] = (double*)(W + ml.at[k]);
@@ -862,8 +863,7 @@ bcm_status mg_iteration_graph(bcm_grid* g, const SolveParams& prm, cudaGraphExec
   x.stream = m.capture_stream;
   CUDA_TRY(cudaStreamBeginCapture(m.capture_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_cg_a(x, prm);
-  if (e == cudaSuccess) e = launch_cg_b(x, prm);
-  if (e == cudaSuccess) e = launch_mg_vcycle(x, prm, 1);
+  if (e == cudaSuccess) e = launch_mg_vcycle(x, prm, 1);  // pass B inside
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(m.capture_stream, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -945,14 +945,16 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     while (!flags[0] && it < max_iter) {
       for (int m = 0; m < every && it < max_iter; ++m, ++it)
       {
-        if (mg_graph) {  // pass A, pass B and the V-cycle as one graph
+        if (mg_graph) {  // pass A and the V-cycle (with pass B) as one graph
           CUDA_TRY(cudaGraphLaunch(mg_exec, g->stream));
           g->launch_count += g->mgg.kernels;
           continue;
         }
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
-        RUN(BCM_K_CG_B, launch_cg_b(x, prm));
-        if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));
+        if (mg)
+          RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));  // pass B inside
+        else
+          RUN(BCM_K_CG_B, launch_cg_b(x, prm));
       }
       if ((st = read_flags(g, flags)) != BCM_OK) return st;
     }
@@ -964,14 +966,16 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     while (!flags[0] && it < max_iter) {
       for (int m = 0; m < every && it < max_iter; ++m, ++it)
       {
-        if (mg_graph) {  // pass A, pass B and the V-cycle as one graph
+        if (mg_graph) {  // pass A and the V-cycle (with pass B) as one graph
           CUDA_TRY(cudaGraphLaunch(mg_exec, g->stream));
           g->launch_count += g->mgg.kernels;
           continue;
         }
         RUN(BCM_K_CG_A, launch_cg_a(x, prm));
-        RUN(BCM_K_CG_B, launch_cg_b(x, prm));
-        if (mg) RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));
+        if (mg)
+          RUN(BCM_K_MG, launch_mg_vcycle(x, prm, 1));  // pass B inside
+        else
+          RUN(BCM_K_CG_B, launch_cg_b(x, prm));
       }
       if ((st = read_flags(g, flags)) != BCM_OK) return st;
     }

@@ -54,6 +54,7 @@ struct MgDev {
   void* r[kMgMaxL + 1];  // residual of level l (r[0] is the PCG residual)
   void* rr;              // level L: residual after pre-smoothing, one value per cube
   int n[kMgMaxM];        // nodes of aggregate level k
+  int nnz[kMgMaxM];      // off-diagonal entries of level k
   double *ar[kMgMaxM], *ax[kMgMaxM], *at[kMgMaxM];  // residual, iterate, scratch
   double *diag[kMgMaxM], *val[kMgMaxM];              // K: diagonal, -off-diagonal (CSR)
   int *row[kMgMaxM], *col[kMgMaxM];
@@ -99,8 +100,8 @@ cudaError_t launch_step_end(const Ctx& x);
 cudaError_t launch_fill_halo(const Ctx& x, const void* f, int f64_field, int kind, double* out);
 cudaError_t launch_apply_poisson(const Ctx& x, const double* in, double* out);
 // One V-cycle z = M^-1 r on the PCG residual.  mode 0: after the residual kernel
-// (<r,z> becomes the PCG's rz); 1: after pass B (<r,z>, beta and the convergence
-// decision); 2: standalone (every sim, no dot products).
+// (<r,z> becomes the PCG's rz); 1: after pass A, doing pass B too (<r,r>), then <r,z>,
+// beta and the convergence decision; 2: standalone (every sim, no dot products).
 cudaError_t launch_mg_vcycle(const Ctx& x, const SolveParams& prm, int mode);
 
 }  // namespace bcm

@@ -142,6 +142,50 @@ __global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale
   mg_down_item<BL, TV>(g, wscale, cscale, r, x, rc, all, t);
 }
 
+// The same with one thread per fine cell (BL >= 2): the eight children of a coarse cell
+// are eight consecutive threads of one warp (child bits in the low three bits of the
+// thread index), so the restriction is a three-step shuffle sum.  Threads of finished
+// sims and of the tail take part in the shuffles with zeros.
+template <int BL, class TV>
+__global__ __launch_bounds__(256) void k_mg_down_cell(DevGrid g, TV wscale, TV cscale,
+                                                      const TV* __restrict__ r,
+                                                      TV* __restrict__ x, TV* __restrict__ rc,
+                                                      int all) {
+  static_assert(BL >= 2, "restriction over 2x2x2 children");
+  constexpr int CB = BL / 2, C3 = CB * CB * CB, B3 = BL * BL * BL;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)g.n_cubes * B3;
+  const int c = (int)(t / B3), q = (int)(t - (long long)c * B3);
+  const int d = q & 7, ci = q >> 3;
+  TV val = TV(0);
+  if (t < total && (all || !g.ss[g.sim[c]].done)) {
+    const int I = ci % CB, J = (ci / CB) % CB, Kc = ci / (CB * CB);
+    const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * Kc + (d >> 2);
+    const SimParams& sp = g.sp[g.sim[c]];
+    const TV coef = sim_h<TV>(sp) * cscale;
+    const size_t gi = (size_t)c * B3 + lcell<BL>(i, j, k);
+    const TV rv = r[gi];
+    const TV xc = smooth_w<BL, TV>(g, sp, c, i, j, k, wscale) * rv;
+    TV acc = TV(0);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      int nc, ni, nj, nk, sign = 1;
+      TV xn;
+      if (level_nb<BL>(g, c, i, j, k, f, nc, ni, nj, nk, sign))
+        xn = smooth_w<BL, TV>(g, sp, nc, ni, nj, nk, wscale) * r[(size_t)nc * B3 + lcell<BL>(ni, nj, nk)];
+      else
+        xn = TV(sign) * xc;
+      acc += xc - xn;
+    }
+    x[gi] = xc;
+    val = rv - coef * acc;
+  }
+  val += __shfl_xor_sync(0xffffffffu, val, 1);
+  val += __shfl_xor_sync(0xffffffffu, val, 2);
+  val += __shfl_xor_sync(0xffffffffu, val, 4);
+  if (d == 0 && t < total && (all || !g.ss[g.sim[c]].done)) rc[(size_t)c * C3 + ci] = val;
+}
+
 // ---- up: x~ = x + P y_coarse (on the fly for the cell and its neighbours), then
 // y = x~ + S (r - K x~).  One thread per cell.  On the level with one cell per cube the
 // coarse values come from aggregate level 0 (FP64, through the cube's parent).
@@ -284,28 +328,84 @@ __global__ __launch_bounds__(NT) void k_mg_up0(DevGrid g, const TV* __restrict__
   if (last_block(g.counter)) mg_decide(g, prm, mode, NT);
 }
 
-// ---- finest level of 8^3 / 16^3 cubes, one block per cube with the (B+2)^3 tile of the
-// PCG passes: down stages x = S r with the face halo, marches each column for
-// rr = r - K x and sums the 2x2x2 children of rr into r_1; up stages x~ = x + P y_1, marches
-// for z = x~ + S (r - K x~) and forms <r, z>.  Same values as the per-cell kernels above.
-template <int B, class TV>
-__global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __restrict__ r,
+// ---- levels of 8^3 / 16^3 cells per cube, one block per cube with the (B+2)^3 tile of
+// the PCG passes: down stages x = S r with the face halo, marches each column for
+// rr = r - K x and sums the 2x2x2 children of rr into r_{l+1}; up stages
+// x~ = x + s P y_{l+1}, marches for y = x~ + S (r - K x~) and, on the finest level, forms
+// <r, z>.  On level l, S = (omega / 4^l) D^-1 and K = 4^l h (sum of differences) with
+// the finest level's D: the launch passes wl = omega / 4^l and cl = 4^l.  Same values as
+// the per-cell kernels above.
+//
+// With FB the down launch also does the PCG's pass B (x_pcg += alpha p, r -= alpha q,
+// <r, r>): it reads the residual r_in of the iteration and writes the new one to the
+// other buffer r_out (blocks read their neighbours' r_in for the halo, so it is not
+// updated in place), forming the halo's new residual on the fly.  The buffers swap
+// with the parity of the sim's iteration count.
+template <class TV>
+struct PassB {
+  TV* x;                 // PCG iterate
+  const TV *p0, *p1, *q; // search directions (by iteration parity), q = K p
+  TV *ra, *rb;           // residual: in ra, out rb at even iterations; swapped at odd
+};
+
+template <int B, class TV, bool FB>
+__global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __restrict__ r0,
                                                          TV* __restrict__ x,
-                                                         TV* __restrict__ r1, int all) {
+                                                         TV* __restrict__ r1, int all,
+                                                         PassB<TV> pb, TV wl, TV cl) {
   using SL = Slab<B, B>;
   constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TV* S = reinterpret_cast<TV*>(smem_raw);
   TV* RR = S + (SL::N + 3) / 4 * 4;
   __shared__ CubeSh<TV> cs;
+  __shared__ double red[32];
   const int c = blockIdx.x;
-  if (!all && g.ss[g.sim[c]].done) return;
+  SimState& st = g.ss[g.sim[c]];
+  if (!all && st.done) return;
   load_cube(cs, g, c);
+  const TV* __restrict__ r = r0;
+  TV* __restrict__ rout = nullptr;
+  const TV* __restrict__ pn = nullptr;
+  TV alpha = TV(0);
+  if constexpr (FB) {
+    const int it = st.iter;
+    r = (it & 1) ? pb.rb : pb.ra;
+    rout = (it & 1) ? pb.ra : pb.rb;
+    pn = (it & 1) ? pb.p0 : pb.p1;
+    alpha = st.nonfinite ? TV(0) : TV(st.alpha);
+  }
   __syncthreads();
-  const TV w = TV(kMgOmega);
+  const TV w = wl;
+  TV rr2 = TV(0);
+  // the iteration's residual of a cell: r (FB: r_in - alpha q)
+  auto res = [&](size_t gi) {
+    if constexpr (FB) return r[gi] - alpha * pb.q[gi];
+    else return r[gi];
+  };
   auto val4 = [&](int cube, int cell0, int face, TV (&v)[4]) {
+    const size_t gi = (size_t)cube * B3 + cell0;
     TV rr[4];
-    ld4(r + (size_t)cube * B3 + cell0, rr);
+    ld4(r + gi, rr);
+    if constexpr (FB) {
+      TV qv[4];
+      ld4(pb.q + gi, qv);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) rr[m] = rr[m] - alpha * qv[m];
+      if (face < 0) {  // own cells: pass B
+        TV xv[4], pv[4];
+        ld4(pb.x + gi, xv);
+        ld4(pn + gi, pv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          xv[m] = xv[m] + alpha * pv[m];
+          rr2 += rr[m] * rr[m];
+          RR[cell0 + m] = rr[m];
+        }
+        st4(pb.x + gi, xv);
+        st4(rout + gi, rr);
+      }
+    }
     const int mask = face < 0 ? cs.smask : cs.nbmask[face];
     const int* w3 = face < 0 ? cs.w3 : cs.nbw3[face];
     const int kz = cell0 / BB, j = (cell0 / B) % B, i0 = cell0 % B;
@@ -317,13 +417,13 @@ __global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __
     const TV inv = cs.nbmask[f] == 0
                        ? cs.invtab[18]
                        : cs.invtab[s3_of<B>(cs.nbw3[f], cell % B, (cell / B) % B, cell / BB)];
-    return w * r[(size_t)n * B3 + cell] * inv;
+    return w * res((size_t)n * B3 + cell) * inv;
   };
   auto valg = [&](int n, int cell) {
-    return w * r[(size_t)n * B3 + cell] * inv_diag_any<B, TV>(g, n, cell);
+    return w * res((size_t)n * B3 + cell) * inv_diag_any<B, TV>(g, n, cell);
   };
   stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg);
-  const TV h = sim_h<TV>(g.sp[g.sim[c]]);
+  const TV h = sim_h<TV>(g.sp[g.sim[c]]) * cl;
   const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
   int o = SL::at(i, j, 1);
   TV below = S[o - PP], cur = S[o];
@@ -335,7 +435,8 @@ __global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __
     const int cell = (kk * B + j) * B + i;
     const size_t gi = (size_t)c * B3 + cell;
     x[gi] = cur;
-    RR[cell] = r[gi] - h * acc;
+    // FB: RR holds the cell's new residual, stored during the staging
+    RR[cell] = (FB ? RR[cell] : r[gi]) - h * acc;
     below = cur;
     cur = above;
     o += PP;
@@ -349,14 +450,20 @@ __global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __
       sum += RR[((2 * K + (d >> 2)) * B + 2 * J + ((d >> 1) & 1)) * B + 2 * I + (d & 1)];
     r1[(size_t)c * CB * CB * CB + q] = sum;
   }
+  if constexpr (FB) {
+    double vals[1] = {double(rr2)};
+    block_sum<NT, 1>(vals, red);
+    if (threadIdx.x == 0) acc_add(st, ACC_RR, vals[0]);
+  }
 }
 
 template <int B, class TV>
-__global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __restrict__ r,
+__global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __restrict__ ra,
+                                                       const TV* __restrict__ rb,
                                                        const TV* __restrict__ x,
                                                        const TV* __restrict__ y1,
                                                        TV* __restrict__ z, SolveParams prm,
-                                                       int mode) {
+                                                       int mode, TV wl, TV cl, int finest) {
   using SL = Slab<B, B>;
   constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -367,6 +474,9 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
   SimState& st = g.ss[s];
   const bool all = mode == 2;
   const bool active = all || !st.done;
+  // after a down launch with pass B (rb set) the new residual is in the buffer that
+  // the iteration's parity selects, else in ra
+  const TV* __restrict__ r = (mode == 1 && rb && !(st.iter & 1)) ? rb : ra;
   double rz = 0.0;
   if (active) {
     load_cube(cs, g, c);
@@ -391,7 +501,7 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
     auto val1 = [&](int, int n, int cell) { return xt(n, cell); };
     auto valg = [&](int n, int cell) { return xt(n, cell); };
     stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg);
-    const TV h = sim_h<TV>(g.sp[s]), w = TV(kMgOmega);
+    const TV h = sim_h<TV>(g.sp[s]) * cl, w = wl;
     const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
     int o = SL::at(i, j, 1);
     TV below = S[o - PP], cur = S[o];
@@ -413,7 +523,7 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
     }
     rz = double(part);
   }
-  if (all) return;
+  if (all || !finest) return;
   double vals[1] = {rz};
   block_sum<NT, 1>(vals, red);
   if (threadIdx.x == 0 && active) acc_add(st, ACC_RZ, vals[0]);
@@ -421,96 +531,181 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
 }
 
 // ---- the aggregate levels, in one block: gather of the cubes' residuals, the V-cycle
-// on the CSR levels k = 0 .. M-1 (k = M-1 the top), result y = ax[0].  The node vectors
-// live in shared memory when they fit (use_smem), else in the workspace; the CSR tables
-// are read from the workspace.
+// on the CSR levels k = 0 .. M-1 (k = M-1 the top), result y = ax[0].  The work is a
+// chain of small dependent steps, so it runs from shared memory: with smem_mode 2 the
+// node vectors and the level tables (diagonal, CSR rows, children, parents) are copied
+// in first, all copies in flight at once (cp.async); with 1 only the node vectors live
+// there; with 0 everything stays in the workspace.
+struct TopLevel {
+  double *ar, *ax, *at, *inv;
+  const double *diag, *val;
+  const int *row, *col, *cptr, *cidx, *parent;
+  int n;
+};
+
+// Shared-memory bytes of the node vectors (3 per node) and of the staged tables: per
+// level the inverse diagonal, the diagonal, the CSR values, rows and columns, and above
+// level 0 the children and parents; every piece 16-byte aligned.
+__host__ __device__ inline size_t top_piece(size_t bytes) { return (bytes + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t top_vec_bytes(const MgDev& mg) {
+  size_t nodes = 0;
+  for (int k = 0; k < mg.M; ++k) nodes += (size_t)mg.n[k];
+  return top_piece(3 * 8 * nodes);
+}
+__host__ __device__ inline size_t top_table_bytes(const MgDev& mg) {
+  size_t b = 0;
+  for (int k = 0; k < mg.M; ++k) {
+    const size_t n = (size_t)mg.n[k], nnz = (size_t)mg.nnz[k], np = k ? (size_t)mg.n[k - 1] : 0;
+    b += 2 * top_piece(8 * n) + top_piece(8 * nnz) + top_piece(4 * (n + 1)) + top_piece(4 * nnz);
+    if (k) b += top_piece(4 * (n + 1)) + 2 * top_piece(4 * np);
+  }
+  return b;
+}
+
+// asynchronous global -> shared copy of `count` elements of 4 or 8 bytes, by the block
+template <int E>
+__device__ __forceinline__ void copy_async(void* dst, const void* src, int count) {
+  static_assert(E == 4 || E == 8, "element size");
+  for (int a = threadIdx.x; a < count; a += blockDim.x) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(static_cast<char*>(dst) + (size_t)E * a);
+    const char* s = static_cast<const char*>(src) + (size_t)E * a;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(s), "n"(E) : "memory");
+  }
+}
+
 template <class TV>
-__device__ void mg_top(const MgDev& mg, const TV* __restrict__ rr, int use_smem, double* sm) {
-  __shared__ int offs[kMgMaxM + 1];
+__device__ void mg_top(const MgDev& mg, const TV* __restrict__ rr, int smem_mode, double* sm) {
+  __shared__ TopLevel lv[kMgMaxM];
   const int tid = threadIdx.x, NT = blockDim.x;
   const double w = kMgOmega;
-  if (tid == 0) {
-    offs[0] = 0;
-    for (int k = 0; k < mg.M; ++k) offs[k + 1] = offs[k] + mg.n[k];
+  if (tid == 0) {  // layout from the sizes alone (no memory reads)
+    int tot = 0;
+    for (int k = 0; k < mg.M; ++k) tot += mg.n[k];
+    int off = 0;
+    unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+    size_t o = top_vec_bytes(mg);
+    auto take = [&](size_t bytes) {
+      unsigned char* p = base + o;
+      o += top_piece(bytes);
+      return p;
+    };
+    for (int k = 0; k < mg.M; ++k) {
+      TopLevel& L = lv[k];
+      const int n = mg.n[k], nnz = mg.nnz[k], np = k ? mg.n[k - 1] : 0;
+      L.n = n;
+      L.ar = smem_mode ? sm + off : mg.ar[k];
+      L.ax = smem_mode ? sm + tot + off : mg.ax[k];
+      L.at = smem_mode ? sm + 2 * tot + off : mg.at[k];
+      off += n;
+      if (smem_mode == 2) {
+        L.inv = reinterpret_cast<double*>(take(8 * (size_t)n));
+        L.diag = reinterpret_cast<double*>(take(8 * (size_t)n));
+        L.val = reinterpret_cast<double*>(take(8 * (size_t)nnz));
+        L.row = reinterpret_cast<int*>(take(4 * ((size_t)n + 1)));
+        L.col = reinterpret_cast<int*>(take(4 * (size_t)nnz));
+        L.cptr = k ? reinterpret_cast<int*>(take(4 * ((size_t)n + 1))) : mg.cptr[k];
+        L.cidx = k ? reinterpret_cast<int*>(take(4 * (size_t)np)) : mg.cidx[k];
+        L.parent = k ? reinterpret_cast<int*>(take(4 * (size_t)np)) : mg.parent[k];
+      } else {
+        L.inv = nullptr;
+        L.diag = mg.diag[k];
+        L.val = mg.val[k];
+        L.row = mg.row[k];
+        L.col = mg.col[k];
+        L.cptr = mg.cptr[k];
+        L.cidx = mg.cidx[k];
+        L.parent = mg.parent[k];
+      }
+    }
   }
   __syncthreads();
-  const int tot = offs[mg.M];
-  auto AR = [&](int k) { return use_smem ? sm + offs[k] : mg.ar[k]; };
-  auto AX = [&](int k) { return use_smem ? sm + tot + offs[k] : mg.ax[k]; };
-  auto AT = [&](int k) { return use_smem ? sm + 2 * tot + offs[k] : mg.at[k]; };
-  auto dinv = [&](int k, int a) {
-    const double d = mg.diag[k][a];
+  if (smem_mode == 2) {
+    for (int k = 0; k < mg.M; ++k) {
+      const TopLevel& L = lv[k];
+      const int n = L.n, nnz = mg.nnz[k], np = k ? mg.n[k - 1] : 0;
+      copy_async<8>(const_cast<double*>(L.diag), mg.diag[k], n);
+      copy_async<8>(const_cast<double*>(L.val), mg.val[k], nnz);
+      copy_async<4>(const_cast<int*>(L.row), mg.row[k], n + 1);
+      copy_async<4>(const_cast<int*>(L.col), mg.col[k], nnz);
+      if (k) {
+        copy_async<4>(const_cast<int*>(L.cptr), mg.cptr[k], n + 1);
+        copy_async<4>(const_cast<int*>(L.cidx), mg.cidx[k], np);
+        copy_async<4>(const_cast<int*>(L.parent), mg.parent[k], np);
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    for (int k = 0; k < mg.M; ++k) {
+      const TopLevel& L = lv[k];
+      for (int a = tid; a < L.n; a += NT) {
+        const double d = L.diag[a];
+        L.inv[a] = d > 0.0 ? 1.0 / d : 0.0;
+      }
+    }
+  }
+  auto dinv = [&](const TopLevel& L, int a) {
+    if (L.inv) return L.inv[a];
+    const double d = L.diag[a];
     return d > 0.0 ? 1.0 / d : 0.0;
   };
   // at = ar - K ax on level k
-  auto residual = [&](int k) {
-    const double* ar = AR(k);
-    const double* ax = AX(k);
-    double* at = AT(k);
-    for (int a = tid; a < mg.n[k]; a += NT) {
-      double kx = mg.diag[k][a] * ax[a];
-      for (int e = mg.row[k][a]; e < mg.row[k][a + 1]; ++e) kx -= mg.val[k][e] * ax[mg.col[k][e]];
-      at[a] = ar[a] - kx;
+  auto residual = [&](const TopLevel& L) {
+    for (int a = tid; a < L.n; a += NT) {
+      double kx = L.diag[a] * L.ax[a];
+      for (int e = L.row[a]; e < L.row[a + 1]; ++e) kx -= L.val[e] * L.ax[L.col[e]];
+      L.at[a] = L.ar[a] - kx;
     }
     __syncthreads();
   };
-  {
-    double* ar = AR(0);
-    for (int a = tid; a < mg.n[0]; a += NT) {
-      double sum = 0.0;
-      for (int e = mg.cptr[0][a]; e < mg.cptr[0][a + 1]; ++e) sum += double(rr[mg.cidx[0][e]]);
-      ar[a] = sum;
-    }
+  for (int a = tid; a < mg.n[0]; a += NT) {  // level 0: sums of the cubes' residuals
+    double sum = 0.0;
+    for (int e = mg.cptr[0][a]; e < mg.cptr[0][a + 1]; ++e) sum += double(rr[mg.cidx[0][e]]);
+    lv[0].ar[a] = sum;
   }
   __syncthreads();
   const int top = mg.M - 1;
   for (int k = 0; k < top; ++k) {
-    double* ax = AX(k);
-    const double* ar = AR(k);
-    for (int a = tid; a < mg.n[k]; a += NT) ax[a] = w * dinv(k, a) * ar[a];
+    const TopLevel& L = lv[k];
+    for (int a = tid; a < L.n; a += NT) L.ax[a] = w * dinv(L, a) * L.ar[a];
     __syncthreads();
-    residual(k);
-    const double* at = AT(k);
-    double* arn = AR(k + 1);
-    for (int a = tid; a < mg.n[k + 1]; a += NT) {
+    residual(L);
+    const TopLevel& C = lv[k + 1];
+    for (int a = tid; a < C.n; a += NT) {
       double sum = 0.0;
-      for (int e = mg.cptr[k + 1][a]; e < mg.cptr[k + 1][a + 1]; ++e) sum += at[mg.cidx[k + 1][e]];
-      arn[a] = sum;
+      for (int e = C.cptr[a]; e < C.cptr[a + 1]; ++e) sum += L.at[C.cidx[e]];
+      C.ar[a] = sum;
     }
     __syncthreads();
   }
   {
-    double* ax = AX(top);
-    for (int a = tid; a < mg.n[top]; a += NT) ax[a] = 0.0;
+    const TopLevel& L = lv[top];
+    for (int a = tid; a < L.n; a += NT) L.ax[a] = 0.0;
     __syncthreads();
     for (int sweep = 0; sweep < kMgNuTop; ++sweep) {
-      residual(top);
-      const double* at = AT(top);
-      for (int a = tid; a < mg.n[top]; a += NT) ax[a] += w * dinv(top, a) * at[a];
+      residual(L);
+      for (int a = tid; a < L.n; a += NT) L.ax[a] += w * dinv(L, a) * L.at[a];
       __syncthreads();
     }
   }
   for (int k = top - 1; k >= 0; --k) {
-    double* ax = AX(k);
-    const double* axc = AX(k + 1);
-    for (int a = tid; a < mg.n[k]; a += NT) ax[a] += kMgOver * axc[mg.parent[k + 1][a]];
+    const TopLevel& L = lv[k];
+    const TopLevel& C = lv[k + 1];
+    for (int a = tid; a < L.n; a += NT) L.ax[a] += kMgOver * C.ax[C.parent[a]];
     __syncthreads();
-    residual(k);
-    const double* at = AT(k);
-    for (int a = tid; a < mg.n[k]; a += NT) ax[a] += w * dinv(k, a) * at[a];
+    residual(L);
+    for (int a = tid; a < L.n; a += NT) L.ax[a] += w * dinv(L, a) * L.at[a];
     __syncthreads();
   }
-  if (use_smem) {  // the level-0 result for the up launches
-    const double* ax = AX(0);
-    for (int a = tid; a < mg.n[0]; a += NT) mg.ax[0][a] = ax[a];
+  if (smem_mode) {  // the level-0 result for the up launches
+    for (int a = tid; a < mg.n[0]; a += NT) mg.ax[0][a] = lv[0].ax[a];
   }
 }
 
 template <class TV>
 __global__ __launch_bounds__(1024) void k_mg_top(MgDev mg, const TV* __restrict__ rr,
-                                                 int use_smem) {
+                                                 int smem_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  mg_top<TV>(mg, rr, use_smem, reinterpret_cast<double*>(smem_raw));
+  mg_top<TV>(mg, rr, smem_mode, reinterpret_cast<double*>(smem_raw));
 }
 
 // ---------------------------------------------------------------- launcher
@@ -518,13 +713,19 @@ __global__ __launch_bounds__(1024) void k_mg_top(MgDev mg, const TV* __restrict_
 template <int BL, class TV>
 static cudaError_t down_t(const Ctx& x, int l, int all) {
   constexpr int CB = BL > 1 ? BL / 2 : 1;
-  const long long n = (long long)x.g.n_cubes * CB * CB * CB;
   const TV* r = (const TV*)x.mg.r[l];
   TV* xv = (TV*)x.mg.x[l];
   TV* rc = BL > 1 ? (TV*)x.mg.r[l + 1] : (TV*)x.mg.rr;
   const double c4 = double(1 << (2 * l));
-  k_mg_down<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
-      x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+  if constexpr (BL > 1) {  // one thread per fine cell
+    const long long n = (long long)x.g.n_cubes * BL * BL * BL;
+    k_mg_down_cell<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
+        x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+  } else {
+    const long long n = (long long)x.g.n_cubes * CB * CB * CB;
+    k_mg_down<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
+        x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+  }
   return cudaGetLastError();
 }
 
@@ -566,26 +767,41 @@ static cudaError_t up0_t(const Ctx& x, const SolveParams& prm, int mode) {
 }
 
 template <int B, class TV>
-static cudaError_t down0_tile_t(const Ctx& x, int all) {
+static cudaError_t down0_tile_t(const Ctx& x, int l, int all, bool fb) {
   using SL = Slab<B, B>;
   const size_t sm = sizeof(TV) * ((SL::N + 3) / 4 * 4 + (size_t)B * B * B);
-  auto kern = k_mg_down0_tile<B, TV>;
+  PassB<TV> pb{};
+  if (fb) {
+    pb.x = x.f64 ? (TV*)x.f.p : (TV*)x.f.e;
+    pb.p0 = (const TV*)x.f.p0;
+    pb.p1 = (const TV*)x.f.p1;
+    pb.q = (const TV*)x.f.q;
+    pb.ra = (TV*)x.f.r;
+    pb.rb = (TV*)x.f.s0;
+  }
+  const double c4 = double(1 << (2 * l));
+  auto kern = fb ? k_mg_down0_tile<B, TV, true> : k_mg_down0_tile<B, TV, false>;
   cudaError_t e = allow_dynamic_smem(kern, sm);
   if (e != cudaSuccess) return e;
-  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[0], (TV*)x.mg.x[0],
-                                            (TV*)x.mg.r[1], all);
+  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[l], (TV*)x.mg.x[l],
+                                            (TV*)x.mg.r[l + 1], all, pb, TV(kMgOmega / c4),
+                                            TV(c4));
   return cudaGetLastError();
 }
 
 template <int B, class TV>
-static cudaError_t up0_tile_t(const Ctx& x, const SolveParams& prm, int mode) {
+static cudaError_t up0_tile_t(const Ctx& x, int l, const SolveParams& prm, int mode, bool fb) {
   using SL = Slab<B, B>;
   const size_t sm = sizeof(TV) * SL::N;
+  const double c4 = double(1 << (2 * l));
   auto kern = k_mg_up0_tile<B, TV>;
   cudaError_t e = allow_dynamic_smem(kern, sm);
   if (e != cudaSuccess) return e;
-  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[0], (const TV*)x.mg.x[0],
-                                            (const TV*)x.mg.y[1], (TV*)x.mg.y[0], prm, mode);
+  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[l],
+                                            fb ? (const TV*)x.f.s0 : nullptr,
+                                            (const TV*)x.mg.x[l], (const TV*)x.mg.y[l + 1],
+                                            (TV*)x.mg.y[l], prm, mode, TV(kMgOmega / c4),
+                                            TV(c4), l == 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -593,26 +809,39 @@ template <class TV>
 static cudaError_t vcycle_t(const Ctx& x, const SolveParams& prm, int mode) {
   const int all = mode == 2 ? 1 : 0;
   cudaError_t e;
-  // the finest level of 8^3 and 16^3 cubes through the shared-memory tile
+  // the finest level of 8^3 and 16^3 cubes through the shared-memory tile, which after
+  // pass A also does the PCG's pass B; other cube sizes launch pass B first
   const bool tile = x.B == 8 || x.B == 16;
-  e = tile ? (x.B == 16 ? down0_tile_t<16, TV>(x, all) : down0_tile_t<8, TV>(x, all))
+  const bool fb = tile && mode == 1;
+  if (mode == 1 && !fb && (e = launch_cg_b(x, prm)) != cudaSuccess) return e;
+  e = tile ? (x.B == 16 ? down0_tile_t<16, TV>(x, 0, all, fb) : down0_tile_t<8, TV>(x, 0, all, fb))
            : level_t<TV>(x, 0, true, all);
   if (e != cudaSuccess) return e;
+  // levels of 8^3 cells per cube through the tile too, the smaller ones per cell
   for (int l = 1; l <= x.mg.L; ++l)
-    if ((e = level_t<TV>(x, l, true, all)) != cudaSuccess) return e;
+    if ((e = (x.B >> l) == 8 ? down0_tile_t<8, TV>(x, l, all, false)
+                             : level_t<TV>(x, l, true, all)) != cudaSuccess)
+      return e;
   {
-    size_t nodes = 0;
-    for (int k = 0; k < x.mg.M; ++k) nodes += (size_t)x.mg.n[k];
-    const size_t sm = 3 * nodes * sizeof(double);
-    const int use_smem = sm <= 160 * 1024 ? 1 : 0;
+    // node vectors and, where they fit, the level tables in shared memory
+    const size_t vec = top_vec_bytes(x.mg), tables = top_table_bytes(x.mg);
+    const int smem_mode = vec + tables <= 200 * 1024 ? 2 : vec <= 160 * 1024 ? 1 : 0;
+    const size_t sm = smem_mode == 2 ? vec + tables : smem_mode == 1 ? vec : 0;
+    int maxn = 0;
+    for (int k = 0; k < x.mg.M; ++k) maxn = x.mg.n[k] > maxn ? x.mg.n[k] : maxn;
+    const int nt = maxn < 64 ? 64 : maxn > 1024 ? 1024 : (maxn + 31) / 32 * 32;
     auto kern = k_mg_top<TV>;
-    if (use_smem && (e = allow_dynamic_smem(kern, sm)) != cudaSuccess) return e;
-    kern<<<1, 1024, use_smem ? sm : 0, x.stream>>>(x.mg, (const TV*)x.mg.rr, use_smem);
+    if (smem_mode && (e = allow_dynamic_smem(kern, sm)) != cudaSuccess) return e;
+    kern<<<1, nt, sm, x.stream>>>(x.mg, (const TV*)x.mg.rr, smem_mode);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   for (int l = x.mg.L; l >= 1; --l)
-    if ((e = level_t<TV>(x, l, false, all)) != cudaSuccess) return e;
-  if (tile) return x.B == 16 ? up0_tile_t<16, TV>(x, prm, mode) : up0_tile_t<8, TV>(x, prm, mode);
+    if ((e = (x.B >> l) == 8 ? up0_tile_t<8, TV>(x, l, prm, mode, false)
+                             : level_t<TV>(x, l, false, all)) != cudaSuccess)
+      return e;
+  if (tile)
+    return x.B == 16 ? up0_tile_t<16, TV>(x, 0, prm, mode, fb)
+                     : up0_tile_t<8, TV>(x, 0, prm, mode, fb);
   switch (x.B) {
     case 4: return up0_t<4, TV>(x, prm, mode);
     case 8: return up0_t<8, TV>(x, prm, mode);
