@@ -457,7 +457,8 @@ def gpu_arm(args, ws, rank, local):
                      "rel_resid_last_step": st64["rel_resid"], "kernels": k64},
             "speedup_mixed_vs_fp64": value / fp64_value,
             "mg": dict(mg, note="multigrid-preconditioned PCG (a NEXT row beyond the "
-                                "Jacobi-PCG hot path), eager steps, same workload and "
+                                "Jacobi-PCG hot path): steps issued from the host, each PCG "
+                                "iteration one replayed CUDA graph; same workload and "
                                 "residual"),
             "mixed_paths_ms_per_step": {"eager": ms_eager / args.steps,
                                         "graph": ms_graph / args.steps,

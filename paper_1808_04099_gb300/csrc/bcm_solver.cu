@@ -126,7 +126,12 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
         } else {
           t.rz = rz;
           t.rr = rr;
-          t.inner_tol2 = prm.inner_rtol * prm.inner_rtol * rr;
+          // inner target: the reduction eta = inner_rtol per cycle, or, once the
+          // reduction rho still needed (||r|| rho = the outer tolerance) is within 4 eta,
+          // rho / 2, so the cycle ends the solve instead of overshooting it or stopping
+          // just short of it
+          const double in2 = prm.inner_rtol * prm.inner_rtol, need2 = 0.25 * t.tol2 / rr64;
+          t.inner_tol2 = (16.0 * need2 >= in2 ? need2 : in2) * rr;
           t.iter = 0;
           t.beta = 0.0;
           t.done = (rr == 0.0);
