@@ -70,6 +70,14 @@ def lib():
         L.orc_solve_pressure.restype = C.c_int
         L.orc_step.argtypes = [P] * 10 + [C.c_int, C.c_double, C.c_int, P]
         L.orc_step.restype = C.c_int
+        L.orc_delta3.argtypes = [C.c_double]
+        L.orc_delta3.restype = C.c_double
+        L.orc_ib_interpolate.argtypes = [P, P, C.c_int, P, P, P]
+        L.orc_ib_spread.argtypes = [P, C.c_int, P, P, P, P, P]
+        L.orc_ib_body_velocity.argtypes = [P, C.c_int, P, P, P, P, P]
+        L.orc_step_particles.argtypes = [P] * 10 + [C.c_int, C.c_double, C.c_int, P, C.c_int] + \
+            [P] * 5
+        L.orc_step_particles.restype = C.c_int
         _lib = L
     return _lib
 
@@ -192,6 +200,55 @@ class Oracle:
                             _p(st["nx"]), _p(st["ny"]), _p(st["nz"]), _p(ub), _p(st["step"]),
                             nsteps, rtol, max_iter, stats)
         return [s.as_dict() for s in stats], rc
+
+    # ------------------------------------------------ Lagrangian particles (R19)
+    @staticmethod
+    def delta3(r: float) -> float:
+        return lib().orc_delta3(float(r))
+
+    def ib_interpolate(self, f, parts) -> np.ndarray:
+        """I[f] at every particle of a workloads.Particles set (Eq. ddeltai)."""
+        f = _f64(f)
+        X, sim = _f64(parts.X), np.ascontiguousarray(parts.sim, np.int32)
+        out = np.zeros(parts.n)
+        lib().orc_ib_interpolate(self._h, _p(f), parts.n, _p(X), _p(sim), _p(out))
+        return out
+
+    def ib_spread(self, F, parts, out=None) -> np.ndarray:
+        """out += P[F] (Eq. ddeltap), F one value per particle."""
+        out = np.zeros(self.n_cells) if out is None else out
+        F = _f64(F)
+        X, sim, dV = _f64(parts.X), np.ascontiguousarray(parts.sim, np.int32), _f64(parts.dV)
+        lib().orc_ib_spread(self._h, parts.n, _p(X), _p(sim), _p(F), _p(dV), _p(out))
+        return out
+
+    def ib_body_velocity(self, X, parts, t) -> np.ndarray:
+        X = _f64(X)
+        sim = np.ascontiguousarray(parts.sim, np.int32)
+        body = np.ascontiguousarray(parts.body, np.int32)
+        t = _f64(np.broadcast_to(np.asarray(t, np.float64), (self.spec.n_sims,)))
+        vel = np.zeros((parts.n, 3))
+        lib().orc_ib_body_velocity(self._h, parts.n, _p(X), _p(sim), _p(body), _p(t), _p(vel))
+        return vel
+
+    def step_particles(self, st, X, parts, nsteps=1, rtol=1e-12, max_iter=100000):
+        """Steps with the particle forcing; X ([n, 3] float64) is advanced in place.
+        Returns (stats, rc, F) with F the last step's force per particle [n, 3]."""
+        stats = (Stats * self.spec.n_sims)()
+        ub = st["ub"]
+        if ub.size == 0:
+            ub = np.zeros(1)
+            st["ub"] = ub
+        assert X.dtype == np.float64 and X.flags.c_contiguous and X.shape == (parts.n, 3)
+        sim = np.ascontiguousarray(parts.sim, np.int32)
+        body = np.ascontiguousarray(parts.body, np.int32)
+        dV = _f64(parts.dV)
+        F = np.zeros((parts.n, 3))
+        rc = lib().orc_step_particles(self._h, _p(st["u"]), _p(st["v"]), _p(st["w"]),
+                                      _p(st["p"]), _p(st["nx"]), _p(st["ny"]), _p(st["nz"]),
+                                      _p(ub), _p(st["step"]), nsteps, rtol, max_iter, stats,
+                                      parts.n, _p(X), _p(sim), _p(body), _p(dV), _p(F))
+        return [s.as_dict() for s in stats], rc, F
 
     @staticmethod
     def threads() -> int:

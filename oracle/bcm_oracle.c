@@ -45,6 +45,15 @@
  *   R10 all-Neumann sims: the volume mean of b is removed before the solve.
  *   R11 Jacobi-preconditioned CG (Saad, Alg. 9.1) on K p = -V b, warm start p^n,
  *      stop when the recurrence residual ||r|| <= rtol ||-V b||.
+ *   R19 Lagrangian particles (orc_step_particles; section "Lagrangian-Eulerian
+ *      Interaction", Eqs. ddeltai and ddeltap, the forcing sub-step and the position
+ *      update of "Numerical algorithm"), on single-level grids: the 27 cells whose
+ *      centres lie within 1.5 h of a particle per axis carry the weights
+ *      phi(r_x) phi(r_y) phi(r_z) of the smoothed 3-point delta; cells outside the
+ *      domain are left out of both sums (no wrap at periodic faces).  U_s^n is the
+ *      velocity of the particle's body at (X^n, t^n); the position update takes the
+ *      body velocity at (X^n, t^{n+1}).  rho = 1; the force on the body is
+ *      -sum_p F_p dV_p.  The solid fraction is zero in this mode.
  */
 #include "bcm_oracle.h"
 
@@ -500,6 +509,95 @@ void orc_solid_fraction(const orc_grid *g, const double *t, double *phi, double 
                 }
 }
 
+/* ------------------------------------------------ Lagrangian particles (R19) */
+
+/* One-dimensional smoothed 3-point delta phi(r) (section "Lagrangian-Eulerian
+ * Interaction", the function printed after Eq. ddeltap). */
+double orc_delta3(double r) {
+    double a = fabs(r);
+    if (a <= 0.5) return 0.75 - r * r;
+    if (a <= 1.5) return 0.5 * (2.25 - 3.0 * a + r * r);
+    return 0.0;
+}
+
+/* Index of level-0 cell (I, J, K) of sim s (cells counted from the sim origin), or -1
+ * outside the domain or where no cube covers it. */
+static long particle_cell(const orc_grid *g, int s, int I, int J, int K) {
+    const int *ext = &g->extent[3 * s];
+    int B = g->B;
+    if (I < 0 || J < 0 || K < 0 || I >= ext[0] || J >= ext[1] || K >= ext[2]) return -1;
+    int c = find_cube(g, s, 0, I - I % B, J - J % B, K - K % B);
+    if (c < 0) return -1;
+    return (long)cidx(B, c, I % B, J % B, K % B);
+}
+
+/* The 27 cells around particle X of sim s and their delta weights (product of the
+ * three 1-D weights, which already carry the h^3 of Eq. ddeltai).  Returns the count;
+ * cells outside the domain are dropped. */
+static int particle_stencil(const orc_grid *g, int s, const double *X, long *cell, double *wt) {
+    double h = g->h0[s];
+    int n = 0;
+    int ic[3];
+    double xi[3];
+    for (int e = 0; e < 3; ++e) {
+        xi[e] = (X[e] - g->origin[3 * s + e]) / h;
+        ic[e] = (int)floor(xi[e]);
+    }
+    for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                int I = ic[0] + di, J = ic[1] + dj, K = ic[2] + dk;
+                double w = orc_delta3(I + 0.5 - xi[0]) * orc_delta3(J + 0.5 - xi[1]) *
+                           orc_delta3(K + 0.5 - xi[2]);
+                long id = particle_cell(g, s, I, J, K);
+                if (id < 0) continue;
+                cell[n] = id;
+                wt[n] = w;
+                ++n;
+            }
+    return n;
+}
+
+void orc_ib_interpolate(const orc_grid *g, const double *f, int n, const double *X,
+                        const int32_t *psim, double *out) {
+    for (int q = 0; q < n; ++q) {
+        long cell[27];
+        double wt[27], U = 0.0;
+        int m = particle_stencil(g, psim[q], X + 3 * q, cell, wt);
+        for (int a = 0; a < m; ++a) U += f[cell[a]] * wt[a];
+        out[q] = U;
+    }
+}
+
+void orc_ib_spread(const orc_grid *g, int n, const double *X, const int32_t *psim,
+                   const double *F, const double *dV, double *out) {
+    for (int q = 0; q < n; ++q) {
+        long cell[27];
+        double wt[27];
+        int s = psim[q];
+        double h = g->h0[s];
+        int m = particle_stencil(g, s, X + 3 * q, cell, wt);
+        for (int a = 0; a < m; ++a) out[cell[a]] += F[q] * wt[a] * (dV[q] / (h * h * h));
+    }
+}
+
+/* Body velocity of particle q at time t (the rigid motion of its body). */
+static void particle_body_velocity(const orc_grid *g, int s, int b, const double *X, double t,
+                                   double *vel) {
+    const double *body = g->bodies + ((size_t)s * ORC_MAX_BODIES + b) * ORC_BODY_STRIDE;
+    if ((int)body[0] == BODY_NONE) {
+        vel[0] = vel[1] = vel[2] = 0.0;
+        return;
+    }
+    (void)body_sd(body, t, X, vel);
+}
+
+void orc_ib_body_velocity(const orc_grid *g, int n, const double *X, const int32_t *psim,
+                          const int32_t *pbody, const double *t, double *vel) {
+    for (int q = 0; q < n; ++q)
+        particle_body_velocity(g, psim[q], pbody[q], X + 3 * q, t[psim[q]], vel + 3 * q);
+}
+
 /* ------------------------------------------------------ momentum operators */
 
 /* Conservative central convection N_comp and Laplacian of component comp at (i,j,k),
@@ -841,9 +939,18 @@ static double face_gradient(const orc_grid *g, const double *p, int c, int fc, i
     return (fc % 2) ? G : -G; /* gradient along +axis */
 }
 
-int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, double *nx,
-             double *ny, double *nz, double *ub, int32_t *step, int nsteps, double rtol,
-             int max_iter, orc_stats *stats) {
+/* Lagrangian particles of a step (R19); NULL in orc_step (solid fraction). */
+typedef struct {
+    int n;
+    double *X;
+    const int32_t *sim, *body;
+    const double *dV;
+    double *F; /* [n*3] force per particle of the last step, may be NULL */
+} particle_args;
+
+static int step_impl(const orc_grid *g, double *u, double *v, double *w, double *p, double *nx,
+                     double *ny, double *nz, double *ub, int32_t *step, int nsteps, double rtol,
+                     int max_iter, orc_stats *stats, const particle_args *P) {
     int B = g->B, B3 = B * B * B, status = 0;
     size_t n = (size_t)g->n_cubes * B3, G3 = (size_t)g->G * g->G * g->G;
     size_t nub = (size_t)g->n_slots * 3 * B * B;
@@ -860,11 +967,20 @@ int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, doub
     double *tt = (double *)malloc(sizeof(double) * (g->n_sims + 1));
     orc_stats *st = (orc_stats *)calloc(g->n_sims + 1, sizeof(orc_stats));
     double *vel[3] = {u, v, w}, *vstar[3] = {us, vs, ws}, *Nl[3] = {nx, ny, nz};
+    int np = P ? P->n : 0;
+    double *pU = (double *)malloc(sizeof(double) * (3 * (size_t)np + 1));
+    double *pF = (double *)malloc(sizeof(double) * (3 * (size_t)np + 1));
+    double *pS = (double *)malloc(sizeof(double) * ((size_t)np + 1));
+    double *pdrag = (double *)calloc(3 * (size_t)g->n_sims + 1, sizeof(double));
 
     for (int it = 0; it < nsteps; ++it) {
-        /* (a) body geometry and velocity at t^n */
+        /* (a) body geometry and velocity at t^n (particles: no solid fraction) */
         for (int s = 0; s < g->n_sims; ++s) tt[s] = step[s] * g->dt[s];
-        orc_solid_fraction(g, tt, phi, bu, bv, bw);
+        if (P) {
+            for (size_t q = 0; q < n; ++q) phi[q] = bu[q] = bv[q] = bw[q] = 0.0;
+        } else {
+            orc_solid_fraction(g, tt, phi, bu, bv, bw);
+        }
         /* (b) halo of u^n (outflow ghosts from u_b^n) */
         orc_fill_ghosts(g, u, 0, ub, gu);
         orc_fill_ghosts(g, v, 1, ub, gv);
@@ -896,6 +1012,28 @@ int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, doub
                         }
                     }
             drag[3 * c] = -fx; drag[3 * c + 1] = -fy; drag[3 * c + 2] = -fz;
+        }
+        /* (c') particles (R19): U = I[u~] at every particle, F = (U_s - U) / dt, then
+         * u* = u~ + dt P[F]; the force on the body is -sum F dV */
+        if (P) {
+            for (int s = 0; s < 3 * g->n_sims; ++s) pdrag[s] = 0.0;
+            for (int comp = 0; comp < 3; ++comp)
+                orc_ib_interpolate(g, vstar[comp], np, P->X, P->sim, pU + (size_t)comp * np);
+            for (int q = 0; q < np; ++q) {
+                int s = P->sim[q];
+                double Us[3];
+                particle_body_velocity(g, s, P->body[q], P->X + 3 * q, tt[s], Us);
+                for (int comp = 0; comp < 3; ++comp) {
+                    double F = (Us[comp] - pU[(size_t)comp * np + q]) / g->dt[s];
+                    pF[(size_t)comp * np + q] = F;
+                    pdrag[3 * s + comp] -= F * P->dV[q];
+                    if (P->F) P->F[3 * q + comp] = F;
+                }
+            }
+            for (int comp = 0; comp < 3; ++comp) {
+                for (int q = 0; q < np; ++q) pS[q] = g->dt[P->sim[q]] * pF[(size_t)comp * np + q];
+                orc_ib_spread(g, np, P->X, P->sim, pS, P->dV, vstar[comp]);
+            }
         }
         /* (d) outflow face values u_b^{n+1} (R8) */
         for (int c = 0; c < g->n_cubes; ++c)
@@ -971,6 +1109,8 @@ int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, doub
                             if (m2 > um) um = m2;
                         }
             }
+            if (P)
+                for (int e = 0; e < 3; ++e) F[e] += pdrag[3 * s + e];
             if (stats) {
                 stats[s].cg_iters = st[s].cg_iters;
                 stats[s].rel_resid = st[s].rel_resid;
@@ -982,8 +1122,35 @@ int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, doub
             step[s] += 1;
         }
         memcpy(ub, ubn, sizeof(double) * nub);
+        /* (i) particles move with their body: X^{n+1} = X^n + dt U_s(X^n, t^{n+1}) */
+        for (int q = 0; q < np; ++q) {
+            int s = P->sim[q];
+            double Us[3];
+            particle_body_velocity(g, s, P->body[q], P->X + 3 * q, step[s] * g->dt[s], Us);
+            for (int e = 0; e < 3; ++e) P->X[3 * q + e] += g->dt[s] * Us[e];
+        }
     }
     free(us); free(vs); free(ws); free(b); free(phi); free(bu); free(bv); free(bw);
     free(gu); free(gv); free(gw); free(ubn); free(drag); free(tt); free(st);
+    free(pU); free(pF); free(pS); free(pdrag);
     return status;
+}
+
+int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, double *nx,
+             double *ny, double *nz, double *ub, int32_t *step, int nsteps, double rtol,
+             int max_iter, orc_stats *stats) {
+    return step_impl(g, u, v, w, p, nx, ny, nz, ub, step, nsteps, rtol, max_iter, stats, NULL);
+}
+
+int orc_step_particles(const orc_grid *g, double *u, double *v, double *w, double *p,
+                       double *nx, double *ny, double *nz, double *ub, int32_t *step,
+                       int nsteps, double rtol, int max_iter, orc_stats *stats, int n_particles,
+                       double *X, const int32_t *psim, const int32_t *pbody, const double *dV,
+                       double *F) {
+    if (g->max_level != 0) {
+        snprintf(g_err, sizeof g_err, "Lagrangian particles need a single-level grid");
+        return -1;
+    }
+    particle_args P = {n_particles, X, psim, pbody, dV, F};
+    return step_impl(g, u, v, w, p, nx, ny, nz, ub, step, nsteps, rtol, max_iter, stats, &P);
 }

@@ -101,6 +101,28 @@ int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, doub
              double *ny, double *nz, double *ub, int32_t *step, int nsteps, double rtol,
              int max_iter, orc_stats *stats);
 
+/* Lagrangian particles (R19 in the .c file header), single-level grids.
+ * Particle q: position X[3q..3q+2], sim psim[q], body pbody[q] (0 .. ORC_MAX_BODIES-1 of
+ * its sim), weight dV[q] (the particle's volume dc1 dc2 dc3 of Eq. ddeltap). */
+double orc_delta3(double r);
+/* out[q] = sum over cells of f * delta weight (Eq. ddeltai) */
+void orc_ib_interpolate(const orc_grid *g, const double *f, int n, const double *X,
+                        const int32_t *psim, double *out);
+/* out[cell] += sum over particles of F[q] * delta weight * dV[q] / h^3 (Eq. ddeltap) */
+void orc_ib_spread(const orc_grid *g, int n, const double *X, const int32_t *psim,
+                   const double *F, const double *dV, double *out);
+/* vel[3q..] = velocity of particle q's body at X and time t[psim[q]] */
+void orc_ib_body_velocity(const orc_grid *g, int n, const double *X, const int32_t *psim,
+                          const int32_t *pbody, const double *t, double *vel);
+/* orc_step with the particle forcing in place of the solid fraction; X is advanced in
+ * place; F[3q..] (may be NULL) receives the last step's force per particle.  Returns
+ * -1 on a two-level grid. */
+int orc_step_particles(const orc_grid *g, double *u, double *v, double *w, double *p,
+                       double *nx, double *ny, double *nz, double *ub, int32_t *step,
+                       int nsteps, double rtol, int max_iter, orc_stats *stats, int n_particles,
+                       double *X, const int32_t *psim, const int32_t *pbody, const double *dV,
+                       double *F);
+
 #ifdef __cplusplus
 }
 #endif

@@ -374,6 +374,59 @@ def initial_state(spec: GridSpec, seed: int = 0, noise: float = 0.0,
     return State(u, v, w, np.zeros(n), ub)
 
 
+@dataclasses.dataclass
+class Particles:
+    """Lagrangian particles on body surfaces (section "Lagrangian Data Structure"):
+    position X at t = 0, the sim and the body (index into that sim's bodies) each one
+    belongs to, and its volume weight dV (dc1 dc2 dc3 of Eq. ddeltap)."""
+    X: np.ndarray        # f64 [n, 3]
+    sim: np.ndarray      # int32 [n]
+    body: np.ndarray     # int32 [n]
+    dV: np.ndarray       # f64 [n]
+
+    @property
+    def n(self) -> int:
+        return int(self.X.shape[0])
+
+
+def surface_particles(spec: GridSpec, sim: int = 0, body: int = 0, spacing: float = 1.0,
+                      seed: Optional[int] = None) -> Particles:
+    """Particles on the surface of one body at t = 0, about one per surface cell: a
+    Fibonacci lattice of N = round(area / (spacing h)^2) points on the unit sphere,
+    scaled by the semi-axes and turned by the body's quaternion; weight dV = h^3.
+    With a seed the lattice is turned by a seeded random rotation."""
+    bd = spec.bodies[sim][body]
+    h = float(spec.sim_h0[sim]) / (1 << spec.max_level)
+    a, b, c = (float(x) for x in (bd.axes if bd.kind == BODY_ELLIPSOID else
+                                  [bd.axes[0]] * 3))
+    # Knud Thomsen's approximation of the ellipsoid area (the count only)
+    pw = 1.6075
+    area = 4 * math.pi * (((a * b) ** pw + (a * c) ** pw + (b * c) ** pw) / 3) ** (1 / pw)
+    n = max(1, int(round(area / (spacing * h) ** 2)))
+    k = np.arange(n) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    th = math.pi * (1.0 + math.sqrt(5.0)) * k
+    u = np.stack([r * np.cos(th), r * np.sin(th), z], axis=1)
+    if seed is not None:
+        q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+        u = u @ q.T
+    w, x, y, zq = (float(e) for e in bd.quat)
+    R = np.array([[1 - 2 * (y * y + zq * zq), 2 * (x * y - w * zq), 2 * (x * zq + w * y)],
+                  [2 * (x * y + w * zq), 1 - 2 * (x * x + zq * zq), 2 * (y * zq - w * x)],
+                  [2 * (x * zq - w * y), 2 * (y * zq + w * x), 1 - 2 * (x * x + y * y)]])
+    X = (u * np.array([a, b, c])) @ R.T + np.asarray(bd.center, np.float64)
+    return Particles(np.ascontiguousarray(X), np.full(n, sim, np.int32),
+                     np.full(n, body, np.int32), np.full(n, h ** 3))
+
+
+def concat_particles(parts: List[Particles]) -> Particles:
+    return Particles(np.ascontiguousarray(np.concatenate([p.X for p in parts])),
+                     np.concatenate([p.sim for p in parts]).astype(np.int32),
+                     np.concatenate([p.body for p in parts]).astype(np.int32),
+                     np.concatenate([p.dV for p in parts]))
+
+
 def config_cavity64(steps: int = 10) -> GridSpec:
     """Lid-driven cavity, 4x4x4 cubes of 16^3, Re 100, FP64, rtol 1e-10."""
     return cavity(4, 16, 100.0, steps, 1e-10, "cavity_64^3_Re100")
