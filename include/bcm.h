@@ -279,6 +279,54 @@ bcm_status bcm_adjoint_step(bcm_grid *grid, void *dev_adj, size_t bytes, const v
                             int first_step, double drag_weight, double rtol, int max_iter,
                             double *dev_dJ);
 
+/* ---- Lagrangian-particle immersed boundary (section "Lagrangian Data Structure";
+ * section "Lagrangian-Eulerian Interaction", Eqs. ddeltai and ddeltap with the smoothed
+ * 3-point delta phi(r) = 3/4 - r^2 for |r| <= 1/2, (9/4 - 3|r| + r^2)/2 for
+ * 1/2 < |r| <= 3/2, 0 beyond; the forcing sub-step and the position update of section
+ * "Numerical algorithm"), single-level grids only.
+ *
+ * Particle q sits at xyz[3q..3q+2] (physical coordinates of its sim), belongs to sim
+ * sim[q] and is moved by body body[q] of that sim (0 .. 3, as set by
+ * bcm_set_geometry; a body slot without a body gives U_s = 0); dV[q] > 0 is its volume
+ * weight (dc1 dc2 dc3 of Eq. ddeltap; one particle per surface cell: h^3).  With
+ * particles set, every step replaces the solid-fraction forcing (the solid fraction is
+ * zero) by
+ *   U_q = sum over the 27 nearest cells of u~ phi(r_x) phi(r_y) phi(r_z)   (r = (x - X)/h)
+ *   F_q = (U_s(X_q, t^n) - U_q) / dt                  (rho = 1)
+ *   u*  = u~ + dt sum_q F_q phi phi phi dV_q / h^3
+ * (cells outside the domain are left out of both sums), reports the force on the
+ * bodies -sum_q F_q dV_q as the sim's drag, and after the step moves every particle by
+ * X += dt U_s(X, t^{n+1}) with its body's rigid motion; particles are grouped into
+ * per-cube sets that are rebuilt after every move.
+ *
+ * bcm_particles_bytes: device workspace bytes for n particles on this grid (0 on a
+ *   two-level grid).
+ * bcm_set_particles: copies the host arrays into the caller's device workspace
+ *   (256-byte aligned, at least bcm_particles_bytes; it must outlive the
+ *   particles: until bcm_set_particles(grid, 0, ...) or bcm_destroy_grid) and builds
+ *   the sets.  n = 0 returns to the solid-fraction IB (other arguments ignored).
+ *   Errors: BCM_E_INVALID (two-level grid, NULL array, sim or body out of range,
+ *   dV <= 0, non-finite position, small or misaligned workspace), BCM_E_BOUNDS (a
+ *   particle outside every cube; the grid returns to the solid-fraction IB).  Synchronises.
+ * bcm_get_particles: host copies (each may be NULL) of the positions [n*3], the last
+ *   step's force per particle [n*3] and the cube each particle lies in [n] (-1 outside).
+ * bcm_particle_sets: host copies of the per-cube sets: the particles of cube c are
+ *   ids[start[c] .. start[c+1]) (start: [n_cubes+1], ids: [n]; order within a set
+ *   arbitrary).
+ * bcm_ib_interpolate / bcm_ib_spread (test paths, FP64 device arrays, asynchronous):
+ *   out[q] = sum_cells f phi phi phi;  out[cell] += sum_q F[q] phi phi phi dV_q / h^3.
+ * A particle that leaves every cube carries no force from then on; bcm_step and
+ * bcm_step_graph called with a stats pointer return BCM_E_BOUNDS once that happened.
+ * The adjoint rejects grids with particles. */
+size_t bcm_particles_bytes(const bcm_grid *grid, int32_t n_particles);
+bcm_status bcm_set_particles(bcm_grid *grid, int32_t n_particles, const double *xyz,
+                             const int32_t *sim, const int32_t *body, const double *dV,
+                             void *dev_workspace, size_t bytes);
+bcm_status bcm_get_particles(bcm_grid *grid, double *xyz, double *force, int32_t *cube);
+bcm_status bcm_particle_sets(bcm_grid *grid, int32_t *start, int32_t *ids);
+bcm_status bcm_ib_interpolate(bcm_grid *grid, const double *dev_f, double *dev_out);
+bcm_status bcm_ib_spread(bcm_grid *grid, const double *dev_F, double *dev_out);
+
 /* Kernel classes for bcm_profile_read. */
 enum {
     BCM_K_SOLID_FRACTION = 0, /* solid fraction and body index per cell */
@@ -292,7 +340,8 @@ enum {
     BCM_K_MISC = 8,           /* bookkeeping and test-path kernels */
     BCM_K_PCG = 9,            /* persistent PCG: all iterations of one solve */
     BCM_K_MG = 10,            /* multigrid V-cycle (BCM_PRECOND_MULTIGRID) */
-    BCM_NKERNELS = 11
+    BCM_K_IB = 11,            /* Lagrangian particles: forcing, position update, sets */
+    BCM_NKERNELS = 12
 };
 
 /* Timing of the library's own kernels: while enabled, every kernel the grid launches

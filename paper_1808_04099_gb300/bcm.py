@@ -28,9 +28,11 @@ EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_f
             "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
+            "bcm_particles_bytes", "bcm_set_particles", "bcm_get_particles",
+            "bcm_particle_sets", "bcm_ib_interpolate", "bcm_ib_spread",
             "bcm_last_error"]
 KERNEL_NAMES = ["solid_fraction", "momentum", "rhs", "residual", "cg_a", "cg_b",
-                "add_correction", "correct", "misc", "pcg", "mg"]
+                "add_correction", "correct", "misc", "pcg", "mg", "ib"]
 
 
 class GridDesc(C.Structure):
@@ -106,9 +108,16 @@ def lib(build: bool = True):
         L.bcm_solve_pressure_static.argtypes = [P, P, P, C.c_double, C.c_int, P]
         L.bcm_profile.argtypes = [P, C.c_int]
         L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
+        L.bcm_particles_bytes.restype = C.c_size_t
+        L.bcm_particles_bytes.argtypes = [P, C.c_int32]
+        L.bcm_set_particles.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_size_t]
+        L.bcm_get_particles.argtypes = [P, P, P, P]
+        L.bcm_particle_sets.argtypes = [P, P, P]
+        L.bcm_ib_interpolate.argtypes = [P, P, P]
+        L.bcm_ib_spread.argtypes = [P, P, P]
         L.bcm_last_error.restype = C.c_char_p
         for name in EXPORTED:
-            if name != "bcm_adjoint_bytes":
+            if name not in ("bcm_adjoint_bytes", "bcm_particles_bytes"):
                 getattr(L, name).restype = getattr(L, name).restype or C.c_int
         _lib = L
     return _lib
@@ -242,6 +251,66 @@ class Grid:
         _check(lib().bcm_apply_preconditioner(self._h, C.c_void_p(r.data_ptr()),
                                               C.c_void_p(z.data_ptr())))
         return z
+
+    # ------------------------------------------------ Lagrangian particles
+    def set_particles(self, parts):
+        """Lagrangian-particle IB with a workloads.Particles set (None or an empty set:
+        back to the solid fraction).  The particle workspace is a torch tensor kept
+        alive by the grid."""
+        import torch
+        L = lib()
+        n = 0 if parts is None else int(parts.n)
+        if n == 0:
+            _check(L.bcm_set_particles(self._h, 0, None, None, None, None, None, 0))
+            self._pws = None
+            return
+        nbytes = L.bcm_particles_bytes(self._h, n)
+        if nbytes == 0:
+            raise BCMError(BCM_E_INVALID, "particles need a single-level grid")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-ws.data_ptr()) % 256
+        X = np.ascontiguousarray(parts.X, np.float64)
+        sim = np.ascontiguousarray(parts.sim, np.int32)
+        body = np.ascontiguousarray(parts.body, np.int32)
+        dV = np.ascontiguousarray(parts.dV, np.float64)
+        self.stream.synchronize()
+        _check(L.bcm_set_particles(self._h, n, X.ctypes.data, sim.ctypes.data, body.ctypes.data,
+                                   dV.ctypes.data, C.c_void_p(ws.data_ptr() + off), nbytes))
+        self._pws = ws
+        self._np = n
+
+    def particles(self):
+        """(positions [n, 3], last step's force per particle [n, 3], cube per particle)."""
+        n = getattr(self, "_np", 0) if getattr(self, "_pws", None) is not None else 0
+        X, F = np.zeros((n, 3)), np.zeros((n, 3))
+        cube = np.zeros(n, np.int32)
+        _check(lib().bcm_get_particles(self._h, X.ctypes.data, F.ctypes.data, cube.ctypes.data))
+        return X, F, cube
+
+    def particle_sets(self):
+        """Per-cube sets: (start [n_cubes + 1], ids [n])."""
+        start = np.zeros(self.spec.n_cubes + 1, np.int32)
+        ids = np.zeros(self._np, np.int32)
+        _check(lib().bcm_particle_sets(self._h, start.ctypes.data, ids.ctypes.data))
+        return start, ids
+
+    def ib_interpolate(self, f):
+        """I[f] at every particle (FP64 test path)."""
+        import torch
+        f = torch.as_tensor(f).to(self.device, torch.float64).contiguous()
+        out = torch.zeros(self._np, dtype=torch.float64, device=self.device)
+        _check(lib().bcm_ib_interpolate(self._h, C.c_void_p(f.data_ptr()),
+                                        C.c_void_p(out.data_ptr())))
+        return out
+
+    def ib_spread(self, F):
+        """P[F] on the cells, F one value per particle (FP64 test path)."""
+        import torch
+        F = torch.as_tensor(F).to(self.device, torch.float64).contiguous()
+        out = torch.zeros(self.spec.n_cells, dtype=torch.float64, device=self.device)
+        _check(lib().bcm_ib_spread(self._h, C.c_void_p(F.data_ptr()),
+                                   C.c_void_p(out.data_ptr())))
+        return out
 
     def set_launch(self, slabs_a: int = 1, slabs_b: int = 1, persistent: int = 1):
         """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG

@@ -460,6 +460,8 @@ extern "C" bcm_status bcm_adjoint_step(bcm_grid* grid, void* dev_adj, size_t byt
   if (grid_two_level(grid)) return grid_fail(BCM_E_INVALID, "the adjoint needs a single-level grid");
   const Ctx& base = *grid_ctx(grid);
   if (!base.f64) return grid_fail(BCM_E_INVALID, "the adjoint runs on FP64 grids");
+  if (base.part.n > 0)
+    return grid_fail(BCM_E_INVALID, "the adjoint differentiates the solid-fraction IB, not particles");
   if (bytes < bcm_adjoint_bytes(grid)) return grid_fail(BCM_E_INVALID, "adjoint workspace too small");
   const size_t n = (size_t)base.g.n_cubes * base.B * base.B * base.B;
   void* ubp = nullptr;

@@ -7,11 +7,13 @@
 // bcm_kernels.cu on the grid's stream.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <stdarg.h>
 #include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <array>
 #include <map>
@@ -675,6 +677,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.err = (int*)(W + L.err);
   x.use_mg = 0;
   x.mg = MgDev{};
+  x.part = PartDev{};
   if (mgh.ok) {
     MgDev& D = x.mg;
     D.L = mgh.L;
@@ -991,6 +994,13 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
 bcm_status collect(bcm_grid* g, bcm_stats* out) {
   bcm_status est = read_err(g);
   if (est != BCM_OK) return est;
+  if (g->ctx.part.n > 0) {
+    int perr = 0;
+    CUDA_TRY(cudaMemcpyAsync(&perr, g->ctx.part.err, sizeof(int), cudaMemcpyDeviceToHost,
+                             g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (perr) return fail(BCM_E_BOUNDS, "a Lagrangian particle lies outside every cube");
+  }
   std::vector<SimState> ss(g->desc.n_sims);
   CUDA_TRY(cudaMemcpyAsync(ss.data(), g->ws + g->L.ss, sizeof(SimState) * ss.size(),
                            cudaMemcpyDeviceToHost, g->stream));
@@ -1029,14 +1039,23 @@ extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_it
   bool moving = false;
   for (const auto& p : g->T.sp) moving |= (p.n_bodies > 0 && p.moving);
   bcm_status last = BCM_OK;
+  const bool particles = x.part.n > 0;
   for (int n = 0; n < n_steps; ++n) {
-    if (moving) RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -2));
+    if (moving && !particles) RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -2));
     RUN(BCM_K_MOMENTUM, launch_momentum(x));
+    if (particles) {  // forcing by the Lagrangian particles: force, then spreading
+      RUN(BCM_K_IB, launch_ib_force(x));
+      g->launch_count += 1;
+    }
     RUN(BCM_K_RHS, launch_rhs(x));
     bcm_status st = solve(g, rtol, max_iter);
     if (st != BCM_OK) return st;
     RUN(BCM_K_CORRECT, launch_correct(x));
     RUN(BCM_K_MISC, launch_step_end(x));
+    if (particles && moving) {  // move, then rebuild the per-cube sets
+      RUN(BCM_K_IB, launch_ib_move(x));
+      g->launch_count += 3;
+    }
   }
   if (stats) last = collect(g, stats);
   return last;
@@ -1061,8 +1080,10 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   prm.mixed = g->f64 ? 0 : 1;
   prm.guard = x.f.guard;
   prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
-  if (moving) CUDA_TRY(launch_solid_fraction(x, -2));
+  const bool particles = x.part.n > 0;
+  if (moving && !particles) CUDA_TRY(launch_solid_fraction(x, -2));
   CUDA_TRY(launch_momentum(x));
+  if (particles) CUDA_TRY(launch_ib_force(x));
   CUDA_TRY(launch_rhs(x));
   CUDA_TRY(launch_solve_begin(x));
   CUDA_TRY(launch_residual(x, prm));
@@ -1077,6 +1098,7 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   }
   CUDA_TRY(launch_correct(x));
   CUDA_TRY(launch_step_end(x));
+  if (particles && moving) CUDA_TRY(launch_ib_move(x));
   return BCM_OK;
 }
 }  // namespace
@@ -1231,6 +1253,179 @@ extern "C" bcm_status bcm_fill_halo(bcm_grid* g, int field, int kind, double* de
   if (st != BCM_OK) return st;
   if (field == BCM_UB) return fail(BCM_E_INVALID, "BCM_UB is not a cell field");
   RUN(BCM_K_MISC, launch_fill_halo(g->ctx, ptr, eb == 8, kind, dev_out));
+  return BCM_OK;
+}
+
+// ---- Lagrangian-particle immersed boundary (bcm_ib.cu)
+
+namespace {
+
+struct PartLayout {
+  size_t X, F, sim, body, dV, cube, start, ids, count, lat, meta, err, total;
+};
+
+// Layout of the caller's particle workspace, and the cube lattice of every sim
+// (cube id by cube coordinates, -1 where the sim has no cube).
+PartLayout part_plan(const bcm_grid* g, int n, std::vector<int>* lat, std::vector<int>* meta) {
+  PartLayout P{};
+  const int B = g->B, nc = g->desc.n_cubes, ns = g->desc.n_sims;
+  std::vector<int> m(4 * (size_t)ns);
+  size_t nl = 0;
+  for (int s = 0; s < ns; ++s) {
+    m[4 * s] = (int)nl;
+    size_t cells = 1;
+    for (int e = 0; e < 3; ++e) {
+      m[4 * s + 1 + e] = (g->T.sp[s].extent[e] + B - 1) / B;
+      cells *= (size_t)m[4 * s + 1 + e];
+    }
+    nl += cells;
+  }
+  if (lat) {
+    lat->assign(nl ? nl : 1, -1);
+    for (int c = 0; c < nc; ++c) {
+      const int s = g->T.sim[c];
+      const int* ms = &m[4 * (size_t)s];
+      const int cx = g->T.ijk[3 * c] / B, cy = g->T.ijk[3 * c + 1] / B, cz = g->T.ijk[3 * c + 2] / B;
+      (*lat)[ms[0] + ((size_t)cz * ms[2] + cy) * ms[1] + cx] = c;
+    }
+  }
+  if (meta) *meta = m;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  };
+  const size_t nn = (size_t)(n > 0 ? n : 0);
+  P.X = take(24 * nn);
+  P.F = take(24 * nn);
+  P.sim = take(4 * nn);
+  P.body = take(4 * nn);
+  P.dV = take(8 * nn);
+  P.cube = take(4 * nn);
+  P.start = take(4 * ((size_t)nc + 1));
+  P.ids = take(4 * nn);
+  P.count = take(4 * (size_t)nc);
+  P.lat = take(4 * (nl ? nl : 1));
+  P.meta = take(16 * (size_t)ns);
+  P.err = take(64);
+  P.total = off;
+  return P;
+}
+
+}  // namespace
+
+extern "C" size_t bcm_particles_bytes(const bcm_grid* g, int32_t n_particles) {
+  if (!g || n_particles < 0 || g->desc.max_level != 0) return 0;
+  return part_plan(g, n_particles, nullptr, nullptr).total;
+}
+
+extern "C" bcm_status bcm_set_particles(bcm_grid* g, int32_t n, const double* xyz,
+                                        const int32_t* sim, const int32_t* body,
+                                        const double* dV, void* dev_workspace, size_t bytes) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (g->desc.max_level != 0)
+    return fail(BCM_E_INVALID, "Lagrangian particles need a single-level grid");
+  if (n < 0) return fail(BCM_E_INVALID, "n_particles must be >= 0");
+  Ctx& x = g->ctx;
+  if (n == 0) {  // back to the solid-fraction IB
+    x.part = PartDev{};
+    RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -1));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return BCM_OK;
+  }
+  if (!xyz || !sim || !body || !dV || !dev_workspace)
+    return fail(BCM_E_INVALID, "NULL particle array or workspace");
+  if ((uintptr_t)dev_workspace % kAlign)
+    return fail(BCM_E_INVALID, "particle workspace must be %zu-byte aligned", kAlign);
+  std::vector<int> lat, meta;
+  const PartLayout P = part_plan(g, n, &lat, &meta);
+  if (bytes < P.total)
+    return fail(BCM_E_INVALID, "particle workspace too small: %zu < %zu", bytes, P.total);
+  for (int q = 0; q < n; ++q) {
+    if (sim[q] < 0 || sim[q] >= g->desc.n_sims)
+      return fail(BCM_E_INVALID, "particle %d: sim %d out of range", q, sim[q]);
+    if (body[q] < 0 || body[q] >= kMaxBodies)
+      return fail(BCM_E_INVALID, "particle %d: body %d out of range", q, body[q]);
+    if (!(dV[q] > 0) || !std::isfinite(dV[q]))
+      return fail(BCM_E_INVALID, "particle %d: dV must be > 0", q);
+    for (int e = 0; e < 3; ++e)
+      if (!std::isfinite(xyz[3 * q + e])) return fail(BCM_E_INVALID, "particle %d: position", q);
+  }
+  unsigned char* W = (unsigned char*)dev_workspace;
+  cudaStream_t s = g->stream;
+  CUDA_TRY(cudaMemsetAsync(W, 0, P.total, s));
+  CUDA_TRY(cudaMemcpyAsync(W + P.X, xyz, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(W + P.sim, sim, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(W + P.body, body, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(W + P.dV, dV, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(W + P.lat, lat.data(), 4 * lat.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(W + P.meta, meta.data(), 4 * meta.size(), cudaMemcpyHostToDevice, s));
+  PartDev D{};
+  D.n = n;
+  D.X = (double*)(W + P.X);
+  D.F = (double*)(W + P.F);
+  D.sim = (const int*)(W + P.sim);
+  D.body = (const int*)(W + P.body);
+  D.dV = (const double*)(W + P.dV);
+  D.cube = (int*)(W + P.cube);
+  D.set_start = (int*)(W + P.start);
+  D.set_ids = (int*)(W + P.ids);
+  D.set_count = (int*)(W + P.count);
+  D.lat = (const int*)(W + P.lat);
+  D.lat_meta = (const int*)(W + P.meta);
+  D.err = (int*)(W + P.err);
+  x.part = D;
+  // the solid fraction plays no part with particles
+  CUDA_TRY(cudaMemsetAsync(g->ws + g->L.phi, 0, g->n_cells * (g->f64 ? 8 : 4), s));
+  CUDA_TRY(cudaMemsetAsync(g->ws + g->L.near_, 0, (size_t)g->desc.n_cubes, s));
+  RUN(BCM_K_IB, launch_ib_bin(x));
+  g->launch_count += 2;
+  int perr = 0;
+  CUDA_TRY(cudaMemcpyAsync(&perr, D.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (perr) {
+    x.part = PartDev{};
+    RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -1));
+    return fail(BCM_E_BOUNDS, "a Lagrangian particle lies outside every cube");
+  }
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_get_particles(bcm_grid* g, double* xyz, double* force, int32_t* cube) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  const PartDev& D = g->ctx.part;
+  const size_t n = (size_t)(D.n > 0 ? D.n : 0);
+  if (n == 0) return BCM_OK;
+  if (xyz) CUDA_TRY(cudaMemcpyAsync(xyz, D.X, 24 * n, cudaMemcpyDeviceToHost, g->stream));
+  if (force) CUDA_TRY(cudaMemcpyAsync(force, D.F, 24 * n, cudaMemcpyDeviceToHost, g->stream));
+  if (cube) CUDA_TRY(cudaMemcpyAsync(cube, D.cube, 4 * n, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_particle_sets(bcm_grid* g, int32_t* start, int32_t* ids) {
+  if (!g || !start || !ids) return fail(BCM_E_INVALID, "NULL argument");
+  const PartDev& D = g->ctx.part;
+  if (D.n <= 0) return fail(BCM_E_INVALID, "no particles set");
+  CUDA_TRY(cudaMemcpyAsync(start, D.set_start, 4 * ((size_t)g->desc.n_cubes + 1),
+                           cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(ids, D.set_ids, 4 * (size_t)D.n, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_ib_interpolate(bcm_grid* g, const double* dev_f, double* dev_out) {
+  if (!g || !dev_f || !dev_out) return fail(BCM_E_INVALID, "NULL argument");
+  if (g->ctx.part.n <= 0) return fail(BCM_E_INVALID, "no particles set");
+  RUN(BCM_K_MISC, launch_ib_interpolate(g->ctx, dev_f, dev_out));
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_ib_spread(bcm_grid* g, const double* dev_F, double* dev_out) {
+  if (!g || !dev_F || !dev_out) return fail(BCM_E_INVALID, "NULL argument");
+  if (g->ctx.part.n <= 0) return fail(BCM_E_INVALID, "no particles set");
+  RUN(BCM_K_MISC, launch_ib_spread(g->ctx, dev_F, dev_out));
   return BCM_OK;
 }
 

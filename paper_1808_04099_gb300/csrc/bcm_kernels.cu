@@ -570,6 +570,7 @@ static cudaError_t solid_fraction_t(const Ctx& x, int sim_filter) {
   return cudaGetLastError();
 }
 cudaError_t launch_solid_fraction(const Ctx& x, int sim_filter) {
+  if (x.part.n > 0) return cudaSuccess;  // Lagrangian particles: no solid fraction
   return x.f64 ? solid_fraction_t<double>(x, sim_filter) : solid_fraction_t<float>(x, sim_filter);
 }
 

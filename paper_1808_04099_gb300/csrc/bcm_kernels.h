@@ -62,6 +62,24 @@ struct MgDev {
   int *parent[kMgMaxM];                // parent at level k of each level k-1 node
 };
 
+// Lagrangian particles of the immersed boundary (n = 0: the solid-fraction IB).
+// Arrays live in a caller-provided workspace (bcm_set_particles).
+struct PartDev {
+  int n;
+  double* X;        // [3n] positions, xyz interleaved
+  double* F;        // [3n] force per particle of the last step (rho = 1)
+  const int* sim;   // [n] sim of each particle
+  const int* body;  // [n] body (of its sim) that moves it
+  const double* dV; // [n] volume weight dc1 dc2 dc3
+  int* cube;        // [n] cube containing the particle (-1: outside every cube)
+  int* set_start;   // [n_cubes + 1] per-cube sets: particles of cube c are
+  int* set_ids;     //   set_ids[set_start[c] .. set_start[c+1])
+  int* set_count;   // [n_cubes] scratch: counts, then fill cursors
+  const int* lat;   // cube lattice: cube id at (sim, cube coordinates), -1 none
+  const int* lat_meta;  // [n_sims][4]: offset into lat, cubes along x, y, z
+  int* err;         // set when a particle lies outside every cube
+};
+
 struct Ctx {
   DevGrid g;
   Fields f;
@@ -76,6 +94,7 @@ struct Ctx {
   int lag_bf16;    // mixed mode: N^{n-1} stored as bfloat16
   int use_mg;      // PCG preconditioner: 0 Jacobi, 1 geometric multigrid
   MgDev mg;
+  PartDev part;    // Lagrangian particles (part.n > 0: particle IB, no solid fraction)
   cudaStream_t stream;
 };
 
@@ -103,5 +122,13 @@ cudaError_t launch_apply_poisson(const Ctx& x, const double* in, double* out);
 // (<r,z> becomes the PCG's rz); 1: after pass A, doing pass B too (<r,r>), then <r,z>,
 // beta and the convergence decision; 2: standalone (every sim, no dot products).
 cudaError_t launch_mg_vcycle(const Ctx& x, const SolveParams& prm, int mode);
+// Lagrangian particles: per-cube sets from the positions (counting sort); the
+// forcing sub-step (interpolation of u~, F, spreading into u*); the position update.
+cudaError_t launch_ib_bin(const Ctx& x);
+cudaError_t launch_ib_force(const Ctx& x);
+cudaError_t launch_ib_move(const Ctx& x);
+// test paths on FP64 arrays: out[q] = I[f] at particle q; out += P[F]
+cudaError_t launch_ib_interpolate(const Ctx& x, const double* f, double* out);
+cudaError_t launch_ib_spread(const Ctx& x, const double* F, double* out);
 
 }  // namespace bcm
