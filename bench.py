@@ -58,6 +58,9 @@ def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
         # x_0, r_1 out: 7.125 S) and up (x_0, y_1, r in; z out: 3.125 S), the coarser
         # levels 1/7 of the V-cycle's part (0.75 S)
         "mg": 11 * S,
+        # Lagrangian particles: per particle, not per cell (27 cells x 3 components read
+        # and added per particle); reported as time only
+        "ib": 0.0,
         "misc": 0.0,
     }[kernel]
 
@@ -430,6 +433,41 @@ def gpu_arm(args, ws, rank, local):
                     "rel_resid_last_step": stm["rel_resid"],
                     "kernels": kernel_table(profm, n, prec == bcm.PREC_F64, phi_frac, itm)}
 
+    # ---- the same step with the Lagrangian-particle IB: the sphere's surface particles
+    # (one per surface cell) in place of the solid fraction; a second run rotates the
+    # sphere in place so that the particles move and their per-cube sets are rebuilt
+    # after every step
+    lag = {}
+    parts = W.surface_particles(spec)
+    for name, omega in (("fixed", 0.0), ("rotating", 0.5)):
+        gl = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+        gl.load_state(state)
+        if omega:
+            b = spec.bodies[0][0]
+            gl.set_geometry(0, [W.Body(b.kind, b.center, b.axes, b.quat,
+                                       np.array([0.0, 0.0, omega]), b.vel)])
+        gl.set_particles(parts)
+        for _ in range(args.warmup):
+            gl.step(1, rtol=RTOL, stats=False)
+        msl = timed_steps(gl, args.steps, gl.stream)
+        stl = gl.step(0, rtol=RTOL)[0]
+        gl.profile(True)
+        itl = 0
+        for _ in range(kprof_steps):
+            itl += gl.step(1, rtol=RTOL)[0]["cg_iters"]
+        profl, _ = gl.profile_read(reset=True)
+        gl.profile(False)
+        del gl
+        msl = max_over_ranks(msl, ws)
+        kl = kernel_table(profl, n, False, phi_frac, itl)
+        lag[name] = {"value": n * args.steps / (msl / 1e3) * (ws if ws > 1 else 1),
+                     "unit": "cell-updates/s", "ms_per_step": msl / args.steps,
+                     "particles": parts.n, "body_omega_z": omega,
+                     "cg_iters_last_step": stl["cg_iters"],
+                     "rel_resid_last_step": stl["rel_resid"], "drag_last_step": stl["drag"],
+                     "ib_us_per_step": 1e3 * kl["ib"]["total_ms"] / kprof_steps if "ib" in kl else None,
+                     "kernels": kl}
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -460,6 +498,9 @@ def gpu_arm(args, ws, rank, local):
                                 "Jacobi-PCG hot path): steps issued from the host, each PCG "
                                 "iteration one replayed CUDA graph; same workload and "
                                 "residual"),
+            "lagrangian": dict(lag, note="Lagrangian-particle IB (a NEXT row beyond the hot "
+                                         "path): the mixed Jacobi-PCG step with the sphere's "
+                                         "surface particles in place of the solid fraction"),
             "mixed_paths_ms_per_step": {"eager": ms_eager / args.steps,
                                         "graph": ms_graph / args.steps,
                                         "value_from": "graph" if ms_graph <= ms_eager else "eager"},
