@@ -70,6 +70,9 @@ def lib():
         L.orc_solve_pressure.restype = C.c_int
         L.orc_step.argtypes = [P] * 10 + [C.c_int, C.c_double, C.c_int, P]
         L.orc_step.restype = C.c_int
+        L.orc_convection_quick.argtypes = [P] * 8
+        L.orc_set_scheme.argtypes = [P, C.c_int, C.c_double, C.c_int]
+        L.orc_set_scheme.restype = C.c_int
         L.orc_delta3.argtypes = [C.c_double]
         L.orc_delta3.restype = C.c_double
         L.orc_ib_interpolate.argtypes = [P, P, C.c_int, P, P, P]
@@ -200,6 +203,21 @@ class Oracle:
                             _p(st["nx"]), _p(st["ny"]), _p(st["nz"]), _p(ub), _p(st["step"]),
                             nsteps, rtol, max_iter, stats)
         return [s.as_dict() for s in stats], rc
+
+    # ------------------------------------------- QUICK + Crank-Nicolson (R20)
+    def convection_quick(self, u, v, w, ub=None):
+        n = self.n_cells
+        outs = [np.zeros(n) for _ in range(3)]
+        u, v, w = _f64(u), _f64(v), _f64(w)
+        ubk = _f64(ub) if ub is not None and np.size(ub) else None
+        lib().orc_convection_quick(self._h, _p(u), _p(v), _p(w),
+                                   _p(ubk) if ubk is not None else None, *[_p(o) for o in outs])
+        return outs
+
+    def set_scheme(self, scheme: int, cn_rtol: float = 1e-10, cn_max: int = 100):
+        """Momentum scheme of the following steps: 0 AB2 + central, 1 QUICK + CN."""
+        if lib().orc_set_scheme(self._h, scheme, cn_rtol, cn_max):
+            raise ValueError(lib().orc_error().decode())
 
     # ------------------------------------------------ Lagrangian particles (R19)
     @staticmethod

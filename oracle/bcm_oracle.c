@@ -54,6 +54,18 @@
  *      velocity of the particle's body at (X^n, t^n); the position update takes the
  *      body velocity at (X^n, t^{n+1}).  rho = 1; the force on the body is
  *      -sum_p F_p dV_p.  The solid fraction is zero in this mode.
+ *   R20 QUICK + Crank-Nicolson momentum (orc_set_scheme; Eq. substep1 with the QUICK
+ *      scheme the paper names for its convection): convective face values by
+ *      quadratic upstream interpolation phi_f = 6/8 phi_C + 3/8 phi_D - 1/8 phi_U (C the
+ *      upwind cell, D the downwind one, U the cell upwind of C) on the central face
+ *      velocities; diffusion the 7-point Laplacian.  The implicit half is solved by the
+ *      iteration u^(0) = u^n,
+ *        u^(k+1) = (E - dt/2 N(u^(k)) + dt nu/2 (sum of the 6 neighbours of u^(k))/h^2)
+ *                  / (1 + 3 dt nu / h^2),     E = u^n + dt (-N(u^n)/2 + nu L(u^n)/2),
+ *      whose fixed point is the Crank-Nicolson step; ghosts of u^(k) by the halo rules
+ *      with the outflow face values of t^{n+1}.  A sim stops iterating once
+ *      ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| (all three components) or after
+ *      cn_max iterations.  The IB forcing then acts on the converged u~.
  */
 #include "bcm_oracle.h"
 
@@ -96,6 +108,10 @@ struct orc_grid {
     int32_t *nb_fine;   /* [(c*6+f)*4 + qb*2 + qa] when nb == NB_FINE */
     int32_t *slot;      /* [c*6+f] outflow slot or -1 */
     int32_t *order;     /* cube ids sorted by (sim, level, z, y, x) */
+    int scheme;         /* momentum: 0 AB2 + central, 1 QUICK + Crank-Nicolson (R20) */
+    double cn_rtol;     /* Crank-Nicolson iteration: relative update per sim */
+    int cn_max;         /*   and the most iterations per step */
+    int ab2_restart;    /* the next AB2 step takes N^{n-1} := N^n (after Crank-Nicolson) */
 };
 
 /* ------------------------------------------------------------------ helpers */
@@ -198,6 +214,10 @@ orc_grid *orc_create(int B, int max_level, int n_sims, int n_cubes, const int32_
     g->slot = (int32_t *)malloc(sizeof(int32_t) * 6 * n_cubes + 1);
     g->order = (int32_t *)malloc(sizeof(int32_t) * n_cubes + 1);
     for (int c = 0; c < n_cubes; ++c) g->order[c] = c;
+    g->scheme = 0;
+    g->cn_rtol = 1e-10;
+    g->cn_max = 100;
+    g->ab2_restart = 0;
     g_sort_grid = g;
     qsort(g->order, (size_t)n_cubes, sizeof(int32_t), sort_cmp);
     for (int c = 1; c < n_cubes; ++c) {
@@ -624,6 +644,72 @@ static void conv_diff(const orc_grid *g, double *const gu[3], int comp, int i, i
     *Lout = L / (h * h);
 }
 
+/* QUICK face value from the upwind cell C, the downwind cell D and the cell U upwind of
+ * C (R20). */
+static double quick_face(double pC, double pD, double pU) {
+    return 0.75 * pC + 0.375 * pD - 0.125 * pU;
+}
+
+/* QUICK convection N_comp at (i,j,k) of a ghosted cube: (1/h) sum_d of the face
+ * velocity (central) times the QUICK value of component comp, + face minus - face. */
+static double conv_quick(const orc_grid *g, double *const gu[3], int comp, int i, int j,
+                         int k, double h) {
+    const double *uc = gu[comp];
+    size_t i0 = gidx(g, i, j, k);
+    double N = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        int q1[3] = {i, j, k}, q2[3] = {i, j, k}, m1[3] = {i, j, k}, m2[3] = {i, j, k};
+        q1[d] += 1; q2[d] += 2; m1[d] -= 1; m2[d] -= 2;
+        size_t ip = gidx(g, q1[0], q1[1], q1[2]), ip2 = gidx(g, q2[0], q2[1], q2[2]);
+        size_t im = gidx(g, m1[0], m1[1], m1[2]), im2 = gidx(g, m2[0], m2[1], m2[2]);
+        const double *ud = gu[d];
+        double Up = 0.5 * (ud[i0] + ud[ip]), Um = 0.5 * (ud[im] + ud[i0]);
+        double fp = Up >= 0.0 ? quick_face(uc[i0], uc[ip], uc[im])
+                              : quick_face(uc[ip], uc[i0], uc[ip2]);
+        double fm = Um >= 0.0 ? quick_face(uc[im], uc[i0], uc[im2])
+                              : quick_face(uc[i0], uc[im], uc[ip]);
+        N += Up * fp - Um * fm;
+    }
+    return N / h;
+}
+
+/* QUICK convection of every component (test path, like orc_convection_diffusion). */
+void orc_convection_quick(const orc_grid *g, const double *u, const double *v, const double *w,
+                          const double *ub, double *nx, double *ny, double *nz) {
+    int B = g->B;
+    size_t G3 = (size_t)g->G * g->G * g->G;
+    double *gu = (double *)malloc(sizeof(double) * G3 * g->n_cubes);
+    double *gv = (double *)malloc(sizeof(double) * G3 * g->n_cubes);
+    double *gw = (double *)malloc(sizeof(double) * G3 * g->n_cubes);
+    orc_fill_ghosts(g, u, 0, ub, gu);
+    orc_fill_ghosts(g, v, 1, ub, gv);
+    orc_fill_ghosts(g, w, 2, ub, gw);
+    double *No[3] = {nx, ny, nz};
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < g->n_cubes; ++c) {
+        double *bufs[3] = {gu + c * G3, gv + c * G3, gw + c * G3};
+        double h = cell_h(g, c);
+        for (int k = 0; k < B; ++k)
+            for (int j = 0; j < B; ++j)
+                for (int i = 0; i < B; ++i)
+                    for (int comp = 0; comp < 3; ++comp)
+                        No[comp][cidx(B, c, i, j, k)] = conv_quick(g, bufs, comp, i, j, k, h);
+    }
+    free(gu); free(gv); free(gw);
+}
+
+int orc_set_scheme(orc_grid *g, int scheme, double cn_rtol, int cn_max) {
+    if (scheme != 0 && scheme != 1) {
+        snprintf(g_err, sizeof g_err, "unknown momentum scheme %d", scheme);
+        return -1;
+    }
+    if (scheme == 0 && g->scheme == 1) g->ab2_restart = 1;
+    g->scheme = scheme;
+    g->cn_rtol = cn_rtol;
+    g->cn_max = cn_max;
+    return 0;
+}
+
 void orc_convection_diffusion(const orc_grid *g, const double *u, const double *v,
                               const double *w, const double *ub, double *nx, double *ny,
                               double *nz, double *lx, double *ly, double *lz) {
@@ -972,6 +1058,16 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
     double *pF = (double *)malloc(sizeof(double) * (3 * (size_t)np + 1));
     double *pS = (double *)malloc(sizeof(double) * ((size_t)np + 1));
     double *pdrag = (double *)calloc(3 * (size_t)g->n_sims + 1, sizeof(double));
+    int cn = g->scheme == 1;
+    double *cnbuf = (double *)malloc(sizeof(double) * (cn ? 9 * n : 1));
+    double *cnE[3], *cnA[3], *cnB[3];
+    for (int e = 0; e < 3; ++e) {
+        cnE[e] = cnbuf + (cn ? (size_t)e * n : 0);
+        cnA[e] = cnbuf + (cn ? (size_t)(3 + e) * n : 0);
+        cnB[e] = cnbuf + (cn ? (size_t)(6 + e) * n : 0);
+    }
+    double *cnpart = (double *)malloc(sizeof(double) * (2 * (size_t)g->n_cubes + 1));
+    int *cndone = (int *)calloc((size_t)g->n_sims + 1, sizeof(int));
 
     for (int it = 0; it < nsteps; ++it) {
         /* (a) body geometry and velocity at t^n (particles: no solid fraction) */
@@ -985,6 +1081,121 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
         orc_fill_ghosts(g, u, 0, ub, gu);
         orc_fill_ghosts(g, v, 1, ub, gv);
         orc_fill_ghosts(g, w, 2, ub, gw);
+        /* (d) outflow face values u_b^{n+1} (R8) */
+        for (int c = 0; c < g->n_cubes; ++c)
+            for (int fc = 0; fc < 6; ++fc) {
+                int sl = g->slot[6 * c + fc];
+                if (sl < 0) continue;
+                int s = g->sim_of[c], d = fc / 2, side = fc % 2;
+                double h = cell_h(g, c), dt = g->dt[s], Uc = g->uconv[s];
+                for (int comp = 0; comp < 3; ++comp)
+                    for (int bb = 0; bb < B; ++bb)
+                        for (int aa = 0; aa < B; ++aa) {
+                            size_t id = (((size_t)sl * 3 + comp) * B + bb) * B + aa;
+                            double u0 = fval(g, vel[comp], c, d, side ? B - 1 : 0, aa, bb);
+                            ubn[id] = ub[id] - Uc * dt * (ub[id] - u0) / (0.5 * h);
+                        }
+            }
+        /* (c') QUICK + Crank-Nicolson (R20): explicit half E, the iteration for u~ with
+         * the ghosts of t^{n+1} at outflow faces, then the IB forcing of u~ */
+        if (g->scheme == 1) {
+#pragma omp parallel for schedule(static)
+            for (int c = 0; c < g->n_cubes; ++c) {
+                int s = g->sim_of[c];
+                double h = cell_h(g, c), dt = g->dt[s], nu = g->nu[s];
+                double *bufs[3] = {gu + c * G3, gv + c * G3, gw + c * G3};
+                for (int k = 0; k < B; ++k)
+                    for (int j = 0; j < B; ++j)
+                        for (int i = 0; i < B; ++i)
+                            for (int comp = 0; comp < 3; ++comp) {
+                                double Nc, L, N;
+                                conv_diff(g, bufs, comp, i, j, k, h, &Nc, &L);
+                                N = conv_quick(g, bufs, comp, i, j, k, h);
+                                size_t id = cidx(B, c, i, j, k);
+                                cnE[comp][id] = vel[comp][id] + dt * (-0.5 * N + 0.5 * nu * L);
+                                cnA[comp][id] = vel[comp][id];
+                            }
+            }
+            for (int s = 0; s < g->n_sims; ++s) cndone[s] = 0;
+            for (int kk = 0; kk < g->cn_max; ++kk) {
+                int alive = 0;
+                for (int s = 0; s < g->n_sims; ++s) alive |= !cndone[s];
+                if (!alive) break;
+                orc_fill_ghosts(g, cnA[0], 0, ubn, gu);
+                orc_fill_ghosts(g, cnA[1], 1, ubn, gv);
+                orc_fill_ghosts(g, cnA[2], 2, ubn, gw);
+#pragma omp parallel for schedule(static)
+                for (int c = 0; c < g->n_cubes; ++c) {
+                    int s = g->sim_of[c];
+                    double h = cell_h(g, c), dt = g->dt[s], nu = g->nu[s];
+                    double *bufs[3] = {gu + c * G3, gv + c * G3, gw + c * G3};
+                    double den = 1.0 + 3.0 * dt * nu / (h * h), d2 = 0.0, u2 = 0.0;
+                    for (int k = 0; k < B; ++k)
+                        for (int j = 0; j < B; ++j)
+                            for (int i = 0; i < B; ++i)
+                                for (int comp = 0; comp < 3; ++comp) {
+                                    size_t id = cidx(B, c, i, j, k);
+                                    if (cndone[s]) {
+                                        cnB[comp][id] = cnA[comp][id];
+                                        continue;
+                                    }
+                                    const double *uc = bufs[comp];
+                                    double N = conv_quick(g, bufs, comp, i, j, k, h), sn = 0.0;
+                                    for (int d = 0; d < 3; ++d) {
+                                        int p1[3] = {i, j, k}, m1[3] = {i, j, k};
+                                        p1[d] += 1;
+                                        m1[d] -= 1;
+                                        sn += uc[gidx(g, p1[0], p1[1], p1[2])] +
+                                              uc[gidx(g, m1[0], m1[1], m1[2])];
+                                    }
+                                    double un = (cnE[comp][id] - 0.5 * dt * N +
+                                                 0.5 * dt * nu * sn / (h * h)) / den;
+                                    double dd = un - cnA[comp][id];
+                                    d2 += dd * dd;
+                                    u2 += un * un;
+                                    cnB[comp][id] = un;
+                                }
+                    cnpart[2 * c] = d2;
+                    cnpart[2 * c + 1] = u2;
+                }
+                for (int s = 0; s < g->n_sims; ++s) {
+                    if (cndone[s]) continue;
+                    double d2 = 0.0, u2 = 0.0;
+                    for (int c = g->sim_off[s]; c < g->sim_off[s + 1]; ++c) {
+                        d2 += cnpart[2 * c];
+                        u2 += cnpart[2 * c + 1];
+                    }
+                    if (d2 <= g->cn_rtol * g->cn_rtol * u2) cndone[s] = 1;
+                }
+                for (int comp = 0; comp < 3; ++comp) {
+                    double *tmp = cnA[comp];
+                    cnA[comp] = cnB[comp];
+                    cnB[comp] = tmp;
+                }
+            }
+#pragma omp parallel for schedule(static)
+            for (int c = 0; c < g->n_cubes; ++c) {
+                int s = g->sim_of[c];
+                double h = cell_h(g, c), dt = g->dt[s], V = h * h * h;
+                double fx = 0, fy = 0, fz = 0;
+                const double *usb[3] = {bu, bv, bw};
+                for (int k = 0; k < B; ++k)
+                    for (int j = 0; j < B; ++j)
+                        for (int i = 0; i < B; ++i) {
+                            size_t id = cidx(B, c, i, j, k);
+                            for (int comp = 0; comp < 3; ++comp) {
+                                double ut = cnA[comp][id];
+                                double du = phi[id] * (usb[comp][id] - ut);
+                                vstar[comp][id] = ut + du;
+                                double f = du / dt;
+                                if (comp == 0) fx += f * V;
+                                else if (comp == 1) fy += f * V;
+                                else fz += f * V;
+                            }
+                        }
+                drag[3 * c] = -fx; drag[3 * c + 1] = -fy; drag[3 * c + 2] = -fz;
+            }
+        } else {
         /* (c) momentum sub-step (R3) and IB forcing (R5) */
 #pragma omp parallel for schedule(static)
         for (int c = 0; c < g->n_cubes; ++c) {
@@ -1000,7 +1211,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                         for (int comp = 0; comp < 3; ++comp) {
                             double N, L;
                             conv_diff(g, bufs, comp, i, j, k, h, &N, &L);
-                            double Nprev = step[s] == 0 ? N : Nl[comp][id];
+                            double Nprev = (step[s] == 0 || g->ab2_restart) ? N : Nl[comp][id];
                             double ut = vel[comp][id] + dt * (-(1.5 * N - 0.5 * Nprev) + nu * L);
                             double du = phi[id] * (usb[comp][id] - ut);
                             vstar[comp][id] = ut + du;
@@ -1035,21 +1246,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                 orc_ib_spread(g, np, P->X, P->sim, pS, P->dV, vstar[comp]);
             }
         }
-        /* (d) outflow face values u_b^{n+1} (R8) */
-        for (int c = 0; c < g->n_cubes; ++c)
-            for (int fc = 0; fc < 6; ++fc) {
-                int sl = g->slot[6 * c + fc];
-                if (sl < 0) continue;
-                int s = g->sim_of[c], d = fc / 2, side = fc % 2;
-                double h = cell_h(g, c), dt = g->dt[s], Uc = g->uconv[s];
-                for (int comp = 0; comp < 3; ++comp)
-                    for (int bb = 0; bb < B; ++bb)
-                        for (int aa = 0; aa < B; ++aa) {
-                            size_t id = (((size_t)sl * 3 + comp) * B + bb) * B + aa;
-                            double u0 = fval(g, vel[comp], c, d, side ? B - 1 : 0, aa, bb);
-                            ubn[id] = ub[id] - Uc * dt * (ub[id] - u0) / (0.5 * h);
-                        }
-            }
+        }
         /* (e) Poisson right-hand side from u* and the new outflow values */
         orc_rhs(g, us, vs, ws, ubn, b);
         /* (f) pressure solve */
@@ -1122,6 +1319,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
             step[s] += 1;
         }
         memcpy(ub, ubn, sizeof(double) * nub);
+        if (g->scheme == 0) ((orc_grid *)g)->ab2_restart = 0;
         /* (i) particles move with their body: X^{n+1} = X^n + dt U_s(X^n, t^{n+1}) */
         for (int q = 0; q < np; ++q) {
             int s = P->sim[q];
@@ -1133,6 +1331,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
     free(us); free(vs); free(ws); free(b); free(phi); free(bu); free(bv); free(bw);
     free(gu); free(gv); free(gw); free(ubn); free(drag); free(tt); free(st);
     free(pU); free(pF); free(pS); free(pdrag);
+    free(cnbuf); free(cnpart); free(cndone);
     return status;
 }
 

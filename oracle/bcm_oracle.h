@@ -101,6 +101,13 @@ int orc_step(const orc_grid *g, double *u, double *v, double *w, double *p, doub
              double *ny, double *nz, double *ub, int32_t *step, int nsteps, double rtol,
              int max_iter, orc_stats *stats);
 
+/* QUICK convection N(u) of every component (R20 in the .c file header); ghosts from ub. */
+void orc_convection_quick(const orc_grid *g, const double *u, const double *v, const double *w,
+                          const double *ub, double *nx, double *ny, double *nz);
+/* Momentum scheme of the following steps: 0 AB2 + central (default), 1 QUICK +
+ * Crank-Nicolson iterated to cn_rtol (at most cn_max iterations).  Returns 0, or -1. */
+int orc_set_scheme(orc_grid *g, int scheme, double cn_rtol, int cn_max);
+
 /* Lagrangian particles (R19 in the .c file header), single-level grids.
  * Particle q: position X[3q..3q+2], sim psim[q], body pbody[q] (0 .. ORC_MAX_BODIES-1 of
  * its sim), weight dV[q] (the particle's volume dc1 dc2 dc3 of Eq. ddeltap). */
