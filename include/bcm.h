@@ -279,6 +279,25 @@ bcm_status bcm_adjoint_step(bcm_grid *grid, void *dev_adj, size_t bytes, const v
                             int first_step, double drag_weight, double rtol, int max_iter,
                             double *dev_dJ);
 
+/* ---- Momentum scheme (Eq. substep1).  BCM_SCHEME_AB2_CENTRAL (default): explicit
+ * Adams-Bashforth convection (central) and Euler diffusion.  BCM_SCHEME_QUICK_CN: the
+ * paper's production scheme, QUICK convection (face values by quadratic upstream
+ * interpolation 6/8 C + 3/8 D - 1/8 U on the central face velocities; two ghost layers)
+ * and Crank-Nicolson for convection and diffusion,
+ *   (u~ - u^n)/dt + (N(u~) + N(u^n))/2 = nu (L(u~) + L(u^n))/2,
+ * solved per step by the iteration from the forward-Euler predictor u^(0) = 2 E - u^n,
+ *   u^(k+1) = (E - dt/2 N(u^(k)) + dt nu/2 (sum of the 6 neighbours of u^(k))/h^2)
+ *             / (1 + 3 dt nu/h^2),   E = u^n + dt (-N(u^n) + nu L(u^n))/2,
+ * until ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| per sim (all components), or the
+ * update has reached the rounding floor (<= 64 unit roundoffs of ||u^(k+1)||) and stopped
+ * shrinking (its square >= 0.99 of the previous one), or cn_max_iter iterations; ghosts of u^(k) follow the halo rules with the outflow
+ * values of t^n.  The mixed mode iterates on the increment u^(k) - u^n in FP32.  cn_rtol = 0 / cn_max_iter = 0 select the defaults (1e-10 FP64,
+ * 2e-8 mixed, i.e. down to the FP32 floor; 50).
+ * Switching back to AB2 restarts it with an Euler step (N^{n-1} := N^n).  The adjoint
+ * rejects grids on QUICK + Crank-Nicolson.  Errors: BCM_E_INVALID. */
+enum { BCM_SCHEME_AB2_CENTRAL = 0, BCM_SCHEME_QUICK_CN = 1 };
+bcm_status bcm_set_momentum_scheme(bcm_grid *grid, int scheme, double cn_rtol, int cn_max_iter);
+
 /* ---- Lagrangian-particle immersed boundary (section "Lagrangian Data Structure";
  * section "Lagrangian-Eulerian Interaction", Eqs. ddeltai and ddeltap with the smoothed
  * 3-point delta phi(r) = 3/4 - r^2 for |r| <= 1/2, (9/4 - 3|r| + r^2)/2 for

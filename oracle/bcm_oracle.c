@@ -59,13 +59,15 @@
  *      quadratic upstream interpolation phi_f = 6/8 phi_C + 3/8 phi_D - 1/8 phi_U (C the
  *      upwind cell, D the downwind one, U the cell upwind of C) on the central face
  *      velocities; diffusion the 7-point Laplacian.  The implicit half is solved by the
- *      iteration u^(0) = u^n,
+ *      iteration from the forward-Euler predictor u^(0) = 2 E - u^n,
  *        u^(k+1) = (E - dt/2 N(u^(k)) + dt nu/2 (sum of the 6 neighbours of u^(k))/h^2)
  *                  / (1 + 3 dt nu / h^2),     E = u^n + dt (-N(u^n)/2 + nu L(u^n)/2),
  *      whose fixed point is the Crank-Nicolson step; ghosts of u^(k) by the halo rules
- *      with the outflow face values of t^{n+1}.  A sim stops iterating once
- *      ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| (all three components) or after
- *      cn_max iterations.  The IB forcing then acts on the converged u~.
+ *      with the outflow face values of t^n (the whole sub-step sees u_b^n).  A sim stops iterating once
+ *      ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| (all three components), once the update
+ *      has reached the rounding floor of the arithmetic (at most 64 eps ||u^(k+1)||, eps
+ *      the unit roundoff) and no longer shrinks (its square >= 0.99 of the previous
+ *      one), or after cn_max iterations.  The IB forcing then acts on the result.
  */
 #include "bcm_oracle.h"
 
@@ -1068,6 +1070,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
     }
     double *cnpart = (double *)malloc(sizeof(double) * (2 * (size_t)g->n_cubes + 1));
     int *cndone = (int *)calloc((size_t)g->n_sims + 1, sizeof(int));
+    double *cnprev = (double *)calloc((size_t)g->n_sims + 1, sizeof(double));
 
     for (int it = 0; it < nsteps; ++it) {
         /* (a) body geometry and velocity at t^n (particles: no solid fraction) */
@@ -1096,8 +1099,8 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                             ubn[id] = ub[id] - Uc * dt * (ub[id] - u0) / (0.5 * h);
                         }
             }
-        /* (c') QUICK + Crank-Nicolson (R20): explicit half E, the iteration for u~ with
-         * the ghosts of t^{n+1} at outflow faces, then the IB forcing of u~ */
+        /* (c') QUICK + Crank-Nicolson (R20): explicit half E, the iteration for u~ (ghosts
+         * with the outflow values of t^n), then the IB forcing of u~ */
         if (g->scheme == 1) {
 #pragma omp parallel for schedule(static)
             for (int c = 0; c < g->n_cubes; ++c) {
@@ -1113,17 +1116,20 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                                 N = conv_quick(g, bufs, comp, i, j, k, h);
                                 size_t id = cidx(B, c, i, j, k);
                                 cnE[comp][id] = vel[comp][id] + dt * (-0.5 * N + 0.5 * nu * L);
-                                cnA[comp][id] = vel[comp][id];
+                                cnA[comp][id] = 2.0 * cnE[comp][id] - vel[comp][id];
                             }
             }
-            for (int s = 0; s < g->n_sims; ++s) cndone[s] = 0;
+            for (int s = 0; s < g->n_sims; ++s) {
+                cndone[s] = 0;
+                cnprev[s] = 0.0;
+            }
             for (int kk = 0; kk < g->cn_max; ++kk) {
                 int alive = 0;
                 for (int s = 0; s < g->n_sims; ++s) alive |= !cndone[s];
                 if (!alive) break;
-                orc_fill_ghosts(g, cnA[0], 0, ubn, gu);
-                orc_fill_ghosts(g, cnA[1], 1, ubn, gv);
-                orc_fill_ghosts(g, cnA[2], 2, ubn, gw);
+                orc_fill_ghosts(g, cnA[0], 0, ub, gu);
+                orc_fill_ghosts(g, cnA[1], 1, ub, gv);
+                orc_fill_ghosts(g, cnA[2], 2, ub, gw);
 #pragma omp parallel for schedule(static)
                 for (int c = 0; c < g->n_cubes; ++c) {
                     int s = g->sim_of[c];
@@ -1165,7 +1171,11 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                         d2 += cnpart[2 * c];
                         u2 += cnpart[2 * c + 1];
                     }
-                    if (d2 <= g->cn_rtol * g->cn_rtol * u2) cndone[s] = 1;
+                    const double fl = 64.0 * 0x1p-53;  /* 64 unit roundoffs of FP64 */
+                    if (d2 <= g->cn_rtol * g->cn_rtol * u2 ||
+                        (kk >= 1 && d2 <= fl * fl * u2 && d2 >= 0.99 * cnprev[s]))
+                        cndone[s] = 1;
+                    cnprev[s] = d2;
                 }
                 for (int comp = 0; comp < 3; ++comp) {
                     double *tmp = cnA[comp];
@@ -1224,6 +1234,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                     }
             drag[3 * c] = -fx; drag[3 * c + 1] = -fy; drag[3 * c + 2] = -fz;
         }
+        }
         /* (c') particles (R19): U = I[u~] at every particle, F = (U_s - U) / dt, then
          * u* = u~ + dt P[F]; the force on the body is -sum F dV */
         if (P) {
@@ -1245,7 +1256,6 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                 for (int q = 0; q < np; ++q) pS[q] = g->dt[P->sim[q]] * pF[(size_t)comp * np + q];
                 orc_ib_spread(g, np, P->X, P->sim, pS, P->dV, vstar[comp]);
             }
-        }
         }
         /* (e) Poisson right-hand side from u* and the new outflow values */
         orc_rhs(g, us, vs, ws, ubn, b);
@@ -1331,7 +1341,7 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
     free(us); free(vs); free(ws); free(b); free(phi); free(bu); free(bv); free(bw);
     free(gu); free(gv); free(gw); free(ubn); free(drag); free(tt); free(st);
     free(pU); free(pF); free(pS); free(pdrag);
-    free(cnbuf); free(cnpart); free(cndone);
+    free(cnbuf); free(cnpart); free(cndone); free(cnprev);
     return status;
 }
 

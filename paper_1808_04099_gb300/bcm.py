@@ -19,6 +19,7 @@ BCM_OK, BCM_E_INVALID, BCM_E_CUDA, BCM_E_NOT_CONVERGED = 0, -1, -2, -3
 BCM_E_NONFINITE, BCM_E_TIMEOUT, BCM_E_BOUNDS = -4, -5, -6
 PREC_F64, PREC_F32_REFINE = 0, 1
 PRECOND_JACOBI, PRECOND_MULTIGRID = 0, 1
+SCHEME_AB2_CENTRAL, SCHEME_QUICK_CN = 0, 1
 (U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
@@ -28,6 +29,7 @@ EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_f
             "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
+            "bcm_set_momentum_scheme",
             "bcm_particles_bytes", "bcm_set_particles", "bcm_get_particles",
             "bcm_particle_sets", "bcm_ib_interpolate", "bcm_ib_spread",
             "bcm_last_error"]
@@ -108,6 +110,7 @@ def lib(build: bool = True):
         L.bcm_solve_pressure_static.argtypes = [P, P, P, C.c_double, C.c_int, P]
         L.bcm_profile.argtypes = [P, C.c_int]
         L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
+        L.bcm_set_momentum_scheme.argtypes = [P, C.c_int, C.c_double, C.c_int]
         L.bcm_particles_bytes.restype = C.c_size_t
         L.bcm_particles_bytes.argtypes = [P, C.c_int32]
         L.bcm_set_particles.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_size_t]
@@ -251,6 +254,11 @@ class Grid:
         _check(lib().bcm_apply_preconditioner(self._h, C.c_void_p(r.data_ptr()),
                                               C.c_void_p(z.data_ptr())))
         return z
+
+    def set_momentum_scheme(self, scheme: int, cn_rtol: float = 0.0, cn_max_iter: int = 0):
+        """SCHEME_AB2_CENTRAL (default) or SCHEME_QUICK_CN (0: library defaults)."""
+        _check(lib().bcm_set_momentum_scheme(self._h, int(scheme), float(cn_rtol),
+                                             int(cn_max_iter)))
 
     # ------------------------------------------------ Lagrangian particles
     def set_particles(self, parts):

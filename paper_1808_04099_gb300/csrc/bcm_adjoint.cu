@@ -462,6 +462,8 @@ extern "C" bcm_status bcm_adjoint_step(bcm_grid* grid, void* dev_adj, size_t byt
   if (!base.f64) return grid_fail(BCM_E_INVALID, "the adjoint runs on FP64 grids");
   if (base.part.n > 0)
     return grid_fail(BCM_E_INVALID, "the adjoint differentiates the solid-fraction IB, not particles");
+  if (base.scheme != 0)
+    return grid_fail(BCM_E_INVALID, "the adjoint differentiates the Adams-Bashforth step");
   if (bytes < bcm_adjoint_bytes(grid)) return grid_fail(BCM_E_INVALID, "adjoint workspace too small");
   const size_t n = (size_t)base.g.n_cubes * base.B * base.B * base.B;
   void* ubp = nullptr;

@@ -448,6 +448,7 @@ struct StepGraph {
   double inner_rtol = 0.0;
   int persistent_slabs = 0;
   int recycle = -1;
+  int gen = -1;        // the grid's launch generation the graph was captured at
   size_t kernels = 0;  // kernel nodes in the captured step
 };
 
@@ -474,6 +475,8 @@ struct bcm_grid {
   int recycle = 1;           // mixed + persistent: reliable updates instead of restarts
   int pcg_form = 0;          // PCG form of the last solve (PCG_*)
   int mg_ok = 0;             // the grid has a multigrid hierarchy (single-level)
+  int gen = 0;               // bumped when the kernels of a step change (geometry,
+                             // particles, momentum scheme): captured steps are redone
   KernelTimer timer;
   long long launch_count = 0;
   HostTables T;
@@ -678,6 +681,9 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   x.use_mg = 0;
   x.mg = MgDev{};
   x.part = PartDev{};
+  x.scheme = 0;
+  x.cn_rtol = g->f64 ? 1e-10 : 2e-8;
+  x.cn_max = 50;
   if (mgh.ok) {
     MgDev& D = x.mg;
     D.L = mgh.L;
@@ -753,6 +759,7 @@ extern "C" bcm_status bcm_field(bcm_grid* g, int field, void** dev_ptr, size_t* 
 extern "C" bcm_status bcm_set_geometry(bcm_grid* g, int sim, const bcm_body* bodies, int n_bodies,
                                        const double* inflow_modes) {
   if (!g || sim < 0 || sim >= g->desc.n_sims) return fail(BCM_E_INVALID, "bad grid or sim");
+  g->gen += 1;
   if (n_bodies < 0 || n_bodies > kMaxBodies)
     return fail(BCM_E_BOUNDS, "n_bodies must be in [0, %d]", kMaxBodies);
   if (n_bodies > 0 && !bodies) return fail(BCM_E_INVALID, "bodies is NULL");
@@ -1030,6 +1037,30 @@ bcm_status collect(bcm_grid* g, bcm_stats* out) {
 
 }  // namespace
 
+namespace {
+// The momentum sub-step: Adams-Bashforth + central in one launch, or QUICK +
+// Crank-Nicolson: explicit half, iterations read back every four launches, forcing.
+bcm_status momentum_substep(bcm_grid* g) {
+  Ctx& x = g->ctx;
+  if (x.scheme == 0) {
+    RUN(BCM_K_MOMENTUM, launch_momentum(x));
+    return BCM_OK;
+  }
+  RUN(BCM_K_MOMENTUM, launch_cn_explicit(x));
+  int it = 0;
+  while (it < x.cn_max) {
+    for (int m = 0; m < 4 && it < x.cn_max; ++m, ++it) RUN(BCM_K_MOMENTUM, launch_cn_iter(x));
+    int done = 0;
+    CUDA_TRY(cudaMemcpyAsync(&done, g->ws + g->L.flags + 2 * sizeof(int), sizeof(int),
+                             cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (done) break;
+  }
+  RUN(BCM_K_MOMENTUM, launch_cn_finish(x));
+  return BCM_OK;
+}
+}  // namespace
+
 extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_iter,
                                bcm_stats* stats) {
   if (!g) return fail(BCM_E_INVALID, "grid is NULL");
@@ -1042,7 +1073,10 @@ extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_it
   const bool particles = x.part.n > 0;
   for (int n = 0; n < n_steps; ++n) {
     if (moving && !particles) RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -2));
-    RUN(BCM_K_MOMENTUM, launch_momentum(x));
+    {
+      bcm_status sm = momentum_substep(g);
+      if (sm != BCM_OK) return sm;
+    }
     if (particles) {  // forcing by the Lagrangian particles: force, then spreading
       RUN(BCM_K_IB, launch_ib_force(x));
       g->launch_count += 1;
@@ -1082,7 +1116,13 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
   const bool particles = x.part.n > 0;
   if (moving && !particles) CUDA_TRY(launch_solid_fraction(x, -2));
-  CUDA_TRY(launch_momentum(x));
+  if (x.scheme == 0) {
+    CUDA_TRY(launch_momentum(x));
+  } else {  // QUICK + Crank-Nicolson: the full iteration budget (converged sims return)
+    CUDA_TRY(launch_cn_explicit(x));
+    for (int it = 0; it < x.cn_max; ++it) CUDA_TRY(launch_cn_iter(x));
+    CUDA_TRY(launch_cn_finish(x));
+  }
   if (particles) CUDA_TRY(launch_ib_force(x));
   CUDA_TRY(launch_rhs(x));
   CUDA_TRY(launch_solve_begin(x));
@@ -1124,7 +1164,7 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
   if (!sg.exec || sg.rtol != rtol || sg.max_iter != max_iter || sg.cycles != cycles ||
       sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle ||
       sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass ||
-      sg.resident != g->ctx.resident) {
+      sg.resident != g->ctx.resident || sg.gen != g->gen) {
     if (sg.exec) CUDA_TRY(cudaGraphExecDestroy(sg.exec));
     if (sg.graph) CUDA_TRY(cudaGraphDestroy(sg.graph));
     sg.exec = nullptr;
@@ -1160,6 +1200,7 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     sg.slabs_p = g->ctx.slabs_p;
     sg.single_pass = g->ctx.single_pass;
     sg.resident = g->ctx.resident;
+    sg.gen = g->gen;
   }
   for (int n = 0; n < n_steps; ++n) {
     CUDA_TRY(cudaGraphLaunch(sg.exec, g->stream));
@@ -1256,6 +1297,28 @@ extern "C" bcm_status bcm_fill_halo(bcm_grid* g, int field, int kind, double* de
   return BCM_OK;
 }
 
+extern "C" bcm_status bcm_set_momentum_scheme(bcm_grid* g, int scheme, double cn_rtol,
+                                              int cn_max_iter) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (scheme != BCM_SCHEME_AB2_CENTRAL && scheme != BCM_SCHEME_QUICK_CN)
+    return fail(BCM_E_INVALID, "unknown momentum scheme %d", scheme);
+  if (!(cn_rtol >= 0) || cn_max_iter < 0) return fail(BCM_E_INVALID, "cn_rtol, cn_max_iter >= 0");
+  Ctx& x = g->ctx;
+  if (scheme == BCM_SCHEME_AB2_CENTRAL && x.scheme == BCM_SCHEME_QUICK_CN) {
+    // N^{n-1} was not kept under Crank-Nicolson: the next AB2 step starts with Euler
+    const int one = 1;
+    for (int s = 0; s < g->desc.n_sims; ++s)
+      CUDA_TRY(cudaMemcpyAsync(g->ws + g->L.ss + sizeof(SimState) * s + offsetof(SimState, ab2_restart),
+                               &one, sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+  }
+  x.scheme = scheme;
+  x.cn_rtol = cn_rtol > 0 ? cn_rtol : (g->f64 ? 1e-10 : 2e-8);
+  x.cn_max = cn_max_iter > 0 ? cn_max_iter : 50;
+  g->gen += 1;  // a captured step holds the old momentum launches
+  return BCM_OK;
+}
+
 // ---- Lagrangian-particle immersed boundary (bcm_ib.cu)
 
 namespace {
@@ -1328,6 +1391,7 @@ extern "C" bcm_status bcm_set_particles(bcm_grid* g, int32_t n, const double* xy
     return fail(BCM_E_INVALID, "Lagrangian particles need a single-level grid");
   if (n < 0) return fail(BCM_E_INVALID, "n_particles must be >= 0");
   Ctx& x = g->ctx;
+  g->gen += 1;
   if (n == 0) {  // back to the solid-fraction IB
     x.part = PartDev{};
     RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -1));

@@ -77,6 +77,10 @@ struct SimState {
   int p_off;           // buffer offset of the previous launch's last search direction
   int s_off;           // single-pass PCG: buffer offset of the last A p
   double phi_last;     // single-pass PCG: <p, A p> of the last direction
+  double cn_d2prev;    // QUICK + Crank-Nicolson: ||update||^2 of the previous iteration
+  int cn_iter;         //   iterations of this step's momentum solve
+  int cn_done;         //   that solve has converged (or hit its iteration limit)
+  int ab2_restart;     // the next Adams-Bashforth step takes N^{n-1} := N^n
 };
 
 enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 5,
@@ -84,7 +88,9 @@ enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 
        // persistent PCG: three rotating slots (iteration mod 3) per dot product
        ACC_SLOT_PQ = 8, ACC_SLOT_RZ = 11, ACC_SLOT_RR = 14,
        // single-pass PCG: <r,u>, <w,u>, <u,s_prev>, <r,r>
-       ACC_SLOT_G = 8, ACC_SLOT_D = 11, ACC_SLOT_E = 14, ACC_SLOT_R = 17, ACC_NSLOT = 12 };
+       ACC_SLOT_G = 8, ACC_SLOT_D = 11, ACC_SLOT_E = 14, ACC_SLOT_R = 17, ACC_NSLOT = 12,
+       // QUICK + Crank-Nicolson iteration: ||u^(k+1) - u^(k)||^2, ||u^(k+1)||^2
+       ACC_CN_D = 20, ACC_CN_U = 21 };
 
 // Device view of the grid tables, passed by value to every kernel.
 struct DevGrid {

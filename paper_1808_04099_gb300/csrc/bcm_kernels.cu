@@ -257,7 +257,7 @@ __global__ __launch_bounds__(NT) void k_momentum(
   const double hd = cell_h<B>(g, c);
   const T h = T(hd), ih = T(1.0 / hd), ih2 = T(1.0 / (hd * hd));
   const T dt = T(sp.dt), nu = T(sp.nu);
-  const bool first = g.ss[s].step == 0;
+  const bool first = g.ss[s].step == 0 || g.ss[s].ab2_restart != 0;
   const bool has_phi = g.near[c] != 0;
   const double t = g.ss[s].step * sp.dt;
   const T* Sf[3] = {S0, S1, S2};
@@ -335,6 +335,327 @@ __global__ __launch_bounds__(NT) void k_momentum(
     }
   }
   if (has_phi) {  // drag: force of the fluid on the body = -sum f V, f = du/dt
+    double vals[3] = {double(fsum[0]), double(fsum[1]), double(fsum[2])};
+    block_sum<NT, 3>(vals, red);
+    if (threadIdx.x == 0) {
+      const double scale = -hd * hd * hd / sp.dt;
+      for (int e = 0; e < 3; ++e) atomicAdd(&g.ss[s].drag_acc[e], vals[e] * scale);
+    }
+  }
+}
+
+// ===========================================================================
+// QUICK + Crank-Nicolson momentum (Eq. substep1 with the QUICK convection the paper
+// names; R20):
+//   N_c = (1/h) sum_d [U+ q+ - U- q-], U± the central face velocities, q± the QUICK
+//         face values 6/8 C + 3/8 D - 1/8 U (C upwind, D downwind, U upwind of C);
+//   u^(k+1) = (E - dt/2 N(u^(k)) + dt nu/2 (sum of the 6 neighbours)/h^2) / (1 + 3 a),
+//   E = u^n + dt (-N(u^n) + nu L(u^n))/2, a = dt nu / h^2, from u^(0) = 2 E - u^n,
+// until ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| per sim, or the update has reached the
+// rounding floor of the arithmetic (<= 64 eps ||u^(k+1)||) and stopped shrinking (its
+// square >= 0.99 of the previous one), or cn_max.
+// The kernels iterate on the increment d = u - u^n, which is what FP32 can hold to its
+// own precision (FP32 iterates of u itself settle ~3 roundings of |u| away from the
+// fixed point):
+//   d^(k+1) = (E' - dt/2 N(u^n + d^(k)) + a/2 (sum of the 6 neighbours of d^(k))) / (1 + 3a),
+//   E' = dt (-N(u^n)/2 + nu L(u^n)),  d^(0) = dt (-N(u^n) + nu L(u^n)),
+// the same iteration in exact arithmetic.  Ghosts: u^n + d by the halo rules with the
+// outflow values of t^n; d alone by the same rules made homogeneous (a boundary value
+// minus the mirror cell becomes minus the mirror).  QUICK reads two cells upstream, so
+// the slabs carry the paper's two ghost layers.  Storage: u^n stays in u, E' in u*, d
+// alternates between two sets of PCG scratch vectors (free during the momentum
+// sub-step) by the parity of the sim's iteration count; the last launch writes
+// u* = u~ + phi (u_s - u~) and advances the outflow values to t^{n+1}.
+// ===========================================================================
+template <int B, int KS>
+struct Slab2 {  // planes z0-2 .. z0+KS+1, each (B+4)^2 with a two-cell x/y ring
+  static constexpr int P = B + 4;
+  static constexpr int N = (KS + 4) * P * P;
+  __device__ __forceinline__ static int at(int i, int j, int kk) {
+    return (kk * P + (j + 2)) * P + (i + 2);
+  }
+};
+
+template <int B, int KS, int NT, class T, class Val, class Bc>
+__device__ __forceinline__ void stage_slab2(T* __restrict__ S, const DevGrid& g, int c, int z0,
+                                            const Val& val, const Bc& bc) {
+  using SL = Slab2<B, KS>;
+  constexpr int BB = B * B;
+  for (int idx = threadIdx.x; idx < (KS + 4) * BB; idx += NT) {
+    const int kk = idx / BB, rem = idx - kk * BB, j = rem / B, i = rem - j * B;
+    const int k = z0 - 2 + kk;
+    T v;
+    if (k < 0) v = halo_value<B, T>(g, c, 4, i, j, -1 - k, val, bc);
+    else if (k >= B) v = halo_value<B, T>(g, c, 5, i, j, k - B, val, bc);
+    else v = val(c, (k * B + j) * B + i);
+    S[SL::at(i, j, kk)] = v;
+  }
+  for (int idx = threadIdx.x; idx < 8 * KS * B; idx += NT) {
+    const int f = idx / (2 * KS * B), rem = idx - f * (2 * KS * B), layer = rem / (KS * B);
+    const int rem2 = rem - layer * (KS * B), kk = rem2 / B, t = rem2 - kk * B;
+    const T v = halo_value<B, T>(g, c, f, t, z0 + kk, layer, val, bc);
+    const int n = (f & 1) ? B + layer : -1 - layer;
+    S[f < 2 ? SL::at(n, t, kk + 2) : SL::at(t, n, kk + 2)] = v;
+  }
+}
+
+// interior values of u^n + d
+template <class T>
+struct SumVal {
+  const T* a;
+  const T* d;
+  int B3;
+  __device__ __forceinline__ T operator()(int c, int cell) const {
+    const size_t i = (size_t)c * B3 + cell;
+    return a[i] + d[i];
+  }
+};
+
+// ghost rule of an increment: the velocity rules (R8) without their boundary values
+struct IncrementBC {
+  const SimParams* sp;
+  int comp;
+  template <class T>
+  __device__ __forceinline__ T operator()(int f, int, int, T d0) const {
+    return (sp->bc[f] == BC_SLIP && comp != (f >> 1)) ? d0 : -d0;
+  }
+};
+
+template <class T>
+__device__ __forceinline__ T quick_face(T pC, T pD, T pU) {
+  return T(0.75) * pC + T(0.375) * pD - T(0.125) * pU;
+}
+
+// QUICK convection of component comp at tile position o (axis strides off[])
+template <class T>
+__device__ __forceinline__ T conv_quick(const T* const (&Sf)[3], int comp, int o,
+                                        const int (&off)[3], T ih) {
+  const T* Sc = Sf[comp];
+  T N = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T* Sd = Sf[d];
+    const int e = off[d];
+    const T Up = T(0.5) * (Sd[o] + Sd[o + e]), Um = T(0.5) * (Sd[o - e] + Sd[o]);
+    const T fp = Up >= T(0) ? quick_face(Sc[o], Sc[o + e], Sc[o - e])
+                            : quick_face(Sc[o + e], Sc[o], Sc[o + 2 * e]);
+    const T fm = Um >= T(0) ? quick_face(Sc[o - e], Sc[o], Sc[o - 2 * e])
+                            : quick_face(Sc[o], Sc[o - e], Sc[o + e]);
+    N += Up * fp - Um * fm;
+  }
+  return N * ih;
+}
+
+template <int B, int KS, int NT, class T>
+__global__ __launch_bounds__(NT) void k_cn_explicit(DevGrid g, const T* __restrict__ u,
+                                                    const T* __restrict__ v,
+                                                    const T* __restrict__ w, T* __restrict__ e0,
+                                                    T* __restrict__ e1, T* __restrict__ e2,
+                                                    T* __restrict__ d0, T* __restrict__ d1,
+                                                    T* __restrict__ d2, const T* __restrict__ ub) {
+  using SL = Slab2<B, KS>;
+  constexpr int B3 = B * B * B, NSL = B / KS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + SL::N;
+  T* S2 = S1 + SL::N;
+  const int c = blockIdx.x / NSL, z0 = (blockIdx.x % NSL) * KS;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  if (blockIdx.x == 0) {  // a new momentum solve for every sim
+    for (int q = threadIdx.x; q < g.n_sims; q += NT) {
+      g.ss[q].cn_iter = 0;
+      g.ss[q].cn_done = 0;
+      g.ss[q].cn_d2prev = 0.0;
+    }
+    if (threadIdx.x == 0) g.flags[2] = 0;
+  }
+  {
+    VelocityBC<B, T> b0{&g, &sp, ub, c, 0}, b1{&g, &sp, ub, c, 1}, b2{&g, &sp, ub, c, 2};
+    stage_slab2<B, KS, NT>(S0, g, c, z0, FieldVal<T>{u, B3}, b0);
+    stage_slab2<B, KS, NT>(S1, g, c, z0, FieldVal<T>{v, B3}, b1);
+    stage_slab2<B, KS, NT>(S2, g, c, z0, FieldVal<T>{w, B3}, b2);
+  }
+  __syncthreads();
+  const double hd = cell_h<B>(g, c);
+  const T ih = T(1.0 / hd), ih2 = T(1.0 / (hd * hd)), dt = T(sp.dt), nu = T(sp.nu);
+  const T* const Sf[3] = {S0, S1, S2};
+  T* Es[3] = {e0, e1, e2};
+  T* Ds[3] = {d0, d1, d2};
+  const int off[3] = {1, SL::P, SL::P * SL::P};
+  for (int q = threadIdx.x; q < KS * B * B; q += NT) {
+    const int kk = q / (B * B), rem = q - kk * B * B, j = rem / B, i = rem - j * B;
+    const size_t gi = (size_t)c * B3 + ((z0 + kk) * B + j) * B + i;
+    const int o = SL::at(i, j, kk + 2);
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const T* Sc = Sf[comp];
+      const T u0 = Sc[o];
+      T L = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) L += Sc[o + off[d]] - T(2) * u0 + Sc[o - off[d]];
+      const T N = conv_quick<T>(Sf, comp, o, off, ih);
+      const T DL = dt * nu * (L * ih2);
+      Es[comp][gi] = T(-0.5) * dt * N + DL;  // E' = E - u^n + a/2 (sum nb - 6 u^n)
+      Ds[comp][gi] = -dt * N + DL;           // forward-Euler predictor of d
+    }
+  }
+}
+
+// One iteration on the increment; da / db are the two increment sets, read from the
+// one the sim's iteration parity selects (k even: da).  The last block takes each
+// sim's decision.
+template <int B, int KS, int NT, class T>
+__global__ __launch_bounds__(NT) void k_cn_iter(DevGrid g, const T* __restrict__ u,
+                                                const T* __restrict__ v, const T* __restrict__ w,
+                                                T* da0, T* da1, T* da2, T* db0, T* db1, T* db2,
+                                                const T* __restrict__ e0,
+                                                const T* __restrict__ e1,
+                                                const T* __restrict__ e2,
+                                                const T* __restrict__ ub, double rtol2, int cn_max) {
+  using SL = Slab2<B, KS>;
+  constexpr int B3 = B * B * B, NSL = B / KS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S0 = reinterpret_cast<T*>(smem_raw);  // u^n + d, three components
+  T* D0 = S0 + 3 * SL::N;                  // d, three components
+  __shared__ double red[2 * 32];
+  const int c = blockIdx.x / NSL, z0 = (blockIdx.x % NSL) * KS;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  SimState& st = g.ss[s];
+  const bool active = st.cn_done == 0;
+  double vals[2] = {0.0, 0.0};
+  if (active) {
+    const bool odd = (st.cn_iter & 1) != 0;
+    const T* src[3] = {odd ? db0 : da0, odd ? db1 : da1, odd ? db2 : da2};
+    T* dst[3] = {odd ? da0 : db0, odd ? da1 : db1, odd ? da2 : db2};
+    const T* un[3] = {u, v, w};
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      VelocityBC<B, T> vb{&g, &sp, ub, c, comp};
+      stage_slab2<B, KS, NT>(S0 + comp * SL::N, g, c, z0, SumVal<T>{un[comp], src[comp], B3}, vb);
+      stage_slab2<B, KS, NT>(D0 + comp * SL::N, g, c, z0, FieldVal<T>{src[comp], B3},
+                             IncrementBC{&sp, comp});
+    }
+    __syncthreads();
+    const double hd = cell_h<B>(g, c);
+    const T ih = T(1.0 / hd), dt = T(sp.dt);
+    const T half_a = T(0.5 * sp.dt * sp.nu / (hd * hd));
+    const T den = T(1.0 + 3.0 * sp.dt * sp.nu / (hd * hd));
+    const T* const Sf[3] = {S0, S0 + SL::N, S0 + 2 * SL::N};
+    const T* Es[3] = {e0, e1, e2};
+    const int off[3] = {1, SL::P, SL::P * SL::P};
+    T dd2 = T(0), uu2 = T(0);
+    for (int q = threadIdx.x; q < KS * B * B; q += NT) {
+      const int kk = q / (B * B), rem = q - kk * B * B, j = rem / B, i = rem - j * B;
+      const size_t gi = (size_t)c * B3 + ((z0 + kk) * B + j) * B + i;
+      const int o = SL::at(i, j, kk + 2);
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        const T* Dc = D0 + comp * SL::N;
+        T sn = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sn += Dc[o + off[d]] + Dc[o - off[d]];
+        const T N = conv_quick<T>(Sf, comp, o, off, ih);
+        const T dn = (Es[comp][gi] - T(0.5) * dt * N + half_a * sn) / den;
+        const T ch = dn - Dc[o];
+        const T ut = un[comp][gi] + dn;
+        dd2 += ch * ch;
+        uu2 += ut * ut;
+        dst[comp][gi] = dn;
+      }
+    }
+    vals[0] = double(dd2);
+    vals[1] = double(uu2);
+  }
+  block_sum<NT, 2>(vals, red);
+  if (threadIdx.x == 0 && active) {
+    acc_add(st, ACC_CN_D, vals[0]);
+    acc_add(st, ACC_CN_U, vals[1]);
+  }
+  if (last_block(g.counter)) {
+    int alive = 0;
+    for (int q = threadIdx.x; q < g.n_sims; q += NT) {
+      SimState& t = g.ss[q];
+      const double d2 = acc_take(t, ACC_CN_D), u2 = acc_take(t, ACC_CN_U);
+      if (t.cn_done) continue;
+      // 64 unit roundoffs of the iteration's arithmetic
+      const double fl = 64.0 * (sizeof(T) == 8 ? 0x1p-53 : 0x1p-24);
+      const bool stalled = t.cn_iter >= 1 && d2 <= fl * fl * u2 && d2 >= 0.99 * t.cn_d2prev;
+      t.cn_iter += 1;
+      t.cn_d2prev = d2;
+      if (d2 <= rtol2 * u2 || stalled || t.cn_iter >= cn_max || !isfinite(d2)) t.cn_done = 1;
+      alive |= !t.cn_done;
+    }
+    alive = __syncthreads_or(alive);
+    if (threadIdx.x == 0) g.flags[2] = !alive;
+  }
+}
+
+// u* = u~ + phi (u_s - u~) with u~ = u^n + d (the sim's last increment), the drag (R5),
+// and the convective outflow values advanced to t^{n+1} from u^n (R8).
+template <int B, int NT, class T>
+__global__ __launch_bounds__(NT) void k_cn_finish(DevGrid g, const T* __restrict__ u,
+                                                  const T* __restrict__ v,
+                                                  const T* __restrict__ w, const T* da0,
+                                                  const T* da1, const T* da2, const T* db0,
+                                                  const T* db1, const T* db2, T* us, T* vs,
+                                                  T* ws, const T* __restrict__ phi,
+                                                  const unsigned char* __restrict__ bid,
+                                                  T* __restrict__ ub) {
+  constexpr int B3 = B * B * B;
+  __shared__ double red[3 * 32];
+  const int c = blockIdx.x;
+  const int s = g.sim[c];
+  const SimParams& sp = g.sp[s];
+  // iteration k writes the second set (db) when k is even: the last one is cn_iter - 1
+  const bool last_even = ((g.ss[s].cn_iter - 1) & 1) == 0;
+  const T* dl[3] = {last_even ? db0 : da0, last_even ? db1 : da1, last_even ? db2 : da2};
+  const T* un[3] = {u, v, w};
+  T* outs[3] = {us, vs, ws};
+  const bool has_phi = g.near[c] != 0;
+  const double t = g.ss[s].step * sp.dt;
+  T fsum[3] = {T(0), T(0), T(0)};
+  for (int q = threadIdx.x; q < B3; q += NT) {
+    const int k = q / (B * B), j = (q / B) % B, i = q % B;
+    const size_t gi = (size_t)c * B3 + q;
+    T ph = T(0);
+    T usb[3] = {T(0), T(0), T(0)};
+    if (has_phi) {
+      ph = phi[gi];
+      if (ph != T(0)) {
+        const bcm_body& bd = sp.bodies[bid[gi]];
+        double x[3] = {centre<B>(g, c, 0, i), centre<B>(g, c, 1, j), centre<B>(g, c, 2, k)};
+        double r[3];
+        for (int e = 0; e < 3; ++e) r[e] = x[e] - (bd.center[e] + bd.vel[e] * t);
+        usb[0] = T(bd.vel[0] + bd.omega[1] * r[2] - bd.omega[2] * r[1]);
+        usb[1] = T(bd.vel[1] + bd.omega[2] * r[0] - bd.omega[0] * r[2]);
+        usb[2] = T(bd.vel[2] + bd.omega[0] * r[1] - bd.omega[1] * r[0]);
+      }
+    }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const T ut = un[comp][gi] + dl[comp][gi];
+      const T du = ph * (usb[comp] - ut);
+      outs[comp][gi] = ut + du;
+      fsum[comp] += du;
+    }
+  }
+  // convective outflow: u_b^{n+1} = u_b - U_c dt (u_b - u_0) / (h/2), u_0 from u^n
+  const double hd = cell_h<B>(g, c);
+  for (int f = 0; f < 6; ++f) {
+    const int sl = g.slot[6 * c + f];
+    if (sl < 0) continue;
+    const int d = f >> 1, side = f & 1;
+    const T coef = T(sp.uconv * sp.dt / (0.5 * hd));
+    for (int q = threadIdx.x; q < 3 * B * B; q += NT) {
+      const int comp = q / (B * B), rem = q - comp * B * B, bb = rem / B, a = rem - bb * B;
+      const T u0 = un[comp][(size_t)c * B3 + cell_of<B>(d, side ? B - 1 : 0, a, bb)];
+      T* pb = &ub[((size_t)(sl * 3 + comp) * B + bb) * B + a];
+      *pb = *pb - coef * (*pb - u0);
+    }
+  }
+  if (has_phi) {
     double vals[3] = {double(fsum[0]), double(fsum[1]), double(fsum[2])};
     block_sum<NT, 3>(vals, red);
     if (threadIdx.x == 0) {
@@ -444,6 +765,7 @@ __global__ void k_step_end(DevGrid g) {
     t.div_num = dn;
     t.div_den = dd;
     t.step += 1;
+    t.ab2_restart = 0;
   }
 }
 
@@ -592,6 +914,63 @@ static cudaError_t momentum_t(const Ctx& x) {
 cudaError_t launch_momentum(const Ctx& x) {
   if (x.f64) return momentum_t<double, double>(x);
   return x.lag_bf16 ? momentum_t<float, __nv_bfloat16>(x) : momentum_t<float, float>(x);
+}
+
+// QUICK + Crank-Nicolson: slabs of 2 planes for 16^3 cubes (six (B+4)^2 x 6 tiles)
+template <int B>
+constexpr int cn_slab() { return B == 16 ? 2 : B; }
+
+template <class T>
+static cudaError_t cn_explicit_t(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>(), KS = cn_slab<B>();
+    const size_t sm = 3 * sizeof(T) * Slab2<B, KS>::N;
+    auto kern = k_cn_explicit<B, KS, NT, T>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(
+        x.g, (const T*)x.f.u, (const T*)x.f.v, (const T*)x.f.w, (T*)x.f.us, (T*)x.f.vs,
+        (T*)x.f.ws, (T*)x.f.w1, (T*)x.f.s0, (T*)x.f.s1, (const T*)x.f.ub);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_cn_explicit(const Ctx& x) {
+  return x.f64 ? cn_explicit_t<double>(x) : cn_explicit_t<float>(x);
+}
+
+template <class T>
+static cudaError_t cn_iter_t(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>(), KS = cn_slab<B>();
+    const size_t sm = 6 * sizeof(T) * Slab2<B, KS>::N;
+    auto kern = k_cn_iter<B, KS, NT, T>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(
+        x.g, (const T*)x.f.u, (const T*)x.f.v, (const T*)x.f.w, (T*)x.f.w1, (T*)x.f.s0,
+        (T*)x.f.s1, (T*)x.f.r, (T*)x.f.p0, (T*)x.f.p1, (const T*)x.f.us, (const T*)x.f.vs,
+        (const T*)x.f.ws, (const T*)x.f.ub, x.cn_rtol * x.cn_rtol, x.cn_max);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_cn_iter(const Ctx& x) {
+  return x.f64 ? cn_iter_t<double>(x) : cn_iter_t<float>(x);
+}
+
+template <class T>
+static cudaError_t cn_finish_t(const Ctx& x) {
+  BCM_DISPATCH_B(x.B, {
+    constexpr int NT = threads_for<B>();
+    k_cn_finish<B, NT, T><<<x.g.n_cubes, NT, 0, x.stream>>>(
+        x.g, (const T*)x.f.u, (const T*)x.f.v, (const T*)x.f.w, (const T*)x.f.w1,
+        (const T*)x.f.s0, (const T*)x.f.s1, (const T*)x.f.r, (const T*)x.f.p0,
+        (const T*)x.f.p1, (T*)x.f.us, (T*)x.f.vs, (T*)x.f.ws, (const T*)x.f.phi, x.f.bid,
+        (T*)x.f.ub);
+  });
+  return cudaGetLastError();
+}
+cudaError_t launch_cn_finish(const Ctx& x) {
+  return x.f64 ? cn_finish_t<double>(x) : cn_finish_t<float>(x);
 }
 
 template <class T>

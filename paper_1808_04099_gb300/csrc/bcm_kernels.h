@@ -95,11 +95,19 @@ struct Ctx {
   int use_mg;      // PCG preconditioner: 0 Jacobi, 1 geometric multigrid
   MgDev mg;
   PartDev part;    // Lagrangian particles (part.n > 0: particle IB, no solid fraction)
+  int scheme;       // momentum: 0 Adams-Bashforth + central, 1 QUICK + Crank-Nicolson
+  double cn_rtol;   // Crank-Nicolson iteration: relative update at which a sim stops
+  int cn_max;       //   and its iteration limit per step
   cudaStream_t stream;
 };
 
 cudaError_t launch_solid_fraction(const Ctx& x, int sim_filter);
 cudaError_t launch_momentum(const Ctx& x);
+// QUICK + Crank-Nicolson momentum: explicit half and outflow update, one iteration of
+// the implicit half (sims that converged return at once), IB forcing of the result.
+cudaError_t launch_cn_explicit(const Ctx& x);
+cudaError_t launch_cn_iter(const Ctx& x);
+cudaError_t launch_cn_finish(const Ctx& x);
 cudaError_t launch_rhs(const Ctx& x);
 cudaError_t launch_bmean(const Ctx& x);
 cudaError_t launch_solve_begin(const Ctx& x);
