@@ -468,6 +468,45 @@ def gpu_arm(args, ws, rank, local):
                      "ib_us_per_step": 1e3 * kl["ib"]["total_ms"] / kprof_steps if "ib" in kl else None,
                      "kernels": kl}
 
+    # ---- the same step with the paper's production momentum scheme: QUICK convection and
+    # Crank-Nicolson, iterated per step (mixed: on the FP32 increment to its rounding
+    # floor; FP64: to 1e-10)
+    qcn = {}
+    for name, prec in (("mixed", bcm.PREC_F32_REFINE), ("fp64", bcm.PREC_F64)):
+        gq = bcm.Grid(spec, prec, device=dev)
+        gq.load_state(state)
+        gq.set_momentum_scheme(bcm.SCHEME_QUICK_CN)
+        for _ in range(args.warmup):
+            gq.step(1, rtol=RTOL, stats=False)
+        msq = timed_steps(gq, args.steps, gq.stream)
+        stq = gq.step(0, rtol=RTOL)[0]
+        gq.profile(True)
+        itq, cnq = 0, 0
+        for _ in range(kprof_steps):
+            sq = gq.step(1, rtol=RTOL)[0]
+            itq += sq["cg_iters"]
+            cnq += sq["cn_iters"]
+        profq, _ = gq.profile_read(reset=True)
+        gq.profile(False)
+        del gq
+        msq = max_over_ranks(msq, ws)
+        kq = kernel_table(profq, n, prec == bcm.PREC_F64, phi_frac, itq)
+        Sq = 8 if prec == bcm.PREC_F64 else 4
+        # momentum class per step: explicit half (u^n in; E', d^(0) out: 9 S), every
+        # iteration (u^n, d, E' in; d out: 12 S), the last launch (u^n, d, phi in; u* out,
+        # plus the outflow values: 10 S)
+        mom_ms = kq["momentum"]["total_ms"] / kprof_steps
+        mom_bytes = (19 + 12 * cnq / kprof_steps) * Sq * n
+        qcn[name] = {"value": n * args.steps / (msq / 1e3) * (ws if ws > 1 else 1),
+                     "unit": "cell-updates/s", "ms_per_step": msq / args.steps,
+                     "cn_iters_per_step": cnq / kprof_steps,
+                     "cg_iters_last_step": stq["cg_iters"],
+                     "rel_resid_last_step": stq["rel_resid"],
+                     "momentum_ms_per_step": mom_ms,
+                     "momentum_GBps": mom_bytes / (mom_ms / 1e3) / 1e9,
+                     "momentum_frac_of_hbm": mom_bytes / (mom_ms / 1e3) / 1e9 / peak,
+                     "kernels": kq}
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -498,6 +537,8 @@ def gpu_arm(args, ws, rank, local):
                                 "Jacobi-PCG hot path): steps issued from the host, each PCG "
                                 "iteration one replayed CUDA graph; same workload and "
                                 "residual"),
+            "quick_cn": dict(qcn, note="QUICK convection + Crank-Nicolson momentum (a NEXT "
+                                       "row beyond the hot path), same workload and residual"),
             "lagrangian": dict(lag, note="Lagrangian-particle IB (a NEXT row beyond the hot "
                                          "path): the mixed Jacobi-PCG step with the sphere's "
                                          "surface particles in place of the solid fraction"),
@@ -532,7 +573,11 @@ def ncu_case(args):
         g.set_launch(1, 1, persistent=2)
     if args.ncu_mg:
         g.set_preconditioner(bcm.PRECOND_MULTIGRID)
+    if args.ncu_cn:
+        g.set_momentum_scheme(bcm.SCHEME_QUICK_CN)
     g.load_state(W.initial_state(spec))
+    if args.ncu_particles:
+        g.set_particles(W.surface_particles(spec))
     if args.ncu_iters:
         st = g.step(1, rtol=RTOL)
         # one inner solve whose target is out of reach: exactly ncu_iters iterations
@@ -564,6 +609,10 @@ def main():
                     help="with --ncu-case: the single-reduction persistent PCG")
     ap.add_argument("--ncu-mg", action="store_true",
                     help="with --ncu-case: the multigrid-preconditioned PCG")
+    ap.add_argument("--ncu-cn", action="store_true",
+                    help="with --ncu-case: QUICK + Crank-Nicolson momentum")
+    ap.add_argument("--ncu-particles", action="store_true",
+                    help="with --ncu-case: the Lagrangian-particle IB")
     ap.add_argument("--recycle", type=int, default=-1,
                     help="mixed mode: 1 reliable updates across cycles, 0 restarts (default: library)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,

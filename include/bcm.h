@@ -121,7 +121,8 @@ typedef struct {
                               1 persistent streaming, 2 persistent single-reduction,
                               3 persistent with the state on chip, 4 multigrid-
                               preconditioned (two launches and a V-cycle) */
-    int32_t reserved;
+    int32_t cn_iters;      /* QUICK + Crank-Nicolson: iterations of the last momentum
+                              sub-step (0 with Adams-Bashforth) */
 } bcm_stats;
 
 /* Bytes of device workspace the grid needs (fields, solver vectors, tables).

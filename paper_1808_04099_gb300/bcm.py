@@ -57,13 +57,13 @@ class Stats(C.Structure):
     _fields_ = [("cg_iters", C.c_int32), ("refine_cycles", C.c_int32), ("steps", C.c_int32),
                 ("converged", C.c_int32), ("rel_resid", C.c_double), ("div_rel", C.c_double),
                 ("drag", C.c_double * 3), ("umax", C.c_double), ("pcg_form", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("cn_iters", C.c_int32)]
 
     def as_dict(self):
         return {"cg_iters": self.cg_iters, "refine_cycles": self.refine_cycles,
                 "steps": self.steps, "converged": self.converged, "rel_resid": self.rel_resid,
                 "div_rel": self.div_rel, "drag": list(self.drag), "umax": self.umax,
-                "pcg_form": self.pcg_form}
+                "pcg_form": self.pcg_form, "cn_iters": self.cn_iters}
 
 
 class BCMError(RuntimeError):

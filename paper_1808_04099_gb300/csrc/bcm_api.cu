@@ -1027,6 +1027,7 @@ bcm_status collect(bcm_grid* g, bcm_stats* out) {
     memcpy(&um, &t.umax_bits, sizeof um);
     o.umax = um;
     o.pcg_form = g->pcg_form;
+    o.cn_iters = g->ctx.scheme ? t.cn_iter : 0;
     if (t.nonfinite) st = BCM_E_NONFINITE;
     else if (!t.converged && st == BCM_OK) st = BCM_E_NOT_CONVERGED;
   }
