@@ -73,6 +73,12 @@ def lib():
         L.orc_convection_quick.argtypes = [P] * 8
         L.orc_set_scheme.argtypes = [P, C.c_int, C.c_double, C.c_int]
         L.orc_set_scheme.restype = C.c_int
+        L.orc_dwt3_forward.argtypes = [C.c_int, P]
+        L.orc_dwt3_inverse.argtypes = [C.c_int, P]
+        L.orc_wavelet_compress.argtypes = [C.c_int, C.c_int, P, C.c_double, P, C.c_long]
+        L.orc_wavelet_compress.restype = C.c_long
+        L.orc_wavelet_decompress.argtypes = [P, C.c_long, P]
+        L.orc_wavelet_decompress.restype = C.c_int
         L.orc_delta3.argtypes = [C.c_double]
         L.orc_delta3.restype = C.c_double
         L.orc_ib_interpolate.argtypes = [P, P, C.c_int, P, P, P]
@@ -87,6 +93,34 @@ def lib():
 
 def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def dwt3(x, B: int, inverse: bool = False) -> np.ndarray:
+    """The per-cube 3-D CDF 5/3 transform (R21) of one cube of B^3 values."""
+    y = np.ascontiguousarray(x, np.float64).copy()
+    (lib().orc_dwt3_inverse if inverse else lib().orc_dwt3_forward)(B, _p(y))
+    return y
+
+
+def wavelet_compress(f, B: int, step: float) -> np.ndarray:
+    """Compressed stream (uint32 words) of a cube-major field of n_cubes B^3 values."""
+    f = _f64(f)
+    n_cubes = f.size // B ** 3
+    cap = 8 + n_cubes + n_cubes * (1 + (B ** 3 * 48 + 31) // 32)
+    out = np.zeros(cap, np.uint32)
+    nw = lib().orc_wavelet_compress(B, n_cubes, _p(f), step, _p(out), cap)
+    if nw < 0:
+        raise ValueError("wavelet compression: code out of range")
+    return out[:nw].copy()
+
+
+def wavelet_decompress(words) -> np.ndarray:
+    words = np.ascontiguousarray(words, np.uint32)
+    B, n_cubes = int(words[2]), int(words[3])
+    f = np.zeros(n_cubes * B ** 3)
+    if lib().orc_wavelet_decompress(_p(words), words.size, _p(f)):
+        raise ValueError("wavelet decompression: malformed stream")
+    return f
 
 
 def _f64(a) -> np.ndarray:

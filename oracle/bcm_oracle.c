@@ -68,6 +68,20 @@
  *      has reached the rounding floor of the arithmetic (at most 64 eps ||u^(k+1)||, eps
  *      the unit roundoff) and no longer shrinks (its square >= 0.99 of the previous
  *      one), or after cn_max iterations.  The IB forcing then acts on the result.
+ *   R21 wavelet compression of a field (orc_wavelet_*; section "Data compression"): per
+ *      cube, L = log2 B levels of a separable 3-D CDF 5/3 lifting transform of the B^3
+ *      interior values (the paper cites Sakai et al. for its wavelet without printing
+ *      it; the halo is not transformed: a restart rebuilds it from the neighbours):
+ *        d_i = x_{2i+1} - (x_{2i} + x_{2i+2})/2,  s_i = x_{2i} + (d_{i-1} + d_i)/4,
+ *      symmetric at the ends (x_{2h} := x_{2h-2}, d_{-1} := d_0), passes x, y, z per
+ *      level on the low band, coefficients kept in place (s first, then d along each
+ *      line).  One uniform quantizer q = rint(c / step); a Golomb-Rice coder replaces
+ *      zlib: z = zigzag(q), k = floor(log2(mean z)) per cube (0 if the mean is 0, at most
+ *      24); u = z >> k below 16 is written as u one-bits, a zero-bit and the k low bits of
+ *      z, else as 16 one-bits and the 32 bits of z; bits LSB-first in 32-bit words.
+ *      Stream of 32-bit words: magic, version, B, n_cubes, 0, 0, step (2 words), the
+ *      word count of every cube record, then the records: a word k | nbits << 5 and the
+ *      ceil(nbits / 32) payload words.  All arithmetic in FP64 without contraction.
  */
 #include "bcm_oracle.h"
 
@@ -1362,4 +1376,169 @@ int orc_step_particles(const orc_grid *g, double *u, double *v, double *w, doubl
     }
     particle_args P = {n_particles, X, psim, pbody, dV, F};
     return step_impl(g, u, v, w, p, nx, ny, nz, ub, step, nsteps, rtol, max_iter, stats, &P);
+}
+
+/* ------------------------------------------------- wavelet compression (R21) */
+
+/* one CDF 5/3 lifting step on x[0 .. m) with stride st (m even >= 2); tmp holds m values */
+static void lift53_forward(double *x, int m, int st, double *tmp) {
+    int h = m / 2;
+    for (int i = 0; i < h; ++i) { /* predict */
+        double right = (2 * i + 2 < m) ? x[(2 * i + 2) * st] : x[(2 * i) * st];
+        double t = x[(2 * i) * st] + right;
+        t = 0.5 * t;
+        tmp[h + i] = x[(2 * i + 1) * st] - t;
+    }
+    for (int i = 0; i < h; ++i) { /* update */
+        double dl = i > 0 ? tmp[h + i - 1] : tmp[h];
+        double t = dl + tmp[h + i];
+        t = 0.25 * t;
+        tmp[i] = x[(2 * i) * st] + t;
+    }
+    for (int i = 0; i < m; ++i) x[i * st] = tmp[i];
+}
+
+static void lift53_inverse(double *x, int m, int st, double *tmp) {
+    int h = m / 2;
+    for (int i = 0; i < h; ++i) { /* undo the update */
+        double dl = i > 0 ? x[(h + i - 1) * st] : x[h * st];
+        double t = dl + x[(h + i) * st];
+        t = 0.25 * t;
+        tmp[2 * i] = x[i * st] - t;
+    }
+    for (int i = 0; i < h; ++i) { /* undo the predict */
+        double right = (2 * i + 2 < m) ? tmp[2 * i + 2] : tmp[2 * i];
+        double t = tmp[2 * i] + right;
+        t = 0.5 * t;
+        tmp[2 * i + 1] = x[(h + i) * st] + t;
+    }
+    for (int i = 0; i < m; ++i) x[i * st] = tmp[i];
+}
+
+/* start of line (a, b) along axis d of a cube of edge B, and its stride */
+static int line_base(int B, int d, int a, int b) {
+    return d == 0 ? (b * B + a) * B : (d == 1 ? b * B * B + a : b * B + a);
+}
+static int line_stride(int B, int d) { return d == 0 ? 1 : (d == 1 ? B : B * B); }
+
+/* forward / inverse transform of one cube of B^3 values in place (index (k B + j) B + i) */
+void orc_dwt3_forward(int B, double *x) {
+    double tmp[64];
+    for (int m = B; m >= 2; m /= 2)
+        for (int d = 0; d < 3; ++d)
+            for (int b = 0; b < m; ++b)
+                for (int a = 0; a < m; ++a)
+                    lift53_forward(x + line_base(B, d, a, b), m, line_stride(B, d), tmp);
+}
+
+void orc_dwt3_inverse(int B, double *x) {
+    double tmp[64];
+    for (int m = 2; m <= B; m *= 2)
+        for (int d = 2; d >= 0; --d)
+            for (int b = 0; b < m; ++b)
+                for (int a = 0; a < m; ++a)
+                    lift53_inverse(x + line_base(B, d, a, b), m, line_stride(B, d), tmp);
+}
+
+static uint32_t zigzag(int32_t q) { return ((uint32_t)q << 1) ^ (uint32_t)(q >> 31); }
+static int32_t unzigzag(uint32_t z) { return (int32_t)(z >> 1) ^ -(int32_t)(z & 1u); }
+
+static void put_bit(uint32_t *w, uint64_t pos, int bit) {
+    if (bit) w[pos >> 5] |= 1u << (pos & 31);
+}
+static int get_bit(const uint32_t *w, uint64_t pos) { return (w[pos >> 5] >> (pos & 31)) & 1u; }
+
+/* Compress n_cubes cubes of B^3 values (cube-major) into out (capacity words).
+ * Returns the number of words written, or -1 when the capacity is too small or a code
+ * does not fit in 31 bits. */
+long orc_wavelet_compress(int B, int n_cubes, const double *f, double step, uint32_t *out,
+                          long capacity) {
+    long B3 = (long)B * B * B, head = 8 + (long)n_cubes;
+    if (capacity < head) return -1;
+    memset(out, 0, sizeof(uint32_t) * (size_t)capacity);
+    out[0] = 0x57434d42u; /* "BCMW" */
+    out[1] = 1;
+    out[2] = (uint32_t)B;
+    out[3] = (uint32_t)n_cubes;
+    memcpy(out + 6, &step, sizeof(double));
+    double *x = (double *)malloc(sizeof(double) * (size_t)B3);
+    uint32_t *z = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)B3);
+    long pos = head;
+    for (int c = 0; c < n_cubes; ++c) {
+        memcpy(x, f + (size_t)c * B3, sizeof(double) * (size_t)B3);
+        orc_dwt3_forward(B, x);
+        uint64_t sum = 0;
+        for (long q = 0; q < B3; ++q) {
+            double r = nearbyint(x[q] / step);
+            if (!(fabs(r) < 1073741824.0)) { free(x); free(z); return -1; }
+            z[q] = zigzag((int32_t)r);
+            sum += z[q];
+        }
+        uint64_t mean = sum / (uint64_t)B3;
+        int k = 0;
+        while (k < 24 && (mean >> (k + 1)) != 0) ++k;
+        uint64_t nbits = 0;
+        for (long q = 0; q < B3; ++q) {
+            uint32_t u = z[q] >> k;
+            nbits += u < 16 ? (uint64_t)u + 1 + k : 48;
+        }
+        long words = 1 + (long)((nbits + 31) / 32);
+        if (pos + words > capacity) { free(x); free(z); return -1; }
+        out[pos] = (uint32_t)k | (uint32_t)(nbits << 5);
+        uint32_t *w = out + pos + 1;
+        uint64_t b = 0;
+        for (long q = 0; q < B3; ++q) {
+            uint32_t u = z[q] >> k;
+            if (u < 16) {
+                for (uint32_t e = 0; e < u; ++e) put_bit(w, b++, 1);
+                put_bit(w, b++, 0);
+                for (int e = 0; e < k; ++e) put_bit(w, b++, (z[q] >> e) & 1u);
+            } else {
+                for (int e = 0; e < 16; ++e) put_bit(w, b++, 1);
+                for (int e = 0; e < 32; ++e) put_bit(w, b++, (z[q] >> e) & 1u);
+            }
+        }
+        out[8 + c] = (uint32_t)words;
+        pos += words;
+    }
+    free(x);
+    free(z);
+    return pos;
+}
+
+/* Decode a stream of orc_wavelet_compress into f (n_cubes * B^3 values).  Returns 0, or
+ * -1 on a malformed stream. */
+int orc_wavelet_decompress(const uint32_t *in, long words, double *f) {
+    if (words < 8 || in[0] != 0x57434d42u || in[1] != 1) return -1;
+    int B = (int)in[2], n_cubes = (int)in[3];
+    double step;
+    memcpy(&step, in + 6, sizeof(double));
+    long B3 = (long)B * B * B, pos = 8 + (long)n_cubes;
+    if (words < pos) return -1;
+    for (int c = 0; c < n_cubes; ++c) {
+        long cw = (long)in[8 + c];
+        if (cw < 1 || pos + cw > words) return -1;
+        int k = (int)(in[pos] & 31u);
+        uint64_t nbits = in[pos] >> 5;
+        const uint32_t *w = in + pos + 1;
+        uint64_t b = 0;
+        double *x = f + (size_t)c * B3;
+        for (long q = 0; q < B3; ++q) {
+            uint32_t u = 0, z = 0;
+            while (u < 16 && b < nbits && get_bit(w, b)) { ++u; ++b; }
+            if (u < 16) {
+                ++b; /* the zero */
+                uint32_t r = 0;
+                for (int e = 0; e < k; ++e) r |= (uint32_t)get_bit(w, b++) << e;
+                z = (u << k) | r;
+            } else {
+                for (int e = 0; e < 32; ++e) z |= (uint32_t)get_bit(w, b++) << e;
+            }
+            if (b > nbits) return -1;
+            x[q] = (double)unzigzag(z) * step;
+        }
+        orc_dwt3_inverse(B, x);
+        pos += cw;
+    }
+    return 0;
 }

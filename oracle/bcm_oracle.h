@@ -130,6 +130,13 @@ int orc_step_particles(const orc_grid *g, double *u, double *v, double *w, doubl
                        double *X, const int32_t *psim, const int32_t *pbody, const double *dV,
                        double *F);
 
+/* Wavelet compression of cell fields (R21 in the .c file header). */
+void orc_dwt3_forward(int B, double *x);
+void orc_dwt3_inverse(int B, double *x);
+long orc_wavelet_compress(int B, int n_cubes, const double *f, double step, uint32_t *out,
+                          long capacity);
+int orc_wavelet_decompress(const uint32_t *in, long words, double *f);
+
 #ifdef __cplusplus
 }
 #endif
