@@ -299,6 +299,36 @@ bcm_status bcm_adjoint_step(bcm_grid *grid, void *dev_adj, size_t bytes, const v
 enum { BCM_SCHEME_AB2_CENTRAL = 0, BCM_SCHEME_QUICK_CN = 1 };
 bcm_status bcm_set_momentum_scheme(bcm_grid *grid, int scheme, double cn_rtol, int cn_max_iter);
 
+/* ---- Wavelet compression of cell fields for checkpoints (section "Data compression":
+ * a discrete wavelet transform per cube, one level of quantization, an encoder, one
+ * stream that records the size of every cube's compressed record).
+ * Transform: log2 B levels of a separable 3-D CDF 5/3 lifting transform of each cube's
+ * B^3 values (d_i = x_{2i+1} - (x_{2i} + x_{2i+2})/2, s_i = x_{2i} + (d_{i-1} + d_i)/4,
+ * symmetric at the ends, passes x, y, z per level on the low band, coefficients in place,
+ * FP64 without contraction).  Quantizer q = rint(c / step).  Encoder in place of zlib:
+ * Golomb-Rice on z = zigzag(q) with k = floor(log2(mean z)) per cube (at most 24); a
+ * value with u = z >> k < 16 takes u one-bits, a zero-bit and the k low bits of z, else
+ * 16 one-bits and the 32 bits of z; bits LSB-first in 32-bit little-endian words.
+ * Stream (32-bit words): 0x57434D42 ("BCMW"), 1, B, n_cubes, 0, 0, step (FP64, 2 words),
+ * the word count of every cube record, then the records (k | nbits << 5, then
+ * ceil(nbits / 32) payload words).  The reconstruction error is at most
+ * (1/2 + 7.3125 log2 B) step (the inverse lifting steps bound it).
+ * field: BCM_U .. BCM_RHS except bfloat16 N fields.  The calls use the PCG scratch
+ * vectors and must not overlap a step on the grid's stream (they are stream ordered).
+ * bcm_compress_bound: bytes of the largest possible stream of this grid.
+ * bcm_compress_field: writes the stream into dev_stream (4-byte aligned, capacity
+ *   bytes) and *stream_bytes (host; synchronises).  Errors: BCM_E_INVALID (bad
+ *   argument or field, capacity below the stream), BCM_E_BOUNDS (a coefficient / step
+ *   beyond 2^30).
+ * bcm_decompress_field: decodes a stream of this grid (same B and cube count) into the
+ *   field (rounded to its storage type).  Errors: BCM_E_INVALID (not such a stream, a
+ *   malformed record: the field is then undefined).  Synchronises. */
+size_t bcm_compress_bound(const bcm_grid *grid);
+bcm_status bcm_compress_field(bcm_grid *grid, int field, double step, void *dev_stream,
+                              size_t capacity, size_t *stream_bytes);
+bcm_status bcm_decompress_field(bcm_grid *grid, int field, const void *dev_stream,
+                                size_t bytes);
+
 /* ---- Lagrangian-particle immersed boundary (section "Lagrangian Data Structure";
  * section "Lagrangian-Eulerian Interaction", Eqs. ddeltai and ddeltap with the smoothed
  * 3-point delta phi(r) = 3/4 - r^2 for |r| <= 1/2, (9/4 - 3|r| + r^2)/2 for

@@ -30,6 +30,7 @@ EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_f
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
             "bcm_set_momentum_scheme",
+            "bcm_compress_bound", "bcm_compress_field", "bcm_decompress_field",
             "bcm_particles_bytes", "bcm_set_particles", "bcm_get_particles",
             "bcm_particle_sets", "bcm_ib_interpolate", "bcm_ib_spread",
             "bcm_last_error"]
@@ -111,6 +112,11 @@ def lib(build: bool = True):
         L.bcm_profile.argtypes = [P, C.c_int]
         L.bcm_profile_read.argtypes = [P, P, P, P, C.c_int]
         L.bcm_set_momentum_scheme.argtypes = [P, C.c_int, C.c_double, C.c_int]
+        L.bcm_compress_bound.restype = C.c_size_t
+        L.bcm_compress_bound.argtypes = [P]
+        L.bcm_compress_field.argtypes = [P, C.c_int, C.c_double, P, C.c_size_t,
+                                         C.POINTER(C.c_size_t)]
+        L.bcm_decompress_field.argtypes = [P, C.c_int, P, C.c_size_t]
         L.bcm_particles_bytes.restype = C.c_size_t
         L.bcm_particles_bytes.argtypes = [P, C.c_int32]
         L.bcm_set_particles.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_size_t]
@@ -120,7 +126,7 @@ def lib(build: bool = True):
         L.bcm_ib_spread.argtypes = [P, P, P]
         L.bcm_last_error.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("bcm_adjoint_bytes", "bcm_particles_bytes"):
+            if name not in ("bcm_adjoint_bytes", "bcm_particles_bytes", "bcm_compress_bound"):
                 getattr(L, name).restype = getattr(L, name).restype or C.c_int
         _lib = L
     return _lib
@@ -259,6 +265,24 @@ class Grid:
         """SCHEME_AB2_CENTRAL (default) or SCHEME_QUICK_CN (0: library defaults)."""
         _check(lib().bcm_set_momentum_scheme(self._h, int(scheme), float(cn_rtol),
                                              int(cn_max_iter)))
+
+    # ------------------------------------------------ wavelet compression
+    def compress_field(self, fid: int, step: float):
+        """Wavelet stream of one cell field (a uint32 device tensor of the stream words)."""
+        import torch
+        cap = lib().bcm_compress_bound(self._h)
+        buf = torch.empty(cap // 4, dtype=torch.int32, device=self.device)
+        n = C.c_size_t()
+        _check(lib().bcm_compress_field(self._h, int(fid), float(step),
+                                        C.c_void_p(buf.data_ptr()), cap, C.byref(n)))
+        return buf[:n.value // 4].clone()
+
+    def decompress_field(self, fid: int, stream):
+        """Decode a stream of compress_field into the field."""
+        import torch
+        stream = torch.as_tensor(stream).to(self.device).contiguous()
+        _check(lib().bcm_decompress_field(self._h, int(fid), C.c_void_p(stream.data_ptr()),
+                                          stream.numel() * stream.element_size()))
 
     # ------------------------------------------------ Lagrangian particles
     def set_particles(self, parts):

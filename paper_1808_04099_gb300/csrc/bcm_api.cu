@@ -1320,6 +1320,105 @@ extern "C" bcm_status bcm_set_momentum_scheme(bcm_grid* g, int scheme, double cn
   return BCM_OK;
 }
 
+// ---- wavelet compression of cell fields (bcm_wavelet.cu)
+
+namespace {
+// a cell field (4- or 8-byte elements) by id, for compression
+bcm_status wavelet_field(bcm_grid* g, int field, void** ptr, int* f64) {
+  size_t cnt = 0;
+  int32_t eb = 0;
+  bcm_status st = bcm_field(g, field, ptr, &cnt, &eb);
+  if (st != BCM_OK) return st;
+  if (cnt != g->n_cells || (eb != 4 && eb != 8))
+    return fail(BCM_E_INVALID, "field %d is not a 4- or 8-byte cell field", field);
+  *f64 = eb == 8;
+  return BCM_OK;
+}
+// scratch while no step runs: codes in the PCG residual, per-cube tables in q
+struct WavScratch {
+  uint32_t *zc, *nbits, *k, *off;
+  int* err;
+};
+WavScratch wavelet_scratch(bcm_grid* g) {
+  WavScratch s;
+  s.zc = (uint32_t*)g->ctx.f.r;
+  uint32_t* q = (uint32_t*)g->ctx.f.q;
+  const size_t nc = (size_t)g->desc.n_cubes;
+  s.nbits = q;
+  s.k = q + nc;
+  s.off = q + 2 * nc;
+  s.err = (int*)(g->ws + g->L.err) + 8;
+  return s;
+}
+}  // namespace
+
+extern "C" size_t bcm_compress_bound(const bcm_grid* g) {
+  if (!g) return 0;
+  const size_t nc = (size_t)g->desc.n_cubes, B3 = (size_t)g->B * g->B * g->B;
+  return 4 * (8 + nc + nc * (1 + (48 * B3 + 31) / 32));
+}
+
+extern "C" bcm_status bcm_compress_field(bcm_grid* g, int field, double step, void* dev_stream,
+                                         size_t capacity, size_t* stream_bytes) {
+  if (!g || !dev_stream || !stream_bytes) return fail(BCM_E_INVALID, "NULL argument");
+  if (!(step > 0) || !std::isfinite(step)) return fail(BCM_E_INVALID, "step must be > 0");
+  if ((uintptr_t)dev_stream % 4) return fail(BCM_E_INVALID, "stream must be 4-byte aligned");
+  void* ptr = nullptr;
+  int f64 = 0;
+  bcm_status st = wavelet_field(g, field, &ptr, &f64);
+  if (st != BCM_OK) return st;
+  const WavScratch s = wavelet_scratch(g);
+  const size_t nc = (size_t)g->desc.n_cubes;
+  CUDA_TRY(cudaMemsetAsync(s.err, 0, sizeof(int), g->stream));
+  RUN(BCM_K_MISC, launch_wavelet_analyze(g->ctx, ptr, f64, step, s.zc, s.nbits, s.k, s.off,
+                                         s.err));
+  g->launch_count += 1;
+  uint32_t total = 0;
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, s.off + nc, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(&err, s.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (err) return fail(BCM_E_BOUNDS, "step too small: a quantized coefficient exceeds 2^30");
+  const size_t bytes = 4 * (size_t)total;
+  if (bytes > capacity)
+    return fail(BCM_E_INVALID, "stream capacity %zu < %zu bytes", capacity, bytes);
+  CUDA_TRY(cudaMemsetAsync(dev_stream, 0, bytes, g->stream));
+  RUN(BCM_K_MISC, launch_wavelet_encode(g->ctx, s.zc, s.nbits, s.k, s.off, step,
+                                        (uint32_t*)dev_stream));
+  *stream_bytes = bytes;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_decompress_field(bcm_grid* g, int field, const void* dev_stream,
+                                           size_t bytes) {
+  if (!g || !dev_stream) return fail(BCM_E_INVALID, "NULL argument");
+  if ((uintptr_t)dev_stream % 4 || bytes % 4) return fail(BCM_E_INVALID, "stream not word-sized");
+  void* ptr = nullptr;
+  int f64 = 0;
+  bcm_status st = wavelet_field(g, field, &ptr, &f64);
+  if (st != BCM_OK) return st;
+  const size_t words = bytes / 4, nc = (size_t)g->desc.n_cubes;
+  if (words < 8 + nc) return fail(BCM_E_INVALID, "stream shorter than its header");
+  uint32_t head[8];
+  CUDA_TRY(cudaMemcpyAsync(head, dev_stream, sizeof head, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  double step;
+  memcpy(&step, head + 6, sizeof step);
+  if (head[0] != 0x57434d42u || head[1] != 1u || head[2] != (uint32_t)g->B ||
+      head[3] != (uint32_t)nc || !(step > 0))
+    return fail(BCM_E_INVALID, "not a wavelet stream of this grid");
+  const WavScratch s = wavelet_scratch(g);
+  CUDA_TRY(cudaMemsetAsync(s.err, 0, sizeof(int), g->stream));
+  RUN(BCM_K_MISC, launch_wavelet_decode(g->ctx, ptr, f64, (const uint32_t*)dev_stream, words,
+                                        step, s.off, s.err));
+  g->launch_count += 1;
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, s.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (err) return fail(BCM_E_INVALID, "malformed cube record in the stream");
+  return BCM_OK;
+}
+
 // ---- Lagrangian-particle immersed boundary (bcm_ib.cu)
 
 namespace {

@@ -135,6 +135,16 @@ cudaError_t launch_mg_vcycle(const Ctx& x, const SolveParams& prm, int mode);
 cudaError_t launch_ib_bin(const Ctx& x);
 cudaError_t launch_ib_force(const Ctx& x);
 cudaError_t launch_ib_move(const Ctx& x);
+// wavelet compression of a cell field (bcm_wavelet.cu): codes, Rice parameters and
+// record offsets; the encoded stream (zeroed beforehand); decoding into the field
+cudaError_t launch_wavelet_analyze(const Ctx& x, const void* field, int f64, double step,
+                                   uint32_t* zc, uint32_t* cube_nbits, uint32_t* cube_k,
+                                   uint32_t* off, int* err);
+cudaError_t launch_wavelet_encode(const Ctx& x, const uint32_t* zc, const uint32_t* cube_nbits,
+                                  const uint32_t* cube_k, const uint32_t* off, double step,
+                                  uint32_t* out);
+cudaError_t launch_wavelet_decode(const Ctx& x, void* field, int f64, const uint32_t* in,
+                                  size_t words, double step, uint32_t* off, int* err);
 // test paths on FP64 arrays: out[q] = I[f] at particle q; out += P[F]
 cudaError_t launch_ib_interpolate(const Ctx& x, const double* f, double* out);
 cudaError_t launch_ib_spread(const Ctx& x, const double* F, double* out);
