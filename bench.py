@@ -507,6 +507,39 @@ def gpu_arm(args, ws, rank, local):
                      "momentum_frac_of_hbm": mom_bytes / (mom_ms / 1e3) / 1e9 / peak,
                      "kernels": kq}
 
+    # ---- wavelet compression of the state for checkpoints (paper's error tolerance
+    # O(1e-4): step = 1e-4 of each field's largest value), after the timed steps
+    wav = {}
+    gw = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+    gw.load_state(state)
+    gw.step(args.warmup, rtol=RTOL, stats=False)
+    for fname, fid in (("u", bcm.U), ("v", bcm.V), ("w", bcm.W), ("p", bcm.P)):
+        fld = gw.field(fid)
+        ref = fld.clone()
+        step = 1e-4 * float(fld.abs().max())
+        nbytes_in = fld.numel() * fld.element_size()
+        reps = 5
+        s = gw.compress_field(fid, step)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            s = gw.compress_field(fid, step)
+        torch.cuda.synchronize()
+        tc = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            gw.decompress_field(fid, s)
+        torch.cuda.synchronize()
+        td = (time.perf_counter() - t0) / reps
+        err = float((fld.double() - ref.double()).abs().max())
+        fld.copy_(ref)
+        sbytes = s.numel() * 4
+        wav[fname] = {"ratio": nbytes_in / sbytes, "ratio_vs_fp64": 8 * fld.numel() / sbytes,
+                      "stream_MB": sbytes / 1e6, "compress_GBps": nbytes_in / tc / 1e9,
+                      "decompress_GBps": nbytes_in / td / 1e9,
+                      "max_error_over_step": err / step, "step": step}
+    del gw
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -537,6 +570,11 @@ def gpu_arm(args, ws, rank, local):
                                 "Jacobi-PCG hot path): steps issued from the host, each PCG "
                                 "iteration one replayed CUDA graph; same workload and "
                                 "residual"),
+            "wavelet": dict(wav, note="per-cube wavelet compression of the mixed state "
+                                      "(a NEXT row beyond the hot path): step 1e-4 of each "
+                                      "field's largest value; throughput of the C-ABI calls "
+                                      "(host-synchronised), input bytes in the field's "
+                                      "storage type"),
             "quick_cn": dict(qcn, note="QUICK convection + Crank-Nicolson momentum (a NEXT "
                                        "row beyond the hot path), same workload and residual"),
             "lagrangian": dict(lag, note="Lagrangian-particle IB (a NEXT row beyond the hot "
@@ -585,6 +623,10 @@ def ncu_case(args):
         st = g.solve_pressure_iters(args.ncu_iters)
     else:
         st = g.step(2, rtol=RTOL)
+    if args.ncu_wavelet:  # compress and restore the velocity and the pressure once
+        for fid in (bcm.U, bcm.P):
+            s = g.compress_field(fid, 1e-4 * float(g.field(fid).abs().max()))
+            g.decompress_field(fid, s)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": spec.name, "precision": prec, "stats": st[0]}))
 
@@ -613,6 +655,8 @@ def main():
                     help="with --ncu-case: QUICK + Crank-Nicolson momentum")
     ap.add_argument("--ncu-particles", action="store_true",
                     help="with --ncu-case: the Lagrangian-particle IB")
+    ap.add_argument("--ncu-wavelet", action="store_true",
+                    help="with --ncu-case: compress and restore u and p after the steps")
     ap.add_argument("--recycle", type=int, default=-1,
                     help="mixed mode: 1 reliable updates across cycles, 0 restarts (default: library)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
