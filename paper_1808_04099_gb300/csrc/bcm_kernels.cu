@@ -916,14 +916,15 @@ cudaError_t launch_momentum(const Ctx& x) {
   return x.lag_bf16 ? momentum_t<float, __nv_bfloat16>(x) : momentum_t<float, float>(x);
 }
 
-// QUICK + Crank-Nicolson: slabs of 2 planes for 16^3 cubes (six (B+4)^2 x 6 tiles)
-template <int B>
-constexpr int cn_slab() { return B == 16 ? 2 : B; }
+// QUICK + Crank-Nicolson: z-slabs of 16^3 cubes, 4 planes in FP32 (six (B+4)^2 x 8
+// tiles, 77 KB) and 2 in FP64 (six x 6 tiles, 115 KB)
+template <int B, class T>
+constexpr int cn_slab() { return B == 16 ? (sizeof(T) == 4 ? 4 : 2) : B; }
 
 template <class T>
 static cudaError_t cn_explicit_t(const Ctx& x) {
   BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>(), KS = cn_slab<B>();
+    constexpr int NT = threads_for<B>(), KS = cn_slab<B, T>();
     const size_t sm = 3 * sizeof(T) * Slab2<B, KS>::N;
     auto kern = k_cn_explicit<B, KS, NT, T>;
     cudaError_t e = allow_smem(kern, sm);
@@ -941,7 +942,7 @@ cudaError_t launch_cn_explicit(const Ctx& x) {
 template <class T>
 static cudaError_t cn_iter_t(const Ctx& x) {
   BCM_DISPATCH_B(x.B, {
-    constexpr int NT = threads_for<B>(), KS = cn_slab<B>();
+    constexpr int NT = threads_for<B>(), KS = cn_slab<B, T>();
     const size_t sm = 6 * sizeof(T) * Slab2<B, KS>::N;
     auto kern = k_cn_iter<B, KS, NT, T>;
     cudaError_t e = allow_smem(kern, sm);
