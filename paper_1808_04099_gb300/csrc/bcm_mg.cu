@@ -136,6 +136,7 @@ __global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale
                                                  const TV* __restrict__ r,
                                                  TV* __restrict__ x, TV* __restrict__ rc,
                                                  int all) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   constexpr int CB = BL > 1 ? BL / 2 : 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)g.n_cubes * CB * CB * CB) return;
@@ -151,6 +152,7 @@ __global__ __launch_bounds__(256) void k_mg_down_cell(DevGrid g, TV wscale, TV c
                                                       const TV* __restrict__ r,
                                                       TV* __restrict__ x, TV* __restrict__ rc,
                                                       int all) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   static_assert(BL >= 2, "restriction over 2x2x2 children");
   constexpr int CB = BL / 2, C3 = CB * CB * CB, B3 = BL * BL * BL;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,6 +254,7 @@ __global__ __launch_bounds__(256) void k_mg_up(DevGrid g, TV wscale, TV cscale,
                                                const double* __restrict__ yagg,
                                                const int* __restrict__ agg_parent,
                                                TV* __restrict__ y, int all) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)g.n_cubes * BL * BL * BL) return;
   mg_up_item<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, y, all, t);
@@ -305,6 +308,7 @@ __global__ __launch_bounds__(NT) void k_mg_up0(DevGrid g, const TV* __restrict__
                                               const double* __restrict__ yagg,
                                               const int* __restrict__ agg_parent,
                                               TV* __restrict__ z, SolveParams prm, int mode) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   constexpr int B3 = B * B * B, PER = B3 / NT;
   __shared__ double red[32];
   const int c = blockIdx.x / PER;
@@ -353,6 +357,7 @@ __global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __
                                                          TV* __restrict__ x,
                                                          TV* __restrict__ r1, int all,
                                                          PassB<TV> pb, TV wl, TV cl) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   using SL = Slab<B, B>;
   constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -464,6 +469,7 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
                                                        const TV* __restrict__ y1,
                                                        TV* __restrict__ z, SolveParams prm,
                                                        int mode, TV wl, TV cl, int finest) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   using SL = Slab<B, B>;
   constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -704,6 +710,7 @@ __device__ void mg_top(const MgDev& mg, const TV* __restrict__ rr, int smem_mode
 template <class TV>
 __global__ __launch_bounds__(1024) void k_mg_top(MgDev mg, const TV* __restrict__ rr,
                                                  int smem_mode) {
+  cudaGridDependencySynchronize();  // launched after the previous level's kernel
   extern __shared__ __align__(16) unsigned char smem_raw[];
   mg_top<TV>(mg, rr, smem_mode, reinterpret_cast<double*>(smem_raw));
 }
@@ -719,14 +726,13 @@ static cudaError_t down_t(const Ctx& x, int l, int all) {
   const double c4 = double(1 << (2 * l));
   if constexpr (BL > 1) {  // one thread per fine cell
     const long long n = (long long)x.g.n_cubes * BL * BL * BL;
-    k_mg_down_cell<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
-        x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+    return launch_pdl(k_mg_down_cell<BL, TV>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0,
+                      x.stream, x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
   } else {
     const long long n = (long long)x.g.n_cubes * CB * CB * CB;
-    k_mg_down<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
-        x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+    return launch_pdl(k_mg_down<BL, TV>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0,
+                      x.stream, x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
   }
-  return cudaGetLastError();
 }
 
 template <int BL, class TV>
@@ -734,10 +740,10 @@ static cudaError_t up_t(const Ctx& x, int l, int all) {
   const long long n = (long long)x.g.n_cubes * BL * BL * BL;
   const TV* yc = BL > 1 ? (const TV*)x.mg.y[l + 1] : nullptr;
   const double c4 = double(1 << (2 * l));
-  k_mg_up<BL, TV><<<(unsigned)((n + 255) / 256), 256, 0, x.stream>>>(
-      x.g, TV(kMgOmega / c4), TV(c4), (const TV*)x.mg.r[l], (const TV*)x.mg.x[l], yc,
-      x.mg.ax[0], x.mg.parent[0], (TV*)x.mg.y[l], all);
-  return cudaGetLastError();
+  return launch_pdl(k_mg_up<BL, TV>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, x.stream,
+                    x.g, TV(kMgOmega / c4), TV(c4), (const TV*)x.mg.r[l], (const TV*)x.mg.x[l],
+                    yc, (const double*)x.mg.ax[0], (const int*)x.mg.parent[0], (TV*)x.mg.y[l],
+                    all);
 }
 
 template <class TV>
@@ -760,10 +766,10 @@ template <int B, class TV>
 static cudaError_t up0_t(const Ctx& x, const SolveParams& prm, int mode) {
   constexpr int B3 = B * B * B, NT = B3 < 256 ? B3 : 256;
   const TV* yc = (const TV*)x.mg.y[1];
-  k_mg_up0<B, NT, TV><<<x.g.n_cubes * (B3 / NT), NT, 0, x.stream>>>(
-      x.g, (const TV*)x.mg.r[0], (const TV*)x.mg.x[0], yc, x.mg.ax[0], x.mg.parent[0],
-      (TV*)x.mg.y[0], prm, mode);
-  return cudaGetLastError();
+  return launch_pdl(k_mg_up0<B, NT, TV>, dim3(x.g.n_cubes * (B3 / NT)), dim3(NT), 0, x.stream,
+                    x.g, (const TV*)x.mg.r[0], (const TV*)x.mg.x[0], yc,
+                    (const double*)x.mg.ax[0], (const int*)x.mg.parent[0], (TV*)x.mg.y[0], prm,
+                    mode);
 }
 
 template <int B, class TV>
@@ -783,10 +789,9 @@ static cudaError_t down0_tile_t(const Ctx& x, int l, int all, bool fb) {
   auto kern = fb ? k_mg_down0_tile<B, TV, true> : k_mg_down0_tile<B, TV, false>;
   cudaError_t e = allow_dynamic_smem(kern, sm);
   if (e != cudaSuccess) return e;
-  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[l], (TV*)x.mg.x[l],
-                                            (TV*)x.mg.r[l + 1], all, pb, TV(kMgOmega / c4),
-                                            TV(c4));
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(x.g.n_cubes), dim3(B * B), sm, x.stream, x.g,
+                    (const TV*)x.mg.r[l], (TV*)x.mg.x[l], (TV*)x.mg.r[l + 1], all, pb,
+                    TV(kMgOmega / c4), TV(c4));
 }
 
 template <int B, class TV>
@@ -797,12 +802,10 @@ static cudaError_t up0_tile_t(const Ctx& x, int l, const SolveParams& prm, int m
   auto kern = k_mg_up0_tile<B, TV>;
   cudaError_t e = allow_dynamic_smem(kern, sm);
   if (e != cudaSuccess) return e;
-  kern<<<x.g.n_cubes, B * B, sm, x.stream>>>(x.g, (const TV*)x.mg.r[l],
-                                            fb ? (const TV*)x.f.s0 : nullptr,
-                                            (const TV*)x.mg.x[l], (const TV*)x.mg.y[l + 1],
-                                            (TV*)x.mg.y[l], prm, mode, TV(kMgOmega / c4),
-                                            TV(c4), l == 0 ? 1 : 0);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(x.g.n_cubes), dim3(B * B), sm, x.stream, x.g,
+                    (const TV*)x.mg.r[l], fb ? (const TV*)x.f.s0 : (const TV*)nullptr,
+                    (const TV*)x.mg.x[l], (const TV*)x.mg.y[l + 1], (TV*)x.mg.y[l], prm, mode,
+                    TV(kMgOmega / c4), TV(c4), l == 0 ? 1 : 0);
 }
 
 template <class TV>
@@ -832,8 +835,9 @@ static cudaError_t vcycle_t(const Ctx& x, const SolveParams& prm, int mode) {
     const int nt = maxn < 64 ? 64 : maxn > 1024 ? 1024 : (maxn + 31) / 32 * 32;
     auto kern = k_mg_top<TV>;
     if (smem_mode && (e = allow_dynamic_smem(kern, sm)) != cudaSuccess) return e;
-    kern<<<1, nt, sm, x.stream>>>(x.mg, (const TV*)x.mg.rr, smem_mode);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(kern, dim3(1), dim3(nt), sm, x.stream, x.mg, (const TV*)x.mg.rr,
+                        smem_mode)) != cudaSuccess)
+      return e;
   }
   for (int l = x.mg.L; l >= 1; --l)
     if ((e = (x.B >> l) == 8 ? up0_tile_t<8, TV>(x, l, prm, mode, false)

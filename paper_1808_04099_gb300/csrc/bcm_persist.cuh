@@ -89,6 +89,26 @@ inline cudaError_t allow_dynamic_smem(K kern, size_t dyn) {
   return cudaSuccess;
 }
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel on the stream drains, and must pass cudaGridDependencySynchronize()
+// before it reads or writes anything that kernel touches (a kernel launched without
+// the attribute passes it at once).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <int B>
 constexpr int pcg_threads() { return B == 16 ? 256 : (B == 8 ? 128 : 64); }
 

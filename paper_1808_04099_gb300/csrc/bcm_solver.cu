@@ -18,6 +18,7 @@
 #include "bcm_cube.cuh"
 #include "bcm_internal.cuh"
 #include "bcm_kernels.h"
+#include "bcm_persist.cuh"
 
 namespace bcm {
 
@@ -183,6 +184,7 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
                                              const TV* __restrict__ zv,
                                              TV* __restrict__ p0, TV* __restrict__ p1,
                                              TV* __restrict__ q, SolveParams prm) {
+  cudaGridDependencySynchronize();  // (multigrid iteration: launched while the V-cycle drains)
   using SL = Slab<B, KS>;
   constexpr int B3 = B * B * B, BB = B * B, NSL = B / KS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -568,8 +570,15 @@ static cudaError_t cg_a_t(const Ctx& x, const SolveParams& prm) {
       cudaError_t e = allow_smem(ka, sm);
       if (e != cudaSuccess) return e;
       const TV* zv = prm.mg ? (const TV*)x.mg.y[0] : nullptr;
-      ka<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(x.g, (const TV*)x.f.r, zv, (TV*)x.f.p0,
-                                                       (TV*)x.f.p1, (TV*)x.f.q, prm);
+      if (prm.mg) {  // after the V-cycle's last launch: start while it drains
+        e = launch_pdl(ka, dim3(x.g.n_cubes * (B / KS)), dim3(NT), sm, x.stream, x.g,
+                       (const TV*)x.f.r, zv, (TV*)x.f.p0, (TV*)x.f.p1, (TV*)x.f.q, prm);
+        if (e != cudaSuccess) return e;
+      } else {
+        ka<<<x.g.n_cubes * (B / KS), NT, sm, x.stream>>>(x.g, (const TV*)x.f.r, zv,
+                                                         (TV*)x.f.p0, (TV*)x.f.p1, (TV*)x.f.q,
+                                                         prm);
+      }
     });
   });
   return cudaGetLastError();
