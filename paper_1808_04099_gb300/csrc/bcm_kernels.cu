@@ -360,12 +360,18 @@ __global__ __launch_bounds__(NT) void k_momentum(
 //   d^(k+1) = (E' - dt/2 N(u^n + d^(k)) + a/2 (sum of the 6 neighbours of d^(k))) / (1 + 3a),
 //   E' = dt (-N(u^n)/2 + nu L(u^n)),  d^(0) = dt (-N(u^n) + nu L(u^n)),
 // the same iteration in exact arithmetic.  Ghosts: u^n + d by the halo rules with the
-// outflow values of t^n; d alone by the same rules made homogeneous (a boundary value
-// minus the mirror cell becomes minus the mirror).  QUICK reads two cells upstream, so
-// the slabs carry the paper's two ghost layers.  Storage: u^n stays in u, E' in u*, d
-// alternates between two sets of PCG scratch vectors (free during the momentum
-// sub-step) by the parity of the sim's iteration count; the last launch writes
-// u* = u~ + phi (u_s - u~) and advances the outflow values to t^{n+1}.
+// outflow values of t^n.  Every halo rule is affine in the field with the same boundary
+// value for u^n and u^n + d, so the neighbour sum of d equals that of u^n + d minus that
+// of u^n (both with those ghosts): the explicit kernel folds -a/2 (neighbour sum of u^n)
+// into E'' = E' - a/2 sum u^n, and an iteration needs the tiles of u^n + d alone,
+//   d^(k+1) = (E'' + a/2 (sum of the 6 neighbours of u^n + d^(k)) - dt/2 N(u^n + d^(k))) / (1 + 3a).
+// In FP32 the neighbour sum then carries the rounding of u^n + d: at most
+// 3a / (1 + 3a) of one rounding of |u| on d, below the rounding of the stored u*.
+// QUICK reads two cells upstream, so the slabs carry the paper's two ghost layers.
+// Storage: u^n stays in u, E'' in u*, d alternates between two sets of PCG scratch
+// vectors (free during the momentum sub-step) by the parity of the sim's iteration
+// count; the last launch writes u* = u~ + phi (u_s - u~) and advances the outflow
+// values to t^{n+1}.
 // ===========================================================================
 template <int B, int KS>
 struct Slab2 {  // planes z0-2 .. z0+KS+1, each (B+4)^2 with a two-cell x/y ring
@@ -408,16 +414,6 @@ struct SumVal {
   __device__ __forceinline__ T operator()(int c, int cell) const {
     const size_t i = (size_t)c * B3 + cell;
     return a[i] + d[i];
-  }
-};
-
-// ghost rule of an increment: the velocity rules (R8) without their boundary values
-struct IncrementBC {
-  const SimParams* sp;
-  int comp;
-  template <class T>
-  __device__ __forceinline__ T operator()(int f, int, int, T d0) const {
-    return (sp->bc[f] == BC_SLIP && comp != (f >> 1)) ? d0 : -d0;
   }
 };
 
@@ -479,6 +475,7 @@ __global__ __launch_bounds__(NT) void k_cn_explicit(DevGrid g, const T* __restri
   __syncthreads();
   const double hd = cell_h<B>(g, c);
   const T ih = T(1.0 / hd), ih2 = T(1.0 / (hd * hd)), dt = T(sp.dt), nu = T(sp.nu);
+  const T half_a = T(0.5 * sp.dt * sp.nu / (hd * hd));
   const T* const Sf[3] = {S0, S1, S2};
   T* Es[3] = {e0, e1, e2};
   T* Ds[3] = {d0, d1, d2};
@@ -491,13 +488,16 @@ __global__ __launch_bounds__(NT) void k_cn_explicit(DevGrid g, const T* __restri
     for (int comp = 0; comp < 3; ++comp) {
       const T* Sc = Sf[comp];
       const T u0 = Sc[o];
-      T L = T(0);
+      T L = T(0), sn = T(0);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) L += Sc[o + off[d]] - T(2) * u0 + Sc[o - off[d]];
+      for (int d = 0; d < 3; ++d) {
+        L += Sc[o + off[d]] - T(2) * u0 + Sc[o - off[d]];
+        sn += Sc[o + off[d]] + Sc[o - off[d]];
+      }
       const T N = conv_quick<T>(Sf, comp, o, off, ih);
       const T DL = dt * nu * (L * ih2);
-      Es[comp][gi] = T(-0.5) * dt * N + DL;  // E' = E - u^n + a/2 (sum nb - 6 u^n)
-      Ds[comp][gi] = -dt * N + DL;           // forward-Euler predictor of d
+      Es[comp][gi] = (T(-0.5) * dt * N + DL) - half_a * sn;  // E'' = E' - a/2 sum u^n
+      Ds[comp][gi] = -dt * N + DL;                          // forward-Euler predictor of d
     }
   }
 }
@@ -506,7 +506,7 @@ __global__ __launch_bounds__(NT) void k_cn_explicit(DevGrid g, const T* __restri
 // one the sim's iteration parity selects (k even: da).  The last block takes each
 // sim's decision.
 template <int B, int KS, int NT, class T>
-__global__ __launch_bounds__(NT) void k_cn_iter(DevGrid g, const T* __restrict__ u,
+__global__ __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 3) void k_cn_iter(DevGrid g, const T* __restrict__ u,
                                                 const T* __restrict__ v, const T* __restrict__ w,
                                                 T* da0, T* da1, T* da2, T* db0, T* db1, T* db2,
                                                 const T* __restrict__ e0,
@@ -517,7 +517,6 @@ __global__ __launch_bounds__(NT) void k_cn_iter(DevGrid g, const T* __restrict__
   constexpr int B3 = B * B * B, NSL = B / KS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S0 = reinterpret_cast<T*>(smem_raw);  // u^n + d, three components
-  T* D0 = S0 + 3 * SL::N;                  // d, three components
   __shared__ double red[2 * 32];
   const int c = blockIdx.x / NSL, z0 = (blockIdx.x % NSL) * KS;
   const int s = g.sim[c];
@@ -534,8 +533,6 @@ __global__ __launch_bounds__(NT) void k_cn_iter(DevGrid g, const T* __restrict__
     for (int comp = 0; comp < 3; ++comp) {
       VelocityBC<B, T> vb{&g, &sp, ub, c, comp};
       stage_slab2<B, KS, NT>(S0 + comp * SL::N, g, c, z0, SumVal<T>{un[comp], src[comp], B3}, vb);
-      stage_slab2<B, KS, NT>(D0 + comp * SL::N, g, c, z0, FieldVal<T>{src[comp], B3},
-                             IncrementBC{&sp, comp});
     }
     __syncthreads();
     const double hd = cell_h<B>(g, c);
@@ -552,13 +549,13 @@ __global__ __launch_bounds__(NT) void k_cn_iter(DevGrid g, const T* __restrict__
       const int o = SL::at(i, j, kk + 2);
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
-        const T* Dc = D0 + comp * SL::N;
+        const T* Sc = Sf[comp];
         T sn = T(0);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) sn += Dc[o + off[d]] + Dc[o - off[d]];
+        for (int d = 0; d < 3; ++d) sn += Sc[o + off[d]] + Sc[o - off[d]];
         const T N = conv_quick<T>(Sf, comp, o, off, ih);
-        const T dn = (Es[comp][gi] - T(0.5) * dt * N + half_a * sn) / den;
-        const T ch = dn - Dc[o];
+        const T dn = ((Es[comp][gi] + half_a * sn) - T(0.5) * dt * N) / den;
+        const T ch = dn - src[comp][gi];
         const T ut = un[comp][gi] + dn;
         dd2 += ch * ch;
         uu2 += ut * ut;
@@ -916,8 +913,8 @@ cudaError_t launch_momentum(const Ctx& x) {
   return x.lag_bf16 ? momentum_t<float, __nv_bfloat16>(x) : momentum_t<float, float>(x);
 }
 
-// QUICK + Crank-Nicolson: z-slabs of 16^3 cubes, 4 planes in FP32 (six (B+4)^2 x 8
-// tiles, 77 KB) and 2 in FP64 (six x 6 tiles, 115 KB)
+// QUICK + Crank-Nicolson: z-slabs of 16^3 cubes, 4 planes in FP32 (three (B+4)^2 x 8
+// tiles, 38 KB) and 2 in FP64 (three x 6 tiles, 58 KB)
 template <int B, class T>
 constexpr int cn_slab() { return B == 16 ? (sizeof(T) == 4 ? 4 : 2) : B; }
 
@@ -943,7 +940,7 @@ template <class T>
 static cudaError_t cn_iter_t(const Ctx& x) {
   BCM_DISPATCH_B(x.B, {
     constexpr int NT = threads_for<B>(), KS = cn_slab<B, T>();
-    const size_t sm = 6 * sizeof(T) * Slab2<B, KS>::N;
+    const size_t sm = 3 * sizeof(T) * Slab2<B, KS>::N;
     auto kern = k_cn_iter<B, KS, NT, T>;
     cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
