@@ -77,6 +77,10 @@ struct FieldVal {
   __device__ __forceinline__ T operator()(int c, int cell) const {
     return f[(size_t)c * B3 + cell];
   }
+  // cells cell0 .. cell0+3 (cell0 a multiple of 4: one 16-byte access)
+  __device__ __forceinline__ void get4(int c, int cell0, T (&v)[4]) const {
+    ld4(f + (size_t)c * B3 + cell0, v);
+  }
 };
 
 
@@ -386,15 +390,30 @@ template <int B, int KS, int NT, class T, class Val, class Bc>
 __device__ __forceinline__ void stage_slab2(T* __restrict__ S, const DevGrid& g, int c, int z0,
                                             const Val& val, const Bc& bc) {
   using SL = Slab2<B, KS>;
-  constexpr int BB = B * B;
-  for (int idx = threadIdx.x; idx < (KS + 4) * BB; idx += NT) {
-    const int kk = idx / BB, rem = idx - kk * BB, j = rem / B, i = rem - j * B;
+  constexpr int BB = B * B, Q = BB / 4;
+  // the planes, four cells along x per access: own cube, or a same-level z neighbour
+  // (its plane B + k below, k - B above); 2:1 and domain faces value by value
+  for (int idx = threadIdx.x; idx < (KS + 4) * Q; idx += NT) {
+    const int kk = idx / Q, q = idx - kk * Q, j = (4 * q) / B, i0 = 4 * q - j * B;
     const int k = z0 - 2 + kk;
-    T v;
-    if (k < 0) v = halo_value<B, T>(g, c, 4, i, j, -1 - k, val, bc);
-    else if (k >= B) v = halo_value<B, T>(g, c, 5, i, j, k - B, val, bc);
-    else v = val(c, (k * B + j) * B + i);
-    S[SL::at(i, j, kk)] = v;
+    T v[4];
+    int n = c, pl = k;
+    if (k < 0 || k >= B) {
+      const int f = k < 0 ? 4 : 5;
+      n = g.nb[6 * c + f];
+      pl = k < 0 ? B + k : k - B;
+      if (n < 0) {
+#pragma unroll 1
+        for (int m = 0; m < 4; ++m)
+          v[m] = halo_value<B, T>(g, c, f, i0 + m, j, k < 0 ? -1 - k : k - B, val, bc);
+      }
+    }
+    if (n >= 0) val.get4(n, pl * BB + 4 * q, v);
+    const int o = SL::at(i0, j, kk);
+    S[o] = v[0];
+    S[o + 1] = v[1];
+    S[o + 2] = v[2];
+    S[o + 3] = v[3];
   }
   for (int idx = threadIdx.x; idx < 8 * KS * B; idx += NT) {
     const int f = idx / (2 * KS * B), rem = idx - f * (2 * KS * B), layer = rem / (KS * B);
@@ -414,6 +433,14 @@ struct SumVal {
   __device__ __forceinline__ T operator()(int c, int cell) const {
     const size_t i = (size_t)c * B3 + cell;
     return a[i] + d[i];
+  }
+  __device__ __forceinline__ void get4(int c, int cell0, T (&v)[4]) const {
+    const size_t i = (size_t)c * B3 + cell0;
+    T w[4];
+    ld4(a + i, v);
+    ld4(d + i, w);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v[m] += w[m];
   }
 };
 
