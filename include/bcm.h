@@ -291,9 +291,10 @@ bcm_status bcm_adjoint_step(bcm_grid *grid, void *dev_adj, size_t bytes, const v
  *             / (1 + 3 dt nu/h^2),   E = u^n + dt (-N(u^n) + nu L(u^n))/2,
  * until ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| per sim (all components), or the
  * update has reached the rounding floor (<= 64 unit roundoffs of ||u^(k+1)||) and stopped
- * shrinking (its square >= 0.99 of the previous one), or cn_max_iter iterations; ghosts of u^(k) follow the halo rules with the outflow
- * values of t^n.  The mixed mode iterates on the increment u^(k) - u^n in FP32.  cn_rtol = 0 / cn_max_iter = 0 select the defaults (1e-10 FP64,
- * 2e-8 mixed, i.e. down to the FP32 floor; 50).
+ * shrinking (its square >= 0.99 of the previous one), or cn_max_iter iterations; ghosts
+ * of u^(k) follow the halo rules with the outflow values of t^n.  The mixed mode
+ * iterates on the increment u^(k) - u^n in FP32.  cn_rtol = 0 / cn_max_iter = 0 select
+ * the defaults (1e-10 FP64, 2e-8 mixed, i.e. down to the FP32 floor; 50).
  * Switching back to AB2 restarts it with an Euler step (N^{n-1} := N^n).  The adjoint
  * rejects grids on QUICK + Crank-Nicolson.  Errors: BCM_E_INVALID. */
 enum { BCM_SCHEME_AB2_CENTRAL = 0, BCM_SCHEME_QUICK_CN = 1 };
