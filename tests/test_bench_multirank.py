@@ -46,11 +46,14 @@ def test_reductions_and_barrier_over_two_gloo_ranks(tmp_path):
         "m = bench.max_over_ranks(1.5 + rank, ws)\n"
         "s = bench.sum_over_ranks(1.0 + 2.0 * rank, ws)\n"
         "bench.barrier(ws)\n"
-        "print(json.dumps({'ws': ws, 'rank': rank, 'local': local, 'max': m, 'sum': s}))\n"
+        f"out = open({str(tmp_path)!r} + '/rank%d.json' % rank, 'w')\n"
+        "out.write(json.dumps({'ws': ws, 'rank': rank, 'local': local, 'max': m, 'sum': s}))\n"
+        "out.close()\n"
         "dist.destroy_process_group()\n")
     r = torchrun([str(script)], timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = sorted(json_lines(r.stdout), key=lambda d: d["rank"])
+    # one file per rank: the two ranks' stdout lines may interleave
+    lines = [json.loads((tmp_path / f"rank{q}.json").read_text()) for q in range(2)]
     assert [d["rank"] for d in lines] == [0, 1]
     for d in lines:
         assert d["ws"] == 2 and d["local"] == d["rank"]
