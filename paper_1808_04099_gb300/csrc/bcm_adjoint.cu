@@ -34,7 +34,6 @@ using namespace bcm;
 namespace {
 
 constexpr int kNT = 256;
-constexpr int kNParams = 11;  // 8 inflow amplitudes, sphere centre (x, y, z)
 
 // Adjoint workspace (FP64, n cells each): the 3-vectors carry components x, y, z.
 struct AdjFields {
@@ -46,7 +45,8 @@ struct AdjFields {
   double *lp, *mu, *bsc;  // lambda of p, adjoint pressure, solve right-hand side
   double *lub, *lub2;     // lambda of the outflow face state (ping-pong)
   double *cg[4];          // FP64 CG vectors of the adjoint Poisson solve
-  double *acc;            // [kNParams] FP64 gradient accumulators (caller's dJ)
+  double *acc;            // [11] FP64 gradient accumulators (caller's dJ): 8 inflow
+                          // amplitudes, sphere centre (x, y, z)
 };
 
 size_t adj_layout(size_t n, size_t nub, AdjFields* F, unsigned char* base) {
