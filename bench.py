@@ -494,8 +494,8 @@ def gpu_arm(args, ws, rank, local):
         msq = max_over_ranks(msq, ws)
         kq = kernel_table(profq, n, prec == bcm.PREC_F64, phi_frac, itq)
         Sq = 8 if prec == bcm.PREC_F64 else 4
-        # momentum class per step: explicit half (u^n in; E', d^(0) out: 9 S), every
-        # iteration (u^n, d, E' in; d out: 12 S), the last launch (u^n, d, phi in; u* out,
+        # momentum class per step: explicit half (u^n in; E'', d^(0) out: 9 S), every
+        # iteration (u^n, d, E'' in; d out: 12 S), the last launch (u^n, d, phi in; u* out,
         # plus the outflow values: 10 S)
         mom_ms = kq["momentum"]["total_ms"] / kprof_steps
         mom_bytes = (19 + 12 * cnq / kprof_steps) * Sq * n
