@@ -53,7 +53,9 @@ def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
         "add_correction": 8 + 4 + 8,            # x64, e in; x64 out
         "correct": 8 + 8 + 6 * S,               # p, b, u* in; u out
         "solid_fraction": S + 1,
-        "pcg": 10 * S,                          # per iteration: pass A (4 S) + pass B (6 S)
+        # per iteration, the algorithmic minimum: read and write x, r, p (6 S); the
+        # schedule of each PCG form moves more (PCG_SCHEDULE_BYTES)
+        "pcg": 6 * S,
         # per V-cycle after pass A: finest level down with pass B (r, q, x, p in; x, r,
         # x_0, r_1 out: 7.125 S) and up (x_0, y_1, r in; z out: 3.125 S), the coarser
         # levels 1/7 of the V-cycle's part (0.75 S)
@@ -65,21 +67,50 @@ def bytes_per_cell(kernel: str, f64: bool, phi_frac: float) -> float:
     }[kernel]
 
 
+# Bytes per cell and PCG iteration that each persistent form's schedule moves (halo
+# reads of neighbour faces not counted): streaming two-pass (pass A r, p in, p, q out;
+# pass B x, p, r, q in, x, r out), fused single-barrier (x, r, q, p in and out, plus
+# the six face planes of r, q, p written to the face array: 0.375 of a cell's values
+# for 16^3 cubes).
+def pcg_schedule_bytes(form: int, f64: bool) -> float:
+    S = 8 if f64 else 4
+    return {1: 10 * S, 5: 8 * S + 3 * 0.375 * S}.get(form, 10 * S)
+
+
 PROFILE = "profiles/pcg_sphere_16x8x8_B16_mixed.md"
 PCG_SOURCES = ["bcm_pcg.cu", "bcm_persist.cuh", "bcm_cube.cuh", "bcm_internal.cuh",
                "bcm_kernels.h"]
 
 
-def profiled_pcg_traffic():
-    """DRAM bytes per PCG iteration from the committed ncu summary, or None when the
-    kernel sources changed since those counters were taken (hash recorded there)."""
+# ncu summary and the sources it was taken at, per persistent PCG form
+PROFILES = {1: (PROFILE, PCG_SOURCES),
+            5: ("profiles/pcg_fused_sphere_16x8x8_B16_mixed.md",
+                ["bcm_pcg_fused.cu", "bcm_persist.cuh", "bcm_cube.cuh", "bcm_internal.cuh",
+                 "bcm_kernels.h"])}
+
+
+def profile_for_form(form: int):
+    return PROFILES.get(form, (None, None))[0]
+
+
+def st_form(g) -> int:
+    return int(g.step(0, rtol=RTOL)[0]["pcg_form"])
+
+
+def profiled_pcg_traffic(form: int = 1):
+    """DRAM bytes per PCG iteration from the committed ncu summary of the PCG form, or
+    None when the kernel sources changed since those counters were taken (hash
+    recorded there)."""
     import hashlib
     import re
     here = os.path.dirname(os.path.abspath(__file__))
+    if form not in PROFILES:
+        return None
+    prof_path, sources = PROFILES[form]
     try:
-        text = open(os.path.join(here, PROFILE)).read()
+        text = open(os.path.join(here, prof_path)).read()
         h = hashlib.sha256()
-        for f in PCG_SOURCES:
+        for f in sources:
             with open(os.path.join(here, "paper_1808_04099_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
     except OSError:
@@ -260,14 +291,14 @@ def reference_arm(args, ws, rank):
 
 # ------------------------------------------------------------------- GPU arm
 
-def timed_steps(g, n, stream):
+def timed_steps(g, n, stream, rtol=RTOL):
     import torch
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(n):
-        g.step(1, rtol=RTOL, max_iter=20000, stats=False)
+        g.step(1, rtol=rtol, max_iter=20000, stats=False)
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1)
@@ -283,6 +314,135 @@ def timed_steps_graph(g, n, stream):
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1)
+
+
+def _rate(cells, steps, ms, ws):
+    return cells * steps / (ms / 1e3) * (ws if ws > 1 else 1)
+
+
+def _free():
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def leg_cavity64(dev, args, ws):
+    """The 64^3 lid-driven cavity in FP64 (4x4x4 cubes of 16^3, Re 100, rtol 1e-10)."""
+    from paper_1808_04099_gb300 import bcm
+    spec = W.config_cavity64(10)
+    g = bcm.Grid(spec, bcm.PREC_F64, device=dev)
+    g.load_state(W.initial_state(spec, seed=0, noise=1e-3))
+    g.step(args.warmup, rtol=1e-10, stats=False)
+    g.reset_time()
+    g.load_state(W.initial_state(spec, seed=0, noise=1e-3))
+    ms = max_over_ranks(timed_steps(g, 10, g.stream, rtol=1e-10), ws)
+    st = g.step(0, rtol=1e-10)[0]
+    del g
+    _free()
+    return {"value": _rate(spec.n_cells, 10, ms, ws), "unit": "cell-updates/s",
+            "ms_per_step": round(ms / 10, 4), "steps": 10, "cells": spec.n_cells,
+            "precision": "fp64", "rtol": 1e-10, "cg_iters_last_step": st["cg_iters"],
+            "pcg_form": st["pcg_form"]}
+
+
+def leg_two_level(dev, args, ws, peak):
+    """The two-level grid with three rotating ellipsoids (20,288 cubes of 16^3, 83.1M
+    cells, solid fraction recomputed every step), mixed, rtol 1e-8: its PCG vectors
+    (333 MB each in FP32) are far larger than L2."""
+    import torch
+    from paper_1808_04099_gb300 import bcm
+    spec = W.config_two_level(2)
+    n = spec.n_cells
+    g = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+    g.load_state(W.initial_state(spec))
+    g.step(1, rtol=RTOL, stats=False)
+    steps = 2
+    ms = max_over_ranks(timed_steps(g, steps, g.stream), ws)
+    st = g.step(0, rtol=RTOL)[0]
+    g.profile(True)
+    s1 = g.step(1, rtol=RTOL)[0]
+    prof, _ = g.profile_read(reset=True)
+    g.profile(False)
+    phi_frac = float(torch.count_nonzero(g.field(bcm.PHI)).item()) / n
+    del g
+    _free()
+    k = kernel_table(prof, n, False, phi_frac, s1["cg_iters"])
+    out = {"value": _rate(n, steps, ms, ws), "unit": "cell-updates/s",
+           "ms_per_step": round(ms / steps, 3), "steps": steps, "cells": n,
+           "precision": "FP32 sweeps + FP64 defect correction", "rtol": RTOL,
+           "cg_iters_last_step": st["cg_iters"], "refine_cycles_last_step": st["refine_cycles"],
+           "rel_resid_last_step": st["rel_resid"], "pcg_form": s1["pcg_form"]}
+    if "pcg" in k:
+        d = k["pcg"]
+        out["pcg"] = {"us_per_iter": round(d["us_per_iter"], 2),
+                      "GBps_6S": round(d["GBps"], 1), "frac_6S": round(d["GBps"] / peak, 4),
+                      "schedule_frac": round(pcg_schedule_bytes(s1["pcg_form"], False) *
+                                             n / (d["us_per_iter"] * 1e-6) / 1e9 / peak, 4),
+                      "share_of_step": round(d["total_ms"] / sum(v["total_ms"]
+                                                                for v in k.values()), 4)}
+    out["kernels_us"] = {kk: round(v["avg_us"], 1) for kk, v in k.items()}
+    return out
+
+
+def leg_batched(dev, args, ws):
+    """64 independent cavity / sphere sims (log-uniform 8..512 cubes of 16^3), one
+    flattened grid, graph-captured mixed steps at FP64 residual 1e-8."""
+    from paper_1808_04099_gb300 import bcm
+    spec = W.batched_mix(64, seed=0, steps=args.steps)
+    g = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+    g.load_state(W.initial_state(spec, seed=1, noise=1e-3))
+    g.step_graph(args.warmup, rtol=RTOL, stats=False)
+    ms = max_over_ranks(timed_steps_graph(g, args.steps, g.stream), ws)
+    st = g.step(0, rtol=RTOL)
+    del g
+    _free()
+    iters = [s["cg_iters"] for s in st]
+    return {"value": _rate(spec.n_cells, args.steps, ms, ws), "unit": "cell-updates/s",
+            "ms_per_step": round(ms / args.steps, 3), "steps": args.steps, "sims": spec.n_sims,
+            "cells": spec.n_cells, "cubes": spec.n_cubes, "precision": "mixed", "rtol": RTOL,
+            "converged": int(sum(s["converged"] for s in st)),
+            "cg_iters_last_step_min_max": [min(iters), max(iters)]}
+
+
+def leg_adjoint(dev, args, ws):
+    """Cost of the discrete adjoint on the 33.5M-cell sphere flow (32x16x16 cubes of
+    16^3, eight inflow modes): two FP64 steps forward with checkpoints, then the
+    reverse sweep (recompute and adjoint step), both at rtol 1e-8."""
+    import torch
+    from paper_1808_04099_gb300 import adjoint
+    spec = W.sphere_channel(32, 16, 16, 16, steps=2)
+    steps = 2
+    run = adjoint.AdjointRun(spec, np.zeros(8), np.array([1.0, 1.0, 1.0]), 0.25, steps,
+                             checkpoint_every=1, rtol=RTOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = run.forward()
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ga, gc = run.backward()
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    del run
+    _free()
+    return {"cells": spec.n_cells, "steps": steps, "rtol": RTOL, "precision": "fp64",
+            "forward_ms_per_step": round(1e3 * tf / steps, 1),
+            "backward_ms_per_step": round(1e3 * tb / steps, 1),
+            "backward_over_forward": round(tb / tf, 3),
+            "note": "backward = segment recompute + adjoint step (host-timed, includes "
+                    "the stats reads of the forward steps)",
+            "J": J, "dJ_dcx": float(gc[0])}
+
+
+def leg_fma():
+    from paper_1808_04099_gb300 import bcm
+    f64 = bcm.fma_rate(True)
+    f32 = bcm.fma_rate(False)
+    return {"fp64_tflops": round(f64 / 1e12, 3), "fp32_tflops": round(f32 / 1e12, 2),
+            "how": "bcm_measure_fma_rate: 8 FMA chains per thread, 8 x 256 threads per SM, "
+                   "best of 3 runs of ~20 ms, CUDA events"}
 
 
 def gpu_arm(args, ws, rank, local):
@@ -340,18 +500,28 @@ def gpu_arm(args, ws, rank, local):
     g.profile(False)
     phi_frac = float(torch.count_nonzero(g.field(bcm.PHI)).item()) / n
     kern = kernel_table(prof, n, False, phi_frac, iters32)
+    form32 = st_form(g)
     dom = max(kern, key=lambda k: kern[k]["total_ms"])
     d = kern[dom]
     traffic = None
     if dom == "pcg" and d.get("launches"):
-        per_iter = profiled_pcg_traffic()
+        per_iter = profiled_pcg_traffic(form32)
         if per_iter is not None:
             traffic = per_iter * d["units"] / d["launches"]
+    avg_s = d["avg_us"] * 1e-6
     roofline = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"], "peak": peak,
                 "unit": "GB/s", "frac": d["GBps"] / peak if d["GBps"] else None,
                 "traffic": traffic, "peak_kind": peak_kind,
+                "bytes_model": "6 S per cell and PCG iteration (read and write x, r, p), "
+                               "S = 4 B; units = iterations of the timed launches",
                 "bytes_per_launch": d["bytes_per_launch"],
-                "traffic_source": PROFILE if traffic is not None else None}
+                "us_per_iter": d.get("us_per_iter"),
+                "pcg_form": form32,
+                "schedule_bytes_per_cell_iter": pcg_schedule_bytes(form32, False),
+                "schedule_frac": (pcg_schedule_bytes(form32, False) * n * d["units"] /
+                                  d["launches"] / avg_s / 1e9 / peak) if dom == "pcg" else None,
+                "dram_frac": (traffic / avg_s / 1e9 / peak) if traffic is not None else None,
+                "traffic_source": profile_for_form(form32) if traffic is not None else None}
     share = {k: kern[k]["total_ms"] / sum(v["total_ms"] for v in kern.values()) for k in kern}
 
     # ---- e2e through the C ABI with host buffers (pinned), mixed precision
@@ -542,16 +712,73 @@ def gpu_arm(args, ws, rank, local):
                       "max_error_over_step": err / step, "step": step}
     del gw
 
-    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    _free()
+    # ---- the other workloads, each at its own size (one GPU)
+    legs = {}
+    if not args.no_legs:
+        legs["fma_peak"] = leg_fma()
+        legs["cavity64_fp64"] = leg_cavity64(dev, args, ws)
+        legs["batched64_graph_mixed"] = leg_batched(dev, args, ws)
+        legs["two_level_83M_mixed"] = leg_two_level(dev, args, ws, peak)
+        if not args.no_adjoint:
+            legs["adjoint_33M_fp64"] = leg_adjoint(dev, args, ws)
+    # the FP64 PCG's bound: min(HBM, FP64 FMA rate x arithmetic intensity); pass A
+    # (7-point stencil, <p,q>) and pass B (two axpys, z = r/diag, two dots) take about
+    # 30 FLOPs per cell per iteration against its schedule's 80 bytes
+    fp64_bound = None
+    t_iter = None
+    if "pcg" in k64 and k64["pcg"].get("us_per_iter"):
+        t_iter = k64["pcg"]["us_per_iter"] * 1e-6
+    elif "cg_a" in k64 and "cg_b" in k64 and iters64:
+        t_iter = (k64["cg_a"]["total_ms"] + k64["cg_b"]["total_ms"]) * 1e-3 / iters64
+    if "fma_peak" in legs and t_iter:
+        flops_cell = 30.0
+        t_alu = flops_cell * n / (legs["fma_peak"]["fp64_tflops"] * 1e12)
+        t_hbm = 6 * 8 * n / (peak * 1e9)
+        fp64_bound = {"us_per_iter": round(1e6 * t_iter, 2),
+                      "alu_bound_us": round(1e6 * t_alu, 2), "hbm_bound_us_6S": round(1e6 * t_hbm, 2),
+                      "bound": "fp64_alu" if t_alu > t_hbm else "hbm",
+                      "frac_of_bound": round(max(t_alu, t_hbm) / t_iter, 4),
+                      "flops_per_cell_iter": flops_cell}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only), all cores
+    # and one thread
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle as O
         full = W.config_sphere(1)
         v, dt, cores, _ = run_oracle_sample(full, 1)
+        old_threads = O.Oracle.set_threads(1)
+        small = reference_sample_spec()
+        v1, dt1, _, _ = run_oracle_sample(small, 1)
+        O.Oracle.set_threads(old_threads)
         cpu = {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"one fractional step of the full 4,194,304-cell sphere flow at "
-                         f"rtol 1e-8 from the same initial state ({dt:.1f} s)"}
+                         f"rtol 1e-8 from the same initial state ({dt:.1f} s)",
+               "single_thread": {"value": v1, "cores": 1,
+                                 "sample": f"one step of the same flow at half resolution "
+                                           f"(16x8x8 cubes of 8^3, {dt1:.1f} s)"}}
+
+    def rnd(x, nd=4):
+        if isinstance(x, dict):
+            return {k: rnd(v, nd) for k, v in x.items()}
+        if isinstance(x, list):
+            return [rnd(v, nd) for v in x]
+        if isinstance(x, float):
+            return float(f"{x:.{nd}g}") if x == x else x
+        return x
 
     if rank == 0:
+        summary = {
+            "mixed_value": value, "fp64_value": fp64_value,
+            "speedup_mixed_vs_fp64": value / fp64_value,
+            "pcg_us_per_iter": roofline["us_per_iter"], "pcg_frac_6S": roofline["frac"],
+            "pcg_dram_frac": roofline["dram_frac"], "pcg_form": form32,
+            "fp64_pcg_bound": fp64_bound,
+            "legs": {k: ({kk: vv for kk, vv in v.items() if kk not in ("kernels_us", "how", "note")}
+                         if isinstance(v, dict) else v) for k, v in legs.items()},
+            "mg_mixed_value": mg["mixed"]["value"], "mg_fp64_value": mg["fp64"]["value"],
+        }
         line = {
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
@@ -589,13 +816,15 @@ def gpu_arm(args, ws, rank, local):
                        "fp64": {"slabs_a,slabs_b": shape64, "us_per_iter": tune64}},
             "roofline": roofline,
             "kernels": kern, "kernel_share": share,
+            "legs_detail": legs,
+            "summary": summary,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s",
                     "h2d_bytes_per_step": h2d_step, "d2h_bytes_per_step": d2h_step},
             "gpu_launches": int(launches),
             "clocks": clk,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(rnd(line)), flush=True)
 
 
 def ncu_case(args):
@@ -640,6 +869,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other workloads (cavity, batched, two-level, adjoint)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run two mixed steps of the workload and exit (for ncu captures)")
     ap.add_argument("--ncu-fp64", action="store_true",

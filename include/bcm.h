@@ -191,6 +191,11 @@ bcm_status bcm_step_graph(bcm_grid *grid, int n_steps, double rtol, int max_iter
 bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int check_every,
                           double barrier_timeout_s, int recycle);
 
+/* The current solver controls of bcm_set_solver (any pointer may be NULL); inner_rtol
+ * is 0 while the automatic per-cycle reduction is in effect. */
+bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max_cycles,
+                          int32_t *check_every, double *barrier_timeout_s, int32_t *recycle);
+
 /* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
  * whose blocks loop over the iterations with two grid-wide barriers each, streaming
  * the vectors through global memory (default in mixed mode for grids of at most 256
@@ -232,21 +237,23 @@ bcm_status bcm_solve_pressure(bcm_grid *grid, double rtol, int max_iter, bcm_sta
 bcm_status bcm_fill_halo(bcm_grid *grid, int field, int kind, double *dev_out);
 
 /* Pressure solve that allocates no memory, for callers that cannot allocate device
- * memory at the moment they solve: code running while a CUDA graph is captured, an
- * application that reserves all GPU memory up front for its own pool, or a plugin
- * that must not call the allocator.  There is no counterpart in the paper: it is the
- * FP64 Jacobi-PCG of bcm_solve_pressure with its working memory (CG vectors, per-sim
- * solver state, block counters) in one fixed 32 MiB array inside the library's
- * device image instead of the grid workspace.  dev_b: right-hand side (FP64, grid
- * layout, read); dev_p: start value in, solution out (FP64, grid layout); the
- * grid's own fields are not touched.  The grid's device must be current.
+ * memory at the moment they solve: an application that reserves all GPU memory up
+ * front for its own pool or budget, or a plugin that must not call the allocator of
+ * the process it runs in.  There is no counterpart in the paper: it is the FP64
+ * Jacobi-PCG of bcm_solve_pressure (two launches per iteration) with its working
+ * memory (CG vectors, per-sim solver state, block counters) in one fixed 32 MiB array
+ * inside the library's device image instead of the grid workspace.  It solves in FP64
+ * on grids of either precision.  dev_b: right-hand side (FP64, grid layout, read);
+ * dev_p: start value in, solution out (FP64, grid layout); the grid's own fields are
+ * not touched.  The grid's device must be current.
  * Limits and sharing: grids needing more than 32 MiB (4 FP64 vectors, i.e. about
  * 1M cells, plus per-sim state) are rejected with BCM_E_BOUNDS; single-level grids
- * only.  The array stays allocated on every GPU that loads the library until the
- * process exits, and every call reuses it: calls that overlap on the GPU (other
- * streams or host threads on the same device) race.  The first call on each device
- * looks up the array's device address; make that first call before any stream
- * capture.  Synchronises the grid's stream; stats as in bcm_solve_pressure. */
+ * only (BCM_E_INVALID).  The array stays allocated on every GPU that loads the
+ * library until the process exits, and every call reuses it: calls that overlap on
+ * the GPU (other streams or host threads on the same device) race.  The first call on
+ * each device looks up the array's device address.  Synchronises the grid's stream.
+ * stats (host, [n_sims], or NULL): cg_iters, steps (the grid's step count), converged,
+ * rel_resid and pcg_form are filled; div_rel, drag, umax and cn_iters are 0. */
 bcm_status bcm_solve_pressure_static(bcm_grid *grid, const double *dev_b, double *dev_p,
                                      double rtol, int max_iter, bcm_stats *stats);
 
@@ -405,6 +412,14 @@ bcm_status bcm_profile(bcm_grid *grid, int enable);
  * timed launches are pending.  reset != 0 clears all counters after reading. */
 bcm_status bcm_profile_read(bcm_grid *grid, double *total_ms, int64_t *launches,
                             int64_t *launch_count, int reset);
+
+/* Measured fused multiply-add rate of the current device in FLOP/s (2 per FMA),
+ * FP64 (fp64 = 1) or FP32 (fp64 = 0): eight independent FMA chains per thread, eight
+ * blocks of 256 threads per SM, about 20 ms per timed run, the best of three runs
+ * timed by CUDA events on a stream of its own.  No counterpart in the paper: it is the
+ * denominator of the FP64 kernels' arithmetic roofline.  Uses no device memory
+ * beyond a 16-byte sink in the library image; synchronises its stream. */
+bcm_status bcm_measure_fma_rate(int fp64, double *flops_per_s);
 
 const char *bcm_last_error(void);
 

@@ -59,6 +59,8 @@ def lib():
         L.orc_n_slots.argtypes = [P]
         L.orc_n_slots.restype = C.c_int
         L.orc_threads.restype = C.c_int
+        L.orc_set_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_neighbors.argtypes = [P, P]
         L.orc_fill_ghosts.argtypes = [P, P, C.c_int, P, P]
         L.orc_solid_fraction.argtypes = [P] * 6
@@ -305,3 +307,8 @@ class Oracle:
     @staticmethod
     def threads() -> int:
         return lib().orc_threads()
+
+    @staticmethod
+    def set_threads(n: int) -> int:
+        """Threads of the oracle's parallel loops from now on; returns the previous count."""
+        return lib().orc_set_threads(int(n))

@@ -115,6 +115,18 @@ int orc_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops from now on (n >= 1); returns the previous count.
+ * Results do not depend on it: per-cube partial sums are added in cube order. */
+int orc_set_threads(int n) {
+    const int old = orc_threads();
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return old;
+}
+
 struct orc_grid {
     int B, G, max_level, n_sims, n_cubes, n_slots;
     int32_t *sim_off, *ijk, *extent, *bc, *sim_of, *level;

@@ -59,6 +59,7 @@ void orc_destroy(orc_grid *g);
 const char *orc_error(void);
 int orc_n_slots(const orc_grid *g);
 int orc_threads(void);
+int orc_set_threads(int n); /* threads of the parallel loops; returns the previous count */
 
 /* Face adjacency: out[c*6+f] = same-level neighbour id, -1 domain boundary,
  * -2 coarser neighbour, -3 four finer neighbours. */

@@ -44,7 +44,26 @@ def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
     p = grid.field(bcm.P)
     saved = p.clone()
     times = {}
+    caller_cycles = grid.get_solver()["max_cycles"]
     grid.set_solver(max_cycles=1)  # mixed mode: one inner solve per timing run
+    try:
+        _time_shapes(grid, iters, p, saved, times)
+    finally:
+        p.copy_(saved)
+        grid.set_solver(max_cycles=caller_cycles)
+    best = min(times, key=times.get)
+    pe, sa, sb = map(int, best.split(","))
+    grid.set_launch(sa, sb, persistent=pe)
+    if use_cache:
+        cache[key] = {"best": [pe, sa, sb], "times": times}
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return times
+
+
+def _time_shapes(grid, iters, p, saved, times):
+    """us per PCG iteration of every launch shape, into times."""
     for pe, sa, sb in SHAPES:
         if pe and sa > 1 and grid.spec.B != 16:
             continue
@@ -62,14 +81,3 @@ def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
             times[f"{pe},{sa},{sb}"] = 1e3 * tp / (npc * iters)
         elif na and nb:
             times[f"{pe},{sa},{sb}"] = 1e3 * (ta / na + tb / nb)
-    p.copy_(saved)
-    grid.set_solver(max_cycles=30)
-    best = min(times, key=times.get)
-    pe, sa, sb = map(int, best.split(","))
-    grid.set_launch(sa, sb, persistent=pe)
-    if use_cache:
-        cache[key] = {"best": [pe, sa, sb], "times": times}
-        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        with open(CACHE, "w") as f:
-            json.dump(cache, f, indent=1)
-    return times

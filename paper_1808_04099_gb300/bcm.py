@@ -25,7 +25,7 @@ SCHEME_AB2_CENTRAL, SCHEME_QUICK_CN = 0, 1
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
             "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch",
             "bcm_set_preconditioner", "bcm_apply_preconditioner",
-            "bcm_set_step", "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
+            "bcm_set_step", "bcm_get_solver", "bcm_measure_fma_rate", "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
             "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
             "bcm_fill_halo", "bcm_apply_poisson", "bcm_solve_pressure_static",
             "bcm_profile", "bcm_profile_read",
@@ -101,6 +101,8 @@ def lib(build: bool = True):
                                        C.c_int, P]
         L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int]
         L.bcm_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
+        L.bcm_get_solver.argtypes = [P, P, P, P, P, P]
+        L.bcm_measure_fma_rate.argtypes = [C.c_int, P]
         L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
         L.bcm_step_graph.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
         L.bcm_solve_pressure.argtypes = [P, C.c_double, C.c_int, P]
@@ -147,6 +149,13 @@ def _body_struct(b) -> Body:
     s.omega[:] = list(map(float, b.omega))
     s.vel[:] = list(map(float, b.vel))
     return s
+
+
+def fma_rate(fp64: bool = True) -> float:
+    """Measured FMA rate of the current device in FLOP/s (FP64 or FP32)."""
+    r = C.c_double()
+    _check(lib().bcm_measure_fma_rate(1 if fp64 else 0, C.byref(r)))
+    return r.value
 
 
 class Grid:
@@ -247,6 +256,15 @@ class Grid:
                    barrier_timeout_s: float = 0.0, recycle: int = -1):
         _check(lib().bcm_set_solver(self._h, inner_rtol, max_cycles, check_every,
                                     barrier_timeout_s, recycle))
+
+    def get_solver(self) -> dict:
+        """The solver controls in effect (inner_rtol 0 = automatic)."""
+        ir, bt = C.c_double(), C.c_double()
+        mc, ce, rc = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().bcm_get_solver(self._h, C.byref(ir), C.byref(mc), C.byref(ce),
+                                    C.byref(bt), C.byref(rc)))
+        return {"inner_rtol": ir.value, "max_cycles": mc.value, "check_every": ce.value,
+                "barrier_timeout_s": bt.value, "recycle": rc.value}
 
     def set_preconditioner(self, kind: int):
         """PRECOND_JACOBI (default) or PRECOND_MULTIGRID (single-level grids)."""

@@ -1253,6 +1253,18 @@ extern "C" bcm_status bcm_set_solver(bcm_grid* g, double inner_rtol, int max_cyc
   return BCM_OK;
 }
 
+extern "C" bcm_status bcm_get_solver(const bcm_grid* g, double* inner_rtol, int32_t* max_cycles,
+                                     int32_t* check_every, double* barrier_timeout_s,
+                                     int32_t* recycle) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (inner_rtol) *inner_rtol = g->inner_rtol > 0 ? g->inner_rtol : 0.0;
+  if (max_cycles) *max_cycles = g->max_cycles;
+  if (check_every) *check_every = g->check_every;
+  if (barrier_timeout_s) *barrier_timeout_s = g->barrier_timeout_s;
+  if (recycle) *recycle = g->recycle;
+  return BCM_OK;
+}
+
 extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, int slabs_b) {
   if (!g) return fail(BCM_E_INVALID, "grid is NULL");
   auto ok = [&](int ns) { return ns == 1 || ns == 2 || ns == 4; };

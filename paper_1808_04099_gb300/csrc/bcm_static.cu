@@ -1,9 +1,9 @@
 // bcm_static.cu -- a pressure solve that allocates no memory at all.
 //
-// Some callers cannot allocate device memory when they need a solve: code that runs
-// while a CUDA graph is being captured (a cudaMalloc there breaks the capture), a
-// host application whose GPU memory is fully reserved up front by its own pool or
-// budget, or a plugin that is not allowed to touch the allocator.  For them
+// Some callers cannot allocate device memory when they need a solve: a host
+// application whose GPU memory is fully reserved up front by its own pool or budget
+// (a cudaMalloc would fail or break that budget), or a plugin that is not allowed to
+// touch the allocator of the process it runs in.  For them
 // bcm_solve_pressure_static runs the FP64 Jacobi-PCG of bcm_solve_pressure with all
 // of its working memory (the CG vectors, the per-sim solver state and the block
 // counters) in one fixed array that lives in this library's device image.  The
@@ -13,6 +13,8 @@
 // The array is kStaticBytes (32 MiB) on every GPU that loads the library, held until
 // the process exits.  All calls share it: calls that overlap on the GPU (different
 // streams, or different host threads on the same device) race and corrupt each other.
+// The solve runs in FP64 whatever the grid's precision (the grid's tables and
+// per-sim constants are precision independent; its FP32 fields are not touched).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -146,16 +148,19 @@ extern "C" bcm_status bcm_solve_pressure_static(bcm_grid* grid, const double* de
     }
   }
   bcm_status rc = BCM_OK;
-  for (int q = 0; q < nsim; ++q) {  // one sim at a time through a stack copy
-    SimState t;
+  for (int q = 0; q < nsim; ++q) {  // one sim at a time through stack copies
+    SimState t, own;
     STATIC_TRY(cudaMemcpyAsync(&t, x.g.ss + q, sizeof(SimState), cudaMemcpyDeviceToHost, s));
+    // the step count is the grid's own (the scratch state starts every call at zero)
+    STATIC_TRY(cudaMemcpyAsync(&own, base.g.ss + q, sizeof(SimState), cudaMemcpyDeviceToHost, s));
     STATIC_TRY(cudaStreamSynchronize(s));
     if (stats) {
       memset(&stats[q], 0, sizeof(bcm_stats));
       stats[q].cg_iters = t.total_iters;
-      stats[q].steps = t.step;
+      stats[q].steps = own.step;
       stats[q].converged = t.converged;
       stats[q].rel_resid = t.bb > 0 ? sqrt(t.rr64 / t.bb) : 0.0;
+      stats[q].pcg_form = PCG_TWO_LAUNCH;
     }
     if (t.nonfinite) rc = BCM_E_NONFINITE;
     else if (!t.converged && rc == BCM_OK) rc = BCM_E_NOT_CONVERGED;

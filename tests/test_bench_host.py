@@ -1,7 +1,9 @@
-"""Host-side arithmetic of bench.py on CPU: the algorithmic byte model, the per-kernel
-table the roofline line is built from (GB/s = algorithmic bytes / event time, the
-persistent PCG counted per iteration), and the rule that DRAM traffic from the
-committed ncu summary is used only while the profiled kernel sources are unchanged."""
+"""Host-side arithmetic of bench.py on CPU: the algorithmic byte model (the PCG at
+its minimum of 6 values per cell and iteration: x, r, p read and written), the bytes
+each PCG form's schedule moves, the per-kernel table the roofline line is built from
+(GB/s = algorithmic bytes / event time, the persistent PCG counted per iteration), and
+the rule that DRAM traffic from the committed ncu summary is used only while the
+profiled kernel sources are unchanged."""
 import hashlib
 import os
 
@@ -11,10 +13,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_byte_model():
-    assert bench.bytes_per_cell("pcg", False, 0.0) == 40      # 10 FP32 vectors per cell
-    assert bench.bytes_per_cell("pcg", True, 0.0) == 80
+    assert bench.bytes_per_cell("pcg", False, 0.0) == 24      # 6 FP32 values per cell
+    assert bench.bytes_per_cell("pcg", True, 0.0) == 48
+    # the two-pass schedule moves 10 values: the two passes of one iteration
     assert bench.bytes_per_cell("cg_a", False, 0.0) + bench.bytes_per_cell("cg_b", False, 0.0) \
-        == bench.bytes_per_cell("pcg", False, 0.0)           # the two passes of one iteration
+        == bench.pcg_schedule_bytes(1, False) == 40
+    # the fused single-barrier form: x, r, q, p in and out plus the face planes
+    assert bench.pcg_schedule_bytes(5, False) == 8 * 4 + 3 * 0.375 * 4
     assert bench.bytes_per_cell("momentum", False, 0.5) == 12 * 4 + 0.5 * 4
 
 
@@ -24,8 +29,8 @@ def test_kernel_table_rates():
     assert "mg" not in t                                      # never launched
     p = t["pcg"]
     assert p["units"] == 100 and p["launches"] == 2
-    assert p["bytes_per_launch"] == 40 * 1000 * 100 / 2
-    assert abs(p["GBps"] - 40 * 1000 * 100 / 10e-3 / 1e9) < 1e-12
+    assert p["bytes_per_launch"] == 24 * 1000 * 100 / 2
+    assert abs(p["GBps"] - 24 * 1000 * 100 / 10e-3 / 1e9) < 1e-12
     assert abs(p["us_per_iter"] - 100.0) < 1e-12
     r = t["rhs"]
     assert r["units"] == 5 and abs(r["avg_us"] - 200.0) < 1e-12
@@ -43,11 +48,12 @@ def _source_hash():
 def test_profiled_traffic_only_for_matching_sources(tmp_path, monkeypatch):
     good = tmp_path / "good.md"
     good.write_text(f"sources = `{_source_hash()}`\n\ndram bytes per PCG iteration: 123456\n")
-    monkeypatch.setattr(bench, "PROFILE", str(good))
-    assert bench.profiled_pcg_traffic() == 123456.0
+    monkeypatch.setitem(bench.PROFILES, 1, (str(good), bench.PCG_SOURCES))
+    assert bench.profiled_pcg_traffic(1) == 123456.0
     stale = tmp_path / "stale.md"
     stale.write_text("sources = `0123456789abcdef`\n\ndram bytes per PCG iteration: 123456\n")
-    monkeypatch.setattr(bench, "PROFILE", str(stale))
-    assert bench.profiled_pcg_traffic() is None
-    monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.md"))
-    assert bench.profiled_pcg_traffic() is None
+    monkeypatch.setitem(bench.PROFILES, 1, (str(stale), bench.PCG_SOURCES))
+    assert bench.profiled_pcg_traffic(1) is None
+    monkeypatch.setitem(bench.PROFILES, 1, (str(tmp_path / "missing.md"), bench.PCG_SOURCES))
+    assert bench.profiled_pcg_traffic(1) is None
+    assert bench.profiled_pcg_traffic(0) is None              # no summary for that form
