@@ -463,3 +463,83 @@ def test_taylor_green_decay_converges():
     assert e2 < e1 / 3.0 and e2 < 5e-3
     assert np.all(np.diff(ke2) < 0)             # kinetic energy decays monotonically
     assert w2 < 1e-12                            # stays two-dimensional
+
+
+# ------------------------------------------------ Adams-Bashforth combination (R3)
+
+def test_ab2_transverse_mode_follows_the_recurrence():
+    """A uniform stream u = U carrying a transverse mode v = eps sin(k x) through the
+    all-periodic box.  With u uniform and v constant along y and z, the conservative
+    central convection of v is exactly U times the central difference of v, that of u
+    and w is zero, the Laplacian acts on the mode by its discrete eigenvalue, and every
+    face divergence is zero, so the pressure stays zero and the projection leaves the
+    field alone.  The complex amplitude a of v = Re(a e^{ikx}) then follows the
+    Adams-Bashforth-2 recurrence of the momentum sub-step (Euler first step, R3):
+        a_1     = a_0 + dt (-s a_0 - nu lam a_0)
+        a_{n+1} = a_n + dt (-(3/2 s a_n - 1/2 s a_{n-1}) - nu lam a_n)
+    with s = i U sin(kh)/h and lam = (4/h^2) sin^2(kh/2).  A wrong weight, sign or lag
+    in the combination (or Euler throughout) is off by O(dt^2 |s|^2 |a|) per step, far
+    above the 1e-12 held here."""
+    spec = W.periodic_box(2, 8, nu=0.05)
+    h, dt, nu = spec.sim_h0[0], spec.sim_dt[0], spec.sim_nu[0]
+    U, eps, k = 1.0, 0.1, 2.0
+    X = centres(spec)
+    st0 = W.initial_state(spec)
+    st0.u = np.full(spec.n_cells, U)
+    st0.v = eps * np.sin(k * X[:, 0])
+    st0.w = np.zeros(spec.n_cells)
+    o = O.Oracle(spec)
+    st = o.new_state(st0)
+    s = 1j * U * math.sin(k * h) / h
+    lam = 4.0 / h ** 2 * math.sin(k * h / 2) ** 2
+    a_prev, a = None, -1j * eps
+    phase = np.exp(1j * k * X[:, 0])
+    for n in range(4):
+        stats, rc = o.step(st, 1, rtol=1e-13)
+        assert rc == 0
+        if n == 0:
+            a_next = a + dt * (-s * a - nu * lam * a)
+        else:
+            a_next = a + dt * (-(1.5 * s * a - 0.5 * s * a_prev) - nu * lam * a)
+        a_prev, a = a, a_next
+        v_exact = np.real(a * phase)
+        assert np.abs(st["v"] - v_exact).max() <= 1e-12 * eps, n
+        assert np.abs(st["u"] - U).max() <= 1e-13 and np.abs(st["w"]).max() <= 1e-13
+        assert np.abs(st["p"]).max() <= 1e-12
+    # the recurrence is not the Euler one: after four steps the two differ clearly
+    a_e = -1j * eps
+    for n in range(4):
+        a_e = a_e + dt * (-s * a_e - nu * lam * a_e)
+    assert abs(a_e - a) > 1e3 * 1e-12 * eps
+
+
+# ------------------------------------------------ convective outflow face values (R8)
+
+def test_outflow_face_values_advance_by_the_convective_update():
+    """Outflow face values away from the interior values: one step advances each face
+    value by the explicit convective update of R8, u_b^{n+1} = u_b^n - U_c dt (u_b^n -
+    u_0^n) / (h/2), u_0 the interior cell next to the face at t^n (not the face-to-
+    centre distance h, and with the sign that relaxes u_b towards u_0)."""
+    spec = W.sphere_channel(4, 2, 2, 4, center=(90, 90, 90))
+    B = spec.B
+    rng = np.random.default_rng(12)
+    st0 = W.initial_state(spec, 3, 0.2)
+    st0.ub = st0.ub + rng.uniform(-0.3, 0.3, st0.ub.shape)
+    o = O.Oracle(spec)
+    st = o.new_state(st0)
+    stats, rc = o.step(st, 1, rtol=1e-12)
+    assert rc == 0
+    h, dt, Uc = spec.sim_h0[0], spec.sim_dt[0], spec.sim_uconv[0]
+    slots = W.outflow_slots(spec)
+    assert len(slots) > 0
+    ub1 = st["ub"].reshape(st0.ub.shape)
+    vel = [cube_view(f, spec) for f in (st0.u, st0.v, st0.w)]  # [c, k, j, i]
+    for sl, (c, f) in enumerate(slots):
+        assert f == 1  # +x outflow: tangential a = y (fastest), b = z
+        for comp in range(3):
+            u0 = vel[comp][c, :, :, B - 1]          # [b = z, a = y]
+            ub0 = st0.ub[sl, comp]
+            expect = ub0 - Uc * dt * (ub0 - u0) / (0.5 * h)
+            assert np.abs(ub1[sl, comp] - expect).max() <= 1e-15 * (1 + np.abs(expect).max())
+    # the update moves every face value: u_b^n - u_0^n is nowhere zero here
+    assert np.abs(ub1 - st0.ub).min() > 0.0
