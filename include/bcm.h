@@ -120,7 +120,8 @@ typedef struct {
     int32_t pcg_form;      /* PCG of the last solve: 0 two launches per iteration,
                               1 persistent streaming, 2 persistent single-reduction,
                               3 persistent with the state on chip, 4 multigrid-
-                              preconditioned (two launches and a V-cycle) */
+                              preconditioned (two launches and a V-cycle), 5 persistent
+                              fused (one grid barrier per iteration, bulk-copy staging) */
     int32_t cn_iters;      /* QUICK + Crank-Nicolson: iterations of the last momentum
                               sub-step (0 with Adams-Bashforth) */
 } bcm_stats;
@@ -196,16 +197,22 @@ bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int
 bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max_cycles,
                           int32_t *check_every, double *barrier_timeout_s, int32_t *recycle);
 
-/* Launch shape of the PCG.  persistent = 1: every PCG solve is one cooperative launch
- * whose blocks loop over the iterations with two grid-wide barriers each, streaming
- * the vectors through global memory (default in mixed mode for grids of at most 256
- * sims); persistent = 3: the same iteration with each cube's search direction kept in
+/* Launch shape of the PCG.  persistent = 5 (the default in mixed mode on 16^3 cubes for
+ * grids of at most 256 sims and 256 cubes per SM): one cooperative launch per solve,
+ * one 1024-thread block per SM, one grid barrier per iteration (the beta of the next
+ * iteration follows from <q,z> and <q,D^-1 q> of the same pass), each cube's r, q, p, x
+ * and its neighbours' face planes staged by bulk asynchronous copies two cubes ahead;
+ * grids it does not fit run persistent = 1.  persistent = 1: every PCG solve is one
+ * cooperative launch whose blocks loop over the iterations with two grid-wide barriers
+ * each, streaming the vectors through global memory (the mixed-mode default on 4^3 and
+ * 8^3 cubes); persistent = 3: the same iteration with each cube's search direction kept in
  * shared memory, when every cube fits a co-resident block of at most two cubes (FP32
  * inner solve, 16^3 or 8^3 cubes, slabs_a = 1), else the streaming form; persistent = 2:
  * the single-reduction form of the iteration (Chronopoulos-Gear: one pass and one
  * barrier per iteration, three more vectors, the same iterates in exact arithmetic).
  * slabs_a = z-slabs per cube of the streaming work items (1, 2 or 4; 16^3 cubes only
- * for 2 and 4).  persistent = 0: two launches per iteration (the FP64 default), one CTA
+ * for 2 and 4; slabs_a = 1 with 5).  persistent = 0: two launches per iteration (the FP64
+ * default), one CTA
  * per z-slab, slabs_a / slabs_b slabs per cube for pass A / pass B.  Results do not
  * depend on the shape beyond rounding; bcm_stats.pcg_form says which form ran.
  * BCM_E_INVALID for other values. */
@@ -299,7 +306,8 @@ bcm_status bcm_adjoint_step(bcm_grid *grid, void *dev_adj, size_t bytes, const v
  * until ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| per sim (all components), or the
  * update has reached the rounding floor (<= 64 unit roundoffs of ||u^(k+1)||) and stopped
  * shrinking (its square >= 0.99 of the previous one), or cn_max_iter iterations; ghosts
- * of u^(k) follow the halo rules with the outflow values of t^n.  The mixed mode
+ * of u^(k) (velocities of t^{n+1}) follow the halo rules with the outflow values advanced
+ * to t^{n+1}; those of u^n in E with the outflow values of t^n.  The mixed mode
  * iterates on the increment u^(k) - u^n in FP32.  cn_rtol = 0 / cn_max_iter = 0 select
  * the defaults (1e-10 FP64, 2e-8 mixed, i.e. down to the FP32 floor; 50).
  * Switching back to AB2 restarts it with an Euler step (N^{n-1} := N^n).  The adjoint

@@ -62,8 +62,11 @@
  *      iteration from the forward-Euler predictor u^(0) = 2 E - u^n,
  *        u^(k+1) = (E - dt/2 N(u^(k)) + dt nu/2 (sum of the 6 neighbours of u^(k))/h^2)
  *                  / (1 + 3 dt nu / h^2),     E = u^n + dt (-N(u^n)/2 + nu L(u^n)/2),
- *      whose fixed point is the Crank-Nicolson step; ghosts of u^(k) by the halo rules
- *      with the outflow face values of t^n (the whole sub-step sees u_b^n).  A sim stops iterating once
+ *      whose fixed point is the Crank-Nicolson step; E takes the ghosts of u^n (outflow
+ *      face values of t^n), and the ghosts of u^(k), iterates of u~ and so velocities of
+ *      t^{n+1}, follow the halo rules with the outflow face values of t^{n+1} (R8's update
+ *      from u^n).  The start u^(0) and the two stops below move the result by no more
+ *      than the iteration tolerance: the fixed point is unique.  A sim stops iterating once
  *      ||u^(k+1) - u^(k)|| <= cn_rtol ||u^(k+1)|| (all three components), once the update
  *      has reached the rounding floor of the arithmetic (at most 64 eps ||u^(k+1)||, eps
  *      the unit roundoff) and no longer shrinks (its square >= 0.99 of the previous
@@ -1125,8 +1128,9 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                             ubn[id] = ub[id] - Uc * dt * (ub[id] - u0) / (0.5 * h);
                         }
             }
-        /* (c') QUICK + Crank-Nicolson (R20): explicit half E, the iteration for u~ (ghosts
-         * with the outflow values of t^n), then the IB forcing of u~ */
+        /* (c') QUICK + Crank-Nicolson (R20): explicit half E (ghosts of u^n with the
+         * outflow values of t^n), the iteration for u~ (ghosts of the iterates, velocities
+         * of t^{n+1}, with the outflow values of t^{n+1} from (d)), then the IB forcing */
         if (g->scheme == 1) {
 #pragma omp parallel for schedule(static)
             for (int c = 0; c < g->n_cubes; ++c) {
@@ -1153,9 +1157,9 @@ static int step_impl(const orc_grid *g, double *u, double *v, double *w, double 
                 int alive = 0;
                 for (int s = 0; s < g->n_sims; ++s) alive |= !cndone[s];
                 if (!alive) break;
-                orc_fill_ghosts(g, cnA[0], 0, ub, gu);
-                orc_fill_ghosts(g, cnA[1], 1, ub, gv);
-                orc_fill_ghosts(g, cnA[2], 2, ub, gw);
+                orc_fill_ghosts(g, cnA[0], 0, ubn, gu);
+                orc_fill_ghosts(g, cnA[1], 1, ubn, gv);
+                orc_fill_ghosts(g, cnA[2], 2, ubn, gw);
 #pragma omp parallel for schedule(static)
                 for (int c = 0; c < g->n_cubes; ++c) {
                     int s = g->sim_of[c];

@@ -70,6 +70,31 @@ struct VelocityBC {
   }
 };
 
+// The same rules for a velocity of t^{n+1} (the iterates of the implicit half of
+// Eq. substep1): outflow faces take the face value advanced by the convective update
+// u_b^{n+1} = u_b^n - U_c dt (u_b^n - u_0^n) / (h/2) (R8), u_0^n the face cell of u^n.
+template <int B, class T>
+struct VelocityBCNext {
+  const DevGrid* g;
+  const SimParams* sp;
+  const T* ub;
+  const T* un;  // u^n of this component
+  int c, comp;
+  T coef;       // U_c dt / (h/2) of cube c
+  __device__ __forceinline__ T operator()(int f, int a, int b, T u0) const {
+    const int bc = sp->bc[f];
+    if (bc == BC_SLIP) return (comp == (f >> 1)) ? -u0 : u0;
+    if (bc == BC_OUTFLOW) {
+      const int sl = g->slot[6 * c + f];
+      const T vb = ub[((size_t)(sl * 3 + comp) * B + b) * B + a];
+      const int d = f >> 1;
+      const T uf = un[(size_t)c * B * B * B + cell_of<B>(d, (f & 1) ? B - 1 : 0, a, b)];
+      return T(2) * (vb - coef * (vb - uf)) - u0;
+    }
+    return T(2.0 * face_velocity<B>(*g, c, f, comp, a, b)) - u0;
+  }
+};
+
 template <class T>
 struct FieldVal {
   const T* f;
@@ -556,9 +581,11 @@ __global__ __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 3) void k_cn_iter(DevGrid 
     const T* src[3] = {odd ? db0 : da0, odd ? db1 : da1, odd ? db2 : da2};
     T* dst[3] = {odd ? da0 : db0, odd ? da1 : db1, odd ? da2 : db2};
     const T* un[3] = {u, v, w};
+    // the iterates are velocities of t^{n+1}: outflow ghosts from u_b^{n+1}
+    const T coef = T(sp.uconv * sp.dt / (0.5 * cell_h<B>(g, c)));
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
-      VelocityBC<B, T> vb{&g, &sp, ub, c, comp};
+      VelocityBCNext<B, T> vb{&g, &sp, ub, un[comp], c, comp, coef};
       stage_slab2<B, KS, NT>(S0 + comp * SL::N, g, c, z0, SumVal<T>{un[comp], src[comp], B3}, vb);
     }
     __syncthreads();
@@ -827,6 +854,7 @@ __global__ void k_solve_begin(DevGrid g, unsigned int* guard) {
     t.nonfinite = 0;
     t.zero_rhs = 0;
     t.umax_bits = 0ull;
+    t.fz_valid = 0;
   }
   if (threadIdx.x == 0) guard[0] = 0u;
 }
