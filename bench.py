@@ -840,6 +840,10 @@ def ncu_case(args):
         g.set_launch(1, 1, persistent=0)
     elif args.ncu_single_pass:
         g.set_launch(1, 1, persistent=2)
+    elif args.ncu_streaming:
+        g.set_launch(1, 1, persistent=1)
+    elif args.ncu_fused:
+        g.set_launch(1, 1, persistent=5)
     if args.ncu_mg:
         g.set_preconditioner(bcm.PRECOND_MULTIGRID)
     if args.ncu_cn:
@@ -883,6 +887,10 @@ def main():
                     help="with --ncu-case: two launches per PCG iteration")
     ap.add_argument("--ncu-single-pass", action="store_true",
                     help="with --ncu-case: the single-reduction persistent PCG")
+    ap.add_argument("--ncu-streaming", action="store_true",
+                    help="with --ncu-case: the two-pass streaming persistent PCG")
+    ap.add_argument("--ncu-fused", action="store_true",
+                    help="with --ncu-case: the fused single-barrier persistent PCG")
     ap.add_argument("--ncu-mg", action="store_true",
                     help="with --ncu-case: the multigrid-preconditioned PCG")
     ap.add_argument("--ncu-cn", action="store_true",

@@ -197,15 +197,15 @@ bcm_status bcm_set_solver(bcm_grid *grid, double inner_rtol, int max_cycles, int
 bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max_cycles,
                           int32_t *check_every, double *barrier_timeout_s, int32_t *recycle);
 
-/* Launch shape of the PCG.  persistent = 5 (the default in mixed mode on 16^3 cubes for
- * grids of at most 256 sims and 256 cubes per SM): one cooperative launch per solve,
+/* Launch shape of the PCG.  persistent = 5 (mixed mode on 16^3 cubes, grids of at most
+ * 256 sims and 256 cubes per SM): one cooperative launch per solve,
  * one 1024-thread block per SM, one grid barrier per iteration (the beta of the next
  * iteration follows from <q,z> and <q,D^-1 q> of the same pass), each cube's r, q, p, x
  * and its neighbours' face planes staged by bulk asynchronous copies two cubes ahead;
  * grids it does not fit run persistent = 1.  persistent = 1: every PCG solve is one
  * cooperative launch whose blocks loop over the iterations with two grid-wide barriers
- * each, streaming the vectors through global memory (the mixed-mode default on 4^3 and
- * 8^3 cubes); persistent = 3: the same iteration with each cube's search direction kept in
+ * each, streaming the vectors through global memory (the mixed-mode default);
+ * persistent = 3: the same iteration with each cube's search direction kept in
  * shared memory, when every cube fits a co-resident block of at most two cubes (FP32
  * inner solve, 16^3 or 8^3 cubes, slabs_a = 1), else the streaming form; persistent = 2:
  * the single-reduction form of the iteration (Chronopoulos-Gear: one pass and one

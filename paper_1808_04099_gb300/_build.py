@@ -61,7 +61,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nv, "-shared", *ARCH, *objs, "-o", tmp], capture_output=True, text=True)
+    r = subprocess.run([nv, "-shared", *ARCH, *objs, "-o", tmp, "-ldl"], capture_output=True,
+                       text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -20,11 +20,23 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bcm.h"
 #include "bcm_internal.cuh"
 #include "bcm_kernels.h"
 
 using namespace bcm;
+
+// NVTX range around a phase of the step (no-op unless a profiler is attached): the
+// ranges name the paper's sub-steps in a timeline and let a profiler select the
+// kernels of one phase.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 static thread_local std::string g_last_error;
 
@@ -54,6 +66,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t u, v, w, us, vs, ws, nx, ny, nz, phi, ub, p, b, bid, near_, r, p0, p1, q, e, w1, s0, s1;
+  size_t face;  // fused PCG face planes (mixed mode, 16^3 cubes)
   size_t nb, aux, sim, lvl, ijk, w3, nbw3, slot, sp, ss, counter, flags, guard, bar, err;
   size_t total;
   size_t n_slots;
@@ -384,6 +397,10 @@ Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml)
   L.r = take(n * V); L.p0 = take(n * V); L.p1 = take(n * V); L.q = take(n * V);
   L.e = take(d->precision == BCM_PREC_F64 ? 0 : n * 4);
   L.w1 = take(n * V); L.s0 = take(n * V); L.s1 = take(n * V);
+  // fused PCG: r, q, p on the six face planes of every cube, two parities
+  L.face = (d->precision != BCM_PREC_F64 && d->cells_per_edge == 16)
+               ? take((size_t)2 * d->n_cubes * 6 * 3 * 16 * 16 * sizeof(float))
+               : 0;
   L.nb = take(6 * sizeof(int) * d->n_cubes);
   L.aux = take(24 * sizeof(int) * d->n_cubes);
   L.sim = take(sizeof(int) * d->n_cubes);
@@ -444,7 +461,7 @@ struct StepGraph {
   cudaStream_t capture_stream = nullptr;
   double rtol = 0.0;
   int max_iter = 0, cycles = 0;
-  int slabs_p = 0, single_pass = 0, resident = 0;  // the PCG launch shape captured
+  int slabs_p = 0, single_pass = 0, resident = 0, fused = 0;  // the PCG launch shape captured
   double inner_rtol = 0.0;
   int persistent_slabs = 0;
   int recycle = -1;
@@ -645,6 +662,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
   x.single_pass = 0;
   x.resident = 0;
+  x.fused = 0;  // the fused single-barrier form: selected by bcm_set_launch(5, ...)
   x.lag_bf16 = desc->lagged_bf16;
   x.stream = s;
   DevGrid& G = x.g;
@@ -675,6 +693,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.r = W + L.r; F.p0 = W + L.p0; F.p1 = W + L.p1; F.q = W + L.q;
   F.e = g->f64 ? nullptr : (float*)(W + L.e);
   F.w1 = W + L.w1; F.s0 = W + L.s0; F.s1 = W + L.s1;
+  F.face = L.face ? (float*)(W + L.face) : nullptr;
   F.guard = (unsigned int*)(W + L.guard);
   F.bar = (unsigned int*)(W + L.bar);
   F.err = (int*)(W + L.err);
@@ -1073,20 +1092,28 @@ extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_it
   bcm_status last = BCM_OK;
   const bool particles = x.part.n > 0;
   for (int n = 0; n < n_steps; ++n) {
+    NvtxRange step_range("bcm_step");
     if (moving && !particles) RUN(BCM_K_SOLID_FRACTION, launch_solid_fraction(x, -2));
     {
+      NvtxRange r("momentum_ib");
       bcm_status sm = momentum_substep(g);
       if (sm != BCM_OK) return sm;
+      if (particles) {  // forcing by the Lagrangian particles: force, then spreading
+        RUN(BCM_K_IB, launch_ib_force(x));
+        g->launch_count += 1;
+      }
     }
-    if (particles) {  // forcing by the Lagrangian particles: force, then spreading
-      RUN(BCM_K_IB, launch_ib_force(x));
-      g->launch_count += 1;
+    {
+      NvtxRange r("pressure_poisson");
+      RUN(BCM_K_RHS, launch_rhs(x));
+      bcm_status st = solve(g, rtol, max_iter);
+      if (st != BCM_OK) return st;
     }
-    RUN(BCM_K_RHS, launch_rhs(x));
-    bcm_status st = solve(g, rtol, max_iter);
-    if (st != BCM_OK) return st;
-    RUN(BCM_K_CORRECT, launch_correct(x));
-    RUN(BCM_K_MISC, launch_step_end(x));
+    {
+      NvtxRange r("projection");
+      RUN(BCM_K_CORRECT, launch_correct(x));
+      RUN(BCM_K_MISC, launch_step_end(x));
+    }
     if (particles && moving) {  // move, then rebuild the per-cube sets
       RUN(BCM_K_IB, launch_ib_move(x));
       g->launch_count += 3;
@@ -1165,7 +1192,7 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
   if (!sg.exec || sg.rtol != rtol || sg.max_iter != max_iter || sg.cycles != cycles ||
       sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle ||
       sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass ||
-      sg.resident != g->ctx.resident || sg.gen != g->gen) {
+      sg.resident != g->ctx.resident || sg.fused != g->ctx.fused || sg.gen != g->gen) {
     if (sg.exec) CUDA_TRY(cudaGraphExecDestroy(sg.exec));
     if (sg.graph) CUDA_TRY(cudaGraphDestroy(sg.graph));
     sg.exec = nullptr;
@@ -1201,8 +1228,10 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     sg.slabs_p = g->ctx.slabs_p;
     sg.single_pass = g->ctx.single_pass;
     sg.resident = g->ctx.resident;
+    sg.fused = g->ctx.fused;
     sg.gen = g->gen;
   }
+  NvtxRange r("bcm_step_graph");
   for (int n = 0; n < n_steps; ++n) {
     CUDA_TRY(cudaGraphLaunch(sg.exec, g->stream));
     g->launch_count += (long long)sg.kernels;  // every kernel node of the step
@@ -1273,10 +1302,13 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
     return fail(BCM_E_BOUNDS, "the persistent PCG handles at most 256 sims per grid");
   if (g->B / slabs_a < 1 || g->B / slabs_b < 1 || (g->B * g->B / 4) * (g->B / slabs_b) < 1)
     return fail(BCM_E_INVALID, "slab too thin for this cube size");
-  if (persistent < 0 || persistent > 3) return fail(BCM_E_INVALID, "persistent must be 0 .. 3");
+  if (persistent < 0 || persistent > 5 || persistent == 4)
+    return fail(BCM_E_INVALID, "persistent must be 0, 1, 2, 3 or 5");
   g->ctx.persistent = persistent ? 1 : 0;
   g->ctx.single_pass = persistent == 2 ? 1 : 0;
   g->ctx.resident = persistent == 3 ? 1 : 0;
+  g->ctx.fused = persistent == 5 ? 1 : 0;
+  if (persistent == 5 && slabs_a != 1) return fail(BCM_E_INVALID, "the fused form takes whole cubes");
   if (persistent) {
     if (g->B != 16 && slabs_a != 1) return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
     g->ctx.slabs_p = slabs_a;
@@ -1290,6 +1322,7 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
 extern "C" bcm_status bcm_solve_pressure(bcm_grid* g, double rtol, int max_iter, bcm_stats* stats) {
   if (!g) return fail(BCM_E_INVALID, "grid is NULL");
   if (!(rtol > 0) || max_iter < 1) return fail(BCM_E_INVALID, "need rtol > 0, max_iter >= 1");
+  NvtxRange r("bcm_solve_pressure");
   RUN(BCM_K_MISC, launch_bmean(g->ctx));
   bcm_status st = solve(g, rtol, max_iter);
   if (st != BCM_OK) return st;

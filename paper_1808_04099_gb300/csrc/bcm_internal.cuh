@@ -48,7 +48,7 @@ struct SimParams {
 // Accumulators are striped over kStripes cache lines (block index mod kStripes) so
 // that thousands of blocks adding into one sim do not serialise on one address.
 constexpr int kStripes = 8;
-constexpr int kAccPad = 24;  // doubles per stripe (192 bytes)
+constexpr int kAccPad = 40;  // doubles per stripe (320 bytes)
 
 // Per-sim mutable state (solver scalars and atomic accumulators).
 struct SimState {
@@ -81,6 +81,9 @@ struct SimState {
   int cn_iter;         //   iterations of this step's momentum solve
   int cn_done;         //   that solve has converged (or hit its iteration limit)
   int ab2_restart;     // the next Adams-Bashforth step takes N^{n-1} := N^n
+  int fz_par;          // fused PCG: face-array parity written by the last pass
+  int fz_valid;        //   the last launch of this solve left r, p and faces to resume from
+  double fz_rzpred;    //   the <r,z> its last direction was formed with
 };
 
 enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 5,
@@ -90,7 +93,10 @@ enum { ACC_PQ = 0, ACC_RZ = 1, ACC_RR = 2, ACC_BSUM = 3, ACC_BB = 4, ACC_RR64 = 
        // single-pass PCG: <r,u>, <w,u>, <u,s_prev>, <r,r>
        ACC_SLOT_G = 8, ACC_SLOT_D = 11, ACC_SLOT_E = 14, ACC_SLOT_R = 17, ACC_NSLOT = 12,
        // QUICK + Crank-Nicolson iteration: ||u^(k+1) - u^(k)||^2, ||u^(k+1)||^2
-       ACC_CN_D = 20, ACC_CN_U = 21 };
+       ACC_CN_D = 20, ACC_CN_U = 21,
+       // fused single-barrier PCG: three rotating slots of <p,q>, <q,z>, <q,D^-1 q>,
+       // <r,r>, <r,z>
+       ACC_SLOT_FZ = 24, ACC_FZ_N = 5, ACC_FZ_SLOTS = 15 };
 
 // Device view of the grid tables, passed by value to every kernel.
 struct DevGrid {

@@ -16,6 +16,7 @@ struct Fields {
   void *r, *p0, *p1, *q;  // PCG vectors: FP64 (plain) or FP32 (mixed inner)
   void *w1, *s0, *s1;     // single-pass PCG: second A u buffer and the two A p buffers
   float *e;               // mixed: inner iterate (correction of p)
+  float *face;            // fused PCG: [2][n_cubes][6][3][B^2] face planes of r, q, p
   unsigned int* guard;    // graph-loop body counter
   unsigned int* bar;      // persistent PCG grid barrier words
   int* err;               // persistent PCG: a barrier wait timed out
@@ -91,6 +92,7 @@ struct Ctx {
   int persistent;  // 1: one cooperative launch per PCG solve; 0: two launches per iteration
   int single_pass; // persistent PCG: one pass and one grid barrier per iteration
   int resident;    // persistent PCG: search direction in shared memory where it fits
+  int fused;       // persistent PCG: the single-barrier form with bulk-copy staging
   int lag_bf16;    // mixed mode: N^{n-1} stored as bfloat16
   int use_mg;      // PCG preconditioner: 0 Jacobi, 1 geometric multigrid
   MgDev mg;
@@ -116,11 +118,14 @@ cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm);
 // PCG forms (reported in bcm_stats.pcg_form)
 enum { PCG_TWO_LAUNCH = 0, PCG_STREAMING = 1, PCG_SINGLE_PASS = 2, PCG_RESIDENT = 3,
-       PCG_MULTIGRID = 4 };
+       PCG_MULTIGRID = 4, PCG_FUSED = 5 };
 // The persistent PCG in the form the launch shape and the grid select; *form gets it.
 cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form);
 cudaError_t launch_pcg1(const Ctx& x, const SolveParams& prm);
 cudaError_t launch_pcg_resident(const Ctx& x, const SolveParams& prm, bool* launched);
+// The fused single-barrier form (FP32 inner solve, 16^3 cubes); *launched = false when
+// the grid does not fit it (the caller falls back to the streaming form).
+cudaError_t launch_pcg_fused(const Ctx& x, const SolveParams& prm, bool* launched);
 cudaError_t launch_add_correction(const Ctx& x);
 cudaError_t launch_correct(const Ctx& x);
 cudaError_t launch_step_end(const Ctx& x);

@@ -372,6 +372,14 @@ cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form) {
     const cudaError_t e = cudaMemsetAsync(x.f.bar + 32, 0, 32 * sizeof(unsigned int), x.stream);
     if (e != cudaSuccess) return e;
   }
+  if (x.fused) {
+    bool launched = false;
+    const cudaError_t e = launch_pcg_fused(x, prm, &launched);
+    if (e != cudaSuccess || launched) {
+      *form = PCG_FUSED;
+      return e;
+    }
+  }
   if (x.single_pass) {
     *form = PCG_SINGLE_PASS;
     return launch_pcg1(x, prm);

@@ -163,6 +163,7 @@ __global__ __launch_bounds__(NT) void k_residual(DevGrid g, const double* __rest
     for (int i = threadIdx.x; i < g.n_sims * kStripes; i += NT) {
       SimState& t = g.ss[i / kStripes];
       for (int sl = 0; sl < ACC_NSLOT; ++sl) t.acc[i % kStripes][ACC_SLOT_PQ + sl] = 0.0;
+      for (int sl = 0; sl < ACC_FZ_SLOTS; ++sl) t.acc[i % kStripes][ACC_SLOT_FZ + sl] = 0.0;
     }
     alive = __syncthreads_or(alive);
     outer_alive = __syncthreads_or(outer_alive);
