@@ -198,10 +198,12 @@ bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max
                           int32_t *check_every, double *barrier_timeout_s, int32_t *recycle);
 
 /* Launch shape of the PCG.  persistent = 5 (mixed mode on 16^3 cubes, grids of at most
- * 256 sims and 256 cubes per SM): one cooperative launch per solve,
- * one 1024-thread block per SM, one grid barrier per iteration (the beta of the next
- * iteration follows from <q,z> and <q,D^-1 q> of the same pass), each cube's r, q, p, x
- * and its neighbours' face planes staged by bulk asynchronous copies two cubes ahead;
+ * 160 sims and 256 cubes per SM): one cooperative launch per solve, one block of 256
+ * threads (one x-row of the cube in hand each) per SM,
+ * one grid barrier per iteration (the beta of the next iteration follows from <q,z> and
+ * <q,D^-1 q> of the same pass; q = K p is applied again rather than stored), each cube's
+ * r, p, x and its neighbours' face planes staged by bulk asynchronous copies two cubes
+ * ahead;
  * grids it does not fit run persistent = 1.  persistent = 1: every PCG solve is one
  * cooperative launch whose blocks loop over the iterations with two grid-wide barriers
  * each, streaming the vectors through global memory (the mixed-mode default);

@@ -66,7 +66,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t u, v, w, us, vs, ws, nx, ny, nz, phi, ub, p, b, bid, near_, r, p0, p1, q, e, w1, s0, s1;
-  size_t face;  // fused PCG face planes (mixed mode, 16^3 cubes)
+  size_t face, fcube;  // fused PCG face planes and per-cube records (mixed, 16^3 cubes)
   size_t nb, aux, sim, lvl, ijk, w3, nbw3, slot, sp, ss, counter, flags, guard, bar, err;
   size_t total;
   size_t n_slots;
@@ -376,6 +376,38 @@ MgHost mg_build(const bcm_grid_desc* d, const HostTables& T) {
   return m;
 }
 
+// Per-cube constant records of the fused PCG (the same values the other PCG forms
+// derive in shared memory from the tables at every launch).
+void fused_records(const HostTables& T, int n, FCube* out) {
+  for (int c = 0; c < n; ++c) {
+    FCube& r = out[c];
+    memset(&r, 0, sizeof r);
+    const int s = T.sim[c], l = T.lvl[c];
+    const SimParams& sp = T.sp[s];
+    r.sim = s;
+    r.lvl = l;
+    r.smask = 0;
+    r.has21 = 0;
+    for (int f = 0; f < 6; ++f) {
+      const int nb = T.nb[6 * c + f];
+      r.nb[f] = nb;
+      r.w3[f] = T.w3[6 * c + f];
+      r.bc[f] = sp.bc[f];
+      r.smask |= (r.w3[f] != 3) << f;
+      r.has21 |= nb < NB_BOUNDARY;
+      r.wt[f] = nb == NB_COARSE ? 2.0f / 3.0f : (nb == NB_FINE ? 4.0f / 3.0f : 1.0f);
+      int m = 0;
+      for (int e = 0; e < 6; ++e) {
+        r.nbw3[f][e] = T.nbw3[36 * c + 6 * f + e];
+        m |= (r.nbw3[f][e] != 3) << e;
+      }
+      r.nbmask[f] = m;
+    }
+    for (int w = 0; w < kW3; ++w) r.invtab[w] = (float)sp.invdiag[l][w];
+    r.h = (float)(sp.h0 / double(1 << l));
+  }
+}
+
 Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml) {
   Layout L{};
   const size_t n = (size_t)d->n_cubes * d->cells_per_edge * d->cells_per_edge * d->cells_per_edge;
@@ -398,9 +430,9 @@ Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml)
   L.e = take(d->precision == BCM_PREC_F64 ? 0 : n * 4);
   L.w1 = take(n * V); L.s0 = take(n * V); L.s1 = take(n * V);
   // fused PCG: r, q, p on the six face planes of every cube, two parities
-  L.face = (d->precision != BCM_PREC_F64 && d->cells_per_edge == 16)
-               ? take((size_t)2 * d->n_cubes * 6 * 3 * 16 * 16 * sizeof(float))
-               : 0;
+  const bool fused_ok = d->precision != BCM_PREC_F64 && d->cells_per_edge == 16;
+  L.face = fused_ok ? take((size_t)2 * d->n_cubes * 6 * 3 * 16 * 16 * sizeof(float)) : 0;
+  L.fcube = fused_ok ? take(sizeof(FCube) * d->n_cubes) : 0;
   L.nb = take(6 * sizeof(int) * d->n_cubes);
   L.aux = take(24 * sizeof(int) * d->n_cubes);
   L.sim = take(sizeof(int) * d->n_cubes);
@@ -636,6 +668,12 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   UP(L.nbw3, g->T.nbw3.data(), sizeof(int) * 36 * n);
   UP(L.slot, g->T.slot.data(), sizeof(int) * 6 * n);
   UP(L.sp, g->T.sp.data(), sizeof(SimParams) * desc->n_sims);
+  std::vector<FCube> fcubes;
+  if (L.fcube) {
+    fcubes.resize(n);
+    fused_records(g->T, n, fcubes.data());
+    UP(L.fcube, fcubes.data(), sizeof(FCube) * n);
+  }
   for (size_t k = 0; mgh.ok && k < mgh.agg.size(); ++k) {
     const MgAgg& a = mgh.agg[k];
     UP(ml.diag[k], a.diag.data(), a.diag.size() * sizeof(double));
@@ -694,6 +732,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.e = g->f64 ? nullptr : (float*)(W + L.e);
   F.w1 = W + L.w1; F.s0 = W + L.s0; F.s1 = W + L.s1;
   F.face = L.face ? (float*)(W + L.face) : nullptr;
+  F.fcube = L.fcube ? (const FCube*)(W + L.fcube) : nullptr;
   F.guard = (unsigned int*)(W + L.guard);
   F.bar = (unsigned int*)(W + L.bar);
   F.err = (int*)(W + L.err);

@@ -8,6 +8,24 @@
 
 namespace bcm {
 
+// Constants of one cube for the fused PCG, built on the host at grid creation: a
+// 432-byte record (a multiple of 16 bytes) that reaches shared memory by one bulk copy
+// beside the cube's vectors.
+struct alignas(16) FCube {
+  int nb[6];          // face neighbours / NB_* codes
+  int w3[6];          // Jacobi face weights (thirds) of this cube
+  int nbw3[6][6];     // ... of each same-level neighbour (3 elsewhere)
+  int nbmask[6];      // bit e: face e of neighbour f has a weight other than 3
+  int bc[6];          // the sim's domain-face conditions
+  int smask;          // bit f: face f's weight is not the same-level 3
+  int has21;          // some face is a 2:1 level interface
+  int sim, lvl;
+  float wt[6];        // flux weight of face f relative to a same-level face (R7)
+  float invtab[kW3];  // 1 / diag(K) by face-weight sum
+  float h;            // cell size
+};
+static_assert(sizeof(FCube) % 16 == 0, "FCube must be a whole number of 16-byte units");
+
 // Device pointers of every field and solver vector (all inside the workspace).
 struct Fields {
   void *u, *v, *w, *us, *vs, *ws, *nx, *ny, *nz, *phi, *ub;  // state storage type
@@ -17,6 +35,7 @@ struct Fields {
   void *w1, *s0, *s1;     // single-pass PCG: second A u buffer and the two A p buffers
   float *e;               // mixed: inner iterate (correction of p)
   float *face;            // fused PCG: [2][n_cubes][6][3][B^2] face planes of r, q, p
+  const FCube* fcube;     // fused PCG: per-cube constants [n_cubes]
   unsigned int* guard;    // graph-loop body counter
   unsigned int* bar;      // persistent PCG grid barrier words
   int* err;               // persistent PCG: a barrier wait timed out

@@ -4,24 +4,32 @@
 // The textbook iteration needs two global reductions: <p, K p> for alpha, then <r, z>
 // for beta.  Here both come out of one pass.  Pass m takes alpha_{m-1} and beta_m and
 // computes, cell by cell,
-//     x_m = x_{m-1} + alpha_{m-1} p_{m-1},   r_m = r_{m-1} - alpha_{m-1} q_{m-1},
-//     z_m = D^-1 r_m,   p_m = z_m + beta_m p_{m-1},   q_m = K p_m,
+//     q_{m-1} = K p_{m-1},   x_m = x_{m-1} + alpha_{m-1} p_{m-1},
+//     r_m = r_{m-1} - alpha_{m-1} q_{m-1},   z_m = D^-1 r_m,
+//     p_m = z_m + beta_m p_{m-1},   q_m = K p_m,
 // with the sums <p_m, q_m>, <q_m, z_m>, <q_m, D^-1 q_m>, <r_m, r_m> and <r_m, z_m>.
 // After the barrier alpha_m = <r_m, z_m> / <p_m, q_m>, and since r_{m+1} = r_m -
 // alpha_m q_m, <r_{m+1}, z_{m+1}> = <r_m, z_m> - 2 alpha_m <q_m, z_m> + alpha_m^2 <q_m,
 // D^-1 q_m> follows from the same sums, which gives beta_{m+1} (the exact <r, z> of
 // every pass still sets alpha).  The iterates are those of the textbook PCG in exact
 // arithmetic; the convergence test reads <r_{m-1}, r_{m-1}> one pass later, and x_{m-1}
-// is already stored then.
+// is already stored then.  q is never stored: the pass applies K to p_{m-1} again
+// (from the same staged tile), which costs shared-memory arithmetic instead of two
+// vector streams.
 //
-// Work: one block of 1024 threads per SM, each thread one 4-cell x-run of the cube in
-// hand; block p owns a contiguous run of cubes by the paper's linear distribution
-// (Eq. loaddist).  The vectors r, q, p and x are updated in place (only their owner
-// touches a cube's cells); neighbours read a cube's boundary planes from a face array
+// Work: one block of 256 threads per SM, each thread one x-row (16 cells) of the cube in
+// hand, so both x faces end every thread's row and its x neighbours are its own values;
+// block p owns a contiguous run of cubes by the paper's linear distribution
+// (Eq. loaddist).  r, p and x are updated in place (only their owner touches a cube's
+// cells); neighbours read a cube's boundary planes of r, q, p from a face array
 // [parity][cube][face][r,q,p][16x16] that every pass writes in the other parity.  A
-// cube's r, q, p, x (4 x 16 KB) and its six neighbours' face blocks (3 KB each) reach
-// shared memory by bulk asynchronous copies (cp.async.bulk, completion on an mbarrier),
-// two cubes ahead of the arithmetic.  The first pass of a solve takes the residual
+// cube's r, p, x (3 x 16 KB), its six neighbours' face blocks (3 KB each) and its
+// constant record reach shared memory by bulk asynchronous copies (cp.async.bulk,
+// completion on an mbarrier), two cubes ahead of the arithmetic in three rotating
+// slots; the first two cubes of a pass have their own data copied before the grid
+// barrier that ends the previous pass.  Values across the faces are read (or formed)
+// from the staged face planes where they are needed, domain ghosts in place; only cubes
+// with 2:1 faces stage ghosts first.  The first pass of a solve takes the residual
 // kernel's r (and, resuming a defect-correction cycle, the previous direction) by
 // plain loads for the halo.
 //
@@ -42,26 +50,32 @@ namespace bcm {
 namespace {
 
 constexpr int FB = 16, FBB = FB * FB, FB3 = FB * FB * FB;
-constexpr int FNT = 1024;                 // threads per block: one x-quad each
 constexpr int kFaceVals = 3 * FBB;        // r, q, p of one face plane
 constexpr int kCubeFace = 6 * kFaceVals;  // face-array floats per cube and parity
 constexpr int kMaxBlockCubes = 256;       // cubes one block may own
+constexpr int kMaxFusedSims = 160;        // per-sim scalars fit beside the three stages
+
+constexpr int kSlots = 3;                 // stage slots: two cubes ahead of the one in hand
 
 struct alignas(128) FStage {
-  float R[FB3], Q[FB3], P[FB3], X[FB3];
+  float R[FB3], P[FB3];   // r_{m-1}, p_{m-1} (R then holds p_m)
   float F[6][kFaceVals];  // neighbour face planes: r, q, p each
+  FCube cs;               // the cube's constants
 };
 
 struct FShared {
-  FStage st[2];
-  float G[6][FBB];        // search-direction ghosts of the six faces
-  unsigned long long mbar[2];
-  CubeSh<float> cs[2];
+  FStage st[kSlots];
+  float G1[6][FBB];       // 2:1 ghosts of p_{m-1}
+  float G2[2][6][FBB];    // p_m across every face that is not a domain face, by cube parity
+  unsigned long long mbar[kSlots];
   double red[ACC_FZ_N * 32];
-  int cube[kMaxBlockCubes];  // this pass's cubes (sims still running)
+  int bnb[kMaxBlockCubes][6];  // face neighbours of the block's cubes
+  int bsim[kMaxBlockCubes];    // and their sims
+  int cube[kMaxBlockCubes];    // this pass's cubes (local index; sims still running)
   int warp_n[32];
   int n_list;
-  int ok;
+  int pre[2];   // cubes (local index) whose own data was prefetched into slots 0 and 1
+  int any_alive, any_finished;  // decisions of the pass: a sim runs / a sim just finished
 };
 
 // per-sim scalars after FShared in dynamic shared memory
@@ -71,6 +85,10 @@ struct FSim {
   int rpar;        // face-array parity this pass reads
   int done, cont;  // finished; first pass resumes the previous direction
 };
+// the three stages, the ghosts and the tables, the per-sim scalars of kMaxFusedSims sims
+// and the kernels' static shared memory fit one block per SM (227 KB)
+static_assert((sizeof(FShared) + 15) / 16 * 16 + sizeof(FSim) * kMaxFusedSims + 256 <= 232448,
+              "fused PCG shared memory exceeds the per-block limit");
 
 __device__ __forceinline__ uint32_t s_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -125,13 +143,6 @@ __device__ __forceinline__ void st4s(float* p, float a, float b, float c, float 
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
-// 1 / diag(K) of cell (i, j, k) of a cube with face weights w3 (mask: any face weight
-// other than the same-level one)
-__device__ __forceinline__ float inv_of(const CubeSh<float>& cs, const int* w3, int mask, int i,
-                                        int j, int k) {
-  return mask == 0 ? cs.invtab[18] : cs.invtab[s3_of<FB>(w3, i, j, k)];
-}
-
 // (i, j, k) of the cell at tangential (a, b) on face f of a cube, in the plane of that face
 __device__ __forceinline__ void face_cell(int f, int a, int b, int& i, int& j, int& k) {
   const int d = f >> 1, n = (f & 1) ? FB - 1 : 0;
@@ -147,7 +158,7 @@ __device__ __forceinline__ void face_cell(int f, int a, int b, int& i, int& j, i
 // Sum over the block of NV FP32 partials, in FP64 from the warp level up (FP32 warp
 // shuffles: the part's FP64 rate is a small fraction of its FP32 rate); result in
 // thread 0.
-template <int NV>
+template <int NT, int NV>
 __device__ __forceinline__ void block_sum_f(float (&v)[NV], double (&out)[NV], double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -162,7 +173,7 @@ __device__ __forceinline__ void block_sum_f(float (&v)[NV], double (&out)[NV], d
   if (warp == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double x = red[q * 32 + lane];
+      double x = lane < NT / 32 ? red[q * 32 + lane] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       out[q] = x;
@@ -172,40 +183,46 @@ __device__ __forceinline__ void block_sum_f(float (&v)[NV], double (&out)[NV], d
 
 struct FusedArgs {
   const float* rp;  // residual kernel's r (first pass of a solve)
-  float *r, *q, *p, *x;
+  float *r, *p, *x;
   float* face;
+  const FCube* fc;  // per-cube constants
 };
 
 __device__ __forceinline__ size_t face_off(int par, int n_cubes, int c, int f) {
   return ((size_t)par * n_cubes + c) * kCubeFace + (size_t)f * kFaceVals;
 }
 
-// What the 2:1 ghost of the new search direction needs (kept out of the hot path's
-// registers: the function is not inlined).
+// What the 2:1 ghosts need (kept out of the hot path's registers: the function is not
+// inlined).  mode: kOldP p_{m-1} of the face planes, kNewP p_m from their r, q, p,
+// kFirst the first pass of a solve (the residual kernel's r, and the resumed direction).
+enum { kOldP = 0, kNewP = 1, kFirst = 2 };
 struct GhostCtx {
   const int *aux, *ijk, *lvl, *w3, *sim;
   const SimParams* sp;
   const float *face, *rp;
-  int max_level, nc, rpar, first, cont;
+  int max_level, nc, rpar, mode, cont;
   float alpha, beta, gamma;
 };
 
-// New p at cell (a, b) of face fn of cube nn, from its face planes of the last pass (or,
+// p at cell (a, b) of face fn of cube nn (from its face planes of the last pass, or,
 // in the first pass, the residual kernel's r and the resumed direction).
-__device__ float pnew_face(const GhostCtx& x, int nn, int fn, int a, int b) {
+// Face planes are written by other SMs during the launch: read them at L2 (__ldcg), past
+// this SM's L1, which is not kept coherent with other SMs' stores.
+__device__ float p_face(const GhostCtx& x, int nn, int fn, int a, int b) {
+  const float* F = x.face + face_off(x.rpar, x.nc, nn, fn);
+  const int o = b * FB + a;
+  if (x.mode == kOldP) return __ldcg(F + 2 * FBB + o);
   int ii, jj, kk;
   face_cell(fn, a, b, ii, jj, kk);
   const SimParams& sp = x.sp[x.sim[nn]];
   const float iv = float(sp.invdiag[x.lvl[nn]][s3_of<FB>(x.w3 + 6 * nn, ii, jj, kk)]);
-  const float* F = x.face + face_off(x.rpar, x.nc, nn, fn);
-  const int o = b * FB + a;
-  if (!x.first) {
-    const float r = fmaf(-x.alpha, F[FBB + o], F[o]);
-    return fmaf(x.beta, F[2 * FBB + o], r * iv);
+  if (x.mode == kNewP) {
+    const float r = fmaf(-x.alpha, __ldcg(F + FBB + o), __ldcg(F + o));
+    return fmaf(x.beta, __ldcg(F + 2 * FBB + o), r * iv);
   }
   const float r = x.rp[(size_t)nn * FB3 + (kk * FB + jj) * FB + ii];
   float pn = r * iv;
-  if (x.cont) pn = fmaf(x.gamma, F[2 * FBB + o] - F[o] * iv, pn);
+  if (x.cont) pn = fmaf(x.gamma, __ldcg(F + 2 * FBB + o) - __ldcg(F + o) * iv, pn);
   return pn;
 }
 
@@ -219,19 +236,115 @@ __device__ __noinline__ float ghost_21(const GhostCtx& x, int c, int f, int a, i
     const int sf = 1 << (x.max_level - x.lvl[c]), sc = 2 * sf;
     const int Ac = (x.ijk[3 * c + tan1(d)] + a * sf - x.ijk[3 * C + tan1(d)]) / sc;
     const int Bc = (x.ijk[3 * c + tan2(d)] + b * sf - x.ijk[3 * C + tan2(d)]) / sc;
-    return pnew_face(x, C, f ^ 1, Ac, Bc);
+    return p_face(x, C, f ^ 1, Ac, Bc);
   }
   const int qa = (2 * a) / FB, qb = (2 * b) / FB;
   const int Fc = x.aux[(6 * c + f) * 4 + qb * 2 + qa];
   const int fa = 2 * a - qa * FB, fb = 2 * b - qb * FB;
-  return 0.25f * (pnew_face(x, Fc, f ^ 1, fa, fb) + pnew_face(x, Fc, f ^ 1, fa + 1, fb) +
-                  pnew_face(x, Fc, f ^ 1, fa, fb + 1) + pnew_face(x, Fc, f ^ 1, fa + 1, fb + 1));
+  return 0.25f * (p_face(x, Fc, f ^ 1, fa, fb) + p_face(x, Fc, f ^ 1, fa + 1, fb) +
+                  p_face(x, Fc, f ^ 1, fa, fb + 1) + p_face(x, Fc, f ^ 1, fa + 1, fb + 1));
+}
+
+__device__ __forceinline__ void ld4v(const float* p, float (&v)[4]) {
+  const float4 a = ld4s(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+// 1 / diag(K) of the same-level neighbour's cell across face f at tangential (a, b)
+__device__ __forceinline__ float nb_inv(const FCube& cs, int f, int a, int b) {
+  if (cs.nbmask[f] == 0) return cs.invtab[18];
+  int i, j, k;
+  face_cell(f ^ 1, a, b, i, j, k);
+  return cs.invtab[s3_of<FB>(cs.nbw3[f], i, j, k)];
+}
+
+// The mirror factor of a domain face (the ghost is the mirror cell's value, Neumann,
+// negated at the outflow's Dirichlet 0), 0 for a face that is not a domain face.
+__device__ __forceinline__ float dom_sign(const FCube& cs, int f) {
+  return cs.nb[f] == NB_BOUNDARY ? (cs.bc[f] == BC_OUTFLOW ? -1.f : 1.f) : 0.f;
+}
+
+// q = K p on quad u from the tile T (the cube's p, x fastest) and what lies across the
+// cube's faces: for a face that is not a domain face the value comes from the plane at
+// across + f * stride (16 x 16, tangential (a, b) at b * 16 + a), for a domain face it is
+// the mirror cell's value times dom_sign.  h times the sum over the six faces of
+// (p_c - p_nb), 2:1 faces weighted (R7).  No branch on the lane: a face cell reads its
+// plane where an interior cell reads the tile.  The x neighbours inside the cube come from
+// the adjacent quads of the warp (lanes hold consecutive quads); every lane of the warp
+// must call it.
+__device__ __forceinline__ void stencil_quad(const FCube& cs, const float* T, const float* across,
+                                             int stride, const float (&pv)[4], int u,
+                                             float (&qv)[4]) {
+  const int i0 = (u & 3) * 4, j = (u >> 2) & 15, kz = u >> 6;
+  const float left = __shfl_up_sync(0xffffffffu, pv[3], 1);
+  const float right = __shfl_down_sync(0xffffffffu, pv[0], 1);
+  float sum[4];
+  {
+    const bool f0 = i0 == 0, f1 = i0 == FB - 4;
+    const float g0 = across[kz * FB + j], g1 = across[stride + kz * FB + j];
+    const float s0 = dom_sign(cs, 0), s1 = dom_sign(cs, 1);
+    const float xl = f0 ? (s0 != 0.f ? s0 * pv[0] : g0) : left;
+    const float xr = f1 ? (s1 != 0.f ? s1 * pv[3] : g1) : right;
+    const float wl = f0 ? cs.wt[0] : 1.f, wr = f1 ? cs.wt[1] : 1.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float xm = e == 0 ? xl : pv[e - 1], xp = e == 3 ? xr : pv[e + 1];
+      sum[e] = (e == 0 ? wl : 1.f) * (pv[e] - xm) + (e == 3 ? wr : 1.f) * (pv[e] - xp);
+    }
+  }
+  auto side = [&](int f, bool inside, int off, int o) {
+    const float* src = inside ? T + 4 * u + off : across + f * stride + o;
+    const float4 a = ld4s(src);
+    float nv[4] = {a.x, a.y, a.z, a.w};
+    const float w = inside ? 1.f : cs.wt[f];
+    const float sg = inside ? 0.f : dom_sign(cs, f);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (sg != 0.f) nv[e] = sg * pv[e];
+      sum[e] = fmaf(w, pv[e] - nv[e], sum[e]);
+    }
+  };
+  side(2, j > 0, -FB, kz * FB + i0);
+  side(3, j < FB - 1, FB, kz * FB + i0);
+  side(4, kz > 0, -FBB, j * FB + i0);
+  side(5, kz < FB - 1, FBB, j * FB + i0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) qv[e] = cs.h * sum[e];
+}
+
+// 1 / diag(K) of the four cells of quad (i0, j, kz): the face-weight sum differs from
+// the interior one only on the cube's faces (R7), and along x only at the quad's ends.
+__device__ __forceinline__ void quad_inv(const FCube& cs, int i0, int j, int kz, float (&iv)[4]) {
+  if (cs.smask == 0) {
+    iv[0] = iv[1] = iv[2] = iv[3] = cs.invtab[18];
+    return;
+  }
+  const int s = 18 + (j == 0 ? cs.w3[2] - 3 : 0) + (j == FB - 1 ? cs.w3[3] - 3 : 0) +
+                (kz == 0 ? cs.w3[4] - 3 : 0) + (kz == FB - 1 ? cs.w3[5] - 3 : 0);
+  iv[0] = cs.invtab[s + (i0 == 0 ? cs.w3[0] - 3 : 0)];
+  iv[1] = iv[2] = cs.invtab[s];
+  iv[3] = cs.invtab[s + (i0 == FB - 4 ? cs.w3[1] - 3 : 0)];
+}
+
+// Quad u of vector v on the face planes it lies on (written parity).
+__device__ __forceinline__ void face_store(float* fw, int v, const float (&x)[4], int u) {
+  const int i0 = (u & 3) * 4, j = (u >> 2) & 15, kz = u >> 6;
+  float* b = fw + v * FBB;
+  if (i0 == 0) b[0 * kFaceVals + kz * FB + j] = x[0];
+  if (i0 == FB - 4) b[1 * kFaceVals + kz * FB + j] = x[3];
+  if (j == 0) st4s(b + 2 * kFaceVals + kz * FB + i0, x[0], x[1], x[2], x[3]);
+  if (j == FB - 1) st4s(b + 3 * kFaceVals + kz * FB + i0, x[0], x[1], x[2], x[3]);
+  if (kz == 0) st4s(b + 4 * kFaceVals + j * FB + i0, x[0], x[1], x[2], x[3]);
+  if (kz == FB - 1) st4s(b + 5 * kFaceVals + j * FB + i0, x[0], x[1], x[2], x[3]);
 }
 
 }  // namespace
 
+constexpr int FNT = 1024;  // threads per block: one x-quad of the cube in hand each
+
 __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, SolveParams prm,
                                                       unsigned int* bar, int* err) {
+  constexpr int NT = FNT, NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FShared& S = *reinterpret_cast<FShared*>(smem_raw);
   FSim* sim = reinterpret_cast<FSim*>(smem_raw + (sizeof(FShared) + 15) / 16 * 16);
@@ -244,50 +357,112 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
   const int P = gridDim.x, pb = blockIdx.x;
   const int Lq = nc / P, Rq = nc % P;
   const int c0 = pb * Lq + min(pb, Rq), ncub = (nc + P - pb - 1) / P;
-  // this thread's quad: cells (i0 .. i0+3, j, k)
+  // this thread's quad (cells i0 .. i0+3 of row (j, kz)) and, for lanes 0 .. 11 of every
+  // warp, one of the 384 face quads whose values across the face it forms
   const int i0 = (t & 3) * 4, j = (t >> 2) & 15, kz = t >> 6;
+  const int gq = lane < 12 ? 12 * warp + lane : -1;
 
-  for (int s = t; s < nsim; s += FNT) {
+  for (int s = t; s < nsim; s += NT) {
     sim[s].done = g.ss[s].done ? 1 : 0;
     sim[s].rpar = g.ss[s].fz_par & 1;
   }
+  for (int i = t; i < 7 * ncub; i += NT) {  // the block's neighbour table and sims
+    const int q = i / 7, e = i - 7 * q;
+    if (e < 6) S.bnb[q][e] = g.nb[6 * (c0 + q) + e];
+    else S.bsim[q] = g.sim[c0 + q];
+  }
   if (t == 0) {
-    mbar_init(&S.mbar[0], 1);
-    mbar_init(&S.mbar[1], 1);
+    // two arrivals per phase: the cube's own data, then its neighbours' face planes
+    for (int k = 0; k < kSlots; ++k) mbar_init(&S.mbar[k], 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.pre[0] = S.pre[1] = -1;
+    S.any_alive = S.any_finished = 0;
   }
   __syncthreads();
-  unsigned phase[2] = {0u, 0u};
-  int pend[2] = {0, 0};  // copies issued into a slot and not yet waited for
+  unsigned phase[kSlots] = {0u, 0u, 0u};
+  int pend[kSlots] = {0, 0, 0};  // copies issued into a slot and not yet waited for
   GridBarrier gb;
   gb.init(bar, err, limit);
   bool failed = false;
+  constexpr int IW = NW - 1;  // the warp that issues copies
+
+  // own data of cube ql into slot sl (issuing warp): r and p (the residual kernel's r
+  // and the previous direction in the first pass) and the constants
+  auto issue_own = [&](int ql, int sl, bool first) {
+    const int c = c0 + ql;
+    const FSim& fs = sim[S.bsim[ql]];
+    FStage& stg = S.st[sl];
+    const size_t base = (size_t)c * FB3;
+    const float* src = nullptr;
+    float* dst = nullptr;
+    if (lane == 0) {
+      src = (first ? A.rp : A.r) + base;
+      dst = stg.R;
+    } else if (lane == 1 && (!first || fs.cont)) {
+      src = A.p + base;
+      dst = stg.P;
+    }
+    const bool ocopy = src != nullptr, rcopy = lane == 3;
+    unsigned bytes = (ocopy ? 4u * FB3 : 0u) + (rcopy ? (unsigned)sizeof(FCube) : 0u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0) mbar_expect_tx(&S.mbar[sl], bytes);
+    __syncwarp();
+    if (ocopy) bulk_g2s(dst, src, 4u * FB3, &S.mbar[sl]);
+    if (rcopy) bulk_g2s(&stg.cs, A.fc + c, (unsigned)sizeof(FCube), &S.mbar[sl]);
+  };
+  // the neighbours' face planes of cube ql into slot sl (issuing warp)
+  auto issue_faces = [&](int ql, int sl, bool first, bool none) {
+    const FSim& fs = sim[S.bsim[ql]];
+    int n = -1;
+    if (lane < 6) n = S.bnb[ql][lane];
+    const bool fcopy = !none && lane < 6 && n >= 0 && (!first || fs.cont);
+    unsigned bytes = fcopy ? 4u * kFaceVals : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0) mbar_expect_tx(&S.mbar[sl], bytes);
+    __syncwarp();
+    if (fcopy)
+      bulk_g2s(S.st[sl].F[lane], A.face + face_off(fs.rpar, nc, n, lane ^ 1), 4u * kFaceVals,
+               &S.mbar[sl]);
+  };
 
   for (int m = 0;; ++m) {
-    // ---- decisions for pass m (the same in every block)
-    int alive = 0;
-    for (int s = t; s < nsim; s += FNT) {
+    const bool first = (m == 0);
+    // ---- decisions for pass m (the same in every block): warp w takes sims w, w + NW ..;
+    // its lanes read the 5 x kStripes sums of the last pass together
+    int alive = 0, finished = 0;
+    for (int s = warp; s < nsim; s += NW) {
       FSim& fs = sim[s];
       if (fs.done) continue;
       SimState& st = g.ss[s];
-      double rr, rz, pq = 0.0, qz = 0.0, qdq = 0.0;
+      double v[ACC_FZ_N] = {0.0, 0.0, 0.0, 0.0, 0.0};
       if (m == 0) {
-        rr = st.rr;
-        rz = st.rz;
+        v[3] = st.rr;
+        v[4] = st.rz;
       } else {
         const int b0 = ACC_SLOT_FZ + ACC_FZ_N * ((m - 1) % 3);
-        pq = slot_sum(st, b0 + 0);
-        qz = slot_sum(st, b0 + 1);
-        qdq = slot_sum(st, b0 + 2);
-        rr = slot_sum(st, b0 + 3);
-        rz = slot_sum(st, b0 + 4);
+        // lane = q * 8 + stripe for the first four sums, lanes 0..7 again for the fifth
+        double a = ld_acc(&st.acc[lane & 7][b0 + (lane >> 3)]);
+        double b5 = lane < kStripes ? ld_acc(&st.acc[lane][b0 + 4]) : 0.0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b5 += __shfl_xor_sync(0xffffffffu, b5, o);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __shfl_sync(0xffffffffu, a, 8 * q);
+        v[4] = __shfl_sync(0xffffffffu, b5, 0);
       }
+      if (lane != 0) continue;
+      const double pq = v[0], qz = v[1], qdq = v[2], rr = v[3], rz = v[4];
       const int iters = m > 0 ? m - 1 : 0;  // x updates done so far
       const double tol2 = inner ? st.inner_tol2 : st.tol2;
       const bool bad = !isfinite(rr) || !isfinite(rz) || !isfinite(pq) || !isfinite(qz) ||
                        !isfinite(qdq);
       if (bad || rr <= tol2 || iters >= kmax) {
         fs.done = 1;
+        finished = 1;
         if (blockIdx.x == 0) {  // single writer of the solve's results
           st.iter = iters;
           st.total_iters += iters;
@@ -325,77 +500,65 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
       }
       alive = 1;
     }
-    alive = __syncthreads_or(alive);
+    // one barrier publishes the decisions and whether the cube list changed
+    if (alive) S.any_alive = 1;
+    if (finished) S.any_finished = 1;
+    __syncthreads();
+    alive = S.any_alive;
+    finished = S.any_finished;
     if (!alive) break;
     if (blockIdx.x == 0)  // clear the slot pass m+1 fills (held pass m-2's sums)
-      for (int i = t; i < nsim * kStripes; i += FNT) {
+      for (int i = t; i < nsim * kStripes; i += NT) {
         SimState& st = g.ss[i / kStripes];
         const int b0 = ACC_SLOT_FZ + ACC_FZ_N * ((m + 1) % 3);
 #pragma unroll
         for (int q = 0; q < ACC_FZ_N; ++q) st.acc[i % kStripes][b0 + q] = 0.0;
       }
-    // ---- this pass's cubes: those of running sims, in order (a warp-ballot compaction)
-    {
-      const bool mine = t < ncub && !sim[g.sim[c0 + t]].done;
+    // ---- this pass's cubes: those of running sims, in order (a warp-ballot compaction),
+    // rebuilt when a sim has finished
+    if (first || finished) {
+      const bool mine = t < ncub && !sim[S.bsim[t]].done;
       const unsigned bal = __ballot_sync(0xffffffffu, mine);
       if (lane == 0) S.warp_n[warp] = __popc(bal);
       __syncthreads();
       int off = 0;
       for (int w = 0; w < warp; ++w) off += S.warp_n[w];
-      if (mine) S.cube[off + __popc(bal & ((1u << lane) - 1u))] = c0 + t;
-      if (t == FNT - 1) S.n_list = off + __popc(bal);
+      if (mine) S.cube[off + __popc(bal & ((1u << lane) - 1u))] = t;
+      if (t == NT - 1) S.n_list = off + __popc(bal);
       __syncthreads();
     }
     const int nl = S.n_list;
 
-    // issue cube list[q] into slot sl: constants, then the copies of warp 0
-    auto issue = [&](int q, int sl) {
-      const int c = S.cube[q];
-      load_cube(S.cs[sl], g, c);
-      if (warp == 0) {
-        const FSim& fs = sim[g.sim[c]];
-        const bool first = (m == 0);
-        int n = -1;
-        if (lane < 6) n = g.nb[6 * c + lane];
-        const bool fcopy = lane < 6 && n >= 0 && (!first || fs.cont);
-        bool ocopy = false;
-        const float* src = nullptr;
-        float* dst = nullptr;
-        FStage& stg = S.st[sl];
-        const size_t base = (size_t)c * FB3;
-        if (lane >= 6 && lane < 10) {
-          const int v = lane - 6;  // 0 r, 1 q, 2 p, 3 x
-          if (!first) {
-            ocopy = true;
-            src = (v == 0 ? A.r : v == 1 ? A.q : v == 2 ? A.p : A.x) + base;
-          } else if (v == 0) {  // the residual kernel's r
-            ocopy = true;
-            src = A.rp + base;
-          } else if (fs.cont && v != 3) {  // resume: the previous r (into Q) and p
-            ocopy = true;
-            src = (v == 1 ? A.r : A.p) + base;
-          }
-          dst = v == 0 ? stg.R : v == 1 ? stg.Q : v == 2 ? stg.P : stg.X;
+    // the first two cubes: their own data may already be on its way (prefetched before
+    // the barrier); the face planes follow now.  Every thread decides alike from the
+    // same shared tables whether a prefetch went unused (then the issuing warp completes
+    // its phase and lets it land first).
+    for (int q = 0; q < 2; ++q) {
+      const int pq = S.pre[q];
+      const bool unused = pq >= 0 && (q >= nl || S.cube[q] != pq);
+      if (unused) {
+        if (warp == IW) {
+          issue_faces(pq, q, false, true);
+          mbar_wait(&S.mbar[q], phase[q], 1000000000ull);
         }
-        unsigned bytes = (fcopy ? 4u * kFaceVals : 0u) + (ocopy ? 4u * FB3 : 0u);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-        if (lane == 0) mbar_expect_tx(&S.mbar[sl], bytes);
-        __syncwarp();
-        if (fcopy)
-          bulk_g2s(stg.F[lane], A.face + face_off(fs.rpar, nc, n, lane ^ 1), 4u * kFaceVals,
-                   &S.mbar[sl]);
-        if (ocopy) bulk_g2s(dst, src, 4u * FB3, &S.mbar[sl]);
+        phase[q] ^= 1u;
+        pend[q] = 0;
       }
-      pend[sl] = 1;
-    };
+      if (q < nl) {
+        if (warp == IW) {
+          if (unused || pq != S.cube[q]) issue_own(S.cube[q], q, first);
+          issue_faces(S.cube[q], q, first, false);
+        }
+        pend[q] = 1;
+      }
+    }
 
     // dot-product partials of the block's current sim
     float acc[ACC_FZ_N] = {0.f, 0.f, 0.f, 0.f, 0.f};  // pq, qz, qdq, rr, rz
     int psim = -1;
     auto flush = [&]() {
       double out[ACC_FZ_N];
-      block_sum_f<ACC_FZ_N>(acc, out, S.red);
+      block_sum_f<NT, ACC_FZ_N>(acc, out, S.red);
       if (t == 0) {
         SimState& st = g.ss[psim];
         const int b0 = ACC_SLOT_FZ + ACC_FZ_N * (m % 3);
@@ -406,212 +569,172 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
       for (int q = 0; q < ACC_FZ_N; ++q) acc[q] = 0.f;
     };
 
-    if (nl > 0) issue(0, 0);
-    if (nl > 1) issue(1, 1);
+    // x of the first cube (plain loads, one cube ahead from then on)
+    float xn[4] = {0.f, 0.f, 0.f, 0.f};
+    if (!first && nl > 0) ld4v(A.x + (size_t)(c0 + S.cube[0]) * FB3 + 4 * t, xn);
     for (int q = 0; q < nl; ++q) {
-      const int sl = q & 1, c = S.cube[q], s = g.sim[c];
-      const bool okw = mbar_wait(&S.mbar[sl], phase[sl], limit);
-      if (!__syncthreads_and(okw)) {  // the slot's copies stay pending
+      const int sl = q % kSlots, ql = S.cube[q], c = c0 + ql, s = S.bsim[ql];
+      if (psim >= 0 && psim != s) flush();
+      psim = s;
+      float xc[4] = {xn[0], xn[1], xn[2], xn[3]};
+      if (!first && q + 1 < nl) ld4v(A.x + (size_t)(c0 + S.cube[q + 1]) * FB3 + 4 * t, xn);
+      // a timed-out wait leaves the stage unread by the warp: every barrier below is a
+      // vote on it, so all threads leave the loop together
+      const bool okw = __all_sync(0xffffffffu, mbar_wait(&S.mbar[sl], phase[sl], limit));
+      const FSim& fs = sim[s];
+      const FCube& cs = S.st[sl].cs;
+      FStage& stg = S.st[sl];
+      const bool cont = fs.cont != 0;
+      const float alpha = fs.alpha, beta = fs.beta, gamma = fs.gamma;
+      float* fw = A.face + face_off(fs.rpar ^ 1, nc, c, 0);  // this cube's faces, written
+      const size_t base = (size_t)c * FB3;
+      float (*G2)[FBB] = S.G2[q & 1];
+      if (okw && cs.has21 && !first) {
+        // 2:1 faces: the flux-form ghosts (R7) of p_{m-1}, between two barriers (the
+        // previous cube may still read G1)
+        if (__syncthreads_or(!okw)) {
+          failed = true;
+          break;
+        }
+        if (gq >= 0) {  // every face plane of p_{m-1} into G1 (the stencil reads one array)
+          const int f = gq >> 6, qf = gq & 63, a0 = 4 * (qf & 3), b = qf >> 2;
+          const int n = cs.nb[f], o = b * FB + a0;
+          if (n >= 0) {
+            float pq4[4];
+            ld4v(stg.F[f] + 2 * FBB + o, pq4);
+            st4s(&S.G1[f][o], pq4[0], pq4[1], pq4[2], pq4[3]);
+          } else if (n < NB_BOUNDARY) {
+            const GhostCtx gc{g.aux, g.ijk, g.lvl, g.w3, g.sim, g.sp, A.face, A.rp,
+                              g.max_level, nc, fs.rpar, kOldP, 0, alpha, beta, gamma};
+            for (int e = 0; e < 4; ++e) S.G1[f][o + e] = ghost_21(gc, c, f, a0 + e, b, n);
+          }
+        }
+        __syncthreads();
+      }
+      float zv[4], pv[4], iv[4];
+      if (okw) {
+        // ---- p_m across the faces (lanes 0..11 of every warp, one face quad each)
+        if (gq >= 0) {
+          const int f = gq >> 6, qf = gq & 63, a0 = 4 * (qf & 3), b = qf >> 2;
+          const int n = cs.nb[f], o = b * FB + a0;
+          if (n >= 0) {  // same level: formed from the neighbour's planes of r, q, p
+            float gv[4];
+            if (first && !cont) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) gv[e] = 0.f;
+            }
+            const float* F = stg.F[f];
+            float fr[4] = {0.f, 0.f, 0.f, 0.f}, fq[4] = {0.f, 0.f, 0.f, 0.f},
+                  fp[4] = {0.f, 0.f, 0.f, 0.f};
+            if (!first || cont) {
+              ld4v(F + o, fr);
+              ld4v(F + FBB + o, fq);
+              ld4v(F + 2 * FBB + o, fp);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float ivn = nb_inv(cs, f, a0 + e, b);
+              if (!first) {
+                gv[e] = fmaf(beta, fp[e], fmaf(-alpha, fq[e], fr[e]) * ivn);
+              } else {
+                int ii, jj, kk;
+                face_cell(f ^ 1, a0 + e, b, ii, jj, kk);
+                gv[e] = A.rp[(size_t)n * FB3 + (kk * FB + jj) * FB + ii] * ivn;
+                if (cont) gv[e] = fmaf(gamma, fp[e] - fr[e] * ivn, gv[e]);
+              }
+            }
+            st4s(&G2[f][o], gv[0], gv[1], gv[2], gv[3]);
+          } else if (n < NB_BOUNDARY) {  // 2:1 face: flux-form ghost (R7)
+            const GhostCtx gc{g.aux, g.ijk, g.lvl, g.w3, g.sim, g.sp, A.face, A.rp,
+                              g.max_level, nc, fs.rpar, first ? kFirst : kNewP, cont ? 1 : 0,
+                              alpha, beta, gamma};
+            for (int e = 0; e < 4; ++e) G2[f][o + e] = ghost_21(gc, c, f, a0 + e, b, n);
+          }
+        }
+        // ---- q_{m-1} = K p_{m-1}, then r_m, x_m, p_m of my quad
+        quad_inv(cs, i0, j, kz, iv);
+        float rv[4], po[4] = {0.f, 0.f, 0.f, 0.f};
+        ld4v(stg.R + 4 * t, rv);
+        if (!first || cont) ld4v(stg.P + 4 * t, po);
+        if (!first) {
+          // p_{m-1} across the faces: the staged planes, or G1 on a cube with 2:1 faces
+          const float* acr = cs.has21 ? &S.G1[0][0] : stg.F[0] + 2 * FBB;
+          const int stride = cs.has21 ? FBB : kFaceVals;
+          float qo[4];
+          stencil_quad(cs, stg.P, acr, stride, po, t, qo);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xc[e] = fmaf(alpha, po[e], xc[e]);
+            rv[e] = fmaf(-alpha, qo[e], rv[e]);
+          }
+          st4s(A.x + base + 4 * t, xc[0], xc[1], xc[2], xc[3]);
+        }
+        float ro[4] = {0.f, 0.f, 0.f, 0.f};
+        if (first && cont) ld4v(A.r + base + 4 * t, ro);  // the previous recurrence residual
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          zv[e] = rv[e] * iv[e];
+          if (!first) pv[e] = fmaf(beta, po[e], zv[e]);
+          else if (cont) pv[e] = fmaf(gamma, po[e] - ro[e] * iv[e], zv[e]);  // z + g (p - D^-1 r)
+          else pv[e] = zv[e];
+          acc[3] = fmaf(rv[e], rv[e], acc[3]);
+          acc[4] = fmaf(rv[e], zv[e], acc[4]);
+        }
+        // p_m replaces r in the stage (only this thread reads its quad of R)
+        st4s(stg.R + 4 * t, pv[0], pv[1], pv[2], pv[3]);
+        st4s(A.r + base + 4 * t, rv[0], rv[1], rv[2], rv[3]);
+        st4s(A.p + base + 4 * t, pv[0], pv[1], pv[2], pv[3]);
+        face_store(fw, 0, rv, t);
+        face_store(fw, 2, pv, t);
+      }
+      // one barrier: the copies had landed for every thread, the tile and G2 hold p_m
+      if (__syncthreads_or(!okw)) {  // the slot's copies stay pending
         failed = true;
         break;
       }
       phase[sl] ^= 1u;
       pend[sl] = 0;
-      if (psim >= 0 && psim != s) flush();
-      psim = s;
-      const FSim& fs = sim[s];
-      const CubeSh<float>& cs = S.cs[sl];
-      FStage& stg = S.st[sl];
-      const bool first = (m == 0), cont = fs.cont != 0;
-      const float alpha = fs.alpha, beta = fs.beta, gamma = fs.gamma;
-      const int wpar = fs.rpar ^ 1;
-      float* fw = A.face + face_off(wpar, nc, c, 0);  // this cube's faces, written parity
-      const size_t base = (size_t)c * FB3;
-
-      // ---- phase 1: r, z, p, x of my quad; search-direction ghosts of the faces
-      float rv[4], zv[4], pv[4], inv[4];
-      {
-        const float4 r4 = ld4s(stg.R + 4 * t);
-        rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) inv[e] = inv_of(cs, cs.w3, cs.smask, i0 + e, j, kz);
-        float po[4] = {0.f, 0.f, 0.f, 0.f};
-        if (!first || cont) {
-          const float4 p4 = ld4s(stg.P + 4 * t);
-          po[0] = p4.x; po[1] = p4.y; po[2] = p4.z; po[3] = p4.w;
+      // the slot of cube q-1 is free (every thread fenced its accesses before the
+      // barrier above): refill it with cube q+2
+      if (q + 2 < nl) {
+        const int s2 = (q + 2) % kSlots;
+        if (warp == IW) {
+          issue_own(S.cube[q + 2], s2, first);
+          issue_faces(S.cube[q + 2], s2, first, false);
         }
-        if (!first) {
-          const float4 q4 = ld4s(stg.Q + 4 * t), x4 = ld4s(stg.X + 4 * t);
-          float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-          const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            xv[e] = fmaf(alpha, po[e], xv[e]);
-            rv[e] = fmaf(-alpha, qv[e], rv[e]);
-          }
-          st4s(A.x + base + 4 * t, xv[0], xv[1], xv[2], xv[3]);
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          zv[e] = rv[e] * inv[e];
-          if (!first) {
-            pv[e] = fmaf(beta, po[e], zv[e]);
-          } else if (cont) {  // resume: p = z + gamma (p_old - D^-1 r_old)
-            const float ro = stg.Q[4 * t + e];
-            pv[e] = fmaf(gamma, po[e] - ro * inv[e], zv[e]);
-          } else {
-            pv[e] = zv[e];
-          }
-          acc[3] = fmaf(rv[e], rv[e], acc[3]);
-          acc[4] = fmaf(rv[e], zv[e], acc[4]);
-        }
-        st4s(stg.P + 4 * t, pv[0], pv[1], pv[2], pv[3]);
-        st4s(A.r + base + 4 * t, rv[0], rv[1], rv[2], rv[3]);
-        st4s(A.p + base + 4 * t, pv[0], pv[1], pv[2], pv[3]);
-        // domain faces: the ghost of the new p mirrors this quad's cells (Neumann),
-        // negated at outflow (Dirichlet 0)
-        auto mir = [&](int f) { return cs.bc[f] == BC_OUTFLOW ? -1.f : 1.f; };
-        if (i0 == 0 && cs.nb[0] == NB_BOUNDARY) S.G[0][kz * FB + j] = mir(0) * pv[0];
-        if (i0 == FB - 4 && cs.nb[1] == NB_BOUNDARY) S.G[1][kz * FB + j] = mir(1) * pv[3];
-        if (j == 0 && cs.nb[2] == NB_BOUNDARY) {
-          const float sg = mir(2);
-          st4s(&S.G[2][kz * FB + i0], sg * pv[0], sg * pv[1], sg * pv[2], sg * pv[3]);
-        }
-        if (j == FB - 1 && cs.nb[3] == NB_BOUNDARY) {
-          const float sg = mir(3);
-          st4s(&S.G[3][kz * FB + i0], sg * pv[0], sg * pv[1], sg * pv[2], sg * pv[3]);
-        }
-        if (kz == 0 && cs.nb[4] == NB_BOUNDARY) {
-          const float sg = mir(4);
-          st4s(&S.G[4][j * FB + i0], sg * pv[0], sg * pv[1], sg * pv[2], sg * pv[3]);
-        }
-        if (kz == FB - 1 && cs.nb[5] == NB_BOUNDARY) {
-          const float sg = mir(5);
-          st4s(&S.G[5][j * FB + i0], sg * pv[0], sg * pv[1], sg * pv[2], sg * pv[3]);
-        }
-        // face planes of r and p
-        if (i0 == 0) {
-          fw[0 * kFaceVals + 0 * FBB + kz * FB + j] = rv[0];
-          fw[0 * kFaceVals + 2 * FBB + kz * FB + j] = pv[0];
-        }
-        if (i0 == FB - 4) {
-          fw[1 * kFaceVals + 0 * FBB + kz * FB + j] = rv[3];
-          fw[1 * kFaceVals + 2 * FBB + kz * FB + j] = pv[3];
-        }
-        if (j == 0) {
-          st4s(fw + 2 * kFaceVals + 0 * FBB + kz * FB + i0, rv[0], rv[1], rv[2], rv[3]);
-          st4s(fw + 2 * kFaceVals + 2 * FBB + kz * FB + i0, pv[0], pv[1], pv[2], pv[3]);
-        }
-        if (j == FB - 1) {
-          st4s(fw + 3 * kFaceVals + 0 * FBB + kz * FB + i0, rv[0], rv[1], rv[2], rv[3]);
-          st4s(fw + 3 * kFaceVals + 2 * FBB + kz * FB + i0, pv[0], pv[1], pv[2], pv[3]);
-        }
-        if (kz == 0) {
-          st4s(fw + 4 * kFaceVals + 0 * FBB + j * FB + i0, rv[0], rv[1], rv[2], rv[3]);
-          st4s(fw + 4 * kFaceVals + 2 * FBB + j * FB + i0, pv[0], pv[1], pv[2], pv[3]);
-        }
-        if (kz == FB - 1) {
-          st4s(fw + 5 * kFaceVals + 0 * FBB + j * FB + i0, rv[0], rv[1], rv[2], rv[3]);
-          st4s(fw + 5 * kFaceVals + 2 * FBB + j * FB + i0, pv[0], pv[1], pv[2], pv[3]);
-        }
+        pend[s2] = 1;
       }
-      // ghosts: threads 0 .. 383 take four cells (a .. a+3, b) of face f each
-      if (t < 6 * 64) {
-        const int f = t >> 6, qf = t & 63, a0 = 4 * (qf & 3), b = qf >> 2;
-        const int n = cs.nb[f];
-        float gv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (n >= 0) {  // same level: the neighbour's plane towards this cube
-          const float* F = stg.F[f];
-          const int mask = cs.nbmask[f];
-          const int* w3n = cs.nbw3[f];
-          const int o = b * FB + a0;
-          float fr[4] = {0.f, 0.f, 0.f, 0.f}, fq[4] = {0.f, 0.f, 0.f, 0.f},
-                fp[4] = {0.f, 0.f, 0.f, 0.f};
-          if (!first || cont) {
-            const float4 r4 = ld4s(F + o), q4 = ld4s(F + FBB + o), p4 = ld4s(F + 2 * FBB + o);
-            fr[0] = r4.x; fr[1] = r4.y; fr[2] = r4.z; fr[3] = r4.w;
-            fq[0] = q4.x; fq[1] = q4.y; fq[2] = q4.z; fq[3] = q4.w;
-            fp[0] = p4.x; fp[1] = p4.y; fp[2] = p4.z; fp[3] = p4.w;
-          }
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            int ii, jj, kk;
-            face_cell(f ^ 1, a0 + e, b, ii, jj, kk);
-            const float iv = inv_of(cs, w3n, mask, ii, jj, kk);
-            float pn;
-            if (!first) {
-              const float r = fmaf(-alpha, fq[e], fr[e]);
-              pn = fmaf(beta, fp[e], r * iv);
-            } else {
-              const float r = A.rp[(size_t)n * FB3 + (kk * FB + jj) * FB + ii];
-              pn = r * iv;
-              if (cont) pn = fmaf(gamma, fp[e] - fr[e] * iv, pn);
-            }
-            gv[e] = pn;
-          }
-        } else if (n < NB_BOUNDARY) {  // 2:1 face: flux-form ghost (R7) of the new p
-          const GhostCtx gc{g.aux, g.ijk, g.lvl, g.w3, g.sim, g.sp, A.face, A.rp, g.max_level,
-                            nc, fs.rpar, first ? 1 : 0, cont ? 1 : 0, alpha, beta, gamma};
-          for (int e = 0; e < 4; ++e) gv[e] = ghost_21(gc, c, f, a0 + e, b, n);
-        }
-        if (n != NB_BOUNDARY) st4s(&S.G[f][b * FB + a0], gv[0], gv[1], gv[2], gv[3]);
-      }
-      __syncthreads();
-
-      // ---- phase 2: q = K p on my quad
+      // ---- B: q_m = K p_m on my quad
       {
-        const float h = ldexpf(g.sp[s].h032, -g.lvl[c]);
-        // x neighbours from the adjacent quads of the warp (lanes hold consecutive quads)
-        const float left = __shfl_up_sync(0xffffffffu, pv[3], 1);
-        const float right = __shfl_down_sync(0xffffffffu, pv[0], 1);
-        const float xl = i0 > 0 ? left : S.G[0][kz * FB + j];
-        const float xr = i0 < FB - 4 ? right : S.G[1][kz * FB + j];
-        const float4 ym = j > 0 ? ld4s(stg.P + 4 * t - FB) : ld4s(&S.G[2][kz * FB + i0]);
-        const float4 yp = j < FB - 1 ? ld4s(stg.P + 4 * t + FB) : ld4s(&S.G[3][kz * FB + i0]);
-        const float4 zm = kz > 0 ? ld4s(stg.P + 4 * t - FBB) : ld4s(&S.G[4][j * FB + i0]);
-        const float4 zp = kz < FB - 1 ? ld4s(stg.P + 4 * t + FBB) : ld4s(&S.G[5][j * FB + i0]);
-        const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
-        const float zmv[4] = {zm.x, zm.y, zm.z, zm.w}, zpv[4] = {zp.x, zp.y, zp.z, zp.w};
         float qv[4];
+        stencil_quad(cs, stg.R, &G2[0][0], FBB, pv, t, qv);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float pc = pv[e];
-          const float xm = e == 0 ? xl : pv[e - 1];
-          const float xp = e == 3 ? xr : pv[e + 1];
-          float sum = (pc - xm) + (pc - xp) + (pc - ymv[e]) + (pc - ypv[e]) + (pc - zmv[e]) +
-                      (pc - zpv[e]);
-          if (cs.has21) {
-            const int i = i0 + e;
-            if (i == 0) sum += (cs.wt[0] - 1.f) * (pc - xm);
-            if (i == FB - 1) sum += (cs.wt[1] - 1.f) * (pc - xp);
-            if (j == 0) sum += (cs.wt[2] - 1.f) * (pc - ymv[e]);
-            if (j == FB - 1) sum += (cs.wt[3] - 1.f) * (pc - ypv[e]);
-            if (kz == 0) sum += (cs.wt[4] - 1.f) * (pc - zmv[e]);
-            if (kz == FB - 1) sum += (cs.wt[5] - 1.f) * (pc - zpv[e]);
-          }
-          qv[e] = h * sum;
-          acc[0] = fmaf(pc, qv[e], acc[0]);
+          acc[0] = fmaf(pv[e], qv[e], acc[0]);
           acc[1] = fmaf(qv[e], zv[e], acc[1]);
-          acc[2] = fmaf(qv[e] * inv[e], qv[e], acc[2]);
+          acc[2] = fmaf(qv[e] * iv[e], qv[e], acc[2]);
         }
-        st4s(A.q + base + 4 * t, qv[0], qv[1], qv[2], qv[3]);
-        if (i0 == 0) fw[0 * kFaceVals + FBB + kz * FB + j] = qv[0];
-        if (i0 == FB - 4) fw[1 * kFaceVals + FBB + kz * FB + j] = qv[3];
-        if (j == 0) st4s(fw + 2 * kFaceVals + FBB + kz * FB + i0, qv[0], qv[1], qv[2], qv[3]);
-        if (j == FB - 1) st4s(fw + 3 * kFaceVals + FBB + kz * FB + i0, qv[0], qv[1], qv[2], qv[3]);
-        if (kz == 0) st4s(fw + 4 * kFaceVals + FBB + j * FB + i0, qv[0], qv[1], qv[2], qv[3]);
-        if (kz == FB - 1) st4s(fw + 5 * kFaceVals + FBB + j * FB + i0, qv[0], qv[1], qv[2], qv[3]);
+        face_store(fw, 1, qv, t);
       }
-      // the stage and the ghosts are free once every thread is past them; the next
-      // bulk copy into this slot is ordered after the block's generic accesses
+      // this thread is done with the slot: order its accesses before the slot's next
+      // bulk copy (issued after a later barrier)
       fence_async_shared();
-      __syncthreads();
-      if (q + 2 < nl) issue(q + 2, sl);
     }
     if (failed) break;
-    if (psim >= 0) flush();
     // this pass's global writes, before the barrier, for the next pass's bulk copies
+    // (the flush's barriers order every thread's fence before the prefetch below)
     fence_async_global();
+    if (psim >= 0) flush();
+    else __syncthreads();
+    // prefetch the own data of this pass's first two cubes for the next pass (this
+    // block wrote it; their face planes wait for the barrier)
+    if (warp == IW)
+      for (int q = 0; q < 2 && q < nl; ++q) issue_own(S.cube[q], q, false);
+    if (t == 0) {
+      for (int q = 0; q < 2; ++q) S.pre[q] = q < nl ? S.cube[q] : -1;
+      S.any_alive = S.any_finished = 0;  // every thread read them at the pass's start
+    }
+    for (int q = 0; q < 2 && q < nl; ++q) pend[q] = 1;
     if (!gb.sync()) {
       failed = true;
       break;
@@ -619,13 +742,18 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
   }
   if (failed) {
     if (t == 0) atomicExch(err, 1);
-    // let the copies in flight land before the block's shared memory goes away (a copy
-    // of at most 84 KB takes microseconds; the drain is bounded by one second, not by
-    // the solver's timeout, which a test may set to nanoseconds)
-    for (int sl = 0; sl < 2; ++sl)
-      if (pend[sl]) mbar_wait(&S.mbar[sl], phase[sl], 1000000000ull);
-    return;
   }
+  // a prefetch that no pass used: complete its phase (no face planes) and let it land;
+  // on failure let every copy in flight land (a copy of at most 68 KB takes
+  // microseconds; the drain is bounded by one second, not by the solver's timeout, which
+  // a test may set to nanoseconds)
+  __syncthreads();
+  if (warp == IW)
+    for (int q = 0; q < 2; ++q)
+      if (S.pre[q] >= 0 && pend[q]) issue_faces(S.pre[q], q, false, true);
+  for (int sl = 0; sl < kSlots; ++sl)
+    if (pend[sl]) mbar_wait(&S.mbar[sl], phase[sl], 1000000000ull);
+  if (failed) return;
   if (blockIdx.x == 0 && t == 0) g.flags[0] = 1;
 }
 
@@ -633,7 +761,8 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
 
 cudaError_t launch_pcg_fused(const Ctx& x, const SolveParams& prm, bool* launched) {
   *launched = false;
-  if (x.f64 || x.B != FB || !x.f.face || x.g.n_sims > kMaxPersistentSims) return cudaSuccess;
+  if (x.f64 || x.B != FB || !x.f.face || !x.f.fcube || x.g.n_sims > kMaxFusedSims)
+    return cudaSuccess;
   const size_t sm = (sizeof(FShared) + 15) / 16 * 16 + sizeof(FSim) * (size_t)x.g.n_sims;
   auto kern = k_pcg_fused;
   {
@@ -650,10 +779,10 @@ cudaError_t launch_pcg_fused(const Ctx& x, const SolveParams& prm, bool* launche
   FusedArgs a;
   a.rp = (const float*)x.f.r;
   a.r = (float*)x.f.w1;
-  a.q = (float*)x.f.q;
   a.p = (float*)x.f.p0;
   a.x = x.f.e;
   a.face = x.f.face;
+  a.fc = x.f.fcube;
   SolveParams pp = prm;
   unsigned int* bar = x.f.bar;
   int* err = x.f.err;

