@@ -49,7 +49,14 @@ typedef enum {
     BCM_E_BOUNDS = -6         /* a size exceeds a documented maximum */
 } bcm_status;
 
-enum { BCM_PREC_F64 = 0, BCM_PREC_F32_REFINE = 1 };
+/* Precision of a grid.  BCM_PREC_F64: FP64 state, sweeps and pressure solve.
+ * BCM_PREC_F32_REFINE: FP32 state and sweeps; the pressure solve is an FP32 inner PCG
+ * inside FP64 defect correction (FP64 residual, pressure and divergence check).
+ * BCM_PREC_F64_REFINE: FP64 state and momentum/projection sweeps with the pressure
+ * solve of BCM_PREC_F32_REFINE: the FP32 Poisson sweeps without the rounding of the
+ * state to FP32 every step (which a flow that amplifies perturbations, like the
+ * sphere wake at Re 300, turns into 1e-4 differences over a few hundred steps). */
+enum { BCM_PREC_F64 = 0, BCM_PREC_F32_REFINE = 1, BCM_PREC_F64_REFINE = 2 };
 
 /* Domain-face boundary conditions (face order -x,+x,-y,+y,-z,+z). */
 enum {

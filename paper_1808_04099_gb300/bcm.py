@@ -17,7 +17,7 @@ from . import _build
 # status codes
 BCM_OK, BCM_E_INVALID, BCM_E_CUDA, BCM_E_NOT_CONVERGED = 0, -1, -2, -3
 BCM_E_NONFINITE, BCM_E_TIMEOUT, BCM_E_BOUNDS = -4, -5, -6
-PREC_F64, PREC_F32_REFINE = 0, 1
+PREC_F64, PREC_F32_REFINE, PREC_F64_REFINE = 0, 1, 2
 PRECOND_JACOBI, PRECOND_MULTIGRID = 0, 1
 SCHEME_AB2_CENTRAL, SCHEME_QUICK_CN = 0, 1
 (U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)

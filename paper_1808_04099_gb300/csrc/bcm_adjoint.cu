@@ -459,7 +459,8 @@ extern "C" bcm_status bcm_adjoint_step(bcm_grid* grid, void* dev_adj, size_t byt
   if (!grid || !dev_adj || !state || !dev_dJ) return grid_fail(BCM_E_INVALID, "NULL argument");
   if (grid_two_level(grid)) return grid_fail(BCM_E_INVALID, "the adjoint needs a single-level grid");
   const Ctx& base = *grid_ctx(grid);
-  if (!base.f64) return grid_fail(BCM_E_INVALID, "the adjoint runs on FP64 grids");
+  if (!base.f64 || !base.solve64)
+    return grid_fail(BCM_E_INVALID, "the adjoint runs on FP64 grids (BCM_PREC_F64)");
   if (base.part.n > 0)
     return grid_fail(BCM_E_INVALID, "the adjoint differentiates the solid-fraction IB, not particles");
   if (base.scheme != 0)

@@ -106,7 +106,8 @@ bcm_status validate(const bcm_grid_desc* d) {
   if (d->cells_per_edge != 4 && d->cells_per_edge != 8 && d->cells_per_edge != 16)
     return fail(BCM_E_INVALID, "cells_per_edge must be 4, 8 or 16");
   if (d->max_level < 0 || d->max_level > 1) return fail(BCM_E_INVALID, "max_level must be 0 or 1");
-  if (d->precision != BCM_PREC_F64 && d->precision != BCM_PREC_F32_REFINE)
+  if (d->precision != BCM_PREC_F64 && d->precision != BCM_PREC_F32_REFINE &&
+      d->precision != BCM_PREC_F64_REFINE)
     return fail(BCM_E_INVALID, "unknown precision %d", d->precision);
   if (d->lagged_bf16 != 0 && (d->lagged_bf16 != 1 || d->precision != BCM_PREC_F32_REFINE))
     return fail(BCM_E_INVALID, "lagged_bf16 must be 0, or 1 with BCM_PREC_F32_REFINE");
@@ -411,8 +412,8 @@ void fused_records(const HostTables& T, int n, FCube* out) {
 Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml) {
   Layout L{};
   const size_t n = (size_t)d->n_cubes * d->cells_per_edge * d->cells_per_edge * d->cells_per_edge;
-  const size_t S = d->precision == BCM_PREC_F64 ? 8 : 4;   // state storage
-  const size_t V = S;                                      // PCG vector storage
+  const size_t S = d->precision == BCM_PREC_F32_REFINE ? 4 : 8;  // state storage
+  const size_t V = d->precision == BCM_PREC_F64 ? 8 : 4;         // PCG vector storage
   const size_t nub = (size_t)n_slots * 3 * d->cells_per_edge * d->cells_per_edge;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -427,7 +428,7 @@ Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml)
   L.p = take(n * 8); L.b = take(n * 8);
   L.bid = take(n); L.near_ = take(d->n_cubes);
   L.r = take(n * V); L.p0 = take(n * V); L.p1 = take(n * V); L.q = take(n * V);
-  L.e = take(d->precision == BCM_PREC_F64 ? 0 : n * 4);
+  L.e = take(d->precision == BCM_PREC_F64 ? 0 : n * 4);  // FP32 inner iterate
   L.w1 = take(n * V); L.s0 = take(n * V); L.s1 = take(n * V);
   // fused PCG: r, q, p on the six face planes of every cube, two parities
   const bool fused_ok = d->precision != BCM_PREC_F64 && d->cells_per_edge == 16;
@@ -533,7 +534,7 @@ struct bcm_grid {
   unsigned char* ws = nullptr;
   cudaStream_t stream = nullptr;
   Ctx ctx;
-  int B = 0, f64 = 1;
+  int B = 0, f64 = 1, solve64 = 1;  // state FP64; pressure solve FP64 (else FP32 inner)
   size_t n_cells = 0;
   int device = 0;
 };
@@ -639,7 +640,8 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   g->ws = (unsigned char*)dev_workspace;
   g->stream = (cudaStream_t)cuda_stream;
   g->B = desc->cells_per_edge;
-  g->f64 = desc->precision == BCM_PREC_F64;
+  g->f64 = desc->precision != BCM_PREC_F32_REFINE;
+  g->solve64 = desc->precision == BCM_PREC_F64;
   g->n_cells = (size_t)desc->n_cubes * g->B * g->B * g->B;
   const Layout& L = g->L;
   unsigned char* W = g->ws;
@@ -692,12 +694,13 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   Ctx& x = g->ctx;
   x.B = g->B;
   x.f64 = g->f64;
+  x.solve64 = g->solve64;
   x.slabs_a = 1;
   x.slabs_b = 1;
-  x.slabs_p = (g->B == 16 && g->f64) ? 2 : 1;
+  x.slabs_p = (g->B == 16 && g->solve64) ? 2 : 1;
   // measured on GB300 at 4.2M cells: the persistent solver is on par in FP32 and
   // slower in FP64 (ALU-bound passes), so FP64 defaults to two launches per iteration
-  x.persistent = (!g->f64 && desc->n_sims <= 256) ? 1 : 0;
+  x.persistent = (!g->solve64 && desc->n_sims <= 256) ? 1 : 0;
   x.single_pass = 0;
   x.resident = 0;
   x.fused = 0;  // the fused single-barrier form: selected by bcm_set_launch(5, ...)
@@ -729,7 +732,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   F.p = (double*)(W + L.p); F.b = (double*)(W + L.b);
   F.bid = W + L.bid; F.near = W + L.near_;
   F.r = W + L.r; F.p0 = W + L.p0; F.p1 = W + L.p1; F.q = W + L.q;
-  F.e = g->f64 ? nullptr : (float*)(W + L.e);
+  F.e = g->solve64 ? nullptr : (float*)(W + L.e);
   F.w1 = W + L.w1; F.s0 = W + L.s0; F.s1 = W + L.s1;
   F.face = L.face ? (float*)(W + L.face) : nullptr;
   F.fcube = L.fcube ? (const FCube*)(W + L.fcube) : nullptr;
@@ -970,7 +973,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   prm.max_iter = max_iter;
   prm.inner_max_iter = max_iter;
   prm.max_cycles = g->max_cycles;
-  prm.mixed = g->f64 ? 0 : 1;
+  prm.mixed = g->solve64 ? 0 : 1;
   prm.guard = x.f.guard;
   prm.guard_limit = 0;
   prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
@@ -987,7 +990,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   cudaGraphExec_t mg_exec = nullptr;
   if (mg_graph && (st = mg_iteration_graph(g, prm, &mg_exec)) != BCM_OK) return st;
   if (x.persistent && !mg) {
-    if (g->f64) {
+    if (g->solve64) {
       RUN(BCM_K_PCG, launch_pcg(x, prm, &g->pcg_form));
       return read_err(g);
     }
@@ -1008,7 +1011,7 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
     return BCM_OK;
   }
   if ((st = read_flags(g, flags)) != BCM_OK) return st;
-  if (g->f64) {
+  if (g->solve64) {
     int it = 0;
     while (!flags[0] && it < max_iter) {
       for (int m = 0; m < every && it < max_iter; ++m, ++it)
@@ -1075,7 +1078,7 @@ bcm_status collect(bcm_grid* g, bcm_stats* out) {
     const SimState& t = ss[s];
     bcm_stats& o = out[s];
     o.cg_iters = t.total_iters;
-    o.refine_cycles = g->f64 ? 0 : t.cycles;
+    o.refine_cycles = g->solve64 ? 0 : t.cycles;
     o.steps = t.step;
     o.converged = t.converged;
     o.rel_resid = t.bb > 0 ? sqrt(t.rr64 / t.bb) : 0.0;
@@ -1178,7 +1181,7 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   prm.max_iter = max_iter;
   prm.inner_max_iter = max_iter;
   prm.max_cycles = cycles;
-  prm.mixed = g->f64 ? 0 : 1;
+  prm.mixed = g->solve64 ? 0 : 1;
   prm.guard = x.f.guard;
   prm.barrier_timeout_ns = (unsigned long long)(g->barrier_timeout_s * 1e9);
   const bool particles = x.part.n > 0;
@@ -1194,7 +1197,7 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   CUDA_TRY(launch_rhs(x));
   CUDA_TRY(launch_solve_begin(x));
   CUDA_TRY(launch_residual(x, prm));
-  if (g->f64) {
+  if (g->solve64) {
     CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
   } else {
     for (int c = 0; c < cycles; ++c) {
@@ -1221,7 +1224,7 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     return fail(BCM_E_INVALID, "graph steps use the persistent Jacobi PCG, not multigrid");
   StepGraph& sg = g->sg;
   int cycles = 0;
-  if (!g->f64) {  // enough cycles for rtol at the inner reduction per cycle, plus margin
+  if (!g->solve64) {  // enough cycles for rtol at the inner reduction per cycle, plus margin
     const double eta = effective_inner_rtol(g, g->recycle != 0);
     cycles = g->graph_cycles > 0 ? g->graph_cycles
                                  : (int)ceil(log(rtol) / log(eta)) + 4;
@@ -1689,7 +1692,7 @@ extern "C" bcm_status bcm_set_preconditioner(bcm_grid* g, int kind) {
 
 extern "C" bcm_status bcm_apply_preconditioner(bcm_grid* g, const double* r, double* z) {
   if (!g || !r || !z) return fail(BCM_E_INVALID, "NULL argument");
-  if (!g->f64 || !g->mg_ok)
+  if (!g->solve64 || !g->mg_ok)
     return fail(BCM_E_INVALID, "the preconditioner test path needs an FP64 single-level grid");
   const Ctx& x = g->ctx;
   const size_t bytes = g->n_cells * sizeof(double);

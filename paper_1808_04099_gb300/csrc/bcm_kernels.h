@@ -105,6 +105,7 @@ struct Ctx {
   Fields f;
   int B;
   int f64;      // state in FP64 (plain mode) or FP32 (mixed mode)
+  int solve64;  // pressure solve: FP64 PCG (1) or FP32 inner PCG in FP64 defect correction
   int slabs_a;  // PCG pass A: z-slabs per cube (1, 2 or 4)
   int slabs_b;  // PCG pass B: z-slabs per cube (1, 2 or 4)
   int slabs_p;  // persistent PCG: z-slabs per cube (1, 2 or 4)

@@ -778,7 +778,7 @@ static cudaError_t down0_tile_t(const Ctx& x, int l, int all, bool fb) {
   const size_t sm = sizeof(TV) * ((SL::N + 3) / 4 * 4 + (size_t)B * B * B);
   PassB<TV> pb{};
   if (fb) {
-    pb.x = x.f64 ? (TV*)x.f.p : (TV*)x.f.e;
+    pb.x = x.solve64 ? (TV*)x.f.p : (TV*)x.f.e;
     pb.p0 = (const TV*)x.f.p0;
     pb.p1 = (const TV*)x.f.p1;
     pb.q = (const TV*)x.f.q;
@@ -855,7 +855,7 @@ static cudaError_t vcycle_t(const Ctx& x, const SolveParams& prm, int mode) {
 }
 
 cudaError_t launch_mg_vcycle(const Ctx& x, const SolveParams& prm, int mode) {
-  return x.f64 ? vcycle_t<double>(x, prm, mode) : vcycle_t<float>(x, prm, mode);
+  return x.solve64 ? vcycle_t<double>(x, prm, mode) : vcycle_t<float>(x, prm, mode);
 }
 
 }  // namespace bcm

@@ -393,7 +393,7 @@ cudaError_t launch_pcg(const Ctx& x, const SolveParams& prm, int* form) {
     }
   }
   *form = PCG_STREAMING;
-  return x.f64 ? pcg_dispatch<double, double>(x, prm, x.f.p)
+  return x.solve64 ? pcg_dispatch<double, double>(x, prm, x.f.p)
                : pcg_dispatch<float, float>(x, prm, x.f.e);
 }
 

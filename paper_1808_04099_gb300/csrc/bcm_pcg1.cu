@@ -348,7 +348,7 @@ static cudaError_t pcg1_dispatch(const Ctx& x, const SolveParams& prm, TX* xv) {
 
 cudaError_t launch_pcg1(const Ctx& x, const SolveParams& prm) {
   if (x.g.n_sims > kMaxPersistentSims) return cudaErrorInvalidValue;
-  return x.f64 ? pcg1_dispatch<double, double>(x, prm, x.f.p)
+  return x.solve64 ? pcg1_dispatch<double, double>(x, prm, x.f.p)
                : pcg1_dispatch<float, float>(x, prm, x.f.e);
 }
 

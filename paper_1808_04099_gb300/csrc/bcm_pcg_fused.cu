@@ -761,7 +761,7 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
 
 cudaError_t launch_pcg_fused(const Ctx& x, const SolveParams& prm, bool* launched) {
   *launched = false;
-  if (x.f64 || x.B != FB || !x.f.face || !x.f.fcube || x.g.n_sims > kMaxFusedSims)
+  if (x.solve64 || x.B != FB || !x.f.face || !x.f.fcube || x.g.n_sims > kMaxFusedSims)
     return cudaSuccess;
   const size_t sm = (sizeof(FShared) + 15) / 16 * 16 + sizeof(FSim) * (size_t)x.g.n_sims;
   auto kern = k_pcg_fused;

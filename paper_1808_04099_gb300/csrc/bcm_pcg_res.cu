@@ -338,7 +338,7 @@ static cudaError_t pcg_res_t(const Ctx& x, const SolveParams& prm, bool* launche
 // at most kResCubes cubes per co-resident block); *launched says whether it ran.
 cudaError_t launch_pcg_resident(const Ctx& x, const SolveParams& prm, bool* launched) {
   *launched = false;
-  if (x.f64 || x.g.n_sims > kMaxPersistentSims || x.g.n_cubes < 1) return cudaSuccess;
+  if (x.solve64 || x.g.n_sims > kMaxPersistentSims || x.g.n_cubes < 1) return cudaSuccess;
   switch (x.B) {
     case 8: return pcg_res_t<8>(x, prm, launched);
     case 16: return pcg_res_t<16>(x, prm, launched);

@@ -537,7 +537,7 @@ cudaError_t launch_residual(const Ctx& x, const SolveParams& prm) {
   BCM_DISPATCH_B(x.B, {
     constexpr int NT = threads_for<B>();
     const size_t sm = sizeof(double) * Slab<B, B>::N;
-    if (x.f64) {
+    if (x.solve64) {
       auto kern = k_residual<B, NT, double, false>;
       cudaError_t e = allow_smem(kern, sm);
       if (e != cudaSuccess) return e;
@@ -596,10 +596,10 @@ static cudaError_t cg_b_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   return cudaGetLastError();
 }
 cudaError_t launch_cg_a(const Ctx& x, const SolveParams& prm) {
-  return x.f64 ? cg_a_t<double>(x, prm) : cg_a_t<float>(x, prm);
+  return x.solve64 ? cg_a_t<double>(x, prm) : cg_a_t<float>(x, prm);
 }
 cudaError_t launch_cg_b(const Ctx& x, const SolveParams& prm) {
-  return x.f64 ? cg_b_t<double, double>(x, prm, x.f.p) : cg_b_t<float, float>(x, prm, x.f.e);
+  return x.solve64 ? cg_b_t<double, double>(x, prm, x.f.p) : cg_b_t<float, float>(x, prm, x.f.e);
 }
 
 cudaError_t launch_add_correction(const Ctx& x) {

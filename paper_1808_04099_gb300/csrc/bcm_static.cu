@@ -110,6 +110,7 @@ extern "C" bcm_status bcm_solve_pressure_static(bcm_grid* grid, const double* de
 
   Ctx x = base;
   x.f64 = 1;  // FP64 vectors and two launches per iteration, as bcm_solve_pressure in FP64
+  x.solve64 = 1;
   x.persistent = 0;
   x.f.b = const_cast<double*>(dev_b);
   x.f.p = dev_p;

@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 from oracle import mg_oracle as MGO
 from paper_1808_04099_gb300 import workloads as W
-from _util import demean_per_sim, oracle_run, rel_l2
+from _util import assert_close, demean_per_sim, oracle_run, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,8 +51,7 @@ def velocity(g):
 
 def check(g, ost, spec, tol):
     ref = np.concatenate([ost[k] for k in ("u", "v", "w")])
-    assert rel_l2(velocity(g), ref) <= tol
-    assert rel_l2(demean_per_sim(g.numpy(bcm.P), spec), demean_per_sim(ost["p"], spec)) <= tol
+    assert_close(velocity(g), ref, g.numpy(bcm.P), ost["p"], spec, tol)
 
 
 @pytest.mark.parametrize("prec", [bcm.PREC_F64, bcm.PREC_F32_REFINE])
