@@ -205,8 +205,8 @@ bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max
                           int32_t *check_every, double *barrier_timeout_s, int32_t *recycle);
 
 /* Launch shape of the PCG.  persistent = 5 (mixed mode on 16^3 cubes, grids of at most
- * 160 sims and 256 cubes per SM): one cooperative launch per solve, one block of 256
- * threads (one x-row of the cube in hand each) per SM,
+ * 160 sims and 256 cubes per SM): one cooperative launch per solve, one block of 1024
+ * threads (four x-adjacent cells of the cube in hand each) per SM,
  * one grid barrier per iteration (the beta of the next iteration follows from <q,z> and
  * <q,D^-1 q> of the same pass; q = K p is applied again rather than stored), each cube's
  * r, p, x and its neighbours' face planes staged by bulk asynchronous copies two cubes
