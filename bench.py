@@ -85,8 +85,8 @@ PCG_SOURCES = ["bcm_pcg.cu", "bcm_persist.cuh", "bcm_cube.cuh", "bcm_internal.cu
 # ncu summary and the sources it was taken at, per persistent PCG form
 PROFILES = {1: (PROFILE, PCG_SOURCES),
             5: ("profiles/pcg_fused_sphere_16x8x8_B16_mixed.md",
-                ["bcm_pcg_fused.cu", "bcm_persist.cuh", "bcm_cube.cuh", "bcm_internal.cuh",
-                 "bcm_kernels.h"])}
+                ["bcm_pcg_fused.cu", "bcm_bulk.cuh", "bcm_persist.cuh", "bcm_cube.cuh",
+                 "bcm_internal.cuh", "bcm_kernels.h"])}
 
 
 def profile_for_form(form: int):

@@ -210,8 +210,7 @@ bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max
  * one grid barrier per iteration (the beta of the next iteration follows from <q,z> and
  * <q,D^-1 q> of the same pass; q = K p is applied again rather than stored), each cube's
  * r, p, x and its neighbours' face planes staged by bulk asynchronous copies two cubes
- * ahead;
- * grids it does not fit run persistent = 1.  persistent = 1: every PCG solve is one
+ * ahead; grids it does not fit run persistent = 1.  persistent = 1: every PCG solve is one
  * cooperative launch whose blocks loop over the iterations with two grid-wide barriers
  * each, streaming the vectors through global memory (the mixed-mode default);
  * persistent = 3: the same iteration with each cube's search direction kept in

@@ -1,6 +1,6 @@
-"""Launch-shape autotuner of the PCG: the persistent cooperative solver (the fused
-single-barrier form with bulk-copy staging, two passes per iteration streaming with 1,
-2 or 4 z-slabs per work item or with the search direction in shared memory, or the
+"""Launch-shape autotuner of the PCG: the persistent cooperative solver (two passes per
+iteration streaming with 1, 2 or 4 z-slabs per work item or with the search direction
+in shared memory, the fused single-barrier form with bulk-copy staging, or the
 single-reduction form), or two launches per iteration with z-slabs per pass.
 
 Times a fixed number of PCG iterations on the grid's current right-hand side for

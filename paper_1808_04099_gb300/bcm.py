@@ -366,7 +366,9 @@ class Grid:
         """persistent: 0 two launches per iteration, 1 the persistent two-pass PCG
         streaming its vectors through global memory, 2 the persistent single-reduction
         PCG, 3 the persistent two-pass PCG with the search direction in shared memory
-        where the grid fits one co-resident wave (bool values map to 0 and 1)."""
+        where the grid fits one co-resident wave, 5 the fused single-barrier PCG (mixed
+        precision on 16^3 cubes, else the two-pass form runs; bool values map to 0 and
+        1)."""
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
 
     def set_step(self, step: int):

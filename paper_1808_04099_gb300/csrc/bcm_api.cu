@@ -1346,13 +1346,15 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
     return fail(BCM_E_INVALID, "slab too thin for this cube size");
   if (persistent < 0 || persistent > 5 || persistent == 4)
     return fail(BCM_E_INVALID, "persistent must be 0, 1, 2, 3 or 5");
+  if (persistent == 5 && slabs_a != 1)
+    return fail(BCM_E_INVALID, "the fused form takes whole cubes");
+  if (persistent && g->B != 16 && slabs_a != 1)
+    return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
   g->ctx.persistent = persistent ? 1 : 0;
   g->ctx.single_pass = persistent == 2 ? 1 : 0;
   g->ctx.resident = persistent == 3 ? 1 : 0;
   g->ctx.fused = persistent == 5 ? 1 : 0;
-  if (persistent == 5 && slabs_a != 1) return fail(BCM_E_INVALID, "the fused form takes whole cubes");
   if (persistent) {
-    if (g->B != 16 && slabs_a != 1) return fail(BCM_E_INVALID, "persistent slabs need 16^3 cubes");
     g->ctx.slabs_p = slabs_a;
   } else {
     g->ctx.slabs_a = slabs_a;

@@ -218,6 +218,7 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
       S[o + 3] = v[3];
     }
   }
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < 4 * KS * B; idx += NT) {
     const int f = idx / (KS * B), rem = idx - f * (KS * B), kk = rem / B, t = rem - kk * B;
     const int n = cs.nb[f];

@@ -39,6 +39,8 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TV* S = reinterpret_cast<TV*>(smem_raw);
   __shared__ CubeSh<TV> csa[kCubeCache];  // the block's cubes, or one reloaded per item
+  __shared__ int tsim[kCubeCache];        // ... their sims and cell sizes
+  __shared__ TV th[kCubeCache];
   __shared__ int cs_cube;
   __shared__ double red[2 * 32];
   const int nsim = g.n_sims;
@@ -46,8 +48,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
   double* s_alpha = reinterpret_cast<double*>(smem_raw + (sizeof(TV) * SL::N + 15) / 16 * 16);
   double* s_beta = s_alpha + nsim;
   double* s_rz = s_beta + nsim;
-  double* s_rzprev = s_rz + nsim;
-  unsigned char* s_done = reinterpret_cast<unsigned char*>(s_rzprev + nsim);
+  unsigned char* s_done = reinterpret_cast<unsigned char*>(s_rz + nsim);
   unsigned char* s_first = s_done + nsim;  // restart with p = z at iteration 0
   unsigned char* s_poff = s_first + nsim;  // search-direction buffer offset
   const bool inner = prm.mixed != 0;
@@ -62,7 +63,6 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     SimState& st = g.ss[s];
     const bool cont = st.cont != 0;
     s_rz[s] = cont ? st.rz_last : st.rz;
-    s_rzprev[s] = s_rz[s];
     s_done[s] = st.done ? 1 : 0;
     s_first[s] = cont ? 0 : 1;
     s_poff[s] = cont ? (unsigned char)(st.p_off & 1) : 0;
@@ -71,16 +71,25 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
   // when they fit the cache (every grid up to a few cubes per block)
   const int cA = item0 / NSL, cB = (item0 + max(nitems, 1) - 1) / NSL;
   const bool cached = cB - cA < kCubeCache;
-  if (cached)
+  if (cached) {
     for (int c = cA; c <= cB && c < g.n_cubes; ++c) load_cube(csa[c - cA], g, c);
+    for (int c = cA + threadIdx.x; c <= cB && c < g.n_cubes; c += NT) {
+      tsim[c - cA] = g.sim[c];
+      th[c - cA] = TV(cell_h<B>(g, c));
+    }
+  }
   __syncthreads();
+  auto sim_of = [&](int c) { return cached ? tsim[c - cA] : g.sim[c]; };
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GridBarrier gb;
   gb.init(bar, err, prm.barrier_timeout_ns);
   int k = 0;
   for (;; ++k) {
-    // ---- decisions for iteration k (identical in every block)
+    // ---- decisions for iteration k (identical in every block): warp w takes sims w,
+    // w + NW, ..., its lanes reading the stripes of <r,z> and <r,r> together
     int alive = 0;
-    for (int s = threadIdx.x; s < nsim; s += NT) {
+    for (int s = warp; s < nsim; s += NW) {
       SimState& st = g.ss[s];
       if (s_done[s]) continue;
       double rz, rr;
@@ -88,9 +97,9 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         rz = st.rz;
         rr = st.rr;
       } else {
-        rz = slot_sum(st, ACC_SLOT_RZ + k % 3);
-        rr = slot_sum(st, ACC_SLOT_RR + k % 3);
+        warp_slot_sums(st, ACC_SLOT_RZ + k % 3, ACC_SLOT_RR + k % 3, rz, rr);
       }
+      if (lane != 0) continue;
       const double tol2 = inner ? st.inner_tol2 : st.tol2;
       const bool bad = !isfinite(rr) || !isfinite(rz);
       if (bad || rr <= tol2 || k >= kmax) {
@@ -111,7 +120,6 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         continue;
       }
       s_beta[s] = ((k == 0 && s_first[s]) || s_rz[s] == 0.0) ? 0.0 : rz / s_rz[s];
-      s_rzprev[s] = s_rz[s];
       s_rz[s] = rz;
       alive = 1;
     }
@@ -136,7 +144,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     };
     for (int it = 0; it < nitems; ++it) {
       const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
-      const int s = g.sim[c];
+      const int s = sim_of(c);
       if (s_done[s]) continue;
       if (psim >= 0) {
         if (psim != s) flush_pq();
@@ -196,7 +204,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
         return first ? z : z + beta * pold[gi];
       };
       stage_pressure_slab<B, KS, NT, TV>(S, cs, g, c, z0, val4, val1, valg);
-      const TV h = TV(cell_h<B>(g, c));
+      const TV h = cached ? th[c - cA] : TV(cell_h<B>(g, c));
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
       if (NT == BB) {
         // one thread per (i, j) column marching up the slab: the z neighbours roll
@@ -239,10 +247,11 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     if (psim >= 0) flush_pq();
     if (!gb.sync()) break;
     // ---- alpha per sim from the completed <p, q>
-    for (int s = threadIdx.x; s < nsim; s += NT) {
+    for (int s = warp; s < nsim; s += NW) {
       if (s_done[s]) continue;
-      const double pq = slot_sum(g.ss[s], ACC_SLOT_PQ + k % 3);
-      s_alpha[s] = (pq != 0.0 && isfinite(pq)) ? s_rz[s] / pq : 0.0;
+      double pq, pq2;
+      warp_slot_sums(g.ss[s], ACC_SLOT_PQ + k % 3, ACC_SLOT_PQ + k % 3, pq, pq2);
+      if (lane == 0) s_alpha[s] = (pq != 0.0 && isfinite(pq)) ? s_rz[s] / pq : 0.0;
     }
     __syncthreads();
     // ---- pass B over my items (pointwise); the dots summed per sim as in pass A
@@ -260,7 +269,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     };
     for (int it = 0; it < nitems; ++it) {
       const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
-      const int s = g.sim[c];
+      const int s = sim_of(c);
       if (s_done[s]) continue;
       if (psim >= 0 && psim != s) flush_rz();
       psim = s;
@@ -322,9 +331,9 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
 template <int B, int KS, class TV, class TX>
 static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   constexpr int NT = pcg_threads<B>();
-  // tile (16-byte multiple) + alpha, beta, rz, rz_prev (FP64), done, first, p_off (bytes)
+  // tile (16-byte multiple) + alpha, beta, rz (FP64), done, first, p_off (bytes)
   const size_t tile = (sizeof(TV) * Slab<B, KS>::N + 15) / 16 * 16;
-  const size_t sm = tile + (size_t)x.g.n_sims * (4 * sizeof(double) + 3);
+  const size_t sm = tile + (size_t)x.g.n_sims * (3 * sizeof(double) + 3);
   auto kern = k_pcg<B, KS, NT, TV, TX>;
   {
     const cudaError_t e = allow_dynamic_smem(kern, sm);

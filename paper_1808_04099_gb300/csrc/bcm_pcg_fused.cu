@@ -40,6 +40,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "bcm_bulk.cuh"
 #include "bcm_cube.cuh"
 #include "bcm_internal.cuh"
 #include "bcm_kernels.h"
@@ -89,54 +90,6 @@ struct FSim {
 // and the kernels' static shared memory fit one block per SM (227 KB)
 static_assert((sizeof(FShared) + 15) / 16 * 16 + sizeof(FSim) * kMaxFusedSims + 256 <= 232448,
               "fused PCG shared memory exceeds the per-block limit");
-
-__device__ __forceinline__ uint32_t s_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(s_addr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for phase `parity` of the barrier to complete, at most limit_ns.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity,
-                                          unsigned long long limit_ns) {
-  if (mbar_test(b, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_test(b, parity))
-    if (global_ns() - t0 > limit_ns) return false;
-  return true;
-}
-// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from this GPU's
-// global memory into this block's shared memory, completing on barrier b.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         unsigned long long* b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          s_addr(dst)),
-      "l"(src), "r"(bytes), "r"(s_addr(b))
-      : "memory");
-}
-__device__ __forceinline__ void fence_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 __device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4s(float* p, float a, float b, float c, float d) {

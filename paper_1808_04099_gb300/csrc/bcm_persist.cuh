@@ -77,6 +77,21 @@ __device__ __forceinline__ double slot_sum(SimState& st, int idx) {
   return s;
 }
 
+// The sums of two striped accumulators of one sim, read by one warp in one round trip:
+// lanes 0 .. kStripes-1 load the stripes of idx_a, the next kStripes lanes those of
+// idx_b; every lane gets both sums (a fixed summation order, the same in every block).
+__device__ __forceinline__ void warp_slot_sums(SimState& st, int idx_a, int idx_b, double& a,
+                                               double& b) {
+  static_assert(2 * kStripes <= 32, "one warp reads both accumulators' stripes");
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  if (lane < 2 * kStripes) v = ld_acc(&st.acc[lane % kStripes][lane < kStripes ? idx_a : idx_b]);
+#pragma unroll
+  for (int o = 1; o < kStripes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  a = __shfl_sync(0xffffffffu, v, 0);
+  b = __shfl_sync(0xffffffffu, v, kStripes);
+}
+
 // Dynamic shared memory beyond the default limit (48 KB minus the kernel's static
 // shared memory) needs the kernel's opt-in.
 template <class K>
