@@ -181,7 +181,11 @@ bcm_status bcm_step(bcm_grid *grid, int n_steps, double rtol, int max_iter, bcm_
  * captured step uses the persistent PCG (grids of at most 256 sims) and, in mixed
  * mode, a fixed budget of ceil(log rtol / log inner_rtol) + 4 defect-correction
  * cycles per solve (at most max_cycles; cycles after a sim has converged return at
- * once; a sim needing more is reported not converged). */
+ * once; a sim needing more is reported not converged).  With the multigrid
+ * preconditioner the PCG iterations and the defect-correction cycles run as
+ * conditional while nodes whose conditions the V-cycle's decisions and the FP64
+ * residual set on the device (bounded by max_iter and max_cycles); the launch count
+ * of bcm_profile_read includes the launches inside those loops. */
 bcm_status bcm_step_graph(bcm_grid *grid, int n_steps, double rtol, int max_iter,
                           bcm_stats *stats);
 
@@ -232,9 +236,11 @@ bcm_status bcm_set_launch(bcm_grid *grid, int persistent, int slabs_a, int slabs
  * coarsened 2:1 down to one cell, then the cubes of each sim are aggregated 2x2x2 up
  * to one node; piecewise-constant transfers, Galerkin coarse operators, one damped
  * Jacobi sweep (omega = 0.8) before and after each coarse correction, four on the top
- * level.  Single-level grids only (BCM_E_INVALID otherwise).  With multigrid the solve
- * runs two launches per iteration plus the V-cycle (no persistent form, no graph
- * steps); results agree with the Jacobi solve to the solver tolerance. */
+ * level; on a two-level grid the refined cubes of each level-0 position are aggregated
+ * first (the per-cube levels keep the 2:1 flux form).  With multigrid the solve
+ * runs two launches per iteration plus the V-cycle (no persistent form); in graph
+ * steps its iteration and defect-correction loops are conditional graph nodes.  Results
+ * agree with the Jacobi solve to the solver tolerance. */
 enum { BCM_PRECOND_JACOBI = 0, BCM_PRECOND_MULTIGRID = 1 };
 bcm_status bcm_set_preconditioner(bcm_grid *grid, int kind);
 
@@ -276,7 +282,7 @@ bcm_status bcm_solve_pressure_static(bcm_grid *grid, const double *dev_b, double
 bcm_status bcm_apply_poisson(bcm_grid *grid, const double *dev_x, double *dev_y);
 
 /* z = M^-1 r, one multigrid V-cycle (the preconditioner of BCM_PRECOND_MULTIGRID), on
- * FP64 single-level grids: a test path.  It uses the grid's PCG residual buffer as
+ * FP64 grids: a test path.  It uses the grid's PCG residual buffer as
  * scratch, so call it between solves.  BCM_E_INVALID for other grids. */
 bcm_status bcm_apply_preconditioner(bcm_grid *grid, const double *dev_r, double *dev_z);
 

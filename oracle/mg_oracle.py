@@ -7,14 +7,16 @@ every step below is written from its definition with numpy / scipy.
 
 The method's pressure solve (section "Numerical algorithm", Eq. poisson) is a Krylov
 solve of K p = -V b; the paper solves it with a geometric multigrid on its cubes.
-Here the multigrid is the preconditioner of that CG, on single-level grids:
+Here the multigrid is the preconditioner of that CG, on grids of one or two levels:
 
   levels    per-cube levels l = 0 .. L (L = log2 B): level l has (B / 2^l)^3 cells per
             cube, cell (c, i, j, k) of level l+1 covering cells (c, 2i..2i+1, 2j..2j+1,
-            2k..2k+1) of level l; then cube-aggregate levels L + m, m = 1 .. M: the
-            cubes of one sim whose cube coordinates shifted right by m agree form one
-            node (level L itself has one cell per cube).  M = max(1, ceil(log2 E)),
-            E the largest extent of a sim in cubes, so every sim ends in one node.
+            2k..2k+1) of level l; then cube-aggregate levels (level L itself has one
+            cell per cube): on a two-level grid first the eight refined cubes of each
+            level-0 position join into one node (the other cubes stay as they are),
+            then nodes of one sim whose level-0 cube coordinates shifted right by m
+            agree form one node, m = 1 .. M, M = max(1, ceil(log2 E)), E the largest
+            extent of a sim in level-0 cubes, so every sim ends in one node.
   transfer  P_l: level l+1 -> level l, piecewise constant (each fine unknown takes the
             value of the coarse unknown covering it); restriction P_l^T (sums).
   operators K_0 = K, K_{l+1} = P_l^T K_l P_l (Galerkin).
@@ -66,8 +68,8 @@ def operator_matrix(oracle):
 def parent_maps(spec) -> List[np.ndarray]:
     """parents[l][u] = the level-(l+1) unknown covering level-l unknown u, for every
     level below the top (per-cube levels, then cube aggregates)."""
-    if spec.max_level != 0:
-        raise ValueError("the multigrid preconditioner is defined on single-level grids")
+    if spec.max_level > 1:
+        raise ValueError("the multigrid preconditioner is defined on grids of one or two levels")
     B = spec.B
     L = int(round(math.log2(B)))
     nc = spec.n_cubes
@@ -83,9 +85,12 @@ def parent_maps(spec) -> List[np.ndarray]:
                         par[(c * bl + k) * bl * bl + j * bl + i] = \
                             ((c * bc + k // 2) * bc + j // 2) * bc + i // 2
         maps.append(par)
-    # cube aggregates
+    # cube aggregates.  cube_ijk are corner coordinates in cells of the finest level, so
+    # a cube of level lv spans B 2^(max_level - lv) of them per edge
     sim_of = spec.sim_of_cube()
-    coords = np.asarray(spec.cube_ijk, np.int64).reshape(-1, 3) // B
+    lvl = np.asarray(spec.cube_level, np.int64) if spec.max_level else np.zeros(nc, np.int64)
+    corner = np.asarray(spec.cube_ijk, np.int64).reshape(-1, 3)
+    coords = corner // (B << spec.max_level)  # the level-0 cube position of every cube
     ext = 1
     for s in range(spec.n_sims):
         a, b = spec.sim_cube_offset[s], spec.sim_cube_offset[s + 1]
@@ -94,6 +99,16 @@ def parent_maps(spec) -> List[np.ndarray]:
     M = max(1, int(math.ceil(math.log2(ext))) if ext > 1 else 1)
     keys = [(int(sim_of[c]),) + tuple(coords[c]) for c in range(nc)]
     node_of = np.arange(nc)
+    if spec.max_level:  # the refined cubes of each level-0 position become one node
+        newkeys = {}
+        par = np.empty(nc, np.int64)
+        for c in range(nc):
+            key = keys[c] if lvl[c] else keys[c] + (int(c),)
+            if key not in newkeys:
+                newkeys[key] = len(newkeys)
+            par[c] = newkeys[key]
+        maps.append(par)
+        node_of = par[node_of]
     for m in range(1, M + 1):
         newkeys = {}
         level_keys = {}

@@ -267,11 +267,11 @@ class Grid:
                 "barrier_timeout_s": bt.value, "recycle": rc.value}
 
     def set_preconditioner(self, kind: int):
-        """PRECOND_JACOBI (default) or PRECOND_MULTIGRID (single-level grids)."""
+        """PRECOND_JACOBI (default) or PRECOND_MULTIGRID."""
         _check(lib().bcm_set_preconditioner(self._h, int(kind)))
 
     def apply_preconditioner(self, r):
-        """z = M^-1 r by one multigrid V-cycle (FP64 single-level grids; test path)."""
+        """z = M^-1 r by one multigrid V-cycle (FP64 grids; test path)."""
         import torch
         r = torch.as_tensor(r).to(self.device, torch.float64).contiguous()
         z = torch.empty_like(r)

@@ -81,8 +81,8 @@ struct HostTables {
 
 int face_axis(int f) { return f >> 1; }
 
-// Multigrid hierarchy of a single-level grid (see bcm_mg.cu): per-cube level sizes and
-// the cube-aggregate levels as CSR tables (Galerkin sums of the cube graph).
+// Multigrid hierarchy of a grid of one or two levels (see bcm_mg.cu): per-cube level
+// sizes and the cube-aggregate levels as CSR tables (Galerkin sums of the cube graph).
 struct MgAgg {
   int n = 0;                          // nodes
   std::vector<int> row, col, cptr, cidx, parent;
@@ -275,7 +275,8 @@ bcm_status build_tables(const bcm_grid_desc* d, HostTables& T) {
       const double h = p.h0 / double(1 << l);
       for (int w = 0; w < kW3; ++w) p.invdiag[l][w] = w > 0 ? 3.0 / (h * w) : 0.0;
     }
-    for (int w = 0; w < kW3; ++w) p.invdiag32[w] = (float)p.invdiag[0][w];
+    for (int l = 0; l < 2; ++l)
+      for (int w = 0; w < kW3; ++w) p.invdiag32[l][w] = (float)p.invdiag[l][w];
     p.h032 = (float)p.h0;
   }
   return BCM_OK;
@@ -287,16 +288,19 @@ bcm_status build_tables(const bcm_grid_desc* d, HostTables& T) {
 // faces add 2 B^2 h to the diagonal.
 MgHost mg_build(const bcm_grid_desc* d, const HostTables& T) {
   MgHost m;
-  if (d->max_level != 0) return m;
-  const int B = d->cells_per_edge, nc = d->n_cubes;
+  const int B = d->cells_per_edge, nc = d->n_cubes, ML = d->max_level;
   while ((1 << m.L) < B) ++m.L;
   for (int l = 0; l <= m.L; ++l) m.n.push_back((size_t)nc * (B >> l) * (B >> l) * (B >> l));
+  // a cube's coordinates in cubes of its own level (corner units: finest cells)
+  auto cube_coord = [&](int c, int e) {
+    return d->cube_ijk[3 * c + e] / (B << (ML - d->cube_level[c]));
+  };
   int ext = 1;
   for (int s = 0; s < d->n_sims; ++s) {
     int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
     for (int c = d->sim_cube_offset[s]; c < d->sim_cube_offset[s + 1]; ++c)
       for (int e = 0; e < 3; ++e) {
-        const int x = d->cube_ijk[3 * c + e] / B;
+        const int x = cube_coord(c, e) >> d->cube_level[c];  // level-0 cube units
         lo[e] = lo[e] < x ? lo[e] : x;
         hi[e] = hi[e] > x ? hi[e] : x;
       }
@@ -304,32 +308,51 @@ MgHost mg_build(const bcm_grid_desc* d, const HostTables& T) {
   }
   int M = 1;
   while ((1 << M) < ext) ++M;
+  M += ML;  // first the refined cubes join their level-0 parents, one level per step
   if (M > kMgMaxM) return m;
-  // level "k = -1": the cube graph
-  std::vector<std::array<int, 4>> key(nc);
+  // level "k = -1": the cube graph.  Key: sim, level, cube coordinates at that level.
+  // A face of a cube of level l carries B^2 faces of coefficient h_l; a 2:1 face links
+  // a fine cube and its coarse neighbour with B^2 fine faces of coefficient h_f / 1.5
+  // (R7), entered once from each side.
+  std::vector<std::array<int, 5>> key(nc);
   std::vector<std::map<int, double>> edges(nc);
   std::vector<double> bnd(nc, 0.0);
   for (int c = 0; c < nc; ++c) {
-    const int s = T.sim[c];
-    const double a = double(B) * B * d->sim_h0[s];
-    key[c] = {s, d->cube_ijk[3 * c] / B, d->cube_ijk[3 * c + 1] / B, d->cube_ijk[3 * c + 2] / B};
+    const int s = T.sim[c], lv = d->cube_level[c];
+    const double h = d->sim_h0[s] / double(1 << lv);
+    const double a = double(B) * B * h;
+    key[c] = {s, lv, cube_coord(c, 0), cube_coord(c, 1), cube_coord(c, 2)};
     for (int f = 0; f < 6; ++f) {
       const int nb = T.nb[6 * c + f];
       if (nb >= 0) {
         if (nb != c) edges[c][nb] += a;
-      } else if (nb == NB_BOUNDARY && d->sim_bc[6 * s + f] == BC_OUTFLOW) {
-        bnd[c] += 2.0 * a;
+      } else if (nb == NB_BOUNDARY) {
+        if (d->sim_bc[6 * s + f] == BC_OUTFLOW) bnd[c] += 2.0 * a;
+      } else if (nb == NB_COARSE) {  // this cube is the fine side
+        edges[c][T.aux[(6 * c + f) * 4]] += a / 1.5;
+      } else {  // NB_FINE: four fine cubes of half the cell size
+        for (int q = 0; q < 4; ++q) edges[c][T.aux[(6 * c + f) * 4 + q]] += 0.5 * a / 1.5;
       }
     }
   }
   for (int k = 0; k < M; ++k) {
     MgAgg g;
-    std::map<std::array<int, 4>, int> ids;
+    std::map<std::array<int, 5>, int> ids;
     const int np = (int)key.size();
     g.parent.resize(np);
-    std::vector<std::array<int, 4>> nkey;
+    std::vector<std::array<int, 5>> nkey;
+    int top_level = 0;
+    for (int u = 0; u < np; ++u) top_level = top_level > key[u][1] ? top_level : key[u][1];
     for (int u = 0; u < np; ++u) {
-      const std::array<int, 4> kk = {key[u][0], key[u][1] >> 1, key[u][2] >> 1, key[u][3] >> 1};
+      // refined cubes of the finest level remaining join their parents; once every node
+      // is of level 0, nodes join 2x2x2
+      std::array<int, 5> kk = key[u];
+      if (top_level == 0 || kk[1] == top_level) {
+        kk[1] = kk[1] > 0 ? kk[1] - 1 : 0;
+        kk[2] >>= 1;
+        kk[3] >>= 1;
+        kk[4] >>= 1;
+      }
       auto it = ids.find(kk);
       int id;
       if (it == ids.end()) {
@@ -449,7 +472,7 @@ Layout plan(const bcm_grid_desc* d, int n_slots, const MgHost& mg, MgLayout* ml)
   L.guard = take(64);
   L.bar = take(sizeof(unsigned int) * (kTicketWords + 32));
   L.err = take(64);
-  if (mg.ok && ml) {  // multigrid preconditioner (single-level grids)
+  if (mg.ok && ml) {  // multigrid preconditioner
     for (int l = 0; l <= mg.L; ++l) {
       ml->x[l] = take(mg.n[l] * V);
       ml->y[l] = take(mg.n[l] * V);
@@ -492,6 +515,10 @@ struct StepGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture_stream = nullptr;
+  cudaStream_t body_stream[2] = {nullptr, nullptr};  // capture of conditional bodies
+  int mg = 0;                  // multigrid PCG: conditional loops in the step
+  size_t body_kernels[2] = {0, 0};  // kernel nodes of the inner and the outer loop body
+  unsigned int counted[2] = {0, 0};  // body executions already in the launch count
   double rtol = 0.0;
   int max_iter = 0, cycles = 0;
   int slabs_p = 0, single_pass = 0, resident = 0, fused = 0;  // the PCG launch shape captured
@@ -524,7 +551,7 @@ struct bcm_grid {
   double barrier_timeout_s = 2.0;  // persistent PCG: longest grid-barrier wait
   int recycle = 1;           // mixed + persistent: reliable updates instead of restarts
   int pcg_form = 0;          // PCG form of the last solve (PCG_*)
-  int mg_ok = 0;             // the grid has a multigrid hierarchy (single-level)
+  int mg_ok = 0;             // the grid has a multigrid hierarchy
   int gen = 0;               // bumped when the kernels of a step change (geometry,
                              // particles, momentum scheme): captured steps are redone
   KernelTimer timer;
@@ -780,6 +807,8 @@ extern "C" bcm_status bcm_destroy_grid(bcm_grid* g) {
     if (g->sg.exec) cudaGraphExecDestroy(g->sg.exec);
     if (g->sg.graph) cudaGraphDestroy(g->sg.graph);
     if (g->sg.capture_stream) cudaStreamDestroy(g->sg.capture_stream);
+    for (cudaStream_t bs : g->sg.body_stream)
+      if (bs) cudaStreamDestroy(bs);
     if (g->mgg.exec) cudaGraphExecDestroy(g->mgg.exec);
     if (g->mgg.graph) cudaGraphDestroy(g->mgg.graph);
     if (g->mgg.capture_stream) cudaStreamDestroy(g->mgg.capture_stream);
@@ -1059,9 +1088,25 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
   return BCM_OK;
 }
 
+// Launches inside the conditional loops of captured multigrid steps: the kernel nodes
+// of each loop body times the body executions the device counted since the last call.
+bcm_status graph_body_launches(bcm_grid* g) {
+  StepGraph& sg = g->sg;
+  if (!sg.body_kernels[0] && !sg.body_kernels[1]) return BCM_OK;
+  unsigned int n[2] = {0u, 0u};
+  CUDA_TRY(cudaMemcpyAsync(n, g->ctx.f.guard + 4, sizeof n, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  for (int q = 0; q < 2; ++q) {
+    g->launch_count += (long long)sg.body_kernels[q] * (long long)(n[q] - sg.counted[q]);
+    sg.counted[q] = n[q];
+  }
+  return BCM_OK;
+}
+
 bcm_status collect(bcm_grid* g, bcm_stats* out) {
   bcm_status est = read_err(g);
   if (est != BCM_OK) return est;
+  if ((est = graph_body_launches(g)) != BCM_OK) return est;
   if (g->ctx.part.n > 0) {
     int perr = 0;
     CUDA_TRY(cudaMemcpyAsync(&perr, g->ctx.part.err, sizeof(int), cudaMemcpyDeviceToHost,
@@ -1165,6 +1210,124 @@ extern "C" bcm_status bcm_step(bcm_grid* g, int n_steps, double rtol, int max_it
   return last;
 }
 
+// Kernel nodes of a graph (its own nodes; a conditional node's body is not counted).
+cudaError_t count_kernels(cudaGraph_t graph, size_t* out) {
+  size_t nn = 0;
+  cudaError_t e = cudaGraphGetNodes(graph, nullptr, &nn);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && (e = cudaGraphGetNodes(graph, nodes.data(), &nn)) != cudaSuccess) return e;
+  *out = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if ((e = cudaGraphNodeGetType(nd, &t)) != cudaSuccess) return e;
+    if (t == cudaGraphNodeTypeKernel) ++*out;
+  }
+  return cudaSuccess;
+}
+
+// A condition handle on the graph stream s is capturing into (value 1 at every launch
+// of the graph).
+cudaError_t capture_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(h, graph, 1u, cudaGraphCondAssignDefault);
+}
+
+// Appends a while node of handle h after the work captured on s so far and begins the
+// capture of its body on stream bs (ended by the caller).
+cudaError_t capture_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaStream_t bs) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, graph, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return e;
+  return cudaStreamBeginCaptureToGraph(bs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal);
+}
+
+// The multigrid PCG of a captured step, with the loops the eager solve runs on the host
+// as conditional while nodes.  Inner loop (one PCG iteration: pass A, then the V-cycle
+// with pass B inside), run while the V-cycle's decisions leave a sim running or until
+// the guard of max_iter x (max_cycles + 1) body executions; mixed mode wraps it in the
+// defect-correction loop (V-cycle z = M^-1 r of the new residual, the inner loop, x +=
+// e, the FP64 residual), run while the residual leaves a sim correcting.
+bcm_status capture_mg_solve(bcm_grid* g, const Ctx& x0, SolveParams prm) {
+  StepGraph& sg = g->sg;
+  for (cudaStream_t& bs : sg.body_stream)
+    if (!bs) CUDA_TRY(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  prm.mg = 1;
+  prm.recycle = 0;
+  prm.max_cycles = g->max_cycles;  // the loop ends when the residual says so
+  prm.body_count = x0.f.guard + 4;
+  prm.guard_limit = prm.max_iter * (prm.max_cycles + 1) + 1;
+  CUDA_TRY(cudaMemsetAsync(x0.f.guard, 0, sizeof(unsigned int), x0.stream));  // per step
+  Ctx xi = x0;
+  auto inner_body = [&](cudaStream_t outer, const SolveParams& pin) -> bcm_status {
+    cudaGraphConditionalHandle hin = (cudaGraphConditionalHandle)pin.cond_inner;
+    xi.stream = sg.body_stream[1];
+    CUDA_TRY(capture_while(outer, hin, xi.stream));
+    cudaError_t e = launch_cg_a(xi, pin);
+    if (e == cudaSuccess) e = launch_mg_vcycle(xi, pin, 1);  // pass B inside
+    cudaGraph_t body = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(xi.stream, &body);
+    CUDA_TRY(e);
+    CUDA_TRY(e2);
+    CUDA_TRY(count_kernels(body, &sg.body_kernels[0]));
+    return BCM_OK;
+  };
+  SolveParams pres = prm;  // the residual kernel sets no loop condition of the inner loop
+  pres.cond_inner = 0;
+  if (g->solve64) {
+    cudaGraphConditionalHandle hin;
+    CUDA_TRY(capture_handle(x0.stream, &hin));
+    SolveParams pin = prm;
+    pin.cond_inner = (unsigned long long)hin;
+    CUDA_TRY(launch_residual(x0, pres));
+    CUDA_TRY(launch_mg_vcycle(x0, pin, 0));
+    sg.body_kernels[1] = 0;
+    return inner_body(x0.stream, pin);
+  }
+  cudaGraphConditionalHandle hout;
+  CUDA_TRY(capture_handle(x0.stream, &hout));
+  pres.cond_outer = (unsigned long long)hout;
+  CUDA_TRY(launch_residual(x0, pres));
+  Ctx xo = x0;
+  xo.stream = sg.body_stream[0];
+  CUDA_TRY(capture_while(x0.stream, hout, xo.stream));
+  bcm_status st = BCM_OK;
+  cudaGraphConditionalHandle hin;
+  cudaError_t e = capture_handle(xo.stream, &hin);
+  SolveParams pin = prm;
+  pin.cond_inner = (unsigned long long)hin;
+  pin.cond_outer = 0;
+  if (e == cudaSuccess) e = launch_mg_vcycle(xo, pin, 0);
+  if (e == cudaSuccess) st = inner_body(xo.stream, pin);
+  if (e == cudaSuccess && st == BCM_OK) e = launch_add_correction(xo);
+  if (e == cudaSuccess && st == BCM_OK) e = launch_residual(xo, pres);
+  cudaGraph_t body = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(xo.stream, &body);
+  if (st != BCM_OK) return st;
+  CUDA_TRY(e);
+  CUDA_TRY(e2);
+  CUDA_TRY(count_kernels(body, &sg.body_kernels[1]));
+  return BCM_OK;
+}
+
 // One step as a CUDA graph: no host synchronisation inside.  The PCG is the
 // persistent kernel (one launch per solve); mixed mode issues a fixed budget of
 // defect-correction cycles whose kernels return at once for sims already converged.
@@ -1196,10 +1359,15 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
   if (particles) CUDA_TRY(launch_ib_force(x));
   CUDA_TRY(launch_rhs(x));
   CUDA_TRY(launch_solve_begin(x));
-  CUDA_TRY(launch_residual(x, prm));
-  if (g->solve64) {
+  if (x.use_mg) {
+    const bcm_status st = capture_mg_solve(g, x, prm);
+    if (st != BCM_OK) return st;
+    g->pcg_form = PCG_MULTIGRID;
+  } else if (g->solve64) {
+    CUDA_TRY(launch_residual(x, prm));
     CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
   } else {
+    CUDA_TRY(launch_residual(x, prm));
     for (int c = 0; c < cycles; ++c) {
       CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
       CUDA_TRY(launch_add_correction(x));
@@ -1220,8 +1388,6 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     return fail(BCM_E_INVALID, "need n_steps >= 0, rtol > 0, max_iter >= 1");
   if (g->desc.n_sims > 256)
     return fail(BCM_E_BOUNDS, "graph steps use the persistent PCG: at most 256 sims per grid");
-  if (g->ctx.use_mg)
-    return fail(BCM_E_INVALID, "graph steps use the persistent Jacobi PCG, not multigrid");
   StepGraph& sg = g->sg;
   int cycles = 0;
   if (!g->solve64) {  // enough cycles for rtol at the inner reduction per cycle, plus margin
@@ -1234,7 +1400,11 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
   if (!sg.exec || sg.rtol != rtol || sg.max_iter != max_iter || sg.cycles != cycles ||
       sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle ||
       sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass ||
-      sg.resident != g->ctx.resident || sg.fused != g->ctx.fused || sg.gen != g->gen) {
+      sg.resident != g->ctx.resident || sg.fused != g->ctx.fused || sg.gen != g->gen ||
+      sg.mg != g->ctx.use_mg || (sg.mg && sg.cycles != g->max_cycles)) {
+    bcm_status bst = graph_body_launches(g);  // the old loops' launches so far
+    if (bst != BCM_OK) return bst;
+    sg.body_kernels[0] = sg.body_kernels[1] = 0;
     if (sg.exec) CUDA_TRY(cudaGraphExecDestroy(sg.exec));
     if (sg.graph) CUDA_TRY(cudaGraphDestroy(sg.graph));
     sg.exec = nullptr;
@@ -1272,6 +1442,8 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     sg.resident = g->ctx.resident;
     sg.fused = g->ctx.fused;
     sg.gen = g->gen;
+    sg.mg = g->ctx.use_mg;
+    if (sg.mg) sg.cycles = g->max_cycles;
   }
   NvtxRange r("bcm_step_graph");
   for (int n = 0; n < n_steps; ++n) {
@@ -1295,6 +1467,7 @@ extern "C" bcm_status bcm_profile_read(bcm_grid* g, double* total_ms, int64_t* l
   if (!g) return fail(BCM_E_INVALID, "grid is NULL");
   bcm_status st = drain_timer(g);
   if (st != BCM_OK) return st;
+  if ((st = graph_body_launches(g)) != BCM_OK) return st;
   for (int k = 0; k < BCM_NKERNELS; ++k) {
     if (total_ms) total_ms[k] = g->timer.total_ms[k];
     if (launches) launches[k] = g->timer.launches[k];
@@ -1687,7 +1860,7 @@ extern "C" bcm_status bcm_set_preconditioner(bcm_grid* g, int kind) {
   if (kind != BCM_PRECOND_JACOBI && kind != BCM_PRECOND_MULTIGRID)
     return fail(BCM_E_INVALID, "unknown preconditioner %d", kind);
   if (kind == BCM_PRECOND_MULTIGRID && !g->mg_ok)
-    return fail(BCM_E_INVALID, "the multigrid preconditioner needs a single-level grid");
+    return fail(BCM_E_INVALID, "no multigrid hierarchy for this grid (too many aggregate levels)");
   g->ctx.use_mg = kind == BCM_PRECOND_MULTIGRID ? 1 : 0;
   return BCM_OK;
 }
@@ -1695,7 +1868,7 @@ extern "C" bcm_status bcm_set_preconditioner(bcm_grid* g, int kind) {
 extern "C" bcm_status bcm_apply_preconditioner(bcm_grid* g, const double* r, double* z) {
   if (!g || !r || !z) return fail(BCM_E_INVALID, "NULL argument");
   if (!g->solve64 || !g->mg_ok)
-    return fail(BCM_E_INVALID, "the preconditioner test path needs an FP64 single-level grid");
+    return fail(BCM_E_INVALID, "the preconditioner test path needs an FP64 grid with a multigrid hierarchy");
   const Ctx& x = g->ctx;
   const size_t bytes = g->n_cells * sizeof(double);
   CUDA_TRY(cudaMemcpyAsync(x.f.r, r, bytes, cudaMemcpyDeviceToDevice, g->stream));

@@ -92,14 +92,15 @@ __device__ __forceinline__ TV inv_diag_any(const DevGrid& g, int cube, int cell)
 
 // Poisson ghost across a 2:1 face f of cube c at tangential (a, b) (R7): the coarse
 // cell across the face (fine side), or the mean of the four fine cells that touch
-// the coarse face cell (coarse side).  valg(cube, cell) is the field value.
+// the coarse face cell (coarse side).  valg(cube, cell) is the field value.  On the
+// multigrid's per-cube level lsh the cells span 2^lsh level-0 cells (B per edge).
 template <int B, class TV, class ValG>
 __device__ __forceinline__ TV poisson_ghost_21(const DevGrid& g, int c, int f, int a, int b,
-                                               int code, const ValG& valg) {
+                                               int code, const ValG& valg, int lsh = 0) {
   const int d = f >> 1, side = f & 1;
   if (code == NB_COARSE) {
     const int C = g.aux[(6 * c + f) * 4];
-    const int sf = 1 << (g.max_level - g.lvl[c]), sc = 2 * sf;
+    const int sf = (1 << (g.max_level - g.lvl[c])) << lsh, sc = 2 * sf;
     const int A = (g.ijk[3 * c + tan1(d)] + a * sf - g.ijk[3 * C + tan1(d)]) / sc;
     const int Bb = (g.ijk[3 * c + tan2(d)] + b * sf - g.ijk[3 * C + tan2(d)]) / sc;
     return valg(C, cell_of<B>(d, side ? 0 : B - 1, A, Bb));
@@ -188,7 +189,7 @@ template <int B, int KS, int NT, class TV, class Val4, class Val1, class ValG>
 __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const CubeSh<TV>& cs,
                                                     const DevGrid& g, int c, int z0,
                                                     const Val4& val4, const Val1& val1,
-                                                    const ValG& valg) {
+                                                    const ValG& valg, int lsh = 0) {
   using SL = Slab<B, KS>;
   constexpr int BB = B * B, Q = BB / 4;
   for (int idx = threadIdx.x; idx < (KS + 2) * Q; idx += NT) {
@@ -205,7 +206,8 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
         val4(n, (k < 0 ? B - 1 : 0) * BB + 4 * q, f, v);
       } else if (n < NB_BOUNDARY) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) v[m] = poisson_ghost_21<B, TV>(g, c, f, i0 + m, j, n, valg);
+        for (int m = 0; m < 4; ++m)
+          v[m] = poisson_ghost_21<B, TV>(g, c, f, i0 + m, j, n, valg, lsh);
       } else {
         have = false;
       }
@@ -226,7 +228,7 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
       const TV v = val1(f, n, cell_of<B>(f >> 1, (f & 1) ? 0 : B - 1, t, z0 + kk));
       S[f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1)] = v;
     } else if (n < NB_BOUNDARY) {
-      const TV v = poisson_ghost_21<B, TV>(g, c, f, t, z0 + kk, n, valg);
+      const TV v = poisson_ghost_21<B, TV>(g, c, f, t, z0 + kk, n, valg, lsh);
       S[f < 2 ? SL::at(f == 0 ? -1 : B, t, kk + 1) : SL::at(t, f == 2 ? -1 : B, kk + 1)] = v;
     }
   }

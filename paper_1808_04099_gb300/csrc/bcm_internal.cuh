@@ -34,7 +34,7 @@ struct SimParams {
   double modes[kModes];
   double L[3];        // domain lengths
   double invdiag[2][kW3];  // 1 / diag(K) per level and face-weight sum (thirds)
-  float invdiag32[kW3];    // FP32 copy of invdiag[0] (multigrid levels in FP32)
+  float invdiag32[2][kW3]; // FP32 copy of invdiag (multigrid levels in FP32)
   float h032;              // FP32 copy of h0
   bcm_body bodies[kMaxBodies];
   int n_bodies, has_modes, moving, all_neumann;

@@ -56,6 +56,9 @@ struct SolveParams {
   unsigned long long barrier_timeout_ns;  // persistent PCG: longest wait at a grid barrier
   int recycle;            // mixed + persistent: keep the search direction across cycles
   int pad2;
+  // multigrid PCG inside a captured step: body executions of the inner and the outer
+  // loop, counted on the device for the launch count ([0], [1]; cumulative)
+  unsigned int* body_count;
 };
 
 // Geometric multigrid preconditioner (single-level grids): per-cube levels

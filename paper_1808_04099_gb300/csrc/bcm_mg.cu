@@ -1,15 +1,19 @@
 // bcm_mg.cu -- geometric multigrid V-cycle, the preconditioner M^-1 of the pressure PCG
 // (Eq. poisson; the paper solves the pressure equation with a multigrid on its cubes).
 //
-// Single-level grids.  Per-cube levels l = 0 .. L coarsen every cube by two per level
-// (B, B/2, ..., 1 cells per edge); a level-l+1 cell covers 2x2x2 cells of level l of the
-// same cube.  Above level L (one cell per cube) the cubes of a sim are aggregated by
-// their cube coordinates shifted right by m (m = 1 .. M).  Transfers are piecewise
-// constant, restriction sums, and the coarse operators are the Galerkin products
-// P^T K P.  For the flux-form K these are again flux-form operators: on per-cube level
-// l a face carries 4^l fine faces, coefficient 4^l h, an outflow face twice that on the
-// diagonal, other domain faces nothing; the aggregate levels keep their Galerkin sums
-// as small CSR tables built on the host.  The smoother is damped Jacobi
+// Grids of one or two levels.  Per-cube levels l = 0 .. L coarsen every cube by two per
+// level (B, B/2, ..., 1 cells per edge); a level-l+1 cell covers 2x2x2 cells of level l
+// of the same cube.  Above level L (one cell per cube) the eight refined cubes of each
+// level-0 position first join into one node, then the nodes of a sim are aggregated by
+// their level-0 cube coordinates shifted right by m (m = 1 .. M).  Transfers are
+// piecewise constant, restriction sums, and the coarse operators are the Galerkin
+// products P^T K P.  For the flux-form K these are again flux-form operators: on
+// per-cube level l a face carries 4^l fine faces, coefficient 4^l h of its cube, an
+// outflow face twice that on the diagonal, other domain faces nothing, and a 2:1 face
+// keeps the form of R7 (a coarse face cell against the four fine cells that touch it,
+// weight 4/3 on the coarse side and 2/3 on the fine side, since the 2x2x2 aggregates on
+// both sides keep the coarse cell / four fine cells pairing); the aggregate levels keep
+// their Galerkin sums as small CSR tables built on the host.  The smoother is damped Jacobi
 // S = omega D^-1 (omega = 0.8), one sweep before and one after the coarse correction,
 // which is scaled by s = 1.75 (piecewise-constant transfers leave it too weak), so the
 // V-cycle is symmetric positive definite and M^-1 suits CG:
@@ -36,47 +40,79 @@ namespace bcm {
 template <int BL>
 __device__ __forceinline__ int lcell(int i, int j, int k) { return (k * BL + j) * BL + i; }
 
-// Cell across direction f (0..5: -x, +x, -y, +y, -z, +z) of cell (i, j, k) of cube c on
-// a level with BL cells per edge.  Returns 1 with (nc, ni, nj, nk) for a cell of this
-// or a same-level neighbouring cube, 0 with the mirror sign of a domain face (+1: the
-// ghost equals the cell, Neumann; -1: minus the cell, p = 0 on an outflow face).
-template <int BL>
-__device__ __forceinline__ int level_nb(const DevGrid& g, int c, int i, int j, int k, int f,
-                                        int& nc, int& ni, int& nj, int& nk, int& sign) {
-  const int d = f >> 1, step = (f & 1) ? 1 : -1;
-  int q[3] = {i, j, k};
-  q[d] += step;
-  if (q[d] >= 0 && q[d] < BL) {
-    nc = c;
-  } else {
-    const int n = g.nb[6 * c + f];
-    if (n < 0) {
-      sign = g.sp[g.sim[c]].bc[f] == BC_OUTFLOW ? -1 : 1;
-      return 0;
-    }
-    nc = n;
-    q[d] = (f & 1) ? 0 : BL - 1;
-  }
-  ni = q[0];
-  nj = q[1];
-  nk = q[2];
-  return 1;
-}
-
 // Per-sim constants of a level in the vector type: the FP32 path does no FP64
 // arithmetic (FP64 runs at a small fraction of the FP32 rate on this GPU).
 template <class TV>
-__device__ __forceinline__ TV sim_inv(const SimParams& sp, int s3);
+__device__ __forceinline__ TV sim_inv(const SimParams& sp, int lvl, int s3);
 template <>
-__device__ __forceinline__ float sim_inv<float>(const SimParams& sp, int s3) { return sp.invdiag32[s3]; }
+__device__ __forceinline__ float sim_inv<float>(const SimParams& sp, int lvl, int s3) {
+  return sp.invdiag32[lvl][s3];
+}
 template <>
-__device__ __forceinline__ double sim_inv<double>(const SimParams& sp, int s3) { return sp.invdiag[0][s3]; }
+__device__ __forceinline__ double sim_inv<double>(const SimParams& sp, int lvl, int s3) {
+  return sp.invdiag[lvl][s3];
+}
 template <class TV>
 __device__ __forceinline__ TV sim_h(const SimParams& sp);
 template <>
 __device__ __forceinline__ float sim_h<float>(const SimParams& sp) { return sp.h032; }
 template <>
 __device__ __forceinline__ double sim_h<double>(const SimParams& sp) { return sp.h0; }
+// cell size of cube c (its refinement level halves the sim's level-0 size)
+template <class TV>
+__device__ __forceinline__ TV cube_h(const DevGrid& g, const SimParams& sp, int c) {
+  return g.lvl[c] ? TV(0.5) * sim_h<TV>(sp) : sim_h<TV>(sp);
+}
+
+// The value across face f of cell (i, j, k) of cube c on per-cube level l (BL cells per
+// edge) and the weight w of that face in the level's flux-form operator, whose
+// coefficient 4^l h the caller carries (R7 on the coarser cells; the Galerkin product of
+// the finer level keeps that form): a cell of this cube or of a same-level neighbour
+// (w = 1), a domain ghost (w = 1; the cell itself, or minus it at an outflow face), the
+// coarse cell across a 2:1 face (w = 2/3), or the mean of the four fine cells across it
+// (w = 4/3).  val(cube, i, j, k) is a cell's value, xc this cell's.
+template <int BL, class TV, class Val>
+__device__ __forceinline__ TV mg_across(const DevGrid& g, int c, int l, int i, int j, int k,
+                                        int f, TV xc, const Val& val, TV& w) {
+  const int d = f >> 1, side = f & 1;
+  int q[3] = {i, j, k};
+  q[d] += side ? 1 : -1;
+  w = TV(1);
+  if (q[d] >= 0 && q[d] < BL) return val(c, q[0], q[1], q[2]);
+  const int n = g.nb[6 * c + f];
+  if (n >= 0) {
+    q[d] = side ? 0 : BL - 1;
+    return val(n, q[0], q[1], q[2]);
+  }
+  if (n == NB_BOUNDARY) return g.sp[g.sim[c]].bc[f] == BC_OUTFLOW ? -xc : xc;
+  const int t1 = tan1(d), t2 = tan2(d);
+  const int a = t1 == 0 ? i : (t1 == 1 ? j : k), b = t2 == 0 ? i : (t2 == 1 ? j : k);
+  int r3[3];
+  r3[d] = side ? 0 : BL - 1;  // the cells across lie on the neighbour's facing layer
+  if (n == NB_COARSE) {
+    w = TV(2.0 / 3.0);
+    const int C = g.aux[(6 * c + f) * 4];
+    // corner coordinates in finest-cell units; a level-l cell spans 2^l level-0 cells
+    const int sf = (1 << (g.max_level - g.lvl[c])) << l;
+    const int sc = (1 << (g.max_level - g.lvl[C])) << l;
+    r3[t1] = (g.ijk[3 * c + t1] + a * sf - g.ijk[3 * C + t1]) / sc;
+    r3[t2] = (g.ijk[3 * c + t2] + b * sf - g.ijk[3 * C + t2]) / sc;
+    return val(C, r3[0], r3[1], r3[2]);
+  }
+  w = TV(4.0 / 3.0);  // NB_FINE: the four fine cells that touch this coarse cell's face
+  TV sum = TV(0);
+#pragma unroll
+  for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+    for (int aa = 0; aa < 2; ++aa) {
+      const int ta = 2 * a + aa, tb = 2 * b + bb, qa = ta / BL, qb = tb / BL;
+      const int F = g.aux[(6 * c + f) * 4 + qb * 2 + qa];
+      r3[t1] = ta - qa * BL;
+      r3[t2] = tb - qb * BL;
+      sum += val(F, r3[0], r3[1], r3[2]);
+    }
+  return TV(0.25) * sum;
+}
 
 // omega / diag(K_l) of cell (i, j, k) of cube c on per-cube level l (BL cells per edge):
 // diag(K_l) = 4^l diag(K) of a fine cell with the same boundary faces; wscale =
@@ -84,14 +120,14 @@ __device__ __forceinline__ double sim_h<double>(const SimParams& sp) { return sp
 template <int BL, class TV>
 __device__ __forceinline__ TV smooth_w(const DevGrid& g, const SimParams& sp, int c, int i, int j,
                                        int k, TV wscale) {
-  return wscale * sim_inv<TV>(sp, s3_of<BL>(g.w3 + 6 * c, i, j, k));
+  return wscale * sim_inv<TV>(sp, g.lvl[c], s3_of<BL>(g.w3 + 6 * c, i, j, k));
 }
 
 // ---- down: x = S r, rr = r - K x, restriction of rr (P^T: sums)
 // One thread per coarse cell (its 2x2x2 fine cells), or per cube on the level with one
 // cell per cube (its residual goes to `rc` per cube for the aggregate levels).
 template <int BL, class TV>
-__device__ __forceinline__ void mg_down_item(const DevGrid& g, TV wscale, TV cscale,
+__device__ __forceinline__ void mg_down_item(const DevGrid& g, int l, TV wscale, TV cscale,
                                              const TV* __restrict__ r, TV* __restrict__ x,
                                              TV* __restrict__ rc, int all, long long t) {
   constexpr int CB = BL > 1 ? BL / 2 : 1, C3 = CB * CB * CB, B3 = BL * BL * BL;
@@ -101,7 +137,11 @@ __device__ __forceinline__ void mg_down_item(const DevGrid& g, TV wscale, TV csc
   if (!all && g.ss[s].done) return;
   const int I = ci % CB, J = (ci / CB) % CB, Kc = ci / (CB * CB);
   const SimParams& sp = g.sp[s];
-  const TV coef = sim_h<TV>(sp) * cscale;  // 4^l h
+  const TV coef = cube_h<TV>(g, sp, c) * cscale;  // 4^l h
+  auto sval = [&](int cube, int ci2, int cj2, int ck2) {
+    return smooth_w<BL, TV>(g, sp, cube, ci2, cj2, ck2, wscale) *
+           r[(size_t)cube * B3 + lcell<BL>(ci2, cj2, ck2)];
+  };
   TV sum = TV(0);
 #pragma unroll
   for (int dk = 0; dk < CH; ++dk)
@@ -116,14 +156,9 @@ __device__ __forceinline__ void mg_down_item(const DevGrid& g, TV wscale, TV csc
         TV acc = TV(0);
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-          int nc, ni, nj, nk, sign = 1;
-          TV xn;
-          if (level_nb<BL>(g, c, i, j, k, f, nc, ni, nj, nk, sign))
-            xn = smooth_w<BL, TV>(g, sp, nc, ni, nj, nk, wscale) *
-                 r[(size_t)nc * B3 + lcell<BL>(ni, nj, nk)];
-          else
-            xn = TV(sign) * xc;
-          acc += xc - xn;
+          TV w;
+          const TV xn = mg_across<BL, TV>(g, c, l, i, j, k, f, xc, sval, w);
+          acc += w * (xc - xn);
         }
         x[gi] = xc;
         sum += rv - coef * acc;
@@ -132,7 +167,7 @@ __device__ __forceinline__ void mg_down_item(const DevGrid& g, TV wscale, TV csc
 }
 
 template <int BL, class TV>
-__global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale,
+__global__ __launch_bounds__(256) void k_mg_down(DevGrid g, int l, TV wscale, TV cscale,
                                                  const TV* __restrict__ r,
                                                  TV* __restrict__ x, TV* __restrict__ rc,
                                                  int all) {
@@ -140,7 +175,7 @@ __global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale
   constexpr int CB = BL > 1 ? BL / 2 : 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)g.n_cubes * CB * CB * CB) return;
-  mg_down_item<BL, TV>(g, wscale, cscale, r, x, rc, all, t);
+  mg_down_item<BL, TV>(g, l, wscale, cscale, r, x, rc, all, t);
 }
 
 // The same with one thread per fine cell (BL >= 2): the eight children of a coarse cell
@@ -148,7 +183,7 @@ __global__ __launch_bounds__(256) void k_mg_down(DevGrid g, TV wscale, TV cscale
 // thread index), so the restriction is a three-step shuffle sum.  Threads of finished
 // sims and of the tail take part in the shuffles with zeros.
 template <int BL, class TV>
-__global__ __launch_bounds__(256) void k_mg_down_cell(DevGrid g, TV wscale, TV cscale,
+__global__ __launch_bounds__(256) void k_mg_down_cell(DevGrid g, int l, TV wscale, TV cscale,
                                                       const TV* __restrict__ r,
                                                       TV* __restrict__ x, TV* __restrict__ rc,
                                                       int all) {
@@ -164,20 +199,20 @@ __global__ __launch_bounds__(256) void k_mg_down_cell(DevGrid g, TV wscale, TV c
     const int I = ci % CB, J = (ci / CB) % CB, Kc = ci / (CB * CB);
     const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * Kc + (d >> 2);
     const SimParams& sp = g.sp[g.sim[c]];
-    const TV coef = sim_h<TV>(sp) * cscale;
+    const TV coef = cube_h<TV>(g, sp, c) * cscale;
     const size_t gi = (size_t)c * B3 + lcell<BL>(i, j, k);
     const TV rv = r[gi];
     const TV xc = smooth_w<BL, TV>(g, sp, c, i, j, k, wscale) * rv;
+    auto sval = [&](int cube, int ci2, int cj2, int ck2) {
+      return smooth_w<BL, TV>(g, sp, cube, ci2, cj2, ck2, wscale) *
+             r[(size_t)cube * B3 + lcell<BL>(ci2, cj2, ck2)];
+    };
     TV acc = TV(0);
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-      int nc, ni, nj, nk, sign = 1;
-      TV xn;
-      if (level_nb<BL>(g, c, i, j, k, f, nc, ni, nj, nk, sign))
-        xn = smooth_w<BL, TV>(g, sp, nc, ni, nj, nk, wscale) * r[(size_t)nc * B3 + lcell<BL>(ni, nj, nk)];
-      else
-        xn = TV(sign) * xc;
-      acc += xc - xn;
+      TV w;
+      const TV xn = mg_across<BL, TV>(g, c, l, i, j, k, f, xc, sval, w);
+      acc += w * (xc - xn);
     }
     x[gi] = xc;
     val = rv - coef * acc;
@@ -207,7 +242,7 @@ __device__ __forceinline__ TV up_value(const TV* __restrict__ x, const TV* __res
 }
 
 template <int BL, class TV>
-__device__ __forceinline__ TV up_cell(const DevGrid& g, TV wscale, TV cscale,
+__device__ __forceinline__ TV up_cell(const DevGrid& g, int l, TV wscale, TV cscale,
                                       const TV* __restrict__ r,
                                       const TV* __restrict__ x, const TV* __restrict__ yc,
                                       const double* __restrict__ yagg,
@@ -215,16 +250,17 @@ __device__ __forceinline__ TV up_cell(const DevGrid& g, TV wscale, TV cscale,
                                       int k, TV* rv_out) {
   constexpr int B3 = BL * BL * BL;
   const SimParams& sp = g.sp[g.sim[c]];
-  const TV coef = sim_h<TV>(sp) * cscale;
+  const TV coef = cube_h<TV>(g, sp, c) * cscale;
   const TV xc = up_value<BL, TV>(x, yc, yagg, agg_parent, c, i, j, k);
+  auto uval = [&](int cube, int ci2, int cj2, int ck2) {
+    return up_value<BL, TV>(x, yc, yagg, agg_parent, cube, ci2, cj2, ck2);
+  };
   TV acc = TV(0);
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
-    int nc, ni, nj, nk, sign = 1;
-    const TV xn = level_nb<BL>(g, c, i, j, k, f, nc, ni, nj, nk, sign)
-                      ? up_value<BL, TV>(x, yc, yagg, agg_parent, nc, ni, nj, nk)
-                      : TV(sign) * xc;
-    acc += xc - xn;
+    TV w;
+    const TV xn = mg_across<BL, TV>(g, c, l, i, j, k, f, xc, uval, w);
+    acc += w * (xc - xn);
   }
   const TV rv = r[(size_t)c * B3 + lcell<BL>(i, j, k)];
   *rv_out = rv;
@@ -232,7 +268,7 @@ __device__ __forceinline__ TV up_cell(const DevGrid& g, TV wscale, TV cscale,
 }
 
 template <int BL, class TV>
-__device__ __forceinline__ void mg_up_item(const DevGrid& g, TV wscale, TV cscale,
+__device__ __forceinline__ void mg_up_item(const DevGrid& g, int l, TV wscale, TV cscale,
                                            const TV* __restrict__ r, const TV* __restrict__ x,
                                            const TV* __restrict__ yc,
                                            const double* __restrict__ yagg,
@@ -243,11 +279,11 @@ __device__ __forceinline__ void mg_up_item(const DevGrid& g, TV wscale, TV cscal
   if (!all && g.ss[g.sim[c]].done) return;
   const int i = cell % BL, j = (cell / BL) % BL, k = cell / (BL * BL);
   TV rv;
-  y[t] = up_cell<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
+  y[t] = up_cell<BL, TV>(g, l, wscale, cscale, r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
 }
 
 template <int BL, class TV>
-__global__ __launch_bounds__(256) void k_mg_up(DevGrid g, TV wscale, TV cscale,
+__global__ __launch_bounds__(256) void k_mg_up(DevGrid g, int l, TV wscale, TV cscale,
                                                const TV* __restrict__ r,
                                                const TV* __restrict__ x,
                                                const TV* __restrict__ yc,
@@ -257,7 +293,7 @@ __global__ __launch_bounds__(256) void k_mg_up(DevGrid g, TV wscale, TV cscale,
   cudaGridDependencySynchronize();  // launched after the previous level's kernel
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)g.n_cubes * BL * BL * BL) return;
-  mg_up_item<BL, TV>(g, wscale, cscale, r, x, yc, yagg, agg_parent, y, all, t);
+  mg_up_item<BL, TV>(g, l, wscale, cscale, r, x, yc, yagg, agg_parent, y, all, t);
 }
 
 // The last block of the finest up launch: mode 0 (start of a solve) takes <r, z> as
@@ -296,7 +332,18 @@ __device__ void mg_decide(const DevGrid& g, const SolveParams& prm, int mode, in
     alive |= !t.done;
   }
   alive = __syncthreads_or(alive);
-  if (threadIdx.x == 0 && mode == 1) g.flags[0] = !alive;
+  if (threadIdx.x == 0) {
+    if (mode == 1) g.flags[0] = !alive;
+    // a captured step: this launch ends the inner loop's body (mode 1) or starts an
+    // inner solve (mode 0) and sets the loop's condition; mode 1 also keeps the guard
+    // on the number of body executions
+    if (prm.cond_inner) {
+      unsigned int go = alive ? 1u : 0u;
+      if (mode == 1 && atomicAdd(prm.guard, 1u) + 1u >= (unsigned int)prm.guard_limit) go = 0u;
+      set_cond(prm.cond_inner, go);
+      if (prm.body_count) atomicAdd(prm.body_count + (mode == 1 ? 0 : 1), 1u);
+    }
+  }
 }
 
 // ---- up on the finest level: z = y_0, <r, z> per sim, and the PCG's decisions.
@@ -321,7 +368,8 @@ __global__ __launch_bounds__(NT) void k_mg_up0(DevGrid g, const TV* __restrict__
     const int cell = (blockIdx.x - c * PER) * NT + threadIdx.x;
     const int i = cell % B, j = (cell / B) % B, k = cell / (B * B);
     TV rv;
-    const TV zv = up_cell<B, TV>(g, TV(kMgOmega), TV(1), r, x, yc, yagg, agg_parent, c, i, j, k, &rv);
+    const TV zv = up_cell<B, TV>(g, 0, TV(kMgOmega), TV(1), r, x, yc, yagg, agg_parent, c, i, j,
+                                 k, &rv);
     z[(size_t)c * B3 + cell] = zv;
     rz = double(rv * zv);
   }
@@ -356,7 +404,7 @@ template <int B, class TV, bool FB>
 __global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __restrict__ r0,
                                                          TV* __restrict__ x,
                                                          TV* __restrict__ r1, int all,
-                                                         PassB<TV> pb, TV wl, TV cl) {
+                                                         PassB<TV> pb, TV wl, TV cl, int lsh) {
   cudaGridDependencySynchronize();  // launched after the previous level's kernel
   using SL = Slab<B, B>;
   constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
@@ -427,16 +475,17 @@ __global__ __launch_bounds__(B * B) void k_mg_down0_tile(DevGrid g, const TV* __
   auto valg = [&](int n, int cell) {
     return w * res((size_t)n * B3 + cell) * inv_diag_any<B, TV>(g, n, cell);
   };
-  stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg);
-  const TV h = sim_h<TV>(g.sp[g.sim[c]]) * cl;
+  stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg, lsh);
+  const TV h = cube_h<TV>(g, g.sp[g.sim[c]], c) * cl;
   const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
   int o = SL::at(i, j, 1);
   TV below = S[o - PP], cur = S[o];
 #pragma unroll 4
   for (int kk = 0; kk < B; ++kk) {
     const TV above = S[o + PP];
-    const TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
-                   (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+    TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
+             (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+    if (cs.has21) acc = stencil_sum_w<B, TV, B>(S, o, cs, i, j, kk);
     const int cell = (kk * B + j) * B + i;
     const size_t gi = (size_t)c * B3 + cell;
     x[gi] = cur;
@@ -468,7 +517,8 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
                                                        const TV* __restrict__ x,
                                                        const TV* __restrict__ y1,
                                                        TV* __restrict__ z, SolveParams prm,
-                                                       int mode, TV wl, TV cl, int finest) {
+                                                       int mode, TV wl, TV cl, int finest,
+                                                       int lsh) {
   cudaGridDependencySynchronize();  // launched after the previous level's kernel
   using SL = Slab<B, B>;
   constexpr int NT = B * B, B3 = B * B * B, BB = B * B, PP = SL::P * SL::P, CB = B / 2;
@@ -506,8 +556,8 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
     };
     auto val1 = [&](int, int n, int cell) { return xt(n, cell); };
     auto valg = [&](int n, int cell) { return xt(n, cell); };
-    stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg);
-    const TV h = sim_h<TV>(g.sp[s]) * cl, w = wl;
+    stage_pressure_slab<B, B, NT, TV>(S, cs, g, c, 0, val4, val1, valg, lsh);
+    const TV h = cube_h<TV>(g, g.sp[s], c) * cl, w = wl;
     const int i = threadIdx.x % B, j = column_row<B>(threadIdx.x);
     int o = SL::at(i, j, 1);
     TV below = S[o - PP], cur = S[o];
@@ -515,8 +565,9 @@ __global__ __launch_bounds__(B * B) void k_mg_up0_tile(DevGrid g, const TV* __re
 #pragma unroll 4
     for (int kk = 0; kk < B; ++kk) {
       const TV above = S[o + PP];
-      const TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
-                     (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+      TV acc = (cur - S[o - 1]) + (cur - S[o + 1]) + (cur - S[o - SL::P]) +
+               (cur - S[o + SL::P]) + (cur - below) + (cur - above);
+      if (cs.has21) acc = stencil_sum_w<B, TV, B>(S, o, cs, i, j, kk);
       const size_t gi = (size_t)c * B3 + (kk * B + j) * B + i;
       const TV inv = cs.smask == 0 ? cs.invtab[18] : cs.invtab[s3_of<B>(cs.w3, i, j, kk)];
       const TV rv = r[gi];
@@ -727,11 +778,11 @@ static cudaError_t down_t(const Ctx& x, int l, int all) {
   if constexpr (BL > 1) {  // one thread per fine cell
     const long long n = (long long)x.g.n_cubes * BL * BL * BL;
     return launch_pdl(k_mg_down_cell<BL, TV>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0,
-                      x.stream, x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+                      x.stream, x.g, l, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
   } else {
     const long long n = (long long)x.g.n_cubes * CB * CB * CB;
     return launch_pdl(k_mg_down<BL, TV>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0,
-                      x.stream, x.g, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
+                      x.stream, x.g, l, TV(kMgOmega / c4), TV(c4), r, xv, rc, all);
   }
 }
 
@@ -741,7 +792,7 @@ static cudaError_t up_t(const Ctx& x, int l, int all) {
   const TV* yc = BL > 1 ? (const TV*)x.mg.y[l + 1] : nullptr;
   const double c4 = double(1 << (2 * l));
   return launch_pdl(k_mg_up<BL, TV>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, x.stream,
-                    x.g, TV(kMgOmega / c4), TV(c4), (const TV*)x.mg.r[l], (const TV*)x.mg.x[l],
+                    x.g, l, TV(kMgOmega / c4), TV(c4), (const TV*)x.mg.r[l], (const TV*)x.mg.x[l],
                     yc, (const double*)x.mg.ax[0], (const int*)x.mg.parent[0], (TV*)x.mg.y[l],
                     all);
 }
@@ -791,7 +842,7 @@ static cudaError_t down0_tile_t(const Ctx& x, int l, int all, bool fb) {
   if (e != cudaSuccess) return e;
   return launch_pdl(kern, dim3(x.g.n_cubes), dim3(B * B), sm, x.stream, x.g,
                     (const TV*)x.mg.r[l], (TV*)x.mg.x[l], (TV*)x.mg.r[l + 1], all, pb,
-                    TV(kMgOmega / c4), TV(c4));
+                    TV(kMgOmega / c4), TV(c4), l);
 }
 
 template <int B, class TV>
@@ -805,7 +856,7 @@ static cudaError_t up0_tile_t(const Ctx& x, int l, const SolveParams& prm, int m
   return launch_pdl(kern, dim3(x.g.n_cubes), dim3(B * B), sm, x.stream, x.g,
                     (const TV*)x.mg.r[l], fb ? (const TV*)x.f.s0 : (const TV*)nullptr,
                     (const TV*)x.mg.x[l], (const TV*)x.mg.y[l + 1], (TV*)x.mg.y[l], prm, mode,
-                    TV(kMgOmega / c4), TV(c4), l == 0 ? 1 : 0);
+                    TV(kMgOmega / c4), TV(c4), l == 0 ? 1 : 0, l);
 }
 
 template <class TV>

@@ -11,6 +11,12 @@ namespace bcm {
 
 constexpr int kMaxPersistentSims = 256;
 
+// Condition of a conditional graph node, set from a kernel inside that node's graph or
+// body (a zero handle: no graph loop, nothing to set).
+__device__ __forceinline__ void set_cond(unsigned long long handle, unsigned int v) {
+  if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, v);
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -22,10 +22,6 @@
 
 namespace bcm {
 
-__device__ __forceinline__ void set_cond(unsigned long long handle, unsigned int v) {
-  if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, v);
-}
-
 // ===========================================================================
 // residual r = rhs - K x of the FP64 iterate x = p, rhs = -V (b - mean).
 // FP64 mode: starts the PCG.  Mixed mode: one defect-correction cycle; r goes to
@@ -364,8 +360,9 @@ __global__ __launch_bounds__(NT) void k_cg_b(DevGrid g, TX* __restrict__ x, TV* 
       set_cond(prm.cond_inner, alive ? 1u : 0u);
     }
   }
-  // independent guard on a graph loop: a bounded number of body executions
-  if (prm.cond_inner && blockIdx.x == 0 && threadIdx.x == 0) {
+  // independent guard on a graph loop: a bounded number of body executions (with the
+  // multigrid the V-cycle's decisions keep it)
+  if (prm.cond_inner && !prm.mg && blockIdx.x == 0 && threadIdx.x == 0) {
     const unsigned int n = atomicAdd(prm.guard, 1u) + 1u;
     if (n >= (unsigned int)prm.guard_limit)
       cudaGraphSetConditional((cudaGraphConditionalHandle)prm.cond_inner, 0u);

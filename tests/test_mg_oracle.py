@@ -140,3 +140,70 @@ def test_mg_pcg_matches_direct_solve_in_fewer_iterations():
     d = K.diagonal()
     _, it_j = MGO.pcg(K, b, lambda r: r / d, 1e-11)
     assert it * 3 < it_j, (it, it_j)
+
+
+def two_level_small(nx=2, ny=1, nz=1, B=4):
+    """A level-0 row of cubes of 4^3 whose first cube is split into eight level-1 cubes
+    (2:1 faces in x, and the refined block against the domain walls)."""
+    return W.two_level_channel(nx, ny, nz, B, (0, 0, 0), (1, 1, 1), 1.0 / 8.0, 0)
+
+
+def cell_owner(spec, l):
+    """Per level-l cell: its cube and that cube's level."""
+    bl = spec.B >> l
+    cube = np.repeat(np.arange(spec.n_cubes), bl ** 3)
+    return cube, np.asarray(spec.cube_level, np.int64)[cube]
+
+
+@pytest.mark.parametrize("nx", [2, 3])
+def test_two_level_faces_keep_the_21_form_on_every_level(nx):
+    """On a two-level grid every per-cube level's Galerkin operator keeps the flux form
+    of R7 across a 2:1 face, the form the GPU levels apply: each cell of a coarse cube
+    facing the refined block couples to exactly four cells of fine cubes and each fine
+    cell on such a face to exactly one coarse cell, with the coefficient of the
+    finest level's sub-face scaled by the fine faces it now carries, 4^l h_f / 1.5, and
+    same-level faces keep 4^l h of their cube."""
+    spec = two_level_small(nx)
+    mg = MGO.MG(O.Oracle(spec))
+    h0 = spec.sim_h0[0]
+    L = int(round(math.log2(spec.B)))
+    for l in range(L + 1):
+        K = sp.coo_matrix(mg.Ks[l])
+        cube, lv = cell_owner(spec, l)
+        off = K.row != K.col
+        rows, cols, vals = K.row[off], K.col[off], K.data[off]
+        cross = lv[rows] != lv[cols]
+        assert cross.any()
+        want = (4.0 ** l) * (h0 / 2.0) / 1.5
+        np.testing.assert_allclose(-vals[cross], want, rtol=1e-12)
+        coarse_rows = rows[cross & (lv[rows] == 0)]
+        fine_rows = rows[cross & (lv[rows] == 1)]
+        assert np.all(np.bincount(coarse_rows)[np.unique(coarse_rows)] == 4)
+        assert np.all(np.bincount(fine_rows)[np.unique(fine_rows)] == 1)
+        same = ~cross & (cube[rows] != cube[cols])
+        hc = h0 / (2.0 ** lv[rows[same]])
+        np.testing.assert_allclose(-vals[same], (4.0 ** l) * hc, rtol=1e-12)
+        inner = ~cross & (cube[rows] == cube[cols])
+        hc = h0 / (2.0 ** lv[rows[inner]])
+        np.testing.assert_allclose(-vals[inner], (4.0 ** l) * hc, rtol=1e-12)
+
+
+def test_two_level_preconditioner_symmetric_positive_definite():
+    spec = two_level_small()
+    mg = MGO.MG(O.Oracle(spec))
+    M = mg.matrix()
+    assert np.abs(M - M.T).max() <= 1e-13 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0.0
+
+
+def test_two_level_mg_pcg_matches_direct_solve_in_fewer_iterations():
+    spec = W.two_level_channel(4, 2, 2, 4, (1, 0, 0), (3, 2, 2), 1.0 / 8.0, 0)
+    mg = MGO.MG(O.Oracle(spec))
+    K = mg.K
+    b = np.random.default_rng(4).standard_normal(K.shape[0])
+    x, it = MGO.pcg(K, b, mg.apply, 1e-11)
+    xd = sp.linalg.spsolve(sp.csc_matrix(K), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    d = K.diagonal()
+    _, it_j = MGO.pcg(K, b, lambda r: r / d, 1e-11)
+    assert it * 2 < it_j, (it, it_j)
