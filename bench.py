@@ -410,6 +410,50 @@ def leg_batched(dev, args, ws):
             "cg_iters_last_step_min_max": [min(iters), max(iters)]}
 
 
+def leg_two_level_mg(dev, args, ws):
+    """The two-level grid of 83.1M cells (rotating ellipsoids, solid fraction every
+    step), mixed, rtol 1e-8, with the multigrid preconditioner (2:1 faces on every
+    per-cube level)."""
+    from paper_1808_04099_gb300 import bcm
+    spec = W.config_two_level(2)
+    n = spec.n_cells
+    g = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+    g.set_preconditioner(bcm.PRECOND_MULTIGRID)
+    g.load_state(W.initial_state(spec))
+    g.step(1, rtol=RTOL, stats=False)
+    steps = 2
+    ms = max_over_ranks(timed_steps(g, steps, g.stream), ws)
+    st = g.step(0, rtol=RTOL)[0]
+    del g
+    _free()
+    return {"value": _rate(n, steps, ms, ws), "unit": "cell-updates/s",
+            "ms_per_step": round(ms / steps, 3), "steps": steps, "cells": n,
+            "precision": "FP32 sweeps + FP64 defect correction", "preconditioner": "multigrid",
+            "rtol": RTOL, "cg_iters_last_step": st["cg_iters"],
+            "refine_cycles_last_step": st["refine_cycles"], "rel_resid_last_step": st["rel_resid"]}
+
+
+def leg_batched_mg(dev, args, ws):
+    """The 64-sim batch of leg_batched in graph steps with the multigrid PCG (its
+    iteration and defect-correction loops as conditional graph nodes)."""
+    from paper_1808_04099_gb300 import bcm
+    spec = W.batched_mix(64, seed=0, steps=args.steps)
+    g = bcm.Grid(spec, bcm.PREC_F32_REFINE, device=dev)
+    g.set_preconditioner(bcm.PRECOND_MULTIGRID)
+    g.load_state(W.initial_state(spec, seed=1, noise=1e-3))
+    g.step_graph(args.warmup, rtol=RTOL, stats=False)
+    ms = max_over_ranks(timed_steps_graph(g, args.steps, g.stream), ws)
+    st = g.step(0, rtol=RTOL)
+    del g
+    _free()
+    iters = [s["cg_iters"] for s in st]
+    return {"value": _rate(spec.n_cells, args.steps, ms, ws), "unit": "cell-updates/s",
+            "ms_per_step": round(ms / args.steps, 3), "steps": args.steps, "sims": spec.n_sims,
+            "cells": spec.n_cells, "precision": "mixed", "preconditioner": "multigrid",
+            "rtol": RTOL, "converged": int(sum(s["converged"] for s in st)),
+            "cg_iters_last_step_min_max": [min(iters), max(iters)]}
+
+
 def leg_adjoint(dev, args, ws):
     """Cost of the discrete adjoint on the 33.5M-cell sphere flow (32x16x16 cubes of
     16^3, eight inflow modes): two FP64 steps forward with checkpoints, then the
@@ -724,6 +768,8 @@ def gpu_arm(args, ws, rank, local):
         legs["cavity64_fp64"] = leg_cavity64(dev, args, ws)
         legs["batched64_graph_mixed"] = leg_batched(dev, args, ws)
         legs["two_level_83M_mixed"] = leg_two_level(dev, args, ws, peak)
+        legs["two_level_83M_mixed_mg"] = leg_two_level_mg(dev, args, ws)
+        legs["batched64_graph_mixed_mg"] = leg_batched_mg(dev, args, ws)
         if not args.no_adjoint:
             legs["adjoint_33M_fp64"] = leg_adjoint(dev, args, ws)
     # the FP64 PCG's bound: min(HBM, FP64 FMA rate x arithmetic intensity); pass A

@@ -21,26 +21,39 @@ SHAPES = [(5, 1, 1), (1, 1, 1), (1, 2, 1), (1, 4, 1), (3, 1, 1), (2, 1, 1), (2, 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "bcm_gb300_launch.json")
 
 
-def _key(grid) -> str:
-    import torch
-    name = torch.cuda.get_device_name(grid.device)
-    return f"{name}|B{grid.spec.B}|prec{grid.precision}|cubes{grid.spec.n_cubes}"
+def _key(grid, device_name=None) -> str:
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name(grid.device)
+    # the shape list is part of the key: a cache written for other shapes is not used
+    shapes = ";".join(f"{pe},{sa},{sb}" for pe, sa, sb in SHAPES)
+    return (f"{device_name}|B{grid.spec.B}|prec{grid.precision}|cubes{grid.spec.n_cubes}"
+            f"|shapes{shapes}")
 
 
-def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
-    """Pick and set the fastest (slabs_a, slabs_b); returns {shape: us per iteration}."""
-    key = _key(grid)
-    cache = {}
-    if use_cache and os.path.exists(CACHE):
-        try:
-            with open(CACHE) as f:
-                cache = json.load(f)
-        except (OSError, ValueError):
-            cache = {}
-    if use_cache and key in cache:
-        pe, sa, sb = cache[key]["best"]
+def _read_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+        return cache if isinstance(cache, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def tune(grid, iters: int = 40, use_cache: bool = True, cache_path: str | None = None,
+         device_name: str | None = None) -> dict:
+    """Pick and set the fastest launch shape; returns {"persistent,slabs_a,slabs_b": us
+    per iteration}.  The cache (a JSON file, cache_path or CACHE) maps the device, cube
+    size, precision, cube count and shape list to the best shape and its times; an
+    unreadable cache counts as empty.  The caller's solver controls are restored."""
+    path = cache_path or CACHE
+    key = _key(grid, device_name) if use_cache else None
+    cache = _read_cache(path) if use_cache else {}
+    entry = cache.get(key)
+    if use_cache and isinstance(entry, dict) and tuple(entry.get("best", ())) in SHAPES:
+        pe, sa, sb = entry["best"]
         grid.set_launch(sa, sb, persistent=pe)
-        return cache[key]["times"]
+        return entry["times"]
     p = grid.field(bcm.P)
     saved = p.clone()
     times = {}
@@ -55,10 +68,13 @@ def tune(grid, iters: int = 40, use_cache: bool = True) -> dict:
     pe, sa, sb = map(int, best.split(","))
     grid.set_launch(sa, sb, persistent=pe)
     if use_cache:
+        cache = _read_cache(path)  # another process may have added entries meanwhile
         cache[key] = {"best": [pe, sa, sb], "times": times}
-        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        with open(CACHE, "w") as f:
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
+        os.replace(tmp, path)
     return times
 
 

@@ -1,0 +1,129 @@
+"""The launch-shape autotuner's host logic on the CPU, with a fake grid whose timing
+source is a table: it times every applicable shape, keeps the fastest, writes the JSON
+cache and takes the shape from it on the next call without timing, restores the caller's
+solver controls, ignores an unreadable cache and re-tunes when the cached shape is not
+one it knows."""
+import json
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1808_04099_gb300 import autotune, bcm  # noqa: E402
+
+
+class FakeSpec:
+    def __init__(self, B, n_cubes):
+        self.B = B
+        self.n_cubes = n_cubes
+
+
+class FakeGrid:
+    """The grid calls the tuner makes; solve_pressure_iters 'runs' for the table's time
+    of the current shape (us per iteration) and records the call."""
+
+    def __init__(self, table, B=16, precision=bcm.PREC_F32_REFINE):
+        self.spec = FakeSpec(B, 1024)
+        self.precision = precision
+        self.device = "cpu"
+        self.table = table
+        self.shape = (1, 1, 1)
+        self.max_cycles = 7
+        self.solves = 0
+        self.p = torch.arange(10, dtype=torch.float64)
+        self.last_iters = 0
+        self.profiling = False
+
+    def field(self, fid):
+        assert fid == bcm.P
+        return self.p
+
+    def set_launch(self, slabs_a=1, slabs_b=1, persistent=1):
+        self.shape = (int(persistent), int(slabs_a), int(slabs_b))
+
+    def get_solver(self):
+        return {"inner_rtol": 0.0, "max_cycles": self.max_cycles, "check_every": 8,
+                "barrier_timeout_s": 2.0, "recycle": 1}
+
+    def set_solver(self, max_cycles=0, **_):
+        if max_cycles > 0:
+            self.max_cycles = max_cycles
+
+    def profile(self, on):
+        self.profiling = bool(on)
+
+    def solve_pressure_iters(self, iters):
+        assert self.profiling and self.max_cycles == 1
+        self.solves += 1
+        self.last_iters = iters
+        self.p.add_(1.0)  # the solve changes the pressure; the tuner restores it
+        return [{"cg_iters": iters}]
+
+    def profile_read(self, reset=True):
+        us = self.table[self.shape]
+        ms = 1e-3 * us * self.last_iters
+        if self.shape[0]:  # persistent: one launch for all iterations
+            prof = {"pcg": (ms, 1), "cg_a": (0.0, 0), "cg_b": (0.0, 0)}
+        else:  # two launches per iteration, split evenly
+            n = self.last_iters
+            prof = {"pcg": (0.0, 0), "cg_a": (0.5 * ms, n), "cg_b": (0.5 * ms, n)}
+        return prof, 0
+
+
+def table(best):
+    t = {s: 100.0 + 3.0 * i for i, s in enumerate(autotune.SHAPES)}
+    t[best] = 10.0
+    return t
+
+
+def test_tunes_writes_cache_and_reuses_it(tmp_path):
+    cache = str(tmp_path / "launch.json")
+    g = FakeGrid(table((1, 2, 1)))
+    p0 = g.p.clone()
+    times = autotune.tune(g, iters=5, cache_path=cache, device_name="fake GB300")
+    assert g.shape == (1, 2, 1)
+    assert min(times, key=times.get) == "1,2,1"
+    assert times["1,2,1"] == pytest.approx(10.0)
+    assert g.max_cycles == 7                      # the caller's control is back
+    assert torch.equal(g.p, p0)                   # and the pressure
+    timed = {s for s in autotune.SHAPES if not (s[0] and s[1] > 1 and g.spec.B != 16)}
+    assert g.solves == 2 * len(timed)             # a warm-up pass and a timed pass each
+    data = json.load(open(cache))
+    (key,) = data.keys()
+    assert key.startswith("fake GB300|B16|prec1|cubes1024")
+    assert data[key]["best"] == [1, 2, 1]
+    # second call: from the cache, no timing
+    g2 = FakeGrid(table((0, 1, 2)))
+    times2 = autotune.tune(g2, iters=5, cache_path=cache, device_name="fake GB300")
+    assert g2.solves == 0 and g2.shape == (1, 2, 1) and times2 == data[key]["times"]
+    # another device name: its own entry
+    g3 = FakeGrid(table((0, 1, 2)))
+    autotune.tune(g3, iters=5, cache_path=cache, device_name="other")
+    assert g3.shape == (0, 1, 2) and g3.solves > 0
+    assert len(json.load(open(cache))) == 2
+
+
+def test_fp64_and_small_cubes_skip_the_shapes_they_cannot_run(tmp_path):
+    g = FakeGrid(table((5, 1, 1)), B=8, precision=bcm.PREC_F64)
+    times = autotune.tune(g, iters=3, use_cache=False)
+    assert "5,1,1" not in times                   # the fused form: FP32 on 16^3 only
+    assert all(not (int(k.split(",")[0]) and int(k.split(",")[1]) > 1) for k in times)
+    assert g.shape == tuple(map(int, min(times, key=times.get).split(",")))
+
+
+def test_unreadable_or_stale_cache_is_retuned(tmp_path):
+    cache = tmp_path / "launch.json"
+    cache.write_text("{not json")
+    g = FakeGrid(table((3, 1, 1)))
+    autotune.tune(g, iters=4, cache_path=str(cache), device_name="d")
+    assert g.shape == (3, 1, 1) and g.solves > 0
+    data = json.loads(cache.read_text())
+    (key,) = data.keys()
+    data[key]["best"] = [9, 9, 9]                 # a shape the tuner does not know
+    cache.write_text(json.dumps(data))
+    g2 = FakeGrid(table((2, 1, 1)))
+    autotune.tune(g2, iters=4, cache_path=str(cache), device_name="d")
+    assert g2.solves > 0 and g2.shape == (2, 1, 1)
+    assert json.loads(cache.read_text())[key]["best"] == [2, 1, 1]
+    assert np.isfinite(list(json.loads(cache.read_text())[key]["times"].values())).all()
