@@ -1,4 +1,6 @@
-"""In-tree build of libbcm.so for sm_103a (nvcc, one -gencode, translation units in parallel)."""
+"""In-tree build of libbcm.so for sm_103a (nvcc, one -gencode, translation units in parallel),
+and of libbcm_check.so, the checked build (index checks and NaN-poisoned tiles, see
+BCM_CHECK in csrc/bcm_internal.cuh), on request."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -12,6 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbcm.so")
+OBJ_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(PKG, "libbcm_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
@@ -33,24 +37,28 @@ def _deps():
         glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "bcm.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(check: bool = False) -> bool:
+    lib = LIB_CHECK if check else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libbcm.so next to this file."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libbcm.so (check: libbcm_check.so, with
+    -DBCM_CHECK=1) next to this file."""
+    lib, objdir = (LIB_CHECK, OBJ_CHECK) if check else (LIB, OBJ)
+    if not force and up_to_date(check):
+        return lib
     nv = _nvcc()
-    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     srcs = _sources()
+    extra = ["-DBCM_CHECK=1"] if check else []
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        cmd = [nv, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nv, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -60,10 +68,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nv, "-shared", *ARCH, *objs, "-o", tmp, "-ldl"], capture_output=True,
                        text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib

@@ -77,10 +77,15 @@ _lib = None
 
 
 def lib(build: bool = True):
-    """Load libbcm.so (building it in-tree first when sources are newer)."""
+    """Load libbcm.so (building it in-tree first when sources are newer); with the
+    environment variable BCM_CHECK=1, the checked build libbcm_check.so."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB
+        check = os.environ.get("BCM_CHECK") == "1"
+        if check:
+            path = _build.build(check=True) if build else _build.LIB_CHECK
+        else:
+            path = _build.build() if build else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError("libbcm.so is missing; run __graft_entry__.build()")
         L = C.CDLL(path)

@@ -751,6 +751,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   G.ss = (SimState*)(W + L.ss);
   G.counter = (unsigned int*)(W + L.counter);
   G.flags = (int*)(W + L.flags);
+  G.check = (int*)(W + L.err) + 8;  // a word of its own in the error block
   Fields& F = x.f;
   F.u = W + L.u; F.v = W + L.v; F.w = W + L.w;
   F.us = W + L.us; F.vs = W + L.vs; F.ws = W + L.ws;
@@ -917,9 +918,16 @@ bcm_status read_flags(bcm_grid* g, int flags[2]) {
 // PCG solve as one cooperative launch; the two-launch mode reads the device
 // convergence flags every check_every iterations.  Finished sims skip their cubes.
 bcm_status read_err(bcm_grid* g) {
-  int err = 0;
-  CUDA_TRY(cudaMemcpyAsync(&err, g->ws + g->L.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  int words[9] = {0};  // [0] barrier timeout, [8] failed index check (checked build)
+  CUDA_TRY(cudaMemcpyAsync(words, g->ws + g->L.err, sizeof words, cudaMemcpyDeviceToHost,
+                           g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const int err = words[0];
+  if (words[8]) {
+    CUDA_TRY(cudaMemsetAsync(g->ws + g->L.err + 8 * sizeof(int), 0, sizeof(int), g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return fail(BCM_E_BOUNDS, "index check %d failed in a kernel (checked build)", words[8]);
+  }
   if (err) {
     // a timed-out solve leaves barrier and ticket counters mid-count: start them afresh
     CUDA_TRY(cudaMemsetAsync(g->ws + g->L.err, 0, sizeof(int), g->stream));

@@ -44,9 +44,15 @@ struct CubeSh {
 template <class TV>
 __device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int c) {
   const int t = threadIdx.x;
-  const SimParams& sp = g.sp[g.sim[c]];
+  if (!bcm_expect(g, c >= 0 && c < g.n_cubes, CHK_CUBE)) c = 0;
+  int s = g.sim[c], lv = g.lvl[c];
+  if (!bcm_expect(g, s >= 0 && s < g.n_sims && lv >= 0 && lv <= g.max_level, CHK_SIM)) {
+    s = 0;  // read valid tables; the host reports the failure
+    lv = 0;
+  }
+  const SimParams& sp = g.sp[s];
   if (t < 6) {
-    const int n = g.nb[6 * c + t];
+    const int n = checked_nb(g, g.nb[6 * c + t]);
     cs.nb[t] = n;
     cs.w3[t] = g.w3[6 * c + t];
     cs.bc[t] = sp.bc[t];
@@ -57,7 +63,7 @@ __device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int 
   if (t == 0) {
     int any = 0, m = 0;
     for (int f = 0; f < 6; ++f) {
-      any |= g.nb[6 * c + f] < NB_BOUNDARY;
+      any |= checked_nb(g, g.nb[6 * c + f]) < NB_BOUNDARY;
       m |= (g.w3[6 * c + f] != 3) << f;
     }
     cs.has21 = any;
@@ -72,7 +78,7 @@ __device__ __forceinline__ void load_cube(CubeSh<TV>& cs, const DevGrid& g, int 
     }
   }
   if (t < 36) cs.nbw3[t / 6][t - 6 * (t / 6)] = g.nbw3[36 * c + t];
-  if (t < kW3) cs.invtab[t] = TV(sp.invdiag[g.lvl[c]][t]);
+  if (t < kW3) cs.invtab[t] = TV(sp.invdiag[lv][t]);
 }
 
 // Face-weight sum (thirds) of cell (i, j, k) of a cube with face weights w3.
@@ -100,13 +106,16 @@ __device__ __forceinline__ TV poisson_ghost_21(const DevGrid& g, int c, int f, i
   const int d = f >> 1, side = f & 1;
   if (code == NB_COARSE) {
     const int C = g.aux[(6 * c + f) * 4];
+    if (!bcm_expect(g, C >= 0 && C < g.n_cubes, CHK_AUX)) return TV(0);
     const int sf = (1 << (g.max_level - g.lvl[c])) << lsh, sc = 2 * sf;
     const int A = (g.ijk[3 * c + tan1(d)] + a * sf - g.ijk[3 * C + tan1(d)]) / sc;
     const int Bb = (g.ijk[3 * c + tan2(d)] + b * sf - g.ijk[3 * C + tan2(d)]) / sc;
+    if (!bcm_expect(g, A >= 0 && A < B && Bb >= 0 && Bb < B, CHK_CELL)) return TV(0);
     return valg(C, cell_of<B>(d, side ? 0 : B - 1, A, Bb));
   }
   const int qa = (2 * a) / B, qb = (2 * b) / B;
   const int F = g.aux[(6 * c + f) * 4 + qb * 2 + qa];
+  if (!bcm_expect(g, F >= 0 && F < g.n_cubes, CHK_AUX)) return TV(0);
   const int fa = 2 * a - qa * B, fb = 2 * b - qb * B;
   TV sum = TV(0);
   for (int bb = 0; bb < 2; ++bb)
@@ -151,6 +160,7 @@ __device__ __forceinline__ void stage_pressure_cube(TV* __restrict__ S, const Cu
                                                     const Nbv& nbv, const ValG& valg) {
   using SL = Slab<B, B>;
   constexpr int B3 = B * B * B, BB = B * B;
+  poison_tile(S, SL::N);
   for (int q4 = threadIdx.x; q4 < B3 / 4; q4 += NT) {
     const int cell = 4 * q4, i0 = cell % B, j = (cell / B) % B, k = cell / BB;
     TV v[4];
@@ -192,6 +202,7 @@ __device__ __forceinline__ void stage_pressure_slab(TV* __restrict__ S, const Cu
                                                     const ValG& valg, int lsh = 0) {
   using SL = Slab<B, KS>;
   constexpr int BB = B * B, Q = BB / 4;
+  poison_tile(S, SL::N);
   for (int idx = threadIdx.x; idx < (KS + 2) * Q; idx += NT) {
     const int kk = idx / Q, q = idx - kk * Q;
     const int j = (4 * q) / B, i0 = 4 * q - j * B;

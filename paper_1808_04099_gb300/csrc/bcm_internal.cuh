@@ -114,7 +114,47 @@ struct DevGrid {
   SimState* ss;
   unsigned int* counter;          // last-block tickets
   int* flags;                     // [0] every running CG finished, [1] every defect correction finished
+  int* check;                     // checked build: code of the first failed index check
 };
+
+// Checked build (compiled with -DBCM_CHECK=1): kernels test the cube, sim and cell
+// indexes they take from the grid tables before they use them; a failed test records
+// its code in DevGrid::check (the first one wins), the access is skipped (a neighbour
+// becomes a domain face), and the host reports BCM_E_BOUNDS.  Shared-memory tiles are
+// filled with NaN before staging, so a tile value the stencil reads without it having
+// been staged turns the result non-finite.  In the default build both are no-ops.
+#ifndef BCM_CHECK
+#define BCM_CHECK 0
+#endif
+enum { CHK_CUBE = 1, CHK_SIM = 2, CHK_NEIGHBOUR = 3, CHK_LEVEL = 4, CHK_AUX = 5, CHK_CELL = 6 };
+__device__ __forceinline__ bool bcm_expect(const DevGrid& g, bool ok, int code) {
+#if BCM_CHECK
+  if (!ok) atomicCAS(g.check, 0, code);
+  return ok;
+#else
+  (void)g;
+  (void)code;
+  return true;
+#endif
+}
+// A face-table entry n of cube c (same-level id, or NB_* code), checked: an id outside
+// the grid, or a 2:1 code on a single-level grid, comes back as NB_BOUNDARY.
+__device__ __forceinline__ int checked_nb(const DevGrid& g, int n) {
+  const bool ok = (n >= 0 && n < g.n_cubes) || n == NB_BOUNDARY ||
+                  (g.max_level > 0 && (n == NB_COARSE || n == NB_FINE));
+  return bcm_expect(g, ok, CHK_NEIGHBOUR) ? n : NB_BOUNDARY;
+}
+// NaN into the n values of a tile before it is staged (checked build only).
+template <class T>
+__device__ __forceinline__ void poison_tile(T* S, int n) {
+#if BCM_CHECK
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S[i] = T(__int_as_float(0x7fc00000));
+  __syncthreads();
+#else
+  (void)S;
+  (void)n;
+#endif
+}
 
 __host__ __device__ __forceinline__ int tan1(int d) { return d == 0 ? 1 : 0; }
 __host__ __device__ __forceinline__ int tan2(int d) { return d == 2 ? 1 : 2; }
@@ -186,20 +226,23 @@ template <int B, class T, class Val, class Bc>
 __device__ __forceinline__ T halo_value(const DevGrid& g, int c, int f, int a, int b, int layer,
                                         const Val& val, const Bc& bc) {
   const int d = f >> 1, side = f & 1;
-  const int n = g.nb[6 * c + f];
+  const int n = checked_nb(g, g.nb[6 * c + f]);
   if (n >= 0) return val(n, cell_of<B>(d, side ? layer : B - 1 - layer, a, b));
   if (n == NB_BOUNDARY)
     return bc(f, a, b, val(c, cell_of<B>(d, side ? B - 1 - layer : layer, a, b)));
   if (n == NB_COARSE) {
     const int C = g.aux[(6 * c + f) * 4];
+    if (!bcm_expect(g, C >= 0 && C < g.n_cubes, CHK_AUX)) return T(0);
     const int sf = 1 << (g.max_level - g.lvl[c]), sc = 2 * sf;
     const int A = (g.ijk[3 * c + tan1(d)] + a * sf - g.ijk[3 * C + tan1(d)]) / sc;
     const int Bb = (g.ijk[3 * c + tan2(d)] + b * sf - g.ijk[3 * C + tan2(d)]) / sc;
+    if (!bcm_expect(g, A >= 0 && A < B && Bb >= 0 && Bb < B, CHK_CELL)) return T(0);
     return val(C, cell_of<B>(d, side ? 0 : B - 1, A, Bb));
   }
   // NB_FINE
   const int qa = (2 * a) / B, qb = (2 * b) / B;
   const int F = g.aux[(6 * c + f) * 4 + qb * 2 + qa];
+  if (!bcm_expect(g, F >= 0 && F < g.n_cubes, CHK_AUX)) return T(0);
   const int fa = 2 * a - qa * B, fb = 2 * b - qb * B;
   T sum = T(0);
   for (int l2 = 0; l2 < 2; ++l2) {
@@ -229,6 +272,7 @@ __device__ __forceinline__ void stage_slab(T* __restrict__ S, const DevGrid& g, 
                                            const Val& val, const Bc& bc) {
   using SL = Slab<B, KS>;
   constexpr int BB = B * B;
+  poison_tile(S, SL::N);
   for (int idx = threadIdx.x; idx < (KS + 2) * BB; idx += NT) {
     const int kk = idx / BB, rem = idx - kk * BB, j = rem / B, i = rem - j * B;
     const int k = z0 - 1 + kk;

@@ -79,7 +79,7 @@ __device__ __forceinline__ TV mg_across(const DevGrid& g, int c, int l, int i, i
   q[d] += side ? 1 : -1;
   w = TV(1);
   if (q[d] >= 0 && q[d] < BL) return val(c, q[0], q[1], q[2]);
-  const int n = g.nb[6 * c + f];
+  const int n = checked_nb(g, g.nb[6 * c + f]);
   if (n >= 0) {
     q[d] = side ? 0 : BL - 1;
     return val(n, q[0], q[1], q[2]);
@@ -92,11 +92,14 @@ __device__ __forceinline__ TV mg_across(const DevGrid& g, int c, int l, int i, i
   if (n == NB_COARSE) {
     w = TV(2.0 / 3.0);
     const int C = g.aux[(6 * c + f) * 4];
+    if (!bcm_expect(g, C >= 0 && C < g.n_cubes, CHK_AUX)) return xc;
     // corner coordinates in finest-cell units; a level-l cell spans 2^l level-0 cells
     const int sf = (1 << (g.max_level - g.lvl[c])) << l;
     const int sc = (1 << (g.max_level - g.lvl[C])) << l;
     r3[t1] = (g.ijk[3 * c + t1] + a * sf - g.ijk[3 * C + t1]) / sc;
     r3[t2] = (g.ijk[3 * c + t2] + b * sf - g.ijk[3 * C + t2]) / sc;
+    if (!bcm_expect(g, r3[t1] >= 0 && r3[t1] < BL && r3[t2] >= 0 && r3[t2] < BL, CHK_CELL))
+      return xc;
     return val(C, r3[0], r3[1], r3[2]);
   }
   w = TV(4.0 / 3.0);  // NB_FINE: the four fine cells that touch this coarse cell's face
@@ -107,6 +110,7 @@ __device__ __forceinline__ TV mg_across(const DevGrid& g, int c, int l, int i, i
     for (int aa = 0; aa < 2; ++aa) {
       const int ta = 2 * a + aa, tb = 2 * b + bb, qa = ta / BL, qb = tb / BL;
       const int F = g.aux[(6 * c + f) * 4 + qb * 2 + qa];
+      if (!bcm_expect(g, F >= 0 && F < g.n_cubes && qa < 2 && qb < 2, CHK_AUX)) return xc;
       r3[t1] = ta - qa * BL;
       r3[t2] = tb - qb * BL;
       sum += val(F, r3[0], r3[1], r3[2]);
