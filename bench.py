@@ -882,7 +882,9 @@ def ncu_case(args):
     committed ncu summaries profile (the first step warms caches and allocations)."""
     import torch
     from paper_1808_04099_gb300 import bcm
-    spec = W.config_sphere(2)
+    # the small case: the same flow on cubes of 8^3 (524,288 cells), for counters that do
+    # not depend on the size (instructions per cell)
+    spec = W.sphere_channel(16, 8, 8, 8, steps=2) if args.ncu_small else W.config_sphere(2)
     prec = bcm.PREC_F64 if args.ncu_fp64 else bcm.PREC_F32_REFINE
     g = bcm.Grid(spec, prec)
     g.set_solver(inner_rtol=args.inner_rtol)
@@ -941,6 +943,8 @@ def main():
                     help="with --ncu-case: the two-pass streaming persistent PCG")
     ap.add_argument("--ncu-fused", action="store_true",
                     help="with --ncu-case: the fused single-barrier persistent PCG")
+    ap.add_argument("--ncu-small", action="store_true",
+                    help="with --ncu-case: the sphere flow on 8^3 cubes (524,288 cells)")
     ap.add_argument("--ncu-mg", action="store_true",
                     help="with --ncu-case: the multigrid-preconditioned PCG")
     ap.add_argument("--ncu-cn", action="store_true",

@@ -163,6 +163,13 @@ bcm_status bcm_set_geometry(bcm_grid *grid, int sim, const bcm_body *bodies, int
 /* Reset step counters (time = 0) of all sims; the next step starts AB2 with Euler. */
 bcm_status bcm_reset_time(bcm_grid *grid);
 
+/* The time-averaged force on the bodies of every sim: host out[3 * n_sims] gets, per
+ * sim, the mean over the steps taken since the last reset of the per-step drag
+ * (bcm_stats.drag; its x component averaged over N steps is the objective J of the
+ * adjoint, bcm_adjoint_step).  reset != 0 then starts a new average (bcm_reset_time
+ * does too).  Zeros before the first step.  BCM_E_INVALID for NULL arguments. */
+bcm_status bcm_drag_mean(bcm_grid *grid, int reset, double *out);
+
 /* Set the step counter of every sim (time = step * dt), e.g. when restarting from a
  * checkpoint; step 0 makes the next step the Euler start of AB2. */
 bcm_status bcm_set_step(bcm_grid *grid, int step);

@@ -23,7 +23,8 @@ SCHEME_AB2_CENTRAL, SCHEME_QUICK_CN = 0, 1
 (U, V, W, P, PHI, NX, NY, NZ, USTAR, VSTAR, WSTAR, RHS, UB) = range(13)
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
-            "bcm_set_geometry", "bcm_reset_time", "bcm_set_solver", "bcm_set_launch",
+            "bcm_set_geometry", "bcm_reset_time", "bcm_drag_mean", "bcm_set_solver",
+            "bcm_set_launch",
             "bcm_set_preconditioner", "bcm_apply_preconditioner",
             "bcm_set_step", "bcm_get_solver", "bcm_measure_fma_rate", "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
             "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
@@ -98,6 +99,7 @@ def lib(build: bool = True):
                                 C.POINTER(C.c_int32)]
         L.bcm_set_geometry.argtypes = [P, C.c_int, P, C.c_int, P]
         L.bcm_reset_time.argtypes = [P]
+        L.bcm_drag_mean.argtypes = [P, C.c_int, P]
         L.bcm_set_step.argtypes = [P, C.c_int]
         L.bcm_adjoint_bytes.restype = C.c_size_t
         L.bcm_adjoint_bytes.argtypes = [P]
@@ -381,6 +383,12 @@ class Grid:
 
     def reset_time(self):
         _check(lib().bcm_reset_time(self._h))
+
+    def drag_mean(self, reset: bool = False) -> np.ndarray:
+        """[n_sims, 3]: the mean per-step drag since the last reset (reset: start anew)."""
+        out = np.zeros((self.spec.n_sims, 3), np.float64)
+        _check(lib().bcm_drag_mean(self._h, int(reset), out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def step(self, n: int = 1, rtol: float = 1e-10, max_iter: int = 20000, stats: bool = True,
              allow_not_converged: bool = False) -> Optional[List[dict]]:

@@ -901,6 +901,25 @@ extern "C" bcm_status bcm_reset_time(bcm_grid* g) {
   return BCM_OK;
 }
 
+extern "C" bcm_status bcm_drag_mean(bcm_grid* g, int reset, double* out) {
+  if (!g || !out) return fail(BCM_E_INVALID, "NULL argument");
+  const int ns = g->desc.n_sims;
+  std::vector<SimState> st(ns);
+  CUDA_TRY(cudaMemcpyAsync(st.data(), g->ws + g->L.ss, sizeof(SimState) * ns,
+                           cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  for (int q = 0; q < ns; ++q)
+    for (int e = 0; e < 3; ++e)
+      out[3 * q + e] = st[q].drag_n ? st[q].drag_sum[e] / st[q].drag_n : 0.0;
+  if (reset) {
+    const size_t a = offsetof(SimState, drag_sum), b = offsetof(SimState, drag_n) + sizeof(int);
+    for (int q = 0; q < ns; ++q)
+      CUDA_TRY(cudaMemsetAsync(g->ws + g->L.ss + sizeof(SimState) * q + a, 0, b - a, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+  }
+  return BCM_OK;
+}
+
 // ----------------------------------------------------------- solve drivers
 
 namespace {

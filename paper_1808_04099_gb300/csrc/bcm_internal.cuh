@@ -55,6 +55,8 @@ struct SimState {
   double acc[kStripes][kAccPad];  // atomics: see ACC_* below
   double drag_acc[3];
   double drag[3];
+  double drag_sum[3];  // sum of the steps' drag since the last reset (bcm_drag_mean)
+  int drag_n;          //   and their number
   double bb;           // ||rhs||^2
   double tol2;         // rtol^2 ||rhs||^2 (outer)
   double rz, rr, alpha, beta;
@@ -315,6 +317,40 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
     for (int q = 0; q < NV; ++q) {
       double x = lane < NT / 32 ? red[q * 32 + lane] : 0.0;
       v[q] = warp_sum(x);
+    }
+  }
+}
+
+// The same for NV partial sums held in the vector type TV: FP32 partials are summed in
+// FP32 within each warp (this part's FP64 rate is a small fraction of its FP32 rate,
+// and the warp sums are what every block reaches the grid barrier with) and in FP64
+// across the warps; FP64 partials as block_sum.  Result (FP64) valid in thread 0.
+template <int NT, int NV, class TV>
+__device__ __forceinline__ void block_sum_tv(const TV (&p)[NV], double (&v)[NV], double* red) {
+  if constexpr (sizeof(TV) == 8) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = double(p[q]);
+    block_sum<NT, NV>(v, red);
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float f[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      f[q] = float(p[q]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) red[q * 32 + warp] = double(f[q]);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        double x = lane < NT / 32 ? red[q * 32 + lane] : 0.0;
+        v[q] = warp_sum(x);
+      }
     }
   }
 }

@@ -810,8 +810,10 @@ __global__ void k_step_end(DevGrid g) {
     SimState& t = g.ss[s];
     for (int e = 0; e < 3; ++e) {
       t.drag[e] = t.drag_acc[e];
+      t.drag_sum[e] += t.drag_acc[e];
       t.drag_acc[e] = 0.0;
     }
+    t.drag_n += 1;
     const double dn = acc_take(t, ACC_DIVN), dd = acc_take(t, ACC_DIVD);
     t.div_num = dn;
     t.div_den = dd;

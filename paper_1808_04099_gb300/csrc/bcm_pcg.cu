@@ -137,8 +137,9 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     TV part = TV(0);
     int psim = -1;
     auto flush_pq = [&]() {
-      double vals[1] = {double(part)};
-      block_sum<NT, 1>(vals, red);
+      const TV pp[1] = {part};
+      double vals[1];
+      block_sum_tv<NT, 1, TV>(pp, vals, red);
       if (threadIdx.x == 0) acc_add(g.ss[psim], ACC_SLOT_PQ + k % 3, vals[0]);
       part = TV(0);
     };
@@ -258,8 +259,9 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     TV rz = TV(0), rr = TV(0);
     psim = -1;
     auto flush_rz = [&]() {
-      double vals[2] = {double(rz), double(rr)};
-      block_sum<NT, 2>(vals, red);
+      const TV pp[2] = {rz, rr};
+      double vals[2];
+      block_sum_tv<NT, 2, TV>(pp, vals, red);
       if (threadIdx.x == 0) {
         acc_add(g.ss[psim], ACC_SLOT_RZ + (k + 1) % 3, vals[0]);
         acc_add(g.ss[psim], ACC_SLOT_RR + (k + 1) % 3, vals[1]);

@@ -283,8 +283,9 @@ __global__ __launch_bounds__(NT, 4) void k_pcg1(DevGrid g, TX* __restrict__ x,
           st4(wout + base + cell, wv);
         }
       }
-      double vals[4] = {double(ga), double(de), double(ep), double(rq)};
-      block_sum<NT, 4>(vals, red);
+      const TV pp[4] = {ga, TV(de), ep, rq};
+      double vals[4];
+      block_sum_tv<NT, 4, TV>(pp, vals, red);
       if (threadIdx.x == 0) {
         acc_add(g.ss[s], ACC_SLOT_G + out, vals[0]);
         acc_add(g.ss[s], ACC_SLOT_D + out, vals[1]);

@@ -250,8 +250,9 @@ __global__ __launch_bounds__(B * B, res_min_blocks<B>()) void k_pcg_res(
         const float h = float(cell_h<B>(g, c));
         march_q<B>(T, cs, i, j, h, [&](int, float p, float qv) { pq += p * qv; });
       }
-      double vals[1] = {double(pq)};
-      block_sum<NT, 1>(vals, red);
+      const float pp[1] = {pq};
+      double vals[1];
+      block_sum_tv<NT, 1, float>(pp, vals, red);
       if (tid == 0 && run) acc_add(g.ss[s], ACC_SLOT_PQ + k % 3, vals[0]);
     }
     if (!gb.sync()) break;
@@ -284,8 +285,9 @@ __global__ __launch_bounds__(B * B, res_min_blocks<B>()) void k_pcg_res(
           if (edge || kk == 0 || kk == B - 1) pg[gi] = p;  // the neighbours' halo
         });
       }
-      double vals[2] = {double(rz), double(rs)};
-      block_sum<NT, 2>(vals, red);
+      const float pp[2] = {rz, rs};
+      double vals[2];
+      block_sum_tv<NT, 2, float>(pp, vals, red);
       if (tid == 0 && run) {
         acc_add(g.ss[s], ACC_SLOT_RZ + (k + 1) % 3, vals[0]);
         acc_add(g.ss[s], ACC_SLOT_RR + (k + 1) % 3, vals[1]);

@@ -190,7 +190,7 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
   __shared__ double red[32];
   const int c = blockIdx.x / NSL, z0 = (blockIdx.x - c * NSL) * KS;
   SimState& st = g.ss[g.sim[c]];
-  double pq = 0.0;
+  TV pq = TV(0);
   const bool active = !st.done;
   if (active) {
     load_cube(cs, g, c);
@@ -248,10 +248,11 @@ __global__ __launch_bounds__(NT) void k_cg_a(DevGrid g, const TV* __restrict__ r
       st4(pnew + base + cell, pc);
       st4(q + base + cell, qv);
     }
-    pq = double(part);
+    pq = part;
   }
-  double vals[1] = {pq};
-  block_sum<NT, 1>(vals, red);
+  const TV pp[1] = {pq};
+  double vals[1];
+  block_sum_tv<NT, 1, TV>(pp, vals, red);
   if (threadIdx.x == 0 && active) acc_add(st, ACC_PQ, vals[0]);
   if (last_block(g.counter)) {
     for (int qq = threadIdx.x; qq < g.n_sims; qq += NT) {
@@ -285,7 +286,7 @@ __global__ __launch_bounds__(NT) void k_cg_b(DevGrid g, TX* __restrict__ x, TV* 
   const int c = blockIdx.x / NSL, z0 = (blockIdx.x - c * NSL) * KS;
   const int s = g.sim[c];
   SimState& st = g.ss[s];
-  double vals[2] = {0.0, 0.0};
+  TV sums[2] = {TV(0), TV(0)};
   const bool active = !st.done && !st.nonfinite;
   if (active) {
     if (threadIdx.x < 6) w3s[threadIdx.x] = g.w3[6 * c + threadIdx.x];
@@ -318,10 +319,11 @@ __global__ __launch_bounds__(NT) void k_cg_b(DevGrid g, TX* __restrict__ x, TV* 
         st4(r + base + cell, rv);
       }
     }
-    vals[0] = double(rz);
-    vals[1] = double(rr);
+    sums[0] = rz;
+    sums[1] = rr;
   }
-  block_sum<NT, 2>(vals, red);
+  double vals[2];
+  block_sum_tv<NT, 2, TV>(sums, vals, red);
   if (threadIdx.x == 0 && active) {
     if (!prm.mg) acc_add(st, ACC_RZ, vals[0]);
     acc_add(st, ACC_RR, vals[1]);

@@ -120,3 +120,25 @@ def test_adjoint_gradient_matches_taped_oracle():
     assert abs(J - Jt) <= 1e-11 * abs(Jt)
     g, t = np.concatenate([ga, gc]), np.concatenate([ta, tcg])
     assert np.linalg.norm(g - t) <= 1e-8 * np.linalg.norm(t), (g, t)
+
+
+def test_drag_mean_is_the_mean_of_the_steps_drag():
+    """bcm_drag_mean (the adjoint's objective J in the library) against the mean of the
+    per-step drag the steps report, for every sim of a batch; a reset starts anew."""
+    from paper_1808_04099_gb300 import bcm
+    spec = W.concat([W.sphere_channel(2, 1, 1, 8, length=(2.0, 1.0, 1.0), radius=0.25,
+                                      center=(0.7, 0.5, 0.5), re=100.0),
+                     W.sphere_channel(4, 2, 2, 8, radius=0.3)])
+    g = bcm.Grid(spec, bcm.PREC_F64)
+    g.load_state(W.initial_state(spec, seed=62, noise=1e-3))
+    assert np.all(g.drag_mean(reset=True) == 0.0)
+    drags = []
+    for _ in range(4):
+        st = g.step(1, rtol=1e-12)
+        drags.append([s["drag"] for s in st])
+    ref = np.mean(np.asarray(drags), axis=0)
+    got = g.drag_mean(reset=True)
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+    st = g.step(1, rtol=1e-12)
+    got = g.drag_mean()
+    assert np.abs(got - np.asarray([s["drag"] for s in st])).max() <= 1e-15 * np.abs(got).max()
