@@ -39,6 +39,7 @@ from paper_1808_04099_gb300 import workloads as W  # noqa: E402
 
 RTOL = 1e-8
 METRIC = "cell-updates/s per step & % HBM roofline, FP32+refine vs FP64 at residual 1e-8"
+FP64_INST_PER_CELL_ITER = 22.5  # FP64 instructions per cell of one FP64 PCG iteration (ncu)
 
 # Algorithmic bytes per cell of each kernel class (halo reads of neighbour cubes are
 # counted 0: they are served by L2).  S = state/vector size (4 mixed, 8 FP64).
@@ -772,9 +773,11 @@ def gpu_arm(args, ws, rank, local):
         legs["batched64_graph_mixed_mg"] = leg_batched_mg(dev, args, ws)
         if not args.no_adjoint:
             legs["adjoint_33M_fp64"] = leg_adjoint(dev, args, ws)
-    # the FP64 PCG's bound: min(HBM, FP64 FMA rate x arithmetic intensity); pass A
-    # (7-point stencil, <p,q>) and pass B (two axpys, z = r/diag, two dots) take about
-    # 30 FLOPs per cell per iteration against its schedule's 80 bytes
+    # the FP64 PCG's bound: min(HBM, FP64 pipe).  The pipe issues one FP64 instruction
+    # per lane whether it adds, multiplies or fuses, so its rate is the measured FMA
+    # rate over 2; the two-launch iteration executes 22.5 FP64 instructions per cell
+    # (pass A 16.8, pass B 5.7; ncu on 16^3 cubes,
+    # profiles/fp64_instructions_sphere_16x8x8_B8.md) against 6 x 8 bytes
     fp64_bound = None
     t_iter = None
     if "pcg" in k64 and k64["pcg"].get("us_per_iter"):
@@ -782,14 +785,15 @@ def gpu_arm(args, ws, rank, local):
     elif "cg_a" in k64 and "cg_b" in k64 and iters64:
         t_iter = (k64["cg_a"]["total_ms"] + k64["cg_b"]["total_ms"]) * 1e-3 / iters64
     if "fma_peak" in legs and t_iter:
-        flops_cell = 30.0
-        t_alu = flops_cell * n / (legs["fma_peak"]["fp64_tflops"] * 1e12)
+        inst_cell = FP64_INST_PER_CELL_ITER
+        t_alu = inst_cell * n / (0.5 * legs["fma_peak"]["fp64_tflops"] * 1e12)
         t_hbm = 6 * 8 * n / (peak * 1e9)
         fp64_bound = {"us_per_iter": round(1e6 * t_iter, 2),
-                      "alu_bound_us": round(1e6 * t_alu, 2), "hbm_bound_us_6S": round(1e6 * t_hbm, 2),
-                      "bound": "fp64_alu" if t_alu > t_hbm else "hbm",
+                      "fp64_pipe_bound_us": round(1e6 * t_alu, 2),
+                      "hbm_bound_us_6S": round(1e6 * t_hbm, 2),
+                      "bound": "fp64_pipe" if t_alu > t_hbm else "hbm",
                       "frac_of_bound": round(max(t_alu, t_hbm) / t_iter, 4),
-                      "flops_per_cell_iter": flops_cell}
+                      "fp64_inst_per_cell_iter": inst_cell}
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only), all cores
     # and one thread

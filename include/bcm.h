@@ -237,6 +237,13 @@ bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max
  * BCM_E_INVALID for other values. */
 bcm_status bcm_set_launch(bcm_grid *grid, int persistent, int slabs_a, int slabs_b);
 
+/* z-slabs per 16^3 cube of the momentum and Poisson right-hand-side kernels (one block
+ * per slab, its tiles of u*, v*, w* with their halos in shared memory): 1, 2 or 4; 0
+ * the default (2 in FP32, 4 in FP64).  Other cube sizes take whole cubes (the value is
+ * ignored).  Results do not depend on it.  BCM_E_INVALID for other values. */
+bcm_status bcm_set_stencil_slabs(bcm_grid *grid, int slabs);
+bcm_status bcm_get_stencil_slabs(const bcm_grid *grid, int32_t *slabs);
+
 /* Preconditioner of the pressure PCG.  BCM_PRECOND_JACOBI (the default): M = diag(K).
  * BCM_PRECOND_MULTIGRID: one symmetric V-cycle of a geometric multigrid per iteration
  * (the paper solves the pressure equation by multigrid on its cubes): every cube is

@@ -99,3 +99,63 @@ def _time_shapes(grid, iters, p, saved, times):
             times[f"{pe},{sa},{sb}"] = 1e3 * tp / (npc * iters)
         elif na and nb:
             times[f"{pe},{sa},{sb}"] = 1e3 * (ta / na + tb / nb)
+
+
+STENCIL_SLABS = (1, 2, 4)
+STATE_FIELDS = (bcm.U, bcm.V, bcm.W, bcm.P, bcm.NX, bcm.NY, bcm.NZ, bcm.UB)
+
+
+def tune_stencils(grid, steps: int = 2, use_cache: bool = True, cache_path: str | None = None,
+                  device_name: str | None = None) -> dict:
+    """Pick and set the fastest z-slab depth of the momentum and right-hand-side kernels
+    on 16^3 cubes (bcm_set_stencil_slabs); returns {slabs: us per step of the two}.  Each
+    depth is timed over `steps` steps with the library's kernel timing after one warm-up
+    step; the state, the time and the caller's setting are restored afterwards (the
+    running drag mean of bcm_drag_mean counts the timing steps).  Cached like tune()."""
+    if grid.spec.B != 16:
+        return {}
+    path = cache_path or CACHE
+    key = None
+    if use_cache:
+        key = "stencil|" + _key(grid, device_name) + "|slabs" + ",".join(map(str, STENCIL_SLABS))
+        entry = _read_cache(path).get(key)
+        if isinstance(entry, dict) and entry.get("best") in STENCIL_SLABS:
+            grid.set_stencil_slabs(entry["best"])
+            return {int(k): v for k, v in entry["times"].items()}
+    saved = [grid.field(f).clone() for f in STATE_FIELDS]
+    step0 = grid.step(0)[0]["steps"]
+    caller = grid.get_stencil_slabs()
+    times = {}
+    try:
+        for ns in STENCIL_SLABS:
+            grid.set_stencil_slabs(ns)
+            for rep in range(2):  # a warm-up step, then the timed steps
+                for f, t in zip(STATE_FIELDS, saved):
+                    grid.field(f).copy_(t)
+                grid.set_step(step0)
+                grid.profile(True)
+                grid.step(1 if rep == 0 else steps, stats=False)
+                prof, _ = grid.profile_read(reset=True)
+                grid.profile(False)
+            tm, nm = prof["momentum"]
+            tr, nr = prof["rhs"]
+            if nm and nr:
+                times[ns] = 1e3 * (tm / nm + tr / nr)
+    finally:
+        for f, t in zip(STATE_FIELDS, saved):
+            grid.field(f).copy_(t)
+        grid.set_step(step0)
+        grid.set_stencil_slabs(caller)
+    if not times:
+        return times
+    best = min(times, key=times.get)
+    grid.set_stencil_slabs(best)
+    if use_cache:
+        cache = _read_cache(path)
+        cache[key] = {"best": best, "times": {str(k): v for k, v in times.items()}}
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, path)
+    return times

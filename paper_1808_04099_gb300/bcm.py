@@ -24,7 +24,7 @@ SCHEME_AB2_CENTRAL, SCHEME_QUICK_CN = 0, 1
 
 EXPORTED = ["bcm_workspace_bytes", "bcm_create_grid", "bcm_destroy_grid", "bcm_field",
             "bcm_set_geometry", "bcm_reset_time", "bcm_drag_mean", "bcm_set_solver",
-            "bcm_set_launch",
+            "bcm_set_launch", "bcm_set_stencil_slabs", "bcm_get_stencil_slabs",
             "bcm_set_preconditioner", "bcm_apply_preconditioner",
             "bcm_set_step", "bcm_get_solver", "bcm_measure_fma_rate", "bcm_step", "bcm_step_graph", "bcm_solve_pressure",
             "bcm_adjoint_bytes", "bcm_adjoint_init", "bcm_adjoint_step",
@@ -108,6 +108,8 @@ def lib(build: bool = True):
                                        C.c_int, P]
         L.bcm_set_solver.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int]
         L.bcm_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
+        L.bcm_set_stencil_slabs.argtypes = [P, C.c_int]
+        L.bcm_get_stencil_slabs.argtypes = [P, P]
         L.bcm_get_solver.argtypes = [P, P, P, P, P, P]
         L.bcm_measure_fma_rate.argtypes = [C.c_int, P]
         L.bcm_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
@@ -377,6 +379,16 @@ class Grid:
         precision on 16^3 cubes, else the two-pass form runs; bool values map to 0 and
         1)."""
         _check(lib().bcm_set_launch(self._h, int(persistent), slabs_a, slabs_b))
+
+    def set_stencil_slabs(self, slabs: int):
+        """z-slabs per 16^3 cube of the momentum and right-hand-side kernels (1, 2, 4; 0:
+        the default)."""
+        _check(lib().bcm_set_stencil_slabs(self._h, int(slabs)))
+
+    def get_stencil_slabs(self) -> int:
+        v = C.c_int32()
+        _check(lib().bcm_get_stencil_slabs(self._h, C.byref(v)))
+        return v.value
 
     def set_step(self, step: int):
         _check(lib().bcm_set_step(self._h, step))

@@ -522,6 +522,7 @@ struct StepGraph {
   double rtol = 0.0;
   int max_iter = 0, cycles = 0;
   int slabs_p = 0, single_pass = 0, resident = 0, fused = 0;  // the PCG launch shape captured
+  int slabs_m = -1;  // the momentum / right-hand-side slabs captured
   double inner_rtol = 0.0;
   int persistent_slabs = 0;
   int recycle = -1;
@@ -731,6 +732,7 @@ extern "C" bcm_status bcm_create_grid(const bcm_grid_desc* desc, void* dev_works
   x.single_pass = 0;
   x.resident = 0;
   x.fused = 0;  // the fused single-barrier form: selected by bcm_set_launch(5, ...)
+  x.slabs_m = 0;  // the momentum / right-hand-side slab depth: bcm_set_stencil_slabs
   x.lag_bf16 = desc->lagged_bf16;
   x.stream = s;
   DevGrid& G = x.g;
@@ -1428,7 +1430,8 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
       sg.inner_rtol != g->inner_rtol || sg.recycle != g->recycle ||
       sg.slabs_p != g->ctx.slabs_p || sg.single_pass != g->ctx.single_pass ||
       sg.resident != g->ctx.resident || sg.fused != g->ctx.fused || sg.gen != g->gen ||
-      sg.mg != g->ctx.use_mg || (sg.mg && sg.cycles != g->max_cycles)) {
+      sg.mg != g->ctx.use_mg || (sg.mg && sg.cycles != g->max_cycles) ||
+      sg.slabs_m != g->ctx.slabs_m) {
     bcm_status bst = graph_body_launches(g);  // the old loops' launches so far
     if (bst != BCM_OK) return bst;
     sg.body_kernels[0] = sg.body_kernels[1] = 0;
@@ -1471,6 +1474,7 @@ extern "C" bcm_status bcm_step_graph(bcm_grid* g, int n_steps, double rtol, int 
     sg.gen = g->gen;
     sg.mg = g->ctx.use_mg;
     if (sg.mg) sg.cycles = g->max_cycles;
+    sg.slabs_m = g->ctx.slabs_m;
   }
   NvtxRange r("bcm_step_graph");
   for (int n = 0; n < n_steps; ++n) {
@@ -1560,6 +1564,20 @@ extern "C" bcm_status bcm_set_launch(bcm_grid* g, int persistent, int slabs_a, i
     g->ctx.slabs_a = slabs_a;
     g->ctx.slabs_b = slabs_b;
   }
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_set_stencil_slabs(bcm_grid* g, int slabs) {
+  if (!g) return fail(BCM_E_INVALID, "grid is NULL");
+  if (slabs != 0 && slabs != 1 && slabs != 2 && slabs != 4)
+    return fail(BCM_E_INVALID, "stencil slabs must be 0, 1, 2 or 4");
+  g->ctx.slabs_m = g->B == 16 ? slabs : 0;
+  return BCM_OK;
+}
+
+extern "C" bcm_status bcm_get_stencil_slabs(const bcm_grid* g, int32_t* slabs) {
+  if (!g || !slabs) return fail(BCM_E_INVALID, "NULL argument");
+  *slabs = g->ctx.slabs_m;
   return BCM_OK;
 }
 

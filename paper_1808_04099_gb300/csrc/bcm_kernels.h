@@ -116,6 +116,7 @@ struct Ctx {
   int single_pass; // persistent PCG: one pass and one grid barrier per iteration
   int resident;    // persistent PCG: search direction in shared memory where it fits
   int fused;       // persistent PCG: the single-barrier form with bulk-copy staging
+  int slabs_m;     // momentum and right-hand side: z-slabs per 16^3 cube (0: default)
   int lag_bf16;    // mixed mode: N^{n-1} stored as bfloat16
   int use_mg;      // PCG preconditioner: 0 Jacobi, 1 geometric multigrid
   MgDev mg;

@@ -1,8 +1,9 @@
-"""The launch-shape autotuner's host logic on the CPU, with a fake grid whose timing
-source is a table: it times every applicable shape, keeps the fastest, writes the JSON
-cache and takes the shape from it on the next call without timing, restores the caller's
-solver controls, ignores an unreadable cache and re-tunes when the cached shape is not
-one it knows."""
+"""The autotuner's host logic on the CPU, with fake grids whose timing source is a
+table: it times every applicable PCG launch shape (and every z-slab depth of the
+momentum and right-hand-side kernels), keeps the fastest, writes the JSON cache and
+takes the choice from it on the next call without timing, restores the caller's solver
+controls and the state, ignores an unreadable cache and re-tunes when the cached shape
+is not one it knows."""
 import json
 
 import numpy as np
@@ -127,3 +128,65 @@ def test_unreadable_or_stale_cache_is_retuned(tmp_path):
     assert g2.solves > 0 and g2.shape == (2, 1, 1)
     assert json.loads(cache.read_text())[key]["best"] == [2, 1, 1]
     assert np.isfinite(list(json.loads(cache.read_text())[key]["times"].values())).all()
+
+
+class FakeStencilGrid:
+    """The calls of the stencil-slab tuner; a step 'runs' the momentum and right-hand
+    side for the table's times of the current slab depth and changes the state."""
+
+    def __init__(self, table, B=16):
+        self.spec = FakeSpec(B, 1024)
+        self.precision = bcm.PREC_F32_REFINE
+        self.device = "cpu"
+        self.table = table
+        self.slabs = 0
+        self.fields = {f: torch.full((8,), float(f)) for f in autotune.STATE_FIELDS}
+        self.steps_taken = 5
+        self.last = 0
+        self.profiling = False
+
+    def field(self, fid):
+        return self.fields[fid]
+
+    def get_stencil_slabs(self):
+        return self.slabs
+
+    def set_stencil_slabs(self, s):
+        self.slabs = int(s)
+
+    def step(self, n=1, stats=True, **_):
+        if n:
+            assert self.profiling
+            for t in self.fields.values():
+                t.add_(1.0)
+        self.steps_taken += n
+        self.last = n
+        return [{"steps": self.steps_taken}] if stats else None
+
+    def set_step(self, s):
+        self.steps_taken = s
+
+    def profile(self, on):
+        self.profiling = bool(on)
+
+    def profile_read(self, reset=True):
+        us_m, us_r = self.table[self.slabs]
+        n = self.last
+        return {"momentum": (1e-3 * us_m * n, n), "rhs": (1e-3 * us_r * n, n)}, 0
+
+
+def test_stencil_slabs_tuned_state_restored_and_cached(tmp_path):
+    cache = str(tmp_path / "launch.json")
+    table = {1: (300.0, 200.0), 2: (250.0, 180.0), 4: (200.0, 150.0)}
+    g = FakeStencilGrid(table)
+    before = {f: t.clone() for f, t in g.fields.items()}
+    times = autotune.tune_stencils(g, steps=3, cache_path=cache, device_name="d")
+    assert times == {1: pytest.approx(500.0), 2: pytest.approx(430.0), 4: pytest.approx(350.0)}
+    assert g.slabs == 4 and g.steps_taken == 5
+    assert all(torch.equal(g.fields[f], before[f]) for f in before)
+    g2 = FakeStencilGrid({1: (1.0, 1.0), 2: (9.0, 9.0), 4: (9.0, 9.0)})
+    assert autotune.tune_stencils(g2, cache_path=cache, device_name="d") == times
+    assert g2.slabs == 4 and g2.steps_taken == 5  # from the cache: no steps
+    g3 = FakeStencilGrid(table, B=8)
+    assert autotune.tune_stencils(g3, cache_path=cache, device_name="d") == {}
+    assert g3.slabs == 0
