@@ -366,6 +366,9 @@ __global__ __launch_bounds__(FNT, 1) void k_pcg_fused(DevGrid g, FusedArgs A, So
   };
   // the neighbours' face planes of cube ql into slot sl (issuing warp)
   auto issue_faces = [&](int ql, int sl, bool first, bool none) {
+    // the planes were written by other blocks before the grid barrier this thread has
+    // passed (acquire by thread 0, block barrier): order that before the bulk reads
+    fence_async_global();
     const FSim& fs = sim[S.bsim[ql]];
     int n = -1;
     if (lane < 6) n = S.bnb[ql][lane];

@@ -25,9 +25,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier of a cooperative launch: one arrival counter, bar[32] (a 128-byte
 // line of its own), zeroed before every launch (launch_pcg).  A block arrives with a
-// reduction that returns nothing (thread 0, after a fence that publishes the block's
-// writes) and waits until the counter reaches gridDim.x times the number of barriers
-// it has passed, so the release costs one round trip after the last arrival.
+// release reduction that returns nothing (thread 0, after the block barrier) and waits,
+// reading the counter with acquire loads, until it reaches gridDim.x times the number
+// of barriers it has passed, so the release costs one round trip after the last
+// arrival and no full fence is needed on either side.
 // sync() returns false (and sets *err) when the wait exceeded limit_ns or another
 // block reported an error.
 struct GridBarrier {
@@ -47,15 +48,15 @@ struct GridBarrier {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();  // this block's writes before its arrival
-      atomicAdd(count, 1u);
+      // arrival with release semantics: the block's writes (ordered before this thread
+      // by the block barrier) are visible to every block that acquires the count
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
       passed += 1u;
       const unsigned int target = passed * gridDim.x;
-      volatile unsigned int* c = count;
       int good = 1;
-      if ((int)(*c - target) < 0) {
+      if ((int)(acquire_count() - target) < 0) {
         const unsigned long long t0 = global_ns();
-        while ((int)(*c - target) < 0) {
+        while ((int)(acquire_count() - target) < 0) {
           if (*(volatile int*)err) {
             good = 0;
             break;
@@ -68,11 +69,18 @@ struct GridBarrier {
           __nanosleep(32);
         }
       }
-      __threadfence();
       ok = good;
     }
     __syncthreads();
     return ok != 0;
+  }
+
+  // the arrival count, read with acquire semantics (the other blocks' writes before
+  // their arrivals are visible to this block after the block barrier that follows)
+  __device__ __forceinline__ unsigned int acquire_count() const {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+    return v;
   }
 };
 
