@@ -79,7 +79,9 @@ def tune(grid, iters: int = 40, use_cache: bool = True, cache_path: str | None =
 
 
 def _time_shapes(grid, iters, p, saved, times):
-    """us per PCG iteration of every launch shape, into times."""
+    """us per PCG iteration of every launch shape, into times.  Each includes its share
+    of the defect correction's x += e (one per inner solve): the streaming form does it
+    at the end of its own launch, the others in a launch of their own."""
     for pe, sa, sb in SHAPES:
         if pe and sa > 1 and grid.spec.B != 16:
             continue
@@ -95,10 +97,12 @@ def _time_shapes(grid, iters, p, saved, times):
         ta, na = prof["cg_a"]
         tb, nb = prof["cg_b"]
         tp, npc = prof["pcg"]
+        tc, nc = prof.get("add_correction", (0.0, 0))
+        corr = tc / (nc * iters) if nc else 0.0
         if pe and npc:
-            times[f"{pe},{sa},{sb}"] = 1e3 * tp / (npc * iters)
+            times[f"{pe},{sa},{sb}"] = 1e3 * (tp / (npc * iters) + corr)
         elif na and nb:
-            times[f"{pe},{sa},{sb}"] = 1e3 * (ta / na + tb / nb)
+            times[f"{pe},{sa},{sb}"] = 1e3 * (ta / na + tb / nb + corr)
 
 
 STENCIL_SLABS = (1, 2, 4)

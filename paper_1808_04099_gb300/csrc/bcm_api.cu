@@ -1053,12 +1053,15 @@ bcm_status solve(bcm_grid* g, double rtol, int max_iter) {
       return read_err(g);
     }
     // defect correction: cycles are issued in batches; a finished sim makes every
-    // kernel of a later cycle return at once, so the host reads the flags rarely
+    // kernel of a later cycle return at once, so the host reads the flags rarely.  The
+    // streaming form adds its correction to the FP64 iterate itself.
+    SolveParams pin = prm;
+    pin.x64_add = x.f.p;
     int cycles = 0, batch = 2;
     while (cycles < g->max_cycles) {
       for (int b = 0; b < batch && cycles < g->max_cycles; ++b, ++cycles) {
-        RUN(BCM_K_PCG, launch_pcg(x, prm, &g->pcg_form));
-        RUN(BCM_K_ADD_CORRECTION, launch_add_correction(x));
+        RUN(BCM_K_PCG, launch_pcg(x, pin, &g->pcg_form));
+        if (g->pcg_form != PCG_STREAMING) RUN(BCM_K_ADD_CORRECTION, launch_add_correction(x));
         RUN(BCM_K_RESIDUAL, launch_residual(x, prm));
       }
       if ((st = read_flags(g, flags)) != BCM_OK) return st;
@@ -1397,9 +1400,11 @@ bcm_status issue_graph_step(bcm_grid* g, cudaStream_t s, double rtol, int max_it
     CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
   } else {
     CUDA_TRY(launch_residual(x, prm));
+    SolveParams pin = prm;  // the streaming form adds its correction itself
+    pin.x64_add = x.f.p;
     for (int c = 0; c < cycles; ++c) {
-      CUDA_TRY(launch_pcg(x, prm, &g->pcg_form));
-      CUDA_TRY(launch_add_correction(x));
+      CUDA_TRY(launch_pcg(x, pin, &g->pcg_form));
+      if (g->pcg_form != PCG_STREAMING) CUDA_TRY(launch_add_correction(x));
       CUDA_TRY(launch_residual(x, prm));
     }
   }

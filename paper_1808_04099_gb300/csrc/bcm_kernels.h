@@ -59,6 +59,10 @@ struct SolveParams {
   // multigrid PCG inside a captured step: body executions of the inner and the outer
   // loop, counted on the device for the launch count ([0], [1]; cumulative)
   unsigned int* body_count;
+  // mixed mode, streaming persistent PCG: the FP64 iterate the kernel adds its FP32
+  // correction e to at the end of the inner solve (x64 += e, the defect correction's
+  // update; the separate k_add_correction launch is then left out), or NULL
+  double* x64_add;
 };
 
 // Geometric multigrid preconditioner (single-level grids): per-cube levels

@@ -84,6 +84,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   GridBarrier gb;
   gb.init(bar, err, prm.barrier_timeout_ns);
+  bool failed = false;
   int k = 0;
   for (;; ++k) {
     // ---- decisions for iteration k (identical in every block): warp w takes sims w,
@@ -246,7 +247,10 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       }
     }
     if (psim >= 0) flush_pq();
-    if (!gb.sync()) break;
+    if (!gb.sync()) {
+      failed = true;
+      break;
+    }
     // ---- alpha per sim from the completed <p, q>
     for (int s = warp; s < nsim; s += NW) {
       if (s_done[s]) continue;
@@ -323,7 +327,31 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       }
     }
     if (psim >= 0) flush_rz();
-    if (!gb.sync()) break;
+    if (!gb.sync()) {
+      failed = true;
+      break;
+    }
+  }
+  // mixed mode: the defect correction's x64 += e on the block's own cells of sims still
+  // correcting (the same update as k_add_correction; each cell has one owner and no
+  // block reads x64 before the residual kernel that follows)
+  if constexpr (sizeof(TX) == 4) {
+    if (!failed && prm.x64_add) {
+      for (int it = 0; it < nitems; ++it) {
+        const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
+        if (g.ss[sim_of(c)].outer_done) continue;
+        const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
+        for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
+          double xv[4];
+          TX ev[4];
+          ld4(prm.x64_add + base + 4 * q4, xv);
+          ld4(x + base + 4 * q4, ev);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) xv[m] += double(ev[m]);
+          st4(prm.x64_add + base + 4 * q4, xv);
+        }
+      }
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) g.flags[0] = 1;
 }

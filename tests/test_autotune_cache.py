@@ -24,8 +24,9 @@ class FakeGrid:
     """The grid calls the tuner makes; solve_pressure_iters 'runs' for the table's time
     of the current shape (us per iteration) and records the call."""
 
-    def __init__(self, table, B=16, precision=bcm.PREC_F32_REFINE):
+    def __init__(self, table, B=16, precision=bcm.PREC_F32_REFINE, corr_us=0.0):
         self.spec = FakeSpec(B, 1024)
+        self.corr_us = corr_us  # the x += e launch after every form but the streaming one
         self.precision = precision
         self.device = "cpu"
         self.table = table
@@ -69,6 +70,8 @@ class FakeGrid:
         else:  # two launches per iteration, split evenly
             n = self.last_iters
             prof = {"pcg": (0.0, 0), "cg_a": (0.5 * ms, n), "cg_b": (0.5 * ms, n)}
+        if self.corr_us and self.shape[0] != 1:
+            prof["add_correction"] = (1e-3 * self.corr_us * self.last_iters, 1)
         return prof, 0
 
 
@@ -103,6 +106,15 @@ def test_tunes_writes_cache_and_reuses_it(tmp_path):
     autotune.tune(g3, iters=5, cache_path=cache, device_name="other")
     assert g3.shape == (0, 1, 2) and g3.solves > 0
     assert len(json.load(open(cache))) == 2
+
+
+def test_the_correction_launch_is_charged_to_the_forms_that_need_it():
+    t = table((0, 1, 1))
+    t[(0, 1, 1)], t[(1, 1, 1)] = 9.0, 10.0  # streaming: its x += e inside the launch
+    g = FakeGrid(t, corr_us=2.0)
+    times = autotune.tune(g, iters=5, use_cache=False)
+    assert times["0,1,1"] == pytest.approx(11.0) and times["1,1,1"] == pytest.approx(10.0)
+    assert g.shape == (1, 1, 1)
 
 
 def test_fp64_and_small_cubes_skip_the_shapes_they_cannot_run(tmp_path):
