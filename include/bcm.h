@@ -365,8 +365,10 @@ bcm_status bcm_set_momentum_scheme(bcm_grid *grid, int scheme, double cn_rtol, i
  *   argument or field, capacity below the stream), BCM_E_BOUNDS (a coefficient / step
  *   beyond 2^30).
  * bcm_decompress_field: decodes a stream of this grid (same B and cube count) into the
- *   field (rounded to its storage type).  Errors: BCM_E_INVALID (not such a stream, a
- *   malformed record: the field is then undefined).  Synchronises. */
+ *   field (rounded to its storage type); bits of a record after its first B^3 codes
+ *   are ignored.  Errors: BCM_E_INVALID (not such a stream, a malformed record such as
+ *   one whose B^3 codes do not fit in its bit count: the field is then undefined).
+ *   Synchronises (it reads the header and the record sizes to the host). */
 size_t bcm_compress_bound(const bcm_grid *grid);
 bcm_status bcm_compress_field(bcm_grid *grid, int field, double step, void *dev_stream,
                               size_t capacity, size_t *stream_bytes);

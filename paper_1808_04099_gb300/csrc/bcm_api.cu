@@ -1711,18 +1711,22 @@ extern "C" bcm_status bcm_decompress_field(bcm_grid* g, int field, const void* d
   if (st != BCM_OK) return st;
   const size_t words = bytes / 4, nc = (size_t)g->desc.n_cubes;
   if (words < 8 + nc) return fail(BCM_E_INVALID, "stream shorter than its header");
-  uint32_t head[8];
-  CUDA_TRY(cudaMemcpyAsync(head, dev_stream, sizeof head, cudaMemcpyDeviceToHost, g->stream));
+  // the header and the record-size table: the decoder stages the largest record
+  std::vector<uint32_t> head(8 + nc);
+  CUDA_TRY(cudaMemcpyAsync(head.data(), dev_stream, head.size() * 4, cudaMemcpyDeviceToHost,
+                           g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  uint32_t max_payload = 0;
+  for (size_t c = 0; c < nc; ++c) max_payload = std::max(max_payload, head[8 + c] ? head[8 + c] - 1 : 0u);
   double step;
-  memcpy(&step, head + 6, sizeof step);
+  memcpy(&step, head.data() + 6, sizeof step);
   if (head[0] != 0x57434d42u || head[1] != 1u || head[2] != (uint32_t)g->B ||
       head[3] != (uint32_t)nc || !(step > 0))
     return fail(BCM_E_INVALID, "not a wavelet stream of this grid");
   const WavScratch s = wavelet_scratch(g);
   CUDA_TRY(cudaMemsetAsync(s.err, 0, sizeof(int), g->stream));
   RUN(BCM_K_MISC, launch_wavelet_decode(g->ctx, ptr, f64, (const uint32_t*)dev_stream, words,
-                                        step, s.off, s.err));
+                                        max_payload, step, s.off, s.err));
   g->launch_count += 1;
   int err = 0;
   CUDA_TRY(cudaMemcpyAsync(&err, s.err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));

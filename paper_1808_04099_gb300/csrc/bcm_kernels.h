@@ -176,8 +176,10 @@ cudaError_t launch_wavelet_analyze(const Ctx& x, const void* field, int f64, dou
 cudaError_t launch_wavelet_encode(const Ctx& x, const uint32_t* zc, const uint32_t* cube_nbits,
                                   const uint32_t* cube_k, const uint32_t* off, double step,
                                   uint32_t* out);
+// max_payload: the largest payload (words after a record's first) among the records
 cudaError_t launch_wavelet_decode(const Ctx& x, void* field, int f64, const uint32_t* in,
-                                  size_t words, double step, uint32_t* off, int* err);
+                                  size_t words, uint32_t max_payload, double step, uint32_t* off,
+                                  int* err);
 // test paths on FP64 arrays: out[q] = I[f] at particle q; out += P[F]
 cudaError_t launch_ib_interpolate(const Ctx& x, const double* f, double* out);
 cudaError_t launch_ib_spread(const Ctx& x, const double* F, double* out);

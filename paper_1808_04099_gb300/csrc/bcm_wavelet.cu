@@ -21,10 +21,13 @@
 // One block per cube: the cube sits in shared memory with rows padded to B + 1 doubles
 // (lines along x fall on different banks); a thread per line lifts it; a block scan of
 // the code lengths gives every thread's bit offset, and each code is written as one
-// <= 48-bit pattern OR-ed into at most three words of a zeroed stream.  Decoding reads
-// a record with one thread (a Rice stream has no entry points) and transforms back
-// with the block.
+// <= 48-bit pattern OR-ed into at most three words of a zeroed stream.  Decoding
+// stages a record in shared memory and splits its bits among the block's threads (a
+// Rice stream has no entry points: the threads find the code boundaries by
+// self-synchronisation, see k_wav_decode), then transforms back with the block.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 
@@ -255,53 +258,179 @@ __global__ __launch_bounds__(B * B) void k_wav_encode(const uint32_t* __restrict
   }
 }
 
-// decode one record (thread 0), dequantize, transform back, store the field
+// 64 bits of a staged record from bit p on (W: the record's payload words, then zero
+// words)
+__device__ __forceinline__ unsigned long long rice_window(const uint32_t* W, uint32_t p) {
+  const uint32_t i = p >> 5, sh = p & 31u;
+  const unsigned long long lo = (unsigned long long)W[i] | ((unsigned long long)W[i + 1] << 32);
+  return sh ? (lo >> sh) | ((unsigned long long)W[i + 2] << (64u - sh)) : lo;
+}
+
+// From the code starting at bit p (< lim): past that code, or past the whole run of
+// all-zero codes starting there (u = 0 and k zero bits: the value 0; the run is cut
+// after its last code that starts before lim, and at tgt when a code of the run starts
+// there).  Returns the codes passed; z is the value of a single code (0 for a run).
+// Rice with parameter k; 16 leading one-bits mark the escape, whose next 32 bits are z.
+__device__ __forceinline__ uint32_t rice_adv(const uint32_t* W, uint32_t& p, uint32_t lim, int k,
+                                             uint32_t& z, uint32_t tgt = 0) {
+  const unsigned long long win = rice_window(W, p);
+  const uint32_t len0 = (uint32_t)k + 1;
+  if ((win & ((2ull << k) - 1ull)) == 0) {
+    const uint32_t zeros = win ? (uint32_t)(__ffsll((long long)win) - 1) : 64u;
+    const uint32_t room = (lim - p + (uint32_t)k) / len0;  // codes starting before lim
+    uint32_t m = min(zeros / len0, room);                  // >= 1
+    if (tgt > p && (tgt - p) % len0 == 0 && (tgt - p) / len0 <= m) m = (tgt - p) / len0;
+    p += m * len0;
+    z = 0;
+    return m;
+  }
+  const uint32_t t = (uint32_t)__clzll((long long)__brevll(~win));  // leading one-bits
+  if (t < 16) {
+    z = (t << k) | (uint32_t)((win >> (t + 1)) & ((1ull << k) - 1ull));
+    p += t + len0;
+  } else {
+    z = (uint32_t)(win >> 16);
+    p += 48u;
+  }
+  return 1;
+}
+
+// The new path from ne against the old one from e (which ended at x after n codes)
+// through a segment ending at s1, the one behind first; a run of zero codes stops
+// where the other path stands only when one of its codes starts there (two paths out
+// of step cross a run in one step each).  Where they meet the old path stands; else
+// the new one runs to the segment's end.  Returns whether the exit x moved.
+__device__ __forceinline__ bool rice_rewalk(const uint32_t* W, int k, uint32_t s1, uint32_t ne,
+                                            uint32_t e, uint32_t& x, uint32_t& n) {
+  uint32_t pn = ne, po = e, cn = 0, co = 0, z;
+  while (true) {
+    if (pn >= s1) {  // left the segment without meeting the old path
+      const bool moved = pn != x;
+      x = pn;
+      n = cn;
+      return moved;
+    }
+    if (pn == po) {  // in step: the rest of the old path stands
+      n = cn + (n - co);
+      return false;
+    }
+    if (po < pn)
+      co += rice_adv(W, po, s1, k, z, pn);
+    else
+      cn += rice_adv(W, pn, s1, k, z, po);
+  }
+}
+
+// Entries of a warp's segments: its first lane enters at went, every other lane at the
+// exit of the lane before it; a lane whose entry moved re-walks, until no entry moves
+// (one lane more is exact per pass).
+__device__ __forceinline__ void rice_warp_entries(const uint32_t* W, int k, uint32_t s1,
+                                                  uint32_t went, unsigned mask, int lane,
+                                                  uint32_t& e, uint32_t& x, uint32_t& n) {
+  for (int pass = 0; pass <= 32; ++pass) {
+    const uint32_t px = __shfl_up_sync(mask, x, 1);
+    const uint32_t ne = lane == 0 ? went : px;
+    if (!__any_sync(mask, ne != e)) return;
+    if (ne != e) {
+      rice_rewalk(W, k, s1, ne, e, x, n);
+      e = ne;
+    }
+  }
+}
+
+// decode one record with the block, dequantize, transform back, store the field.
+// The record's bits are cut into one segment per thread.  Each thread decodes its
+// segment from the segment's first bit as if a code started there; a prefix code falls
+// back into step with the true code boundaries after a few codes (the self-
+// synchronisation used for parallel Huffman decoding by Klein and Wiseman, 2003).  The
+// true entry of a segment is the exit of the one before it: each warp first settles
+// the entries of its lanes from its first lane's (shuffles, no block barrier), then
+// block rounds hand every warp the exit of the warp before it and the warps whose
+// entry moved settle again.  A thread whose entry moved re-walks from it only until the
+// new path meets its old one.  Thread 0 starts at bit 0, so after block round r the
+// first r + 2 warps are exact.  Runs of all-zero codes, which keep a path out of step
+// for as long as they last, are passed in one step each.  An exclusive scan of the
+// code counts gives each segment its first index.  Results equal a sequential decode:
+// codes past the B^3-th are ignored, and a record whose B^3 codes do not fit in its bit
+// count is malformed (error bit 2, its values from the first code that does not fit
+// are 0).
 template <int B, class T>
 __global__ __launch_bounds__(B * B) void k_wav_decode(const uint32_t* __restrict__ in,
                                                       const uint32_t* __restrict__ off,
-                                                      size_t words, double step,
+                                                      size_t words, uint32_t wcap, double step,
                                                       T* __restrict__ f, int* __restrict__ err) {
-  constexpr int NT = B * B, B3 = B * B * B;
+  constexpr int NT = B * B, B3 = B * B * B, WS = NT < 32 ? NT : 32, NW = NT / WS;
+  constexpr unsigned kMask = WS == 32 ? 0xffffffffu : (1u << WS) - 1u;
+  constexpr uint32_t kMaxBits = 48u * B3;  // B^3 codes never need more
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* X = reinterpret_cast<double*>(smem_raw);
-  const int c = blockIdx.x;
-  if (threadIdx.x == 0) {
-    const size_t rec = off[c], cw = in[kHead + c];
+  uint32_t* W = reinterpret_cast<uint32_t*>(X + B * B * (B + 1));
+  __shared__ uint32_t s_wexit[NW], s_cnt[NT];
+  __shared__ uint32_t s_head[3];  // bad, k, bit count
+  const int c = blockIdx.x, t = threadIdx.x, lane = t % WS, warp = t / WS;
+  const size_t rec = off[c];
+  if (t == 0) {
+    const size_t cw = in[kHead + c];
     bool bad = cw < 1 || rec + cw > words;
     const uint32_t head = bad ? 0u : in[rec];
-    const int k = (int)(head & 31u);
-    const unsigned long long nbits = head >> 5;
-    bad = bad || k > 24 || (nbits + 31) / 32 + 1 > cw;
-    const uint32_t* w = in + rec + 1;
-    unsigned long long b = 0;
-    for (int q = 0; q < B3; ++q) {
-      uint32_t u = 0, z = 0;
-      if (!bad) {
-        while (u < 16 && b < nbits && ((w[b >> 5] >> (b & 31)) & 1u)) {
-          ++u;
-          ++b;
-        }
-        // every read stays below nbits, hence inside the record
-        if (u < 16) {
-          if (b + 1 + (unsigned long long)k > nbits) {
-            bad = true;
-          } else {
-            ++b;
-            uint32_t r = 0;
-            for (int e = 0; e < k; ++e, ++b) r |= ((w[b >> 5] >> (b & 31)) & 1u) << e;
-            z = (u << k) | r;
-          }
-        } else if (b + 32 > nbits) {
-          bad = true;
-        } else {
-          for (int e = 0; e < 32; ++e, ++b) z |= ((w[b >> 5] >> (b & 31)) & 1u) << e;
-        }
-      }
-      X[tix<B>(q % B, (q / B) % B, q / (B * B))] =
-          bad ? 0.0 : __dmul_rn((double)unzigzag(z), step);
-    }
-    if (bad) atomicOr(err, 2);
+    const uint32_t nbits = head >> 5;
+    const uint32_t nb = nbits < kMaxBits ? nbits : kMaxBits;
+    bad = bad || (head & 31u) > 24u || ((size_t)nbits + 31) / 32 + 1 > cw || (nb + 31) / 32 > wcap;
+    s_head[0] = bad;
+    s_head[1] = head & 31u;
+    s_head[2] = nbits;
   }
+  // every value 0 until a code says otherwise (the codes of value 0 write nothing)
+  for (int q = t; q < B3; q += NT) X[tix<B>(q % B, (q / B) % B, q / (B * B))] = 0.0;
+  __syncthreads();
+  const int k = (int)s_head[1];
+  const uint32_t nbits = s_head[2], nb = nbits < kMaxBits ? nbits : kMaxBits;
+  uint32_t valid = 0;
+  if (!s_head[0]) {
+    const uint32_t nw = (nb + 31) / 32;  // <= the record's payload words and wcap
+    for (uint32_t q = t; q < nw + 3; q += NT) W[q] = q < nw ? in[rec + 1 + q] : 0u;
+    __syncthreads();
+    const uint32_t s0 = (uint32_t)((unsigned long long)nb * t / NT);
+    const uint32_t s1 = (uint32_t)((unsigned long long)nb * (t + 1) / NT);
+    uint32_t e = s0, x = s0, n = 0, z;
+    while (x < s1) n += rice_adv(W, x, s1, k, z);
+    // the warp's lanes from its first lane's speculative entry
+    rice_warp_entries(W, k, s1, __shfl_sync(kMask, e, 0), kMask, lane, e, x, n);
+    if (lane == WS - 1) s_wexit[warp] = x;
+    __syncthreads();
+    for (int round = 0; round <= NW; ++round) {
+      const uint32_t went = warp ? s_wexit[warp - 1] : 0u;
+      __syncthreads();
+      rice_warp_entries(W, k, s1, went, kMask, lane, e, x, n);
+      bool moved = false;
+      if (lane == WS - 1 && x != s_wexit[warp]) {
+        s_wexit[warp] = x;
+        moved = true;
+      }
+      if (!__syncthreads_or(moved)) break;
+    }
+    // first index of each segment: exclusive scan of the counts
+    s_cnt[t] = n;
+    __syncthreads();
+    for (int o = 1; o < NT; o <<= 1) {
+      const uint32_t add = t >= o ? s_cnt[t - o] : 0u;
+      __syncthreads();
+      s_cnt[t] += add;
+      __syncthreads();
+    }
+    const uint32_t total = s_cnt[NT - 1];
+    // the path's last code runs past the bit count when the last exit lies beyond it
+    const uint32_t fit = total - (s_wexit[NW - 1] > nbits ? 1u : 0u);
+    valid = fit < (uint32_t)B3 ? fit : (uint32_t)B3;
+    uint32_t idx = s_cnt[t] - n, p = e;
+    while (p < s1) {
+      const uint32_t m = rice_adv(W, p, s1, k, z);
+      if (z != 0 && idx < valid)  // a single code (m = 1)
+        X[tix<B>(idx % B, (idx / B) % B, idx / (B * B))] = __dmul_rn((double)unzigzag(z), step);
+      idx += m;
+    }
+  }
+  if (t == 0 && valid < (uint32_t)B3) atomicOr(err, 2);
   __syncthreads();
   for (int m = 2; m <= B; m *= 2)
     for (int d = 2; d >= 0; --d) {
@@ -314,6 +443,10 @@ __global__ __launch_bounds__(B * B) void k_wav_decode(const uint32_t* __restrict
 
 template <int B>
 constexpr size_t wav_smem() { return sizeof(double) * B * B * (B + 1); }
+// the decoder also stages a record: wcap payload words (at most 48 B^3 bits, all B^3
+// codes can use) and three zero words
+template <int B>
+size_t wav_dec_smem(uint32_t wcap) { return wav_smem<B>() + 4 * ((size_t)wcap + 3); }
 
 template <class K>
 cudaError_t wav_allow(K kern, size_t bytes) {
@@ -335,12 +468,14 @@ cudaError_t compress_t(const Ctx& x, const void* field, double step, uint32_t* z
 
 template <int B, class T>
 cudaError_t decompress_t(const Ctx& x, void* field, const uint32_t* in, size_t words,
-                         double step, uint32_t* off, int* err) {
+                         uint32_t max_payload, double step, uint32_t* off, int* err) {
   k_wav_offsets<<<1, 1024, 0, x.stream>>>(nullptr, in + kHead, x.g.n_cubes, off);
   auto kd = k_wav_decode<B, T>;
-  cudaError_t e = wav_allow(kd, wav_smem<B>());
+  const uint32_t wcap = std::min<uint32_t>(max_payload, 48u * B * B * B / 32u);
+  const size_t sm = wav_dec_smem<B>(wcap);
+  cudaError_t e = wav_allow(kd, sm);
   if (e != cudaSuccess) return e;
-  kd<<<x.g.n_cubes, B * B, wav_smem<B>(), x.stream>>>(in, off, words, step, (T*)field, err);
+  kd<<<x.g.n_cubes, B * B, sm, x.stream>>>(in, off, words, wcap, step, (T*)field, err);
   return cudaGetLastError();
 }
 
@@ -383,8 +518,9 @@ cudaError_t launch_wavelet_encode(const Ctx& x, const uint32_t* zc, const uint32
 }
 
 cudaError_t launch_wavelet_decode(const Ctx& x, void* field, int f64, const uint32_t* in,
-                                  size_t words, double step, uint32_t* off, int* err) {
-  BCM_WAV_DISPATCH(decompress_t, x, field, in, words, step, off, err)
+                                  size_t words, uint32_t max_payload, double step, uint32_t* off,
+                                  int* err) {
+  BCM_WAV_DISPATCH(decompress_t, x, field, in, words, max_payload, step, off, err)
 }
 
 }  // namespace bcm

@@ -94,3 +94,80 @@ def test_full_size_sphere_streams_match_oracle():
         step = 1e-4 * np.abs(f).max()
         s = g.compress_field(fid, step).cpu().numpy().view(np.uint32)
         assert np.array_equal(s, O.wavelet_compress(f, spec.B, step))
+
+
+def rice_bits(zs, k):
+    """LSB-first bits of the codes of values zs with Rice parameter k (the stream format
+    of the compressor: u < 16 one-bits, a zero-bit, the k low bits; else 16 one-bits and
+    the 32 bits of z)."""
+    bits = []
+    for z in zs:
+        u = int(z) >> k
+        if u < 16:
+            bits += [1] * u + [0] + [(int(z) >> e) & 1 for e in range(k)]
+        else:
+            bits += [1] * 16 + [(int(z) >> e) & 1 for e in range(32)]
+    return bits
+
+
+def crafted_stream(B, records, step):
+    """A stream of the compressor's layout from (k, bits, nbits) per cube."""
+    sb = np.array([step], np.float64).view(np.uint32)
+    head = [0x57434d42, 1, B, len(records), 0, 0, int(sb[0]), int(sb[1])]
+    sizes, body = [], []
+    for k, bits, nbits in records:
+        w = np.zeros((len(bits) + 31) // 32, np.uint64)
+        for i, b in enumerate(bits):
+            w[i >> 5] |= np.uint64(b) << np.uint64(i & 31)
+        sizes.append(1 + w.size)
+        body += [k | (nbits << 5)] + [int(v) for v in w]
+    return np.array(head + sizes + body, np.uint32)
+
+
+def crafted_records(B, n_cubes, seed):
+    """Records the encoder would not write but a decoder must read as the format says:
+    a parameter of 1 with every value 0 (a code boundary every second bit, so a decode
+    started at an odd bit never falls into step), values that mostly escape, the
+    largest parameter, geometric values, and trailing bits past what B^3 codes can use
+    (beyond 48 B^3 bits)."""
+    rng = np.random.default_rng(seed)
+    B3 = B ** 3
+    recs = []
+    for c in range(n_cubes):
+        kind = (c + seed) % 5
+        if kind == 0:
+            k, zs = 1, np.zeros(B3, np.int64)
+        elif kind == 1:
+            k, zs = 0, rng.integers(0, 2 ** 32, B3)
+        elif kind == 2:
+            k, zs = 24, rng.integers(0, 2 ** 29, B3)
+        else:
+            k = int(rng.integers(0, 8))
+            zs = np.minimum(rng.geometric(1.0 / (2 ** k + 1), B3) - 1, 2 ** 32 - 1)
+        bits = rice_bits(zs, k)
+        if kind == 4:
+            bits += list(rng.integers(0, 2, 48 * B3 + 77))
+        recs.append((k, bits, len(bits)))
+    return recs
+
+
+@pytest.mark.parametrize("name", ["sphere_B8", "sphere_B16"])
+def test_crafted_records_decode_as_the_oracle(name):
+    """Block-parallel decoding of records whose code boundaries are hard to find equals
+    the oracle's sequential decoder bit for bit, and a record cut one bit short is
+    malformed on both sides."""
+    spec = GRIDS[name]()
+    g = bcm.Grid(spec, bcm.PREC_F64)
+    for seed in range(5):  # every kind of record in every cube
+        recs = crafted_records(spec.B, spec.n_cubes, seed)
+        s = crafted_stream(spec.B, recs, 0.37)
+        want = O.wavelet_decompress(s)
+        g.decompress_field(bcm.P, torch.from_numpy(s.view(np.int32)))
+        assert np.array_equal(g.numpy(bcm.P), want), seed
+    k1, bits1, nb1 = recs[1]  # seed 4: cube 1 holds the all-zero record, no spare bits
+    short = crafted_stream(spec.B, recs[:1] + [(k1, bits1, nb1 - 1)] + recs[2:], 0.37)
+    with pytest.raises(ValueError):
+        O.wavelet_decompress(short)
+    with pytest.raises(bcm.BCMError) as ei:
+        g.decompress_field(bcm.P, torch.from_numpy(short.view(np.int32)))
+    assert ei.value.status == bcm.BCM_E_INVALID
