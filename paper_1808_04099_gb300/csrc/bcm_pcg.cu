@@ -48,7 +48,8 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
   double* s_alpha = reinterpret_cast<double*>(smem_raw + (sizeof(TV) * SL::N + 15) / 16 * 16);
   double* s_beta = s_alpha + nsim;
   double* s_rz = s_beta + nsim;
-  unsigned char* s_done = reinterpret_cast<unsigned char*>(s_rz + nsim);
+  int* s_kdone = reinterpret_cast<int*>(s_rz + nsim);  // iterations this launch ran
+  unsigned char* s_done = reinterpret_cast<unsigned char*>(s_kdone + nsim);
   unsigned char* s_first = s_done + nsim;  // restart with p = z at iteration 0
   unsigned char* s_poff = s_first + nsim;  // search-direction buffer offset
   const bool inner = prm.mixed != 0;
@@ -64,6 +65,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
     const bool cont = st.cont != 0;
     s_rz[s] = cont ? st.rz_last : st.rz;
     s_done[s] = st.done ? 1 : 0;
+    s_kdone[s] = 0;
     s_first[s] = cont ? 0 : 1;
     s_poff[s] = cont ? (unsigned char)(st.p_off & 1) : 0;
   }
@@ -105,6 +107,7 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       const bool bad = !isfinite(rr) || !isfinite(rz);
       if (bad || rr <= tol2 || k >= kmax) {
         s_done[s] = 1;
+        s_kdone[s] = k;
         if (blockIdx.x == 0) {  // single writer of the solve's results
           st.iter = k;
           st.total_iters += k;
@@ -165,11 +168,21 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       const int pb = (k + s_poff[s]) & 1;
       const TV* __restrict__ pold = pb ? p1 : p0;
       TV* __restrict__ pnew = pb ? p0 : p1;
+      // x += alpha p of the previous iteration, on this item's own cells as their p is
+      // staged (pass B leaves it; every later iteration of the sim comes through here)
+      const TV alpha_prev = TV(s_alpha[s]);
       auto val4 = [&](int cube, int cell0, int face, TV (&v)[4]) {
         const size_t gi = (size_t)cube * B3 + cell0;
         TV rr4[4], pp[4] = {TV(0), TV(0), TV(0), TV(0)};
         ld4(r + gi, rr4);
         if (!first) ld4(pold + gi, pp);
+        if (k > 0 && face < 0 && (unsigned)(cell0 - z0 * BB) < (unsigned)(KS * BB)) {
+          TX xv[4];
+          ld4(x + gi, xv);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) xv[m] = xv[m] + alpha_prev * pp[m];
+          st4(x + gi, xv);
+        }
         const int mask = face < 0 ? cs.smask : cs.nbmask[face];
         if (mask == 0) {  // every face of that cube has the same-level weight
           const TV inv = cs.invtab[18];
@@ -288,41 +301,45 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       const CubeSh<TV>& cs = csa[cached ? c - cA : 0];
       const TV alpha = TV(s_alpha[s]);
       const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
-      const TV* __restrict__ pnew = ((k + s_poff[s]) & 1) ? p0 : p1;
       const bool plain = cs.smask == 0;
-      auto update = [&](int q4, TV (&xv)[4], const TV (&pv)[4], TV (&rv)[4], const TV (&qv)[4]) {
+      auto update = [&](int q4, TV (&rv)[4], const TV (&qv)[4]) {
         const int cell = 4 * q4, kk = cell / BB, j = (cell / B) % B, i0 = cell % B;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          xv[e] = xv[e] + alpha * pv[e];
           rv[e] = rv[e] - alpha * qv[e];
           const TV inv = plain ? cs.invtab[18] : cs.invtab[s3_of<B>(cs.w3, i0 + e, j, z0 + kk)];
           const TV z = rv[e] * inv;
           rz += rv[e] * z;
           rr += rv[e] * rv[e];
         }
-        st4(x + base + cell, xv);
         st4(r + base + cell, rv);
       };
-      // FP32: two quads per step, all eight loads in flight before any use
-      constexpr int NQ = KS * BB / 4, STEP = sizeof(TV) == 4 ? 2 : 1;
+      // FP32: four quads per step, all their loads in flight before any use
+      constexpr int NQ = KS * BB / 4, STEP = sizeof(TV) == 4 ? 4 : 1;
       for (int q4 = threadIdx.x; q4 < NQ; q4 += STEP * NT) {
-        TV xa[4], pa[4], ra[4], qa[4];
-        ld4(x + base + 4 * q4, xa);
-        ld4(pnew + base + 4 * q4, pa);
+        TV ra[4], qa[4];
         ld4(r + base + 4 * q4, ra);
         ld4(q + base + 4 * q4, qa);
-        if (STEP == 2 && q4 + NT < NQ) {
-          const int qb4 = q4 + NT;
-          TV xb[4], pbv[4], rb[4], qb[4];
-          ld4(x + base + 4 * qb4, xb);
-          ld4(pnew + base + 4 * qb4, pbv);
-          ld4(r + base + 4 * qb4, rb);
-          ld4(q + base + 4 * qb4, qb);
-          update(q4, xa, pa, ra, qa);
-          update(qb4, xb, pbv, rb, qb);
+        if (STEP == 4 && q4 + 3 * NT < NQ) {
+          TV rb[4], qb[4], rc[4], qc[4], rd[4], qd[4];
+          ld4(r + base + 4 * (q4 + NT), rb);
+          ld4(q + base + 4 * (q4 + NT), qb);
+          ld4(r + base + 4 * (q4 + 2 * NT), rc);
+          ld4(q + base + 4 * (q4 + 2 * NT), qc);
+          ld4(r + base + 4 * (q4 + 3 * NT), rd);
+          ld4(q + base + 4 * (q4 + 3 * NT), qd);
+          update(q4, ra, qa);
+          update(q4 + NT, rb, qb);
+          update(q4 + 2 * NT, rc, qc);
+          update(q4 + 3 * NT, rd, qd);
         } else {
-          update(q4, xa, pa, ra, qa);
+          update(q4, ra, qa);
+          for (int u = 1; u < STEP && q4 + u * NT < NQ; ++u) {
+            TV rb[4], qb[4];
+            ld4(r + base + 4 * (q4 + u * NT), rb);
+            ld4(q + base + 4 * (q4 + u * NT), qb);
+            update(q4 + u * NT, rb, qb);
+          }
         }
       }
     }
@@ -332,23 +349,38 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
       break;
     }
   }
-  // mixed mode: the defect correction's x64 += e on the block's own cells of sims still
-  // correcting (the same update as k_add_correction; each cell has one owner and no
-  // block reads x64 before the residual kernel that follows)
-  if constexpr (sizeof(TX) == 4) {
-    if (!failed && prm.x64_add) {
-      for (int it = 0; it < nitems; ++it) {
-        const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
-        if (g.ss[sim_of(c)].outer_done) continue;
-        const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
-        for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
-          double xv[4];
-          TX ev[4];
-          ld4(prm.x64_add + base + 4 * q4, xv);
-          ld4(x + base + 4 * q4, ev);
+  // the last iteration's x += alpha p, on the block's own cells of sims that ran one in
+  // this launch; in mixed mode also the defect correction's x64 += e on the cells of
+  // sims still correcting (the same update as k_add_correction; each cell has one
+  // owner and no block reads x64 before the residual kernel that follows)
+  if (!failed) {
+    for (int it = 0; it < nitems; ++it) {
+      const int item = item0 + it, c = item / NSL, z0 = (item - c * NSL) * KS;
+      const int s = sim_of(c), kd = s_kdone[s];
+      bool add64 = false;
+      if constexpr (sizeof(TX) == 4) add64 = prm.x64_add && !g.ss[s].outer_done;
+      if (kd == 0 && !add64) continue;
+      const TV alpha = TV(s_alpha[s]);
+      const TV* __restrict__ plast = ((kd - 1 + s_poff[s]) & 1) ? p0 : p1;
+      const size_t base = (size_t)c * B3 + (size_t)z0 * BB;
+      for (int q4 = threadIdx.x; q4 < KS * BB / 4; q4 += NT) {
+        TX ev[4];
+        ld4(x + base + 4 * q4, ev);
+        if (kd > 0) {
+          TV pv[4];
+          ld4(plast + base + 4 * q4, pv);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) xv[m] += double(ev[m]);
-          st4(prm.x64_add + base + 4 * q4, xv);
+          for (int m = 0; m < 4; ++m) ev[m] = ev[m] + alpha * pv[m];
+          st4(x + base + 4 * q4, ev);
+        }
+        if constexpr (sizeof(TX) == 4) {
+          if (add64) {
+            double xv[4];
+            ld4(prm.x64_add + base + 4 * q4, xv);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xv[m] += double(ev[m]);
+            st4(prm.x64_add + base + 4 * q4, xv);
+          }
         }
       }
     }
@@ -361,9 +393,10 @@ __global__ __launch_bounds__(NT, 4) void k_pcg(DevGrid g, TX* __restrict__ x, TV
 template <int B, int KS, class TV, class TX>
 static cudaError_t pcg_t(const Ctx& x, const SolveParams& prm, TX* xv) {
   constexpr int NT = pcg_threads<B>();
-  // tile (16-byte multiple) + alpha, beta, rz (FP64), done, first, p_off (bytes)
+  // tile (16-byte multiple) + alpha, beta, rz (FP64), iterations run (int), done,
+  // first, p_off (bytes)
   const size_t tile = (sizeof(TV) * Slab<B, KS>::N + 15) / 16 * 16;
-  const size_t sm = tile + (size_t)x.g.n_sims * (3 * sizeof(double) + 3);
+  const size_t sm = tile + (size_t)x.g.n_sims * (3 * sizeof(double) + sizeof(int) + 3);
   auto kern = k_pcg<B, KS, NT, TV, TX>;
   {
     const cudaError_t e = allow_dynamic_smem(kern, sm);
