@@ -5,8 +5,10 @@
 // paper's load-balanced linear distribution (Eq. loaddist: L = floor(N/P), R = N mod P,
 // n_p = floor((N + P - p - 1) / P)), so Z-ordered neighbours mostly share a block, and
 // keeps the constants of its cubes in shared memory for the whole solve.  Each
-// iteration is pass A (p = z + beta p, q = K p, <p,q>), a grid barrier, pass B
-// (x += alpha p, r -= alpha q, <r,z>, <r,r>), and a second grid barrier.
+// iteration is pass A (p = z + beta p, q = K p, <p,q>, and the previous iteration's
+// x += alpha p on the own cells while their old p is staged), a grid barrier, pass B
+// (r -= alpha q, <r,z>, <r,r>), and a second grid barrier; the last iteration's
+// x += alpha p runs at the launch's exit.
 //
 // The per-sim scalars never need a single writer: the dot products go to striped
 // accumulators in three rotating slots (iteration k mod 3), and after each barrier

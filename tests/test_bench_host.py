@@ -15,9 +15,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_byte_model():
     assert bench.bytes_per_cell("pcg", False, 0.0) == 24      # 6 FP32 values per cell
     assert bench.bytes_per_cell("pcg", True, 0.0) == 48
-    # the two-pass schedule moves 10 values: the two passes of one iteration
+    # the two-launch schedule moves 10 values: the two passes of one iteration
     assert bench.bytes_per_cell("cg_a", False, 0.0) + bench.bytes_per_cell("cg_b", False, 0.0) \
-        == bench.pcg_schedule_bytes(1, False) == 40
+        == bench.pcg_schedule_bytes(0, False) == 40
+    # the streaming form: x += alpha p moved into pass A's staging of p saves p's reread
+    assert bench.pcg_schedule_bytes(1, False) == 36
     # the fused single-barrier form: x, r, p in and out (q recomputed) plus the face planes
     assert bench.pcg_schedule_bytes(5, False) == 6 * 4 + 3 * 0.375 * 4
     assert bench.bytes_per_cell("momentum", False, 0.5) == 12 * 4 + 0.5 * 4
