@@ -151,11 +151,11 @@ def crafted_records(B, n_cubes, seed):
     return recs
 
 
-@pytest.mark.parametrize("name", ["sphere_B8", "sphere_B16"])
+@pytest.mark.parametrize("name", ["cavity_B4", "sphere_B8", "sphere_B16"])
 def test_crafted_records_decode_as_the_oracle(name):
     """Block-parallel decoding of records whose code boundaries are hard to find equals
-    the oracle's sequential decoder bit for bit, and a record cut one bit short is
-    malformed on both sides."""
+    the oracle's sequential decoder bit for bit (4^3 cubes: one partial warp per
+    block), and a record cut one bit short is malformed on both sides."""
     spec = GRIDS[name]()
     g = bcm.Grid(spec, bcm.PREC_F64)
     for seed in range(5):  # every kind of record in every cube
