@@ -223,7 +223,9 @@ bcm_status bcm_get_solver(const bcm_grid *grid, double *inner_rtol, int32_t *max
  * r, p, x and its neighbours' face planes staged by bulk asynchronous copies two cubes
  * ahead; grids it does not fit run persistent = 1.  persistent = 1: every PCG solve is one
  * cooperative launch whose blocks loop over the iterations with two grid-wide barriers
- * each, streaming the vectors through global memory (the mixed-mode default);
+ * each, streaming the vectors through global memory (the mixed-mode default; in a
+ * defect-correction cycle it also adds its correction to the FP64 pressure before it
+ * returns, where the other forms launch BCM_K_ADD_CORRECTION);
  * persistent = 3: the same iteration with each cube's search direction kept in
  * shared memory, when every cube fits a co-resident block of at most two cubes (FP32
  * inner solve, 16^3 or 8^3 cubes, slabs_a = 1), else the streaming form; persistent = 2:
@@ -431,10 +433,11 @@ enum {
     BCM_K_RESIDUAL = 3,       /* FP64 residual (PCG start / defect-correction cycle) */
     BCM_K_CG_A = 4,           /* PCG pass A: new direction, K p, <p, Kp> */
     BCM_K_CG_B = 5,           /* PCG pass B: iterate and residual update, <r,z>, <r,r> */
-    BCM_K_ADD_CORRECTION = 6, /* mixed: x += e */
+    BCM_K_ADD_CORRECTION = 6, /* mixed: x += e (forms other than persistent = 1) */
     BCM_K_CORRECT = 7,        /* projection + FP64 divergence check */
     BCM_K_MISC = 8,           /* bookkeeping and test-path kernels */
-    BCM_K_PCG = 9,            /* persistent PCG: all iterations of one solve */
+    BCM_K_PCG = 9,            /* persistent PCG: all iterations of one solve (with
+                                 persistent = 1 also the cycle's x += e) */
     BCM_K_MG = 10,            /* multigrid V-cycle (BCM_PRECOND_MULTIGRID) */
     BCM_K_IB = 11,            /* Lagrangian particles: forcing, position update, sets */
     BCM_NKERNELS = 12
